@@ -1,0 +1,394 @@
+"""FP64 CPU oracle for the ionising-MD hot path -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+leg (and its ``--impl reference`` arm) may import this module.  The product
+path (the CUDA library and its Python binding) never does, and this module
+never imports the product.  The two share only the seeded input generators
+(``paper_2401_03180_gb300.workloads``), which hold none of the method's
+arithmetic.
+
+What it computes, in the paper's order (arXiv 2401.03180):
+
+* Sec. II.A, Eq. 2: Debye-screened Coulomb between integer ion charges.
+* Sec. II.A, Eq. 3: Debye length from the free-electron density and
+  temperature, kappa = 1/lambda_D.
+* Sec. II.B, Eq. 8: screened LJ, with LJ parameters scaled per charge state
+  (Eq. 11) and LJ excluded inside a native fragment.
+* Sec. II.B, Eq. 12: Newton's equation, integrated with velocity Verlet.
+* Sec. II.A (stochastic integer charges, processes named there): the
+  reading "RCM-1" -- at most one photo-ionisation, Auger, collisional
+  ionisation or recombination event per atom per step, drawn with
+  Philox4x32-10 keyed by (seed, atom, step); the free-electron gas is
+  homogeneous, thermalised and never escapes, its energy is tracked in
+  integer meV.
+
+Parity pins (``tests/test_oracle_*.py``, all ``-m "not gpu"``):
+
+* ``philox``: the cuRAND host generator CURAND_RNG_PSEUDO_PHILOX4_32_10 run
+  as a library, block by block.
+* ``u53``: extreme values and a uniformity test.
+* ``one_minus_exp_neg``: numpy ``expm1`` to a few ulp over 0..40.
+* ``lj_table``: textbook LJ facts (zero at sigma, minimum -eps at
+  2^(1/6) sigma) and the Eq. 11 scaling limits (q = Z gives no LJ).
+* ``pair``: force = -dU/dr by finite differences; the Coulomb energy of two
+  elementary charges 1 nm apart (a CODATA-derived golden value); the
+  Yukawa ratio e^{-kappa r}; the shift U(r_c) = 0.
+* ``forces``: Newton III (net force 0), invariance under translation and
+  periodic images, pair counts against a KD-tree.
+* ``pulse_table``: total fluence, symmetry, flat-top closed form, FWHM.
+* ``plasma_scalars``: the NRL-formulary Debye length.
+* ``cr_step``: closed forms (PI-only survival e^{-sigma F}; Auger-only
+  decay), master-equation chi-squared on histograms, exact charge
+  conservation.
+* ``OracleMD`` (velocity Verlet): NVE energy conservation and second-order
+  convergence in dt.
+Trajectory agreement with the GPU beyond short horizons is *parity
+unpinned*: MD is chaotic, so only the first steps are compared.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_SRC = os.path.join(_HERE, "md_oracle.c")
+_lock = threading.Lock()
+_lib = None
+
+# Physical constants in the units of the method (nm, ps, amu, kJ/mol, e).
+COULOMB_F = 138.935458          # 1/(4 pi eps0), kJ mol^-1 nm e^-2
+EV_KJMOL = 96.48533212          # kJ/mol per eV
+N_ETAB = 16 * 40                # exp table covers lambda < 40
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle C file (FP contraction off, OpenMP on)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = ctypes.CDLL(build())
+            _declare(_lib)
+    return _lib
+
+
+_P = ctypes.c_void_p
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _declare(L):
+    i32, i64, u64, u32, f64 = ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double
+    L.orc_philox_many.argtypes = [u64, _P, _P, u32, u32, i64, _P]
+    L.orc_philox_blocks.argtypes = [u64, _P, i64, _P]
+    L.orc_u53.argtypes = [u32, u32]; L.orc_u53.restype = f64
+    L.orc_exp_tables.argtypes = [_P, i32, _P]
+    L.orc_one_minus_exp_neg_many.argtypes = [i64, _P, _P, _P, i32, _P]
+    L.orc_lj_table.argtypes = [i32, _P, _P, _P, _P, _P]
+    L.orc_pair.argtypes = [f64] * 8 + [i32, _P, _P]
+    L.orc_forces.argtypes = [i32, _P, _P, _P, _P, i32, _P, _P, _P, f64, f64, i32, _P, _P, _P, _P, _P]
+    L.orc_forces_subset.argtypes = [i32, _P, _P, _P, _P, _P, _P, _P, _P, f64, f64, i32, _P, _P, i32, _P, _P]
+    L.orc_pulse_table.argtypes = [i32, _P, f64, f64, i32, _P]
+    L.orc_cr_step.argtypes = ([i32, _P, _P, _P, _P, _P, i64, _P, _P, _P, _P, _P, i32, _P, _P, _P,
+                               _P, _P, i32, _P, _P, _P, _P, i32, _P, _P, _P, _P])
+    L.orc_cr_step.restype = i32
+
+
+# ---------------------------------------------------------------------------
+# Small building blocks
+# ---------------------------------------------------------------------------
+def philox(seed: int, c0, c1, c2: int = 0, c3: int = 0) -> np.ndarray:
+    """Philox4x32-10 blocks for counters (c0[i], c1[i], c2, c3), key = seed."""
+    c0 = np.ascontiguousarray(c0, dtype=np.uint32)
+    c1 = np.ascontiguousarray(c1, dtype=np.uint32)
+    out = np.empty((len(c0), 4), dtype=np.uint32)
+    lib().orc_philox_many(int(seed), _ptr(c0), _ptr(c1), c2, c3, len(c0), _ptr(out))
+    return out
+
+
+def philox_blocks(seed: int, ctr4) -> np.ndarray:
+    """Philox4x32-10 for arbitrary counters ctr4[n][4], key = seed."""
+    ctr4 = np.ascontiguousarray(ctr4, dtype=np.uint32).reshape(-1, 4)
+    out = np.empty_like(ctr4)
+    lib().orc_philox_blocks(int(seed), _ptr(ctr4), len(ctr4), _ptr(out))
+    return out
+
+
+def u53(a: int, b: int) -> float:
+    return lib().orc_u53(int(a), int(b))
+
+
+def exp_tables():
+    etab = np.empty(N_ETAB); inv = np.empty(13)
+    lib().orc_exp_tables(_ptr(etab), N_ETAB, _ptr(inv))
+    return etab, inv
+
+
+def one_minus_exp_neg(x) -> np.ndarray:
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    etab, inv = exp_tables()
+    p = np.empty_like(x)
+    lib().orc_one_minus_exp_neg_many(x.size, _ptr(x), _ptr(p), _ptr(etab), N_ETAB, _ptr(inv))
+    return p
+
+
+def lj_table(z, sigma0, eps0):
+    z = np.ascontiguousarray(z, dtype=np.int32)
+    nts = int((z + 1).sum())
+    c6 = np.zeros((nts, nts)); c12 = np.zeros((nts, nts))
+    lib().orc_lj_table(len(z), _ptr(z), _ptr(np.ascontiguousarray(sigma0, np.float64)),
+                       _ptr(np.ascontiguousarray(eps0, np.float64)), _ptr(c6), _ptr(c12))
+    return c6, c12
+
+
+def pair(r, qi, qj, c6, c12, kappa, rc, lj_on=True, coulomb_f=COULOMB_F):
+    """(F(r)/r, U(r) - U(rc)) for one pair (Eqs. 2 and 8)."""
+    fr = ctypes.c_double(); u = ctypes.c_double()
+    lib().orc_pair(r, qi, qj, c6, c12, kappa, coulomb_f, rc, int(bool(lj_on)),
+                   ctypes.byref(fr), ctypes.byref(u))
+    return fr.value, u.value
+
+
+def pulse_table(pulses, t_start_fs: float, dt_fs: float, n_steps: int) -> np.ndarray:
+    """Photons/nm^2 per step for a list of pulses (photon keV, FWHM fs,
+    fluence ph/um^2, centre fs, shape)."""
+    P = np.ascontiguousarray([[p.photon_kev, p.fwhm_fs, p.fluence_ph_um2, p.t_center_fs, p.shape]
+                              for p in pulses], dtype=np.float64).reshape(-1, 5)
+    out = np.empty(n_steps)
+    lib().orc_pulse_table(len(P), _ptr(P), float(t_start_fs), float(dt_fs), int(n_steps), _ptr(out))
+    return out
+
+
+def plasma_scalars(n_e_count: int, e_gas_mev: int, volume: float, *, dt_ps: float,
+                   te_floor_ev: float, dte_ev: float, n_te: int,
+                   coulomb_f: float = COULOMB_F, prescribed=None):
+    """Free-electron-gas scalars (Sec. II.A, Eq. 3).
+
+    T_e = (2/3) E_gas / N_e (E_gas in meV -> eV: divide by 1500 N_e),
+    n_e = N_e / V, kappa^2 = 4 pi f n_e / (k_B T_e) with k_B T_e in kJ/mol
+    and T_e floored at ``te_floor_ev``; kappa = 0 when n_e = 0.
+    Also the CR helpers n_e*dt and the uniform-grid position (i0, w).
+    ``prescribed`` = (n_e, T_e) replaces the bookkeeping values.
+    """
+    if prescribed is not None:
+        n_e, te = float(prescribed[0]), float(prescribed[1])
+    elif n_e_count > 0:
+        te = float(e_gas_mev) / (1500.0 * float(n_e_count))
+        n_e = float(n_e_count) / volume
+    else:
+        te, n_e = 0.0, 0.0
+    if n_e > 0.0:
+        tc = te if te > te_floor_ev else te_floor_ev
+        four_pi_f = 4.0 * math.pi * coulomb_f
+        k2 = (four_pi_f * n_e) / (tc * EV_KJMOL)
+        kappa = math.sqrt(k2)
+    else:
+        kappa = 0.0
+    ne_dt = n_e * dt_ps
+    x = te * (1.0 / dte_ev)
+    if x > float(n_te - 1):
+        x = float(n_te - 1)
+    if x < 0.0:
+        x = 0.0
+    i0 = int(x)
+    if i0 > n_te - 2:
+        i0 = n_te - 2
+    w = x - float(i0)
+    return dict(te_ev=te, n_e=n_e, kappa=kappa, ne_dt=ne_dt, it0=i0, wt=w)
+
+
+# ---------------------------------------------------------------------------
+# Whole-system oracle
+# ---------------------------------------------------------------------------
+class OracleMD:
+    """The full step of the method on the CPU, in FP64.
+
+    Step n (reading of the step order; the paper is silent):
+      1. v += (dt/2) F/m          2. x += dt v (periodic wrap)
+      3. CR update with the plasma scalars of step n-1 and the step-n RNG
+      4. reduce -> N_e, E_gas -> kappa for step n+1
+      5. F(x, q, kappa)           6. v += (dt/2) F/m
+    """
+
+    def __init__(self, sample, atomic, *, dt_ps=5e-5, r_cut=1.2, cr_enabled=True,
+                 kappa_fixed=-1.0, te_floor_ev=1.0, t_start_fs=0.0, pulses=None,
+                 dF_table=None, prescribed=None, n_steps_max=0, coulomb_f=COULOMB_F,
+                 sigma0=None, eps0=None, mass=None, threads=None):
+        from paper_2401_03180_gb300 import workloads as W
+        self.s = sample
+        self.a = atomic
+        self.dt = float(dt_ps)
+        self.rc = float(r_cut)
+        self.cr_enabled = bool(cr_enabled)
+        self.kappa_fixed = float(kappa_fixed)
+        self.te_floor = float(te_floor_ev)
+        self.f = float(coulomb_f)
+        self.n = sample.n_atoms
+        self.R = sample.n_replicas
+        self.z = np.ascontiguousarray(atomic.z, dtype=np.int32)
+        self.off = np.concatenate([[0], np.cumsum(self.z + 1)]).astype(np.int32)
+        self.mass = np.asarray(W.MASS if mass is None else mass, dtype=np.float64)
+        sig0 = W.LJ_SIGMA0 if sigma0 is None else sigma0
+        e0 = W.LJ_EPS0 if eps0 is None else eps0
+        self.c6, self.c12 = lj_table(self.z, sig0, e0)
+        self.nts = self.c6.shape[0]
+        self.x = np.array(sample.x, dtype=np.float64, copy=True)
+        self.v = np.array(sample.v, dtype=np.float64, copy=True)
+        self.sp = np.ascontiguousarray(sample.species, dtype=np.uint8)
+        self.frag = np.ascontiguousarray(sample.fragment, dtype=np.int32)
+        self.q = np.array(sample.q0, dtype=np.uint8, copy=True)
+        self.h = np.zeros(self.n, dtype=np.uint8)
+        self.rep_off = np.ascontiguousarray(sample.replica_offset, dtype=np.int32)
+        self.rep_of = np.repeat(np.arange(self.R, dtype=np.int32), np.diff(self.rep_off))
+        self.local = (np.arange(self.n) - self.rep_off[self.rep_of]).astype(np.int32)
+        self.box = np.ascontiguousarray(sample.box, dtype=np.float64).reshape(self.R, 3)
+        self.vol = np.asarray(sample.volume, dtype=np.float64)
+        self.seed = np.ascontiguousarray(sample.seed, dtype=np.uint64)
+        self.step_index = 0
+        self.etab, self.inv = exp_tables()
+        with np.errstate(divide="ignore"):
+            tau = np.asarray(atomic.tau_auger_ps, dtype=np.float64)
+            self.auger_dt = np.where(tau > 0, self.dt / np.where(tau > 0, tau, 1.0), 0.0)
+        self.hdtm = (0.5 * self.dt) / self.mass
+        self.prescribed = prescribed   # (ne[R][steps+1], te[R][steps+1]) or None
+        # per-step fluence tables, per replica
+        if dF_table is not None:
+            self.dF = np.asarray(dF_table, dtype=np.float64).reshape(self.R, -1)
+        elif pulses is not None:
+            n_max = max(int(n_steps_max), 1)
+            self.dF = np.stack([pulse_table(pulses[r], t_start_fs, self.dt * 1000.0, n_max)
+                                for r in range(self.R)])
+        else:
+            self.dF = np.zeros((self.R, max(int(n_steps_max), 1)))
+        self.n_e = np.array([int(self.q[self.rep_off[r]:self.rep_off[r + 1]].astype(np.int64).sum())
+                             for r in range(self.R)], dtype=np.int64)
+        self.e_gas = np.zeros(self.R, dtype=np.int64)
+        self.counts = np.zeros((self.R, 4), dtype=np.int64)
+        self.scal = [self._scalars(r, 0) for r in range(self.R)]
+        self.F, self.U, self.n_pairs = self.forces()
+
+    # -- pieces ------------------------------------------------------------
+    def _scalars(self, r, step):
+        pres = None
+        if self.prescribed is not None:
+            pres = (self.prescribed[0][r][step], self.prescribed[1][r][step])
+        return plasma_scalars(int(self.n_e[r]), int(self.e_gas[r]), float(self.vol[r]),
+                              dt_ps=self.dt, te_floor_ev=self.te_floor, dte_ev=self.a.dte_ev,
+                              n_te=self.a.n_te, coulomb_f=self.f, prescribed=pres)
+
+    def kappa(self):
+        if self.kappa_fixed >= 0.0:
+            return np.full(self.R, self.kappa_fixed)
+        return np.array([s["kappa"] for s in self.scal])
+
+    def type_state(self):
+        return (self.off[self.sp.astype(np.int64)] + self.q).astype(np.int32)
+
+    def forces(self, x=None, q=None, kappa=None):
+        x = self.x if x is None else x
+        q = self.q if q is None else q
+        kap = self.kappa() if kappa is None else np.asarray(kappa, np.float64)
+        ts = (self.off[self.sp.astype(np.int64)] + q).astype(np.int32)
+        xf = np.ascontiguousarray(x, dtype=np.float64)
+        qd = np.ascontiguousarray(q, dtype=np.float64)
+        F = np.zeros((self.n, 3)); U = np.zeros(self.n); npairs = ctypes.c_int64(0)
+        lib().orc_forces(self.n, _ptr(xf), _ptr(ts), _ptr(qd), _ptr(self.frag), self.R,
+                         _ptr(self.rep_off), _ptr(self.box), _ptr(np.ascontiguousarray(kap)),
+                         self.rc, self.f, self.nts, _ptr(self.c6), _ptr(self.c12), _ptr(F),
+                         _ptr(U), ctypes.byref(npairs))
+        return F, U, int(npairs.value)
+
+    def forces_subset(self, sel, x=None, q=None, kappa=None):
+        x = self.x if x is None else x
+        q = self.q if q is None else q
+        kap = self.kappa() if kappa is None else np.asarray(kappa, np.float64)
+        ts = (self.off[self.sp.astype(np.int64)] + q).astype(np.int32)
+        sel = np.ascontiguousarray(sel, dtype=np.int32)
+        out = np.zeros((len(sel), 3))
+        lib().orc_forces_subset(self.n, _ptr(np.ascontiguousarray(x)), _ptr(ts),
+                                _ptr(np.ascontiguousarray(q, np.float64)), _ptr(self.frag),
+                                _ptr(self.rep_of), _ptr(self.rep_off), _ptr(self.box),
+                                _ptr(np.ascontiguousarray(kap)), self.rc, self.f, self.nts,
+                                _ptr(self.c6), _ptr(self.c12), len(sel), _ptr(sel), _ptr(out))
+        return out
+
+    def cr_step(self, step):
+        """One CR update of all atoms with the current scalars."""
+        R = self.R
+        dF = np.ascontiguousarray([self.dF[r][step] for r in range(R)], dtype=np.float64)
+        ne_dt = np.ascontiguousarray([s["ne_dt"] for s in self.scal], dtype=np.float64)
+        it0 = np.ascontiguousarray([s["it0"] for s in self.scal], dtype=np.int32)
+        wt = np.ascontiguousarray([s["wt"] for s in self.scal], dtype=np.float64)
+        dNe = np.zeros(R, dtype=np.int64); dE = np.zeros(R, dtype=np.int64)
+        cnt = np.zeros((R, 4), dtype=np.int64)
+        a = self.a
+        lib().orc_cr_step(self.n, _ptr(self.sp), _ptr(self.q), _ptr(self.h), _ptr(self.local),
+                          _ptr(self.rep_of), int(step), _ptr(self.seed), _ptr(dF), _ptr(ne_dt),
+                          _ptr(it0), _ptr(wt), len(self.z), _ptr(self.z),
+                          _ptr(np.ascontiguousarray(a.sigma_pi, np.float64)), _ptr(self.auger_dt),
+                          _ptr(np.ascontiguousarray(a.k_ci, np.float64)),
+                          _ptr(np.ascontiguousarray(a.k_rec, np.float64)), int(a.n_te),
+                          _ptr(np.ascontiguousarray(a.ip_mev, np.int64)),
+                          _ptr(np.ascontiguousarray(a.e_pi_mev, np.int64)),
+                          _ptr(np.ascontiguousarray(a.e_auger_mev, np.int64)), _ptr(self.etab),
+                          N_ETAB, _ptr(self.inv), _ptr(dNe), _ptr(dE), _ptr(cnt))
+        return dNe, dE, cnt
+
+    def _wrap(self):
+        for r in range(self.R):
+            L = self.box[r]
+            if L[0] > 0 and L[1] > 0 and L[2] > 0:
+                sl = slice(self.rep_off[r], self.rep_off[r + 1])
+                self.x[sl] -= L * np.floor(self.x[sl] / L)
+
+    # -- the step ----------------------------------------------------------
+    def step(self):
+        n = self.step_index
+        hd = self.hdtm[self.sp][:, None]
+        self.v += hd * self.F
+        self.x += self.dt * self.v
+        self._wrap()
+        if self.cr_enabled:
+            dNe, dE, cnt = self.cr_step(n)
+            self.n_e += dNe
+            self.e_gas = np.maximum(self.e_gas + dE, 0)
+            self.counts += cnt
+        self.scal = [self._scalars(r, n + 1) for r in range(self.R)]
+        self.F, self.U, self.n_pairs = self.forces()
+        self.v += hd * self.F
+        self.step_index = n + 1
+
+    def run(self, n_steps, record=None):
+        for _ in range(n_steps):
+            self.step()
+            if record is not None:
+                record(self)
+
+    # -- observables ---------------------------------------------------------
+    def kinetic(self):
+        m = self.mass[self.sp]
+        return np.array([0.5 * float((m[self.rep_off[r]:self.rep_off[r + 1], None]
+                                      * self.v[self.rep_off[r]:self.rep_off[r + 1]] ** 2).sum())
+                         for r in range(self.R)])
+
+    def potential(self):
+        return np.array([float(self.U[self.rep_off[r]:self.rep_off[r + 1]].sum())
+                         for r in range(self.R)])
