@@ -1,0 +1,384 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 ionising-MD hot path.
+
+One step = one full timestep of the method on the whole sample: kick/drift,
+stochastic charge update and free-electron reduction, cell-list rebuild,
+screened pair forces.  The default workload is the 30,000-atom periodic
+water box irradiated by a 6 keV, 25 fs, 5e12 ph/um^2 pulse, 1,000 steps of
+50 as (10 warm-up + 990 timed), mixed precision (FP32 pairs with 64-bit
+fixed-point sums, FP64 integrator and charge update).
+
+Prints ONE JSON line (rank 0).  Multi-GPU (torchrun): every rank runs an
+independent replica of the workload (weak scaling, no collective on the data
+path; the barrier and the max-over-ranks timing use torch.distributed).
+
+--impl reference runs the FP64 CPU oracle on the host cores instead (the
+reference arm for this build; a deliberately slow, obviously correct program).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "atom-steps/s (pair forces + ionisation) on 1 GB300, mixed vs FP64 at stated error"
+UNIT = "atom-steps/s"
+FLOPS_PER_PAIR = 41          # FP32 operations per in-cutoff pair in the pair kernel (FMA = 2)
+L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_pair_c2_water_30k.md")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=990)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="c2_water_30k")
+    ap.add_argument("--scale", type=float, default=1.0)
+    ap.add_argument("--fp64-steps", type=int, default=100)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# inputs
+# ---------------------------------------------------------------------------
+def make_workload(name, scale, rank):
+    from paper_2401_03180_gb300 import workloads as W
+    wl = W.workload(name, scale=scale)
+    if rank:   # an independent replica per rank: its own RNG key
+        wl.sample.seed[:] = wl.sample.seed + np.uint64(7919 * rank)
+    atom = W.atomic_data(wl.photon_kev)
+    return wl, atom
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        rows = [l.strip().split(", ") for l in open(self.path) if l.strip()]
+        os.unlink(self.path)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1])); smax.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].strip().lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def kernel_source_digest():
+    src = os.path.join(ROOT, "paper_2401_03180_gb300", "csrc", "k_pair.cu")
+    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per pair-kernel launch from the committed ncu summary, if
+    the kernel source is unchanged since the capture."""
+    if not os.path.exists(PROFILE_SUMMARY):
+        return None, None
+    txt = open(PROFILE_SUMMARY).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    h = re.search(r"k_pair_source_sha256_16:\s*([0-9a-f]+)", txt)
+    if not m or not h or h.group(1) != kernel_source_digest():
+        return None, (h.group(1) if h else None)
+    return float(m.group(1)), h.group(1)
+
+
+def fp32_peak_tflops(torch):
+    props = torch.cuda.get_device_properties(0)
+    sms = props.multi_processor_count
+    max_mhz = 2070.0
+    try:
+        mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        max_mhz = float(mp.get("sm_max_mhz", max_mhz))
+    except Exception:
+        pass
+    return sms * 128 * 2 * max_mhz * 1e6 / 1e12, sms, max_mhz
+
+
+def run_gpu(args, rank, world, local):
+    import torch
+    from paper_2401_03180_gb300 import build as B
+    from paper_2401_03180_gb300 import md as M
+
+    B.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    wl, atom = make_workload(args.workload, args.scale, rank)
+    s = wl.sample
+    n_atoms = s.n_atoms
+    W_, K = args.warmup, args.steps
+    max_steps = max(wl.n_steps, W_ + K + 1)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def make(prec, profile):
+        g = M.IonisingMD(s, atom, precision=prec, r_cut=1.2, dt_ps=5e-5, max_steps=max_steps,
+                         t_start_fs=wl.t_start_fs, autotune=(prec == "mixed"), profile=profile)
+        for r in range(s.n_replicas):
+            g.set_pulse(wl.pulses[r], replica=r)
+        return g
+
+    def timed_steps(g, k_steps):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(k_steps)]
+        for k in range(k_steps):
+            flush.zero_()                       # evict the 129 MB L2 between steps
+            ev[k][0].record(stream)
+            g.step(1)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev)
+
+    # ---- mixed path, device-timed ----
+    g = make("mixed", profile=True)
+    for _ in range(W_):
+        g.step(1)
+    _, _, pairs0 = g.energies()
+    g.reset_timing()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ms = timed_steps(g, K)
+    torch.cuda.synchronize()
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    tim = g.timing()
+    _, _, pairs1 = g.energies()
+    state = g.get_state(M.MD_FIELD_PLASMA | M.MD_FIELD_COUNTS | M.MD_FIELD_Q)
+    g.close()
+    pair_ms = tim.pair_ms / max(tim.pair_launches, 1)
+    pairs = 0.5 * (pairs0 + pairs1)
+    value = world * n_atoms * K / (ms / 1e3)
+    peak, sms, max_mhz = fp32_peak_tflops(torch)
+    achieved = FLOPS_PER_PAIR * pairs / (pair_ms / 1e3) / 1e12
+    traffic, _ = profiled_traffic()
+
+    # ---- FP64 path on the same inputs ----
+    k64 = min(args.fp64_steps, K)
+    g64 = make("fp64", profile=False)
+    for _ in range(min(W_, 3)):
+        g64.step(1)
+    ms64 = timed_steps(g64, k64)
+    g64.close()
+    value64 = world * n_atoms * k64 / (ms64 / 1e3)
+
+    # ---- end to end through the C ABI, host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        from paper_2401_03180_gb300 import md as M2
+        ge = make("mixed", profile=False)
+        dF_all = M2.md_pulse_table([p for p in wl.pulses[0]], wl.t_start_fs, 5e-5 * 1000.0, max_steps)
+        h_in = torch.empty(s.n_replicas, dtype=torch.float64, pin_memory=True).numpy()
+        h_q = torch.empty(n_atoms, dtype=torch.uint8, pin_memory=True).numpy()
+        outs = {"q": h_q, "n_e": np.empty(s.n_replicas, np.int64), "e_gas_mev": np.empty(s.n_replicas, np.int64),
+                "te_ev": np.empty(s.n_replicas), "kappa": np.empty(s.n_replicas)}
+        for _ in range(W_):
+            ge.step(1)
+        tot = 0.0
+        for k in range(K):
+            flush.zero_()
+            torch.cuda.synchronize()
+            step = W_ + k
+            h_in[:] = dF_all[step]
+            t0 = time.perf_counter()
+            M2.md_set_pulse_table_at(ge.h, -1, step, h_in)          # H2D: this step's fluence
+            ge.step(1)
+            ge.get_state(M2.MD_FIELD_Q | M2.MD_FIELD_PLASMA, out=outs)  # D2H: charges + plasma
+            tot += time.perf_counter() - t0
+        ge.close()
+        e2e = {"value": world * n_atoms * K / tot, "unit": UNIT,
+               "h2d_bytes_per_step": int(8 * s.n_replicas),
+               "d2h_bytes_per_step": int(n_atoms + 32 * s.n_replicas)}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W_,
+        "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+i64 pairs, f64 integrator/charge update",
+        "data": "synthetic (seeded generators; no paper sample or atomic data available)",
+        "config": {"workload": args.workload if args.scale == 1.0 else f"{args.workload}@{args.scale}",
+                   "n_atoms": n_atoms, "replicas_per_gpu": s.n_replicas,
+                   "box_nm": float(s.box[0, 0]) if s.box[0, 0] > 0 else None, "r_cut_nm": 1.2, "dt_as": 50,
+                   "pulse": [vars(p) for p in wl.pulses[0]], "t_start_fs": wl.t_start_fs,
+                   "l2": "flushed between steps (256 MB write, untimed)",
+                   "pair_tile": {"warps": tim.tile_warps, "blocks_per_sm": tim.tile_blocks_per_sm},
+                   "parallelism": f"replicas{world}"},
+        "pair_interactions_per_s": world * pairs * K / (ms / 1e3),
+        "pairs_per_step": pairs,
+        "fp64_gpu": {"value": value64, "unit": UNIT, "steps": k64, "ms_per_step": ms64 / k64,
+                     "speedup_mixed_vs_fp64": value / value64},
+        "roofline": {"bound": "alu", "kernel": "k_pair (FP32 FMA pipe)", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                     "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz (max SM clock)",
+                     "flops_per_pair": FLOPS_PER_PAIR, "pair_kernel_ms": pair_ms,
+                     "pair_kernel_share": pair_ms / (ms / K)},
+        "e2e": e2e,
+        "gpu_launches": 6 * K,
+        "clocks": clk.summary(),
+        "charge_state": {"n_e": [int(v) for v in state["n_e"]], "te_ev": [float(v) for v in state["te_ev"]],
+                         "events_pi_auger_ci_rec": [int(v) for v in state["event_counts"][0]]},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"], out["force_error_vs_oracle"] = cpu_baseline(args, wl, atom)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return out
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle: baseline leg and reference arm
+# ---------------------------------------------------------------------------
+def _oracle_run(wl, atom, seconds, max_steps_cap=50):
+    from oracle import oracle as O
+    threads = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(threads))
+    s = wl.sample
+    t0 = time.perf_counter()
+    md = O.OracleMD(s, atom, r_cut=1.2, t_start_fs=wl.t_start_fs, pulses=wl.pulses,
+                    n_steps_max=max(wl.n_steps, max_steps_cap + 1))
+    t_init = time.perf_counter() - t0
+    md.F0 = md.F.copy()
+    steps = 0
+    t0 = time.perf_counter()
+    while steps < max_steps_cap and (time.perf_counter() - t0) < seconds:
+        md.step()
+        steps += 1
+    dt = time.perf_counter() - t0
+    return md, steps, dt, t_init, int(os.environ["OMP_NUM_THREADS"])
+
+
+def cpu_baseline(args, wl, atom):
+    md, steps, dt, t_init, cores = _oracle_run(wl, atom, args.cpu_seconds)
+    s = wl.sample
+    val = s.n_atoms * steps / dt
+    base = {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{steps} steps of {args.workload} ({s.n_atoms} atoms), all-pairs FP64, "
+                      f"after an untimed initial force evaluation ({t_init:.1f} s)"}
+    # force error of the GPU paths vs the oracle on the initial state (same inputs)
+    err = None
+    try:
+        from paper_2401_03180_gb300 import md as M
+        F_ref = md.F0
+        err = {}
+        for prec in ("mixed", "fp64"):
+            g = M.IonisingMD(s, atom, precision=prec, r_cut=1.2, max_steps=wl.n_steps, t_start_fs=wl.t_start_fs)
+            F = g.get_state(M.MD_FIELD_F)["f"]
+            g.close()
+            d = F - F_ref
+            rms_f = float(np.sqrt((F_ref ** 2).sum(1).mean()))
+            err[prec] = {"rms_rel": float(np.linalg.norm(d) / np.linalg.norm(F_ref)),
+                         "max_abs_over_rms": float(np.abs(d).max() / rms_f)}
+        err["state"] = "initial state (neutral sample, kappa = 0), all atoms"
+    except Exception as e:  # the baseline number stands even if the comparison fails
+        err = {"error": str(e)[:200]}
+    return base, err
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    wl, atom = make_workload(args.workload, args.scale, 0)
+    s = wl.sample
+    # each timed step is one oracle step; a bounded number keeps the arm within minutes
+    k = min(args.steps, 10)
+    w = min(args.warmup, 1)
+    md, steps, dt, t_init, cores = _oracle_run(wl, atom, seconds=1e9, max_steps_cap=w)
+    t0 = time.perf_counter()
+    for _ in range(k):
+        md.step()
+    dt = time.perf_counter() - t0
+    val = s.n_atoms * k / dt
+    sample = f"{k} timed steps (after {w} warm-up) of {args.workload}, FP64 all-pairs oracle"
+    return {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world, "steps": k,
+            "warmup": w, "ms_per_step": 1e3 * dt / k, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "n_atoms": s.n_atoms, "r_cut_nm": 1.2, "dt_as": 50},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_gpu(args, rank, world, local)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,263 @@
+/*
+ * md.h -- C ABI of the GB300 ionising-MD hot path.
+ *
+ * One timestep of an X-ray-irradiated sample, following the hybrid
+ * collisional-radiative / molecular-dynamics method of arXiv 2401.03180:
+ *   (a) cell-list neighbour build (cutoff chosen from the screening, Sec. II.B);
+ *   (b) screened Coulomb (Sec. II.A, Eq. 2) plus screened, charge-scaled LJ
+ *       (Sec. II.B, Eqs. 8 and 11) pair forces, LJ excluded inside a native
+ *       fragment (Sec. II.B);
+ *   (c) stochastic integer charge update from photo-ionisation, Auger decay,
+ *       collisional ionisation and recombination (Sec. II.A: processes named
+ *       there, charges assigned stochastically per atom);
+ *   (d) free-electron-gas reduction giving the Debye length (Sec. II.A, Eq. 3);
+ *   (e) velocity-Verlet integration of Newton's equation (Sec. II.B, Eq. 12).
+ *
+ * Units: nm, ps, amu, kJ/mol, elementary charge; pulse times in fs, fluence
+ * in photons/um^2, electron-gas energies in integer meV.
+ *
+ * Ownership: every pointer passed in is read during the call only (inputs are
+ * copied); outputs are written to caller-owned buffers.  The library owns its
+ * device memory, obtained from md_config.dev_alloc when set (e.g. a PyTorch
+ * caching allocator) and from cudaMalloc otherwise.  Arrays are host pointers
+ * unless a name starts with d_.
+ *
+ * Errors: every call returns an md_status; md_last_error() gives the text.
+ * After a device-side error (MD_ERR_FIXED_OVERFLOW, MD_ERR_NONFINITE,
+ * MD_ERR_CELL_OVERFLOW) the handle accepts only md_get_state, md_last_error
+ * and md_finalize.  No kernel traps or spins without a bound.
+ *
+ * Threading: one handle is driven by one host thread at a time.  All device
+ * work of a handle is issued on its stream (md_set_stream; default: the
+ * legacy default stream).
+ */
+#ifndef MD_GB300_H
+#define MD_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int md_status;
+enum {
+    MD_OK = 0,
+    MD_ERR_INVALID_ARG = 1,    /* argument out of range / inconsistent      */
+    MD_ERR_BAD_STATE = 2,      /* call order violated, or handle poisoned   */
+    MD_ERR_OOM = 3,            /* device allocation failed                  */
+    MD_ERR_CUDA = 4,           /* a CUDA runtime call failed                */
+    MD_ERR_FIXED_OVERFLOW = 5, /* a force/energy exceeded the fixed-point range */
+    MD_ERR_TIMEOUT = 6,        /* a bounded device wait gave up             */
+    MD_ERR_NONFINITE = 7,      /* NaN/Inf in positions or velocities        */
+    MD_ERR_CELL_OVERFLOW = 8,  /* cell-list capacity exceeded               */
+    MD_ERR_TABLE_END = 9       /* stepped past the per-step pulse table     */
+};
+
+#define MD_MAX_SPECIES 8
+#define MD_MAX_Z 32
+#define MD_MAX_TYPE_STATES 128 /* sum over species of (Z + 1)              */
+
+enum { MD_PREC_MIXED = 0, MD_PREC_FP64 = 1 };
+enum { MD_PLASMA_BOOKKEEPING = 0, MD_PLASMA_PRESCRIBED = 1 };
+enum { MD_PULSE_GAUSSIAN = 0, MD_PULSE_FLAT_TOP = 1 };
+
+/*
+ * Run configuration and atomic data.
+ *
+ * precision: MD_PREC_MIXED = FP32 pair arithmetic with per-atom 64-bit
+ *   fixed-point force sums (scale 2^32 kJ/mol/nm), FP64 positions,
+ *   velocities, integrator and plasma sums; MD_PREC_FP64 = the same path
+ *   with FP64 pair arithmetic.
+ * plasma_mode: MD_PLASMA_BOOKKEEPING derives n_e = N_e/V and
+ *   k_B T_e = (2/3) E_gas/N_e from the integer electron count and gas energy
+ *   of each replica; MD_PLASMA_PRESCRIBED reads n_e and T_e per step from
+ *   md_set_plasma_table (the paper reads T_e from the CR calculation, Sec. II.B).
+ * kappa_fixed: >= 0 forces 1/lambda_D to this value (nm^-1) in the pair
+ *   forces (the CR rates still use the plasma scalars); < 0 derives it (Eq. 3).
+ * The CR tables are indexed by type state ts = off[s] + q with
+ *   off[0] = 0, off[s+1] = off[s] + Z[s] + 1, and:
+ *   sigma_pi   [n_ts][2]    photo-ionisation cross section (nm^2), column = K-hole flag
+ *   k_ci       [n_ts][n_te] collisional-ionisation rate coefficient (nm^3/ps)
+ *   k_rec      [n_ts][n_te] recombination rate coefficient (nm^3/ps)
+ *   ip_mev     [n_ts]       ionisation potential q -> q+1 (meV)
+ *   e_pi_mev   [n_ts][2]    energy given to the electron gas per PI event (meV)
+ *   e_auger_mev[n_species]  energy given per Auger event (meV)
+ *   T_e grid: T_k = k * dte_ev, k = 0 .. n_te-1, linear interpolation, clamped.
+ */
+typedef struct md_config {
+    double dt_ps;            /* timestep (ps), > 0                          */
+    double r_cut;            /* pair cutoff (nm), > 0                       */
+    int precision;           /* MD_PREC_*                                   */
+    int cr_enabled;          /* 1: charge update on; 0: charges frozen      */
+    int plasma_mode;         /* MD_PLASMA_*                                 */
+    int max_steps;           /* length of the per-step tables (>= 1)        */
+    double kappa_fixed;      /* see above                                   */
+    double t_start_fs;       /* time of step 0 (fs)                         */
+    double te_floor_ev;      /* lower bound of T_e used in kappa (eV), > 0  */
+    double coulomb_f;        /* 1/(4 pi eps0) in kJ mol^-1 nm e^-2          */
+    double photon_kev;       /* photon energy the sigma_pi column is for    */
+    int n_species;           /* 1 .. MD_MAX_SPECIES                         */
+    int z[MD_MAX_SPECIES];   /* nuclear charge, 1 .. MD_MAX_Z               */
+    double mass[MD_MAX_SPECIES];        /* amu                              */
+    double lj_sigma0[MD_MAX_SPECIES];   /* neutral LJ sigma (nm)            */
+    double lj_eps0[MD_MAX_SPECIES];     /* LJ epsilon (kJ/mol)              */
+    double tau_auger_ps[MD_MAX_SPECIES];/* K-hole Auger lifetime; <= 0: none */
+    const double* sigma_pi;
+    const double* k_ci;
+    const double* k_rec;
+    const int64_t* ip_mev;
+    const int64_t* e_pi_mev;
+    const int64_t* e_auger_mev;
+    int n_te;                /* >= 2                                        */
+    double dte_ev;           /* > 0                                         */
+    /* optional device allocator (both or neither); ctx is passed back     */
+    void* (*dev_alloc)(size_t bytes, void* ctx);
+    void (*dev_free)(void* ptr, void* ctx);
+    void* alloc_ctx;
+    int autotune;            /* 1: time launch shapes at init and keep the fastest */
+    int profile;             /* 1: time the pair kernel with CUDA events in md_step */
+} md_config;
+
+/*
+ * The sample: n_atoms atoms of n_replicas independent replicas stored
+ * back to back (replica r owns atoms replica_offset[r] .. replica_offset[r+1]-1).
+ * Replicas share the configuration but have their own RNG seed, box, gas
+ * volume and pulses; a replica run alone gives the same result bit for bit.
+ * box[3r..3r+2] > 0: periodic (minimum image; every edge >= 3 r_cut);
+ * all zero: vacuum.  volume[r]: electron-gas volume (nm^3) for n_e = N_e/V.
+ * fragment: LJ is excluded between atoms with equal fragment id.
+ */
+typedef struct md_system {
+    int n_atoms;                      /* >= 1                               */
+    const double* x;                  /* [3*n_atoms] AoS positions (nm)     */
+    const double* v;                  /* [3*n_atoms] AoS velocities (nm/ps) */
+    const uint8_t* species;           /* [n_atoms] < n_species              */
+    const int32_t* fragment;          /* [n_atoms]                          */
+    const uint8_t* q0;                /* [n_atoms] initial charge <= Z, or NULL (0) */
+    int n_replicas;                   /* >= 1                               */
+    const int32_t* replica_offset;    /* [n_replicas+1], 0 .. n_atoms       */
+    const uint64_t* seed;             /* [n_replicas] Philox key            */
+    const double* box;                /* [3*n_replicas]                     */
+    const double* volume;             /* [n_replicas] > 0                   */
+} md_system;
+
+/* One X-ray pulse (Sec. II.A: pulse energy, duration, photon energy). */
+typedef struct md_pulse {
+    double photon_kev;       /* must equal md_config.photon_kev              */
+    double fwhm_fs;          /* > 0; the width of a flat-top pulse          */
+    double fluence_ph_um2;   /* >= 0                                        */
+    double t_center_fs;
+    int shape;               /* MD_PULSE_*                                  */
+} md_pulse;
+
+/* State exchange (md_get_state / md_set_state).  Unused pointers may be NULL. */
+enum {
+    MD_FIELD_X = 1,        /* x [3n] AoS                                     */
+    MD_FIELD_V = 2,        /* v [3n] AoS, at the integer step                */
+    MD_FIELD_F = 4,        /* f [3n] AoS (get only)                          */
+    MD_FIELD_Q = 8,        /* q [n]                                          */
+    MD_FIELD_H = 16,       /* h [n] K-hole flag                              */
+    MD_FIELD_PLASMA = 32,  /* n_e, e_gas_mev [R]; te_ev, kappa [R] get only  */
+    MD_FIELD_COUNTS = 64,  /* event_counts [R][4] (PI, Auger, CI, REC), get only */
+    MD_FIELD_STEP = 128,   /* step                                           */
+    MD_FIELD_ALL = 255
+};
+typedef struct md_state {
+    double* x;
+    double* v;
+    double* f;
+    uint8_t* q;
+    uint8_t* h;
+    int64_t* n_e;
+    int64_t* e_gas_mev;
+    double* te_ev;
+    double* kappa;
+    int64_t* event_counts;
+    int64_t step;
+} md_state;
+
+/* Accumulated device time of the pair kernel (md_config.profile = 1). */
+typedef struct md_timing {
+    double pair_ms;          /* sum of CUDA-event durations                 */
+    int64_t pair_launches;
+    int64_t steps;
+    int64_t pair_count_last; /* in-cutoff pairs of the last evaluated step (md_get_energies) */
+    int tile_warps;          /* launch shape in use                         */
+    int tile_blocks_per_sm;
+} md_timing;
+
+typedef struct md_handle md_handle;
+
+/* Create a handle: validate, copy inputs, allocate, build the first cell
+ * list and the initial forces F_0(x_0, q_0).  *out receives the handle or
+ * NULL.  Errors: INVALID_ARG, OOM, CUDA. */
+md_status md_init(const md_config* cfg, const md_system* sys, md_handle** out);
+
+/* Issue all later device work on this cudaStream_t (NULL = legacy default). */
+md_status md_set_stream(md_handle* h, void* cuda_stream);
+
+/* Fluence per step of replica `replica` (-1: all) from n_pulses pulses,
+ * over steps 0 .. max_steps-1.  Gaussian pulses integrate the normal CDF
+ * with sigma_t = FWHM / (2 sqrt(2 ln 2)) over each step; flat-top pulses
+ * the overlap.  Uploads the table (the only host-to-device copy of a run). */
+md_status md_set_pulse(md_handle* h, int replica, const md_pulse* p, int n_pulses);
+
+/* Same table given directly: dF[n] photons/nm^2 in step n (n < n_steps <= max_steps). */
+md_status md_set_pulse_table(md_handle* h, int replica, const double* dF, int n_steps);
+
+/* Overwrite entries first_step .. first_step+n-1 of the fluence table
+ * (e.g. a per-step input streamed from the host); other entries unchanged. */
+md_status md_set_pulse_table_at(md_handle* h, int replica, int first_step, const double* dF, int n);
+
+/* Prescribed plasma (plasma_mode = MD_PLASMA_PRESCRIBED): n_e (nm^-3) and
+ * T_e (eV) for steps 0 .. n_steps-1 (n_steps <= max_steps + 1). */
+md_status md_set_plasma_table(md_handle* h, int replica, const double* ne,
+                              const double* te_ev, int n_steps);
+
+/* Advance every replica by n_steps timesteps (asynchronous on the handle's
+ * stream except for a final 4-byte status read).  Errors: BAD_STATE,
+ * TABLE_END, FIXED_OVERFLOW, NONFINITE, CELL_OVERFLOW, CUDA. */
+md_status md_step(md_handle* h, int n_steps);
+
+/* Copy the requested fields (MD_FIELD_* mask) to caller buffers, in the
+ * original atom order.  Synchronises the handle's stream. */
+md_status md_get_state(md_handle* h, md_state* out, unsigned fields);
+
+/* Overwrite x, v, q, h, plasma counters and/or the step counter (mask);
+ * recomputes the cell list, plasma scalars and forces.  Checkpoint/resume
+ * with md_get_state(MD_FIELD_ALL) continues bit for bit. */
+md_status md_set_state(md_handle* h, const md_state* in, unsigned fields);
+
+/* Kinetic and cutoff-shifted potential energy per replica ([n_replicas]
+ * each) and the number of in-cutoff pairs at the current state. */
+md_status md_get_energies(md_handle* h, double* e_kin, double* e_pot, int64_t* n_pairs);
+
+md_status md_get_timing(md_handle* h, md_timing* out);
+md_status md_reset_timing(md_handle* h);
+
+/* Last error message of the handle (or of the last failed md_init when h is NULL). */
+const char* md_last_error(const md_handle* h);
+
+/* Release the handle and its device memory.  NULL is a no-op. */
+void md_finalize(md_handle* h);
+
+/* Host-only: the per-step fluence table md_set_pulse would upload
+ * (out[n_steps]); dt_fs is the timestep in fs.  Needs no GPU. */
+md_status md_pulse_table(const md_pulse* p, int n_pulses, double t_start_fs, double dt_fs,
+                         int n_steps, double* out);
+
+/* Diagnostic: the device Philox4x32-10 (Salmon et al., SC'11) used by the
+ * charge update, out[4i..4i+3] = Philox(d_ctr4[4i..4i+3], key = seed), on
+ * device buffers d_ctr4/d_out (n blocks) and the given stream. */
+md_status md_philox(uint64_t seed, const uint32_t* d_ctr4, int64_t n, uint32_t* d_out,
+                    void* cuda_stream);
+
+/* Library version string. */
+const char* md_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MD_GB300_H */

@@ -1,0 +1,496 @@
+// Per-atom part of one timestep: velocity kick + drift (Sec. II.B, Eq. 12,
+// velocity Verlet), the stochastic collisional-radiative charge update
+// (Sec. II.A), and the free-electron-gas reduction that sets the Debye length
+// (Sec. II.A, Eq. 3) together with the next cell grid.
+//
+// The charge update must reproduce the CPU oracle bit for bit, so its
+// floating-point work uses only IEEE double basic operations written with
+// explicit round-to-nearest intrinsics (no fused multiply-add), and this file
+// is compiled with -fmad=false as a second guard.
+#include "md_internal.cuh"
+
+namespace mdg {
+
+constexpr int kAccCopies = 16;   // accumulator copies per replica (spread contention)
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): 10 rounds, multipliers M0, M1 on
+// words 0 and 2, Weyl key schedule W0, W1.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ double u53(unsigned a, unsigned b)
+{
+    double hi = (double)(a >> 5), lo = (double)(b >> 6);
+    return __dmul_rn(__dadd_rn(__dmul_rn(hi, 67108864.0), lo), 1.1102230246251565e-16);
+}
+
+// 1 - e^{-x}: x = k/16 + r, (1 - E_k) + E_k (1 - e^{-r}), degree-12 Taylor
+// polynomial of 1 - e^{-r} in nested form; E_k and 1/m come from host tables.
+__device__ __forceinline__ double one_minus_exp_neg(double x, const double* etab,
+                                                    const double* inv)
+{
+    if (!(x > 0.0)) return 0.0;
+    double xs = __dmul_rn(x, 16.0);
+    if (xs >= (double)kNEtab) return 1.0;
+    int k = (int)xs;
+    double r = __dsub_rn(x, __dmul_rn((double)k, 0.0625));
+    double t = 1.0;
+#pragma unroll
+    for (int m = 12; m >= 2; --m) t = __dsub_rn(1.0, __dmul_rn(__dmul_rn(r, inv[m]), t));
+    double g = __dmul_rn(r, t);
+    if (k == 0) return g;
+    double ek = etab[k];
+    return __dadd_rn(__dsub_rn(1.0, ek), __dmul_rn(ek, g));
+}
+
+__device__ __forceinline__ double interp(const double* K, int i0, double w)
+{
+    return __dadd_rn(K[i0], __dmul_rn(w, __dsub_rn(K[i0 + 1], K[i0])));
+}
+
+// ---------------------------------------------------------------------------
+// Per-replica scalars for the step `step` (Eq. 3 and the CR helpers) and
+// the cell grid for the positions just reduced into the bounding box.
+// Executed by one thread per replica.
+// ---------------------------------------------------------------------------
+__device__ void plasma_scalars(const Params& p, int r, long long step, RepState& st)
+{
+    double te, ne;
+    if (p.plasma_mode == 1) {
+        long long idx = (long long)r * (p.max_steps + 1) + (step <= p.max_steps ? step : p.max_steps);
+        ne = p.pres_ne[idx];
+        te = p.pres_te[idx];
+    } else if (st.n_e > 0) {
+        te = __ddiv_rn((double)st.e_gas, __dmul_rn(1500.0, (double)st.n_e));
+        ne = __ddiv_rn((double)st.n_e, p.volume[r]);
+    } else {
+        te = 0.0;
+        ne = 0.0;
+    }
+    double kap = 0.0;
+    if (ne > 0.0) {
+        double tc = te > p.te_floor ? te : p.te_floor;
+        double k2 = __ddiv_rn(__dmul_rn(p.four_pi_f, ne), __dmul_rn(tc, kEvKJmol));
+        kap = __dsqrt_rn(k2);
+    }
+    st.te_ev = te;
+    st.n_dens = ne;
+    st.kappa = kap;
+    st.ne_dt = __dmul_rn(ne, p.dt);
+    double x = __dmul_rn(te, p.inv_dte);
+    if (x > (double)(p.n_te - 1)) x = (double)(p.n_te - 1);
+    if (x < 0.0) x = 0.0;
+    int i0 = (int)x;
+    if (i0 > p.n_te - 2) i0 = p.n_te - 2;
+    st.it0 = i0;
+    st.wt = __dsub_rn(x, (double)i0);
+    double kf = p.kappa_fixed >= 0.0 ? p.kappa_fixed : kap;
+    st.kappa_force = kf;
+    st.kappa_f = (float)kf;
+}
+
+__device__ void make_grid(const Params& p, int r, const RepAccum* acc)
+{
+    Grid& g = p.grid[r];
+    if (g.periodic) return;   // periodic grids are fixed at init
+    double lo[3], hi[3];
+    for (int d = 0; d < 3; ++d) {
+        unsigned long long mn = ~0ull, mx = 0ull;
+        for (int c = 0; c < kAccCopies; ++c) {
+            unsigned long long a = acc[c].bmin[d], b = acc[c].bmax[d];
+            mn = a < mn ? a : mn;
+            mx = b > mx ? b : mx;
+        }
+        lo[d] = mn == ~0ull ? 0.0 : from_ordered(mn);
+        hi[d] = mx == 0ull ? 0.0 : from_ordered(mx);
+        if (!(hi[d] >= lo[d])) { lo[d] = 0.0; hi[d] = 0.0; }
+    }
+    double f = 1.0;
+    int n[3];
+    for (int it = 0; it < 400; ++it) {
+        long long prod = 1;
+        for (int d = 0; d < 3; ++d) {
+            double m = floor((hi[d] - lo[d]) / (p.r_cut * f));
+            n[d] = m < 1.0 ? 1 : (m > 1.0e6 ? 1000000 : (int)m);
+            prod *= n[d];
+        }
+        if (prod <= g.cell_cap) break;
+        f *= 1.125;
+    }
+    for (int d = 0; d < 3; ++d) {
+        double ext = hi[d] - lo[d];
+        double e = n[d] == 1 ? (ext > p.r_cut ? ext : p.r_cut) : ext / n[d];
+        g.origin[d] = lo[d];
+        g.edge[d] = e;
+        g.inv_edge[d] = 1.0 / e;
+        g.edge_f[d] = (float)e;
+        g.dims[d] = n[d];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_step_a: one thread per atom (original order).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_step_a(Params p, int mode)
+{
+    __shared__ long long s_acc[kRepWindow][6];
+    __shared__ unsigned long long s_bmin[kRepWindow][3], s_bmax[kRepWindow][3];
+    __shared__ int s_last;
+    const int tid = threadIdx.x;
+    for (int k = tid; k < kRepWindow * 6; k += blockDim.x) (&s_acc[0][0])[k] = 0;
+    for (int k = tid; k < kRepWindow * 3; k += blockDim.x) {
+        (&s_bmin[0][0])[k] = ~0ull;
+        (&s_bmax[0][0])[k] = 0ull;
+    }
+    __syncthreads();
+
+    const long long step = *p.step;
+    const int kick_full = *p.kick_full;
+    const int first = blockIdx.x * blockDim.x;
+    const int r0 = p.rep[first < p.n_atoms ? first : p.n_atoms - 1];
+    const int i = first + tid;
+    const bool live = i < p.n_atoms;
+    const int lane = tid & 31;
+    int r = live ? p.rep[i] : -1;
+    double pos[3] = {0.0, 0.0, 0.0};
+    bool vac = false;
+
+    if (live) {
+        const int s = p.species[i];
+        double x = p.x[i], y = p.y[i], z = p.z[i];
+        if (mode & STEP_KICK_DRIFT) {
+            const int slot = p.slot_of[i];
+            const double c = kick_full ? 2.0 * p.hdtm[s] : p.hdtm[s];
+            double vx = p.vx[i] + c * ((double)p.fx[slot] * kFixInv);
+            double vy = p.vy[i] + c * ((double)p.fy[slot] * kFixInv);
+            double vz = p.vz[i] + c * ((double)p.fz[slot] * kFixInv);
+            x += p.dt * vx;
+            y += p.dt * vy;
+            z += p.dt * vz;
+            const Grid& g = p.grid[r];
+            if (g.periodic) {
+                const double L0 = g.box[0], L1 = g.box[1], L2 = g.box[2];
+                x -= L0 * floor(x / L0);
+                y -= L1 * floor(y / L1);
+                z -= L2 * floor(z / L2);
+                // floor rounding may leave x == L; fold back to 0
+                if (x >= L0) x -= L0;
+                if (y >= L1) y -= L1;
+                if (z >= L2) z -= L2;
+            }
+            if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(vx) && isfinite(vy) &&
+                  isfinite(vz)))
+                atomicOr(p.err, ERR_NONFINITE);
+            p.vx[i] = vx; p.vy[i] = vy; p.vz[i] = vz;
+            p.x[i] = x; p.y[i] = y; p.z[i] = z;
+        }
+        pos[0] = x; pos[1] = y; pos[2] = z;
+        vac = !p.grid[r].periodic;
+    }
+
+    // ---- bounding box of vacuum replicas (warp-reduced when uniform) ----
+    {
+        const unsigned full = 0xffffffffu;
+        const int rl0 = __shfl_sync(full, r, 0);
+        const bool uniform = __all_sync(full, r == rl0) && rl0 >= 0;
+        const bool any_vac = __any_sync(full, vac);
+        if (any_vac) {
+            if (uniform) {
+                if (__shfl_sync(full, (int)vac, 0)) {
+                    for (int d = 0; d < 3; ++d) {
+                        unsigned long long mn = ordered_bits(pos[d]), mx = mn;
+                        for (int o = 16; o; o >>= 1) {
+                            unsigned long long a = __shfl_xor_sync(full, mn, o);
+                            unsigned long long b = __shfl_xor_sync(full, mx, o);
+                            mn = a < mn ? a : mn;
+                            mx = b > mx ? b : mx;
+                        }
+                        if (lane == 0) {
+                            const int w = rl0 - r0;
+                            if (w < kRepWindow) {
+                                atomicMin(&s_bmin[w][d], mn);
+                                atomicMax(&s_bmax[w][d], mx);
+                            } else {
+                                RepAccum* a = p.acc + (size_t)rl0 * kAccCopies + (blockIdx.x & (kAccCopies - 1));
+                                atomicMin(&a->bmin[d], mn);
+                                atomicMax(&a->bmax[d], mx);
+                            }
+                        }
+                    }
+                }
+            } else if (vac) {
+                const int w = r - r0;
+                for (int d = 0; d < 3; ++d) {
+                    unsigned long long o = ordered_bits(pos[d]);
+                    if (w < kRepWindow) {
+                        atomicMin(&s_bmin[w][d], o);
+                        atomicMax(&s_bmax[w][d], o);
+                    } else {
+                        RepAccum* a = p.acc + (size_t)r * kAccCopies + (blockIdx.x & (kAccCopies - 1));
+                        atomicMin(&a->bmin[d], o);
+                        atomicMax(&a->bmax[d], o);
+                    }
+                }
+            }
+        }
+    }
+
+    // ---- collisional-radiative update (reading of Sec. II.A) ----
+    if (live && (mode & STEP_CR)) {
+        const int s = p.species[i];
+        const int Z = p.zs[s];
+        const int qi = p.q[i], hi = p.h[i];
+        const int ts = p.ts_off[s] + qi;
+        const RepState st = p.rs[r];
+        double dF = 0.0;
+        if (step < p.max_steps) dF = p.dF[(long long)r * p.max_steps + step];
+        else atomicOr(p.err, ERR_TABLE_END);
+        const double a_pi = __dmul_rn(p.sigma_pi[2 * ts + hi], dF);
+        const double a_a = hi ? p.auger_dt[s] : 0.0;
+        double a_ci = 0.0, a_rec = 0.0;
+        if (qi < Z) a_ci = __dmul_rn(st.ne_dt, interp(p.k_ci + (long long)ts * p.n_te, st.it0, st.wt));
+        if (qi > 0 && hi == 0)
+            a_rec = __dmul_rn(st.ne_dt, interp(p.k_rec + (long long)ts * p.n_te, st.it0, st.wt));
+        const double c1 = __dadd_rn(a_pi, a_a);
+        const double c2 = __dadd_rn(c1, a_ci);
+        const double lam = __dadd_rn(c2, a_rec);
+        int ch = -1;
+        if (lam > 0.0) {
+            const unsigned long long sd = p.seed[r];
+            const uint4 w4 = philox4x32_10(make_uint4((unsigned)p.local_id[i], (unsigned)step, 0u, 0u),
+                                           make_uint2((unsigned)sd, (unsigned)(sd >> 32)));
+            const double u0 = u53(w4.x, w4.y);
+            // 1 - e^{-lam} <= lam, so u0 >= lam decides "no event" exactly
+            if (u0 < lam && u0 < one_minus_exp_neg(lam, p.etab, p.inv12)) {
+                const double t = __dmul_rn(u53(w4.z, w4.w), lam);
+                if (t < a_pi) ch = 0;
+                else if (t < c1) ch = 1;
+                else if (t < c2) ch = 2;
+                else if (t < lam) ch = 3;
+                else ch = a_rec > 0.0 ? 3 : (a_ci > 0.0 ? 2 : (a_a > 0.0 ? 1 : 0));
+            }
+        }
+        if (ch >= 0) {
+            int qn = qi, hn = hi;
+            long long de;
+            if (ch == 0) {
+                qn = qi + 1;
+                de = p.e_pi_mev[2 * ts + hi];
+                if (qn == Z) hn = 0;
+                else if (Z >= 3 && hi == 0 && Z - qn >= 2) hn = 1;
+            } else if (ch == 1) {
+                qn = qi + 1;
+                hn = 0;
+                de = p.e_auger_mev[s];
+            } else if (ch == 2) {
+                qn = qi + 1;
+                if (qn == Z) hn = 0;
+                de = -p.ip_mev[ts];
+            } else {
+                qn = qi - 1;
+                de = p.ip_mev[ts - 1];
+            }
+            p.q[i] = (uint8_t)qn;
+            p.h[i] = (uint8_t)hn;
+            const int w = r - r0;
+            if (w < kRepWindow) {
+                atomicAdd((unsigned long long*)&s_acc[w][0], (unsigned long long)(ch == 3 ? -1ll : 1ll));
+                atomicAdd((unsigned long long*)&s_acc[w][1], (unsigned long long)de);
+                atomicAdd((unsigned long long*)&s_acc[w][2 + ch], 1ull);
+            } else {
+                RepAccum* a = p.acc + (size_t)r * kAccCopies + (blockIdx.x & (kAccCopies - 1));
+                atomicAdd((unsigned long long*)&a->dNe, (unsigned long long)(ch == 3 ? -1ll : 1ll));
+                atomicAdd((unsigned long long*)&a->dE, (unsigned long long)de);
+                atomicAdd((unsigned long long*)&a->counts[ch], 1ull);
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- flush block partials ----
+    {
+        const int last_atom = min(first + (int)blockDim.x, p.n_atoms) - 1;
+        const int r_last = p.rep[last_atom];
+        const int nw = min(r_last - r0 + 1, kRepWindow);
+        for (int k = tid; k < nw * 12; k += blockDim.x) {
+            const int w = k / 12, f = k % 12;
+            RepAccum* a = p.acc + (size_t)(r0 + w) * kAccCopies + (blockIdx.x & (kAccCopies - 1));
+            if (f < 6) {
+                const long long v = s_acc[w][f];
+                if (v != 0) {
+                    unsigned long long* dst = f == 0 ? (unsigned long long*)&a->dNe
+                                            : f == 1 ? (unsigned long long*)&a->dE
+                                                     : (unsigned long long*)&a->counts[f - 2];
+                    atomicAdd(dst, (unsigned long long)v);
+                }
+            } else if (f < 9) {
+                if (s_bmin[w][f - 6] != ~0ull) atomicMin(&a->bmin[f - 6], s_bmin[w][f - 6]);
+            } else {
+                if (s_bmax[w][f - 9] != 0ull) atomicMax(&a->bmax[f - 9], s_bmax[w][f - 9]);
+            }
+        }
+    }
+
+    // ---- last block: per-replica reduction (Eq. 3) and next grid ----
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = (atomicAdd(&p.counters[3], 1) == (int)gridDim.x - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const long long next = (mode & STEP_ADVANCE) ? step + 1 : step;
+    for (int rr = tid; rr < p.n_rep; rr += blockDim.x) {
+        RepAccum* a = p.acc + (size_t)rr * kAccCopies;
+        RepState st = p.rs[rr];
+        long long dNe = 0, dE = 0, cnt[4] = {0, 0, 0, 0};
+        for (int c = 0; c < kAccCopies; ++c) {
+            dNe += __ldcg(&a[c].dNe);
+            dE += __ldcg(&a[c].dE);
+            for (int k = 0; k < 4; ++k) cnt[k] += __ldcg(&a[c].counts[k]);
+        }
+        st.n_e += dNe;
+        st.e_gas += dE;
+        if (st.e_gas < 0) st.e_gas = 0;
+        for (int k = 0; k < 4; ++k) st.counts[k] += cnt[k];
+        plasma_scalars(p, rr, next, st);
+        p.rs[rr] = st;
+        RepAccum bb[kAccCopies];
+        for (int c = 0; c < kAccCopies; ++c)
+            for (int d = 0; d < 3; ++d) {
+                bb[c].bmin[d] = __ldcg(&a[c].bmin[d]);
+                bb[c].bmax[d] = __ldcg(&a[c].bmax[d]);
+            }
+        make_grid(p, rr, bb);
+        for (int c = 0; c < kAccCopies; ++c) {
+            a[c].dNe = 0;
+            a[c].dE = 0;
+            for (int k = 0; k < 4; ++k) a[c].counts[k] = 0;
+            for (int d = 0; d < 3; ++d) {
+                a[c].bmin[d] = ~0ull;
+                a[c].bmax[d] = 0ull;
+            }
+        }
+    }
+    if (tid == 0) {
+        p.counters[3] = 0;
+        if (mode & STEP_ADVANCE) *p.step = next;
+        if (mode & STEP_KICK_DRIFT) *p.kick_full = 1;
+    }
+}
+
+void launch_step_a(const Params& p, int mode, cudaStream_t s, int grid_atoms)
+{
+    k_step_a<<<grid_atoms, 256, 0, s>>>(p, mode);
+}
+
+// ---------------------------------------------------------------------------
+// Velocities at the integer step (state stores v_{n+1/2} once stepping has
+// started), forces in kJ/mol/nm, kinetic energy, Philox diagnostic.
+// ---------------------------------------------------------------------------
+__global__ void k_velocity_out(Params p, double* out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.n_atoms) return;
+    const int full = *p.kick_full;
+    double vx = p.vx[i], vy = p.vy[i], vz = p.vz[i];
+    if (full) {
+        const int slot = p.slot_of[i];
+        const double c = p.hdtm[p.species[i]];
+        vx += c * ((double)p.fx[slot] * kFixInv);
+        vy += c * ((double)p.fy[slot] * kFixInv);
+        vz += c * ((double)p.fz[slot] * kFixInv);
+    }
+    out[3 * i + 0] = vx;
+    out[3 * i + 1] = vy;
+    out[3 * i + 2] = vz;
+}
+
+__global__ void k_force_out(Params p, double* out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.n_atoms) return;
+    const int slot = p.slot_of[i];
+    out[3 * i + 0] = (double)p.fx[slot] * kFixInv;
+    out[3 * i + 1] = (double)p.fy[slot] * kFixInv;
+    out[3 * i + 2] = (double)p.fz[slot] * kFixInv;
+}
+
+// One block per replica, fixed traversal order -> deterministic sums.
+__global__ void k_energy(Params p, double* ekin, long long* epot)
+{
+    __shared__ double s_k[256];
+    __shared__ long long s_u[256];
+    const int r = blockIdx.x;
+    const int a0 = p.rep_off[r], a1 = p.rep_off[r + 1];
+    const int full = *p.kick_full;
+    double k = 0.0;
+    long long u = 0;
+    for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
+        const int slot = p.slot_of[i];
+        const int s = p.species[i];
+        double vx = p.vx[i], vy = p.vy[i], vz = p.vz[i];
+        if (full) {
+            const double c = p.hdtm[s];
+            vx += c * ((double)p.fx[slot] * kFixInv);
+            vy += c * ((double)p.fy[slot] * kFixInv);
+            vz += c * ((double)p.fz[slot] * kFixInv);
+        }
+        k += 0.5 * p.mass[s] * (vx * vx + vy * vy + vz * vz);
+        u += p.epot[slot];
+    }
+    s_k[threadIdx.x] = k;
+    s_u[threadIdx.x] = u;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            s_k[threadIdx.x] += s_k[threadIdx.x + o];
+            s_u[threadIdx.x] += s_u[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        ekin[r] = s_k[0];
+        epot[r] = s_u[0];
+    }
+}
+
+__global__ void k_philox(unsigned long long seed, const uint4* ctr, long long n, uint4* out)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[i] = philox4x32_10(ctr[i], make_uint2((unsigned)seed, (unsigned)(seed >> 32)));
+}
+
+void launch_velocity_out(const Params& p, double* d_v_out, cudaStream_t s)
+{
+    k_velocity_out<<<(p.n_atoms + 255) / 256, 256, 0, s>>>(p, d_v_out);
+}
+void launch_force_out(const Params& p, double* d_f_out, cudaStream_t s)
+{
+    k_force_out<<<(p.n_atoms + 255) / 256, 256, 0, s>>>(p, d_f_out);
+}
+void launch_energy(const Params& p, double* d_ekin, long long* d_epot, cudaStream_t s)
+{
+    k_energy<<<p.n_rep, 256, 0, s>>>(p, d_ekin, d_epot);
+}
+void launch_philox(unsigned long long seed, const uint32_t* ctr, long long n, uint32_t* out,
+                   cudaStream_t s)
+{
+    if (n <= 0) return;
+    const long long blocks = (n + 255) / 256;
+    k_philox<<<(unsigned)blocks, 256, 0, s>>>(seed, (const uint4*)ctr, n, (uint4*)out);
+}
+
+}  // namespace mdg

@@ -1,0 +1,883 @@
+// Host side of the C ABI (include/md.h): validation, host-built tables,
+// device memory, the per-step CUDA graph, state exchange and diagnostics.
+// Compiled with -ffp-contract=off: the pulse table feeds the charge update,
+// which must match the CPU oracle bit for bit.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/md.h"
+#include "md_internal.cuh"
+
+using namespace mdg;
+
+struct md_handle {
+    md_config cfg{};
+    std::string err;
+    int N = 0, R = 0, NS = 0, NTS = 0, NTE = 0;
+    int n_sm = 0;
+    std::vector<int> z, ts_off, rep_off;
+    std::vector<Grid> grid0;
+    Params P{};
+    std::vector<void*> allocs;
+    cudaStream_t stream = nullptr;       // caller's stream (NULL = legacy default)
+    cudaStream_t cap_stream = nullptr;   // private stream used for graph capture
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t ev_pair0 = nullptr, ev_pair1 = nullptr;
+    int grid_atoms = 1, grid_cells = 1;
+    int pair_blocks = 1, pair_warps = 8, pair_nsplit = 14;
+    long long host_step = 0;
+    bool poisoned = false;
+    unsigned* h_err = nullptr;           // pinned
+    double pair_ms = 0.0;
+    long long pair_launches = 0, steps = 0, last_pairs = 0;
+    double* d_scratch = nullptr;         // [3N] doubles for state exchange
+    double* d_ekin = nullptr;
+    long long* d_epot = nullptr;
+};
+
+namespace {
+
+thread_local std::string g_init_error;
+
+md_status fail(md_handle* h, md_status s, const std::string& msg)
+{
+    if (h) h->err = msg;
+    else g_init_error = msg;
+    return s;
+}
+
+#define CU(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(h, MD_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename T>
+md_status dalloc(md_handle* h, T** p, size_t count)
+{
+    size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    bytes = (bytes + 255) / 256 * 256;
+    void* ptr = nullptr;
+    if (h->cfg.dev_alloc) {
+        ptr = h->cfg.dev_alloc(bytes, h->cfg.alloc_ctx);
+        if (!ptr) return fail(h, MD_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+    } else {
+        cudaError_t e = cudaMalloc(&ptr, bytes);
+        if (e != cudaSuccess)
+            return fail(h, MD_ERR_OOM, "cudaMalloc(" + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+    }
+    h->allocs.push_back(ptr);
+    *p = static_cast<T*>(ptr);
+    return MD_OK;
+}
+
+#define DALLOC(ptr, n)                               \
+    do {                                             \
+        md_status s_ = dalloc(h, &(ptr), (size_t)(n)); \
+        if (s_ != MD_OK) return s_;                  \
+    } while (0)
+
+// Per-step fluence of a list of pulses (photons/nm^2 in [t_n, t_{n+1}]).
+void pulse_table_host(const md_pulse* pulses, int n_pulses, double t_start_fs, double dt_fs,
+                      int n_steps, double* out)
+{
+    for (int n = 0; n < n_steps; ++n) {
+        double ta = t_start_fs + (double)n * dt_fs;
+        double tb = t_start_fs + (double)(n + 1) * dt_fs;
+        double acc = 0.0;
+        for (int k = 0; k < n_pulses; ++k) {
+            const md_pulse& P = pulses[k];
+            double fwhm = P.fwhm_fs, flu = P.fluence_ph_um2 * 1e-6, t0 = P.t_center_fs;
+            double frac;
+            if (P.shape == MD_PULSE_GAUSSIAN) {
+                // normal CDF difference, sigma_t = FWHM / (2 sqrt(2 ln 2)); erfc taken on the
+                // side of the centre where it does not cancel
+                double sig = fwhm / (2.0 * std::sqrt(2.0 * std::log(2.0)));
+                double s = sig * std::sqrt(2.0);
+                double za = (ta - t0) / s, zb = (tb - t0) / s;
+                if (za >= 0.0) frac = 0.5 * (std::erfc(za) - std::erfc(zb));
+                else if (zb <= 0.0) frac = 0.5 * (std::erfc(-zb) - std::erfc(-za));
+                else frac = 1.0 - 0.5 * (std::erfc(-za) + std::erfc(zb));
+            } else {
+                double lo = t0 - 0.5 * fwhm, hi = t0 + 0.5 * fwhm;
+                double a = ta > lo ? ta : lo;
+                double b = tb < hi ? tb : hi;
+                frac = b > a ? (b - a) / fwhm : 0.0;
+            }
+            acc = acc + flu * frac;
+        }
+        out[n] = acc;
+    }
+}
+
+md_status check_device_flags(md_handle* h)
+{
+    CU(cudaMemcpyAsync(h->h_err, h->P.err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    unsigned e = *h->h_err;
+    if (!e) return MD_OK;
+    h->poisoned = true;
+    if (e & ERR_NONFINITE) return fail(h, MD_ERR_NONFINITE, "non-finite position or velocity");
+    if (e & ERR_OVERFLOW) return fail(h, MD_ERR_FIXED_OVERFLOW, "force or energy beyond the 64-bit fixed-point range");
+    if (e & ERR_CELL) return fail(h, MD_ERR_CELL_OVERFLOW, "cell-list capacity exceeded");
+    if (e & ERR_TABLE_END) return fail(h, MD_ERR_TABLE_END, "stepped past the pulse table");
+    return fail(h, MD_ERR_CUDA, "unknown device error flag");
+}
+
+// Cell list + forces at the current positions/charges (no time advance).
+void enqueue_rebuild(md_handle* h, cudaStream_t s, bool energy)
+{
+    launch_step_a(h->P, 0, s, h->grid_atoms);
+    launch_cells(h->P, s, h->grid_atoms, h->grid_cells);
+    launch_pair(h->P, s, energy, h->pair_blocks, h->pair_warps, h->pair_nsplit);
+}
+
+void enqueue_step(md_handle* h, cudaStream_t s)
+{
+    int mode = STEP_KICK_DRIFT | STEP_ADVANCE | (h->cfg.cr_enabled ? STEP_CR : 0);
+    launch_step_a(h->P, mode, s, h->grid_atoms);
+    launch_cells(h->P, s, h->grid_atoms, h->grid_cells);
+    if (h->cfg.profile) cudaEventRecord(h->ev_pair0, s);
+    launch_pair(h->P, s, false, h->pair_blocks, h->pair_warps, h->pair_nsplit);
+    if (h->cfg.profile) cudaEventRecord(h->ev_pair1, s);
+}
+
+md_status capture_graph(md_handle* h)
+{
+    if (h->exec) {
+        cudaGraphExecDestroy(h->exec);
+        h->exec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    CU(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    enqueue_step(h, h->cap_stream);
+    CU(cudaStreamEndCapture(h->cap_stream, &graph));
+    cudaError_t e = cudaGraphInstantiate(&h->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(h, MD_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    return MD_OK;
+}
+
+// Choose the pair-kernel launch shape by timing (results are identical for
+// every shape: the fixed-point sums do not depend on it).
+md_status autotune(md_handle* h)
+{
+    const bool fp64 = h->cfg.precision == MD_PREC_FP64;
+    cudaEvent_t a, b;
+    CU(cudaEventCreate(&a));
+    CU(cudaEventCreate(&b));
+    float best = 1e30f;
+    int bw = h->pair_warps, bb = h->pair_blocks, bn = h->pair_nsplit;
+    const int warps_c[] = {4, 8};
+    const int split_c[] = {1, 2, 7, 14};
+    for (int w : warps_c) {
+        int maxb = pair_max_blocks_per_sm(fp64, false, w, h->NTS);
+        for (int bps = 1; bps <= maxb; ++bps) {
+            for (int ns : split_c) {
+                int blocks = bps * h->n_sm;
+                float tot = 0.0f;
+                for (int rep = 0; rep < 3; ++rep) {
+                    // reset the work counter only (forces are rebuilt afterwards)
+                    CU(cudaMemsetAsync(h->P.counters + 2, 0, sizeof(int), h->stream));
+                    CU(cudaEventRecord(a, h->stream));
+                    launch_pair(h->P, h->stream, false, blocks, w, ns);
+                    CU(cudaEventRecord(b, h->stream));
+                    CU(cudaEventSynchronize(b));
+                    float ms = 0.0f;
+                    CU(cudaEventElapsedTime(&ms, a, b));
+                    if (rep) tot += ms;
+                }
+                if (tot < best) {
+                    best = tot;
+                    bw = w; bb = blocks; bn = ns;
+                }
+            }
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    h->pair_warps = bw;
+    h->pair_blocks = bb;
+    h->pair_nsplit = bn;
+    return MD_OK;
+}
+
+md_status validate(const md_config* c, const md_system* s)
+{
+    md_handle* h = nullptr;
+    if (!c || !s) return fail(h, MD_ERR_INVALID_ARG, "null config or system");
+    if (!(c->dt_ps > 0) || !(c->r_cut > 0) || !(c->r_cut < 1e3))
+        return fail(h, MD_ERR_INVALID_ARG, "dt_ps and r_cut must be positive");
+    if (c->precision != MD_PREC_MIXED && c->precision != MD_PREC_FP64)
+        return fail(h, MD_ERR_INVALID_ARG, "precision must be MD_PREC_MIXED or MD_PREC_FP64");
+    if (c->plasma_mode != MD_PLASMA_BOOKKEEPING && c->plasma_mode != MD_PLASMA_PRESCRIBED)
+        return fail(h, MD_ERR_INVALID_ARG, "bad plasma_mode");
+    if (c->max_steps < 1) return fail(h, MD_ERR_INVALID_ARG, "max_steps must be >= 1");
+    if (!(c->te_floor_ev > 0)) return fail(h, MD_ERR_INVALID_ARG, "te_floor_ev must be > 0");
+    if (!(c->coulomb_f > 0)) return fail(h, MD_ERR_INVALID_ARG, "coulomb_f must be > 0");
+    if (c->n_species < 1 || c->n_species > MD_MAX_SPECIES)
+        return fail(h, MD_ERR_INVALID_ARG, "n_species out of range");
+    int nts = 0;
+    for (int k = 0; k < c->n_species; ++k) {
+        if (c->z[k] < 1 || c->z[k] > MD_MAX_Z) return fail(h, MD_ERR_INVALID_ARG, "Z out of range");
+        if (!(c->mass[k] > 0)) return fail(h, MD_ERR_INVALID_ARG, "masses must be positive");
+        if (!(c->lj_sigma0[k] >= 0) || !(c->lj_eps0[k] >= 0))
+            return fail(h, MD_ERR_INVALID_ARG, "LJ parameters must be >= 0");
+        nts += c->z[k] + 1;
+    }
+    if (nts > MD_MAX_TYPE_STATES) return fail(h, MD_ERR_INVALID_ARG, "too many type states");
+    if (c->n_te < 2 || !(c->dte_ev > 0)) return fail(h, MD_ERR_INVALID_ARG, "Te grid needs n_te >= 2, dte_ev > 0");
+    if (!c->sigma_pi || !c->k_ci || !c->k_rec || !c->ip_mev || !c->e_pi_mev || !c->e_auger_mev)
+        return fail(h, MD_ERR_INVALID_ARG, "CR tables missing");
+    if ((c->dev_alloc == nullptr) != (c->dev_free == nullptr))
+        return fail(h, MD_ERR_INVALID_ARG, "dev_alloc and dev_free must be given together");
+    if (s->n_atoms < 1) return fail(h, MD_ERR_INVALID_ARG, "n_atoms must be >= 1");
+    if (!s->x || !s->v || !s->species || !s->fragment || !s->replica_offset || !s->seed || !s->box ||
+        !s->volume)
+        return fail(h, MD_ERR_INVALID_ARG, "system arrays missing");
+    if (s->n_replicas < 1 || s->n_replicas > s->n_atoms)
+        return fail(h, MD_ERR_INVALID_ARG, "n_replicas out of range");
+    if (s->replica_offset[0] != 0 || s->replica_offset[s->n_replicas] != s->n_atoms)
+        return fail(h, MD_ERR_INVALID_ARG, "replica_offset must run from 0 to n_atoms");
+    for (int r = 0; r < s->n_replicas; ++r) {
+        if (s->replica_offset[r + 1] <= s->replica_offset[r])
+            return fail(h, MD_ERR_INVALID_ARG, "every replica needs at least one atom");
+        if (!(s->volume[r] > 0)) return fail(h, MD_ERR_INVALID_ARG, "volume must be > 0");
+        const double* L = s->box + 3 * r;
+        bool per = L[0] > 0 || L[1] > 0 || L[2] > 0;
+        if (per) {
+            for (int d = 0; d < 3; ++d)
+                if (!(L[d] >= 3.0 * c->r_cut))
+                    return fail(h, MD_ERR_INVALID_ARG, "periodic box edges must all be >= 3 r_cut");
+        }
+    }
+    for (int i = 0; i < s->n_atoms; ++i) {
+        if (s->species[i] >= c->n_species) return fail(h, MD_ERR_INVALID_ARG, "species index out of range");
+        if (s->q0 && s->q0[i] > c->z[s->species[i]]) return fail(h, MD_ERR_INVALID_ARG, "q0 above Z");
+        for (int d = 0; d < 3; ++d)
+            if (!std::isfinite(s->x[3 * i + d]) || !std::isfinite(s->v[3 * i + d]))
+                return fail(h, MD_ERR_INVALID_ARG, "non-finite input position or velocity");
+    }
+    return MD_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+extern "C" {
+
+const char* md_version(void) { return "gb300-ionising-md 0.1 (sm_103a)"; }
+
+const char* md_last_error(const md_handle* h)
+{
+    if (!h) return g_init_error.c_str();
+    return h->err.c_str();
+}
+
+md_status md_pulse_table(const md_pulse* p, int n_pulses, double t_start_fs, double dt_fs, int n_steps,
+                         double* out)
+{
+    md_handle* h = nullptr;
+    if ((n_pulses > 0 && !p) || n_pulses < 0 || n_steps < 0 || (n_steps > 0 && !out) || !(dt_fs > 0))
+        return fail(h, MD_ERR_INVALID_ARG, "md_pulse_table: bad arguments");
+    for (int k = 0; k < n_pulses; ++k)
+        if (!(p[k].fwhm_fs > 0) || !(p[k].fluence_ph_um2 >= 0) ||
+            (p[k].shape != MD_PULSE_GAUSSIAN && p[k].shape != MD_PULSE_FLAT_TOP))
+            return fail(h, MD_ERR_INVALID_ARG, "md_pulse_table: bad pulse");
+    pulse_table_host(p, n_pulses, t_start_fs, dt_fs, n_steps, out);
+    return MD_OK;
+}
+
+static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* sys);
+
+md_status md_init(const md_config* cfg, const md_system* sys, md_handle** out)
+{
+    if (out) *out = nullptr;
+    if (!out) return fail(nullptr, MD_ERR_INVALID_ARG, "out is null");
+    md_status st = validate(cfg, sys);
+    if (st != MD_OK) return st;
+    md_handle* h = new md_handle();
+    st = init_impl(h, cfg, sys);
+    if (st != MD_OK) {
+        g_init_error = h->err;
+        md_finalize(h);
+        return st;
+    }
+    *out = h;
+    return MD_OK;
+}
+
+static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* sys)
+{
+    h->cfg = *cfg;
+    const md_config& c = h->cfg;
+    h->N = sys->n_atoms;
+    h->R = sys->n_replicas;
+    h->NS = c.n_species;
+    h->NTE = c.n_te;
+    int dev = 0;
+    CU(cudaGetDevice(&dev));
+    CU(cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, dev));
+    CU(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    CU(cudaEventCreate(&h->ev_pair0));
+    CU(cudaEventCreate(&h->ev_pair1));
+    CU(cudaMallocHost(&h->h_err, sizeof(unsigned)));
+
+    // ---- type states and tables ----
+    h->z.assign(c.z, c.z + c.n_species);
+    h->ts_off.assign(h->NS + 1, 0);
+    for (int s = 0; s < h->NS; ++s) h->ts_off[s + 1] = h->ts_off[s] + h->z[s] + 1;
+    const int nts = h->NTS = h->ts_off[h->NS];
+    // LJ per pair of type states: sigma scaled by (1 - q/Z) (Eq. 11), arithmetic-mean
+    // sigma and geometric-mean epsilon, c6 = 4 eps s^6, c12 = c6 s^6
+    std::vector<double> sig_ts(nts), eps_ts(nts);
+    for (int s = 0; s < h->NS; ++s)
+        for (int q = 0; q <= h->z[s]; ++q) {
+            sig_ts[h->ts_off[s] + q] = c.lj_sigma0[s] * (1.0 - (double)q / (double)h->z[s]);
+            eps_ts[h->ts_off[s] + q] = c.lj_eps0[s];
+        }
+    std::vector<double2> lj_d((size_t)nts * nts);
+    std::vector<float2> lj_f((size_t)nts * nts);
+    for (int a = 0; a < nts; ++a)
+        for (int b = 0; b < nts; ++b) {
+            double sg = 0.5 * (sig_ts[a] + sig_ts[b]);
+            double ep = std::sqrt(eps_ts[a] * eps_ts[b]);
+            double s6 = sg * sg * sg * sg * sg * sg;
+            double c6 = 4.0 * ep * s6, c12 = c6 * s6;
+            lj_d[(size_t)a * nts + b] = make_double2(c6, c12);
+            lj_f[(size_t)a * nts + b] = make_float2((float)c6, (float)c12);
+        }
+    std::vector<double> etab(kNEtab), inv12(13, 0.0);
+    for (int k = 0; k < kNEtab; ++k) etab[k] = std::exp(-(double)k / 16.0);
+    for (int m = 1; m <= 12; ++m) inv12[m] = 1.0 / (double)m;
+    std::vector<double> hdtm(h->NS), auger_dt(h->NS), mass(h->NS);
+    for (int s = 0; s < h->NS; ++s) {
+        hdtm[s] = (0.5 * c.dt_ps) / c.mass[s];
+        auger_dt[s] = c.tau_auger_ps[s] > 0 ? c.dt_ps / c.tau_auger_ps[s] : 0.0;
+        mass[s] = c.mass[s];
+    }
+
+    // ---- replica grids ----
+    h->rep_off.assign(sys->replica_offset, sys->replica_offset + h->R + 1);
+    h->grid0.assign(h->R, Grid{});
+    long long cells_total = 0;
+    for (int r = 0; r < h->R; ++r) {
+        Grid& g = h->grid0[r];
+        const double* L = sys->box + 3 * r;
+        g.periodic = (L[0] > 0 || L[1] > 0 || L[2] > 0) ? 1 : 0;
+        if (g.periodic) {
+            long long prod = 1;
+            for (int d = 0; d < 3; ++d) {
+                int n = (int)std::floor(L[d] / c.r_cut);
+                n = std::max(3, std::min(n, 1024));
+                g.dims[d] = n;
+                g.edge[d] = L[d] / n;
+                g.inv_edge[d] = 1.0 / g.edge[d];
+                g.edge_f[d] = (float)g.edge[d];
+                g.origin[d] = 0.0;
+                g.box[d] = L[d];
+                prod *= n;
+            }
+            g.cell_cap = (int)prod;
+        } else {
+            double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+            for (int i = h->rep_off[r]; i < h->rep_off[r + 1]; ++i)
+                for (int d = 0; d < 3; ++d) {
+                    lo[d] = std::min(lo[d], sys->x[3 * i + d]);
+                    hi[d] = std::max(hi[d], sys->x[3 * i + d]);
+                }
+            long long prod = 1;
+            for (int d = 0; d < 3; ++d) {
+                long long n = std::max(1LL, (long long)std::floor((hi[d] - lo[d]) / c.r_cut));
+                prod *= n;
+                g.dims[d] = 1;
+                g.edge[d] = c.r_cut;
+                g.inv_edge[d] = 1.0 / c.r_cut;
+                g.edge_f[d] = (float)c.r_cut;
+                g.origin[d] = lo[d];
+                g.box[d] = 0.0;
+            }
+            // room for the sample to expand 4x in cell count before cells grow
+            long long cap = std::max(64LL, 4 * prod);
+            cap = std::min(cap, (long long)(1 << 22));
+            g.cell_cap = (int)cap;
+        }
+        g.cell_off = (int)cells_total;
+        cells_total += g.cell_cap;
+    }
+    if (cells_total > (1LL << 26)) return fail(h, MD_ERR_INVALID_ARG, "cell grid too large");
+    const int C = (int)cells_total;
+    const long long slot_cap = (long long)h->N + 7LL * C + 8;
+    if (slot_cap > (1LL << 30)) return fail(h, MD_ERR_INVALID_ARG, "system too large");
+
+    // ---- device memory ----
+    Params& P = h->P;
+    P.n_atoms = h->N; P.n_rep = h->R; P.n_species = h->NS; P.n_ts = nts; P.n_te = h->NTE;
+    P.max_steps = c.max_steps;
+    P.cell_cap_total = C;
+    P.slot_cap = (int)slot_cap;
+    P.cluster_cap = P.slot_cap / kClusterSize + 1;
+    P.sc_cap = P.cluster_cap;
+    P.precision = c.precision; P.cr_enabled = c.cr_enabled; P.plasma_mode = c.plasma_mode;
+    P.dt = c.dt_ps; P.r_cut = c.r_cut; P.rc2 = c.r_cut * c.r_cut; P.kappa_fixed = c.kappa_fixed;
+    P.te_floor = c.te_floor_ev; P.coulomb_f = c.coulomb_f;
+    P.four_pi_f = 4.0 * M_PI * c.coulomb_f;
+    P.inv_dte = 1.0 / c.dte_ev;
+    P.rc_f = (float)c.r_cut;
+    P.rc2_f = P.rc_f * P.rc_f;
+    const int N = h->N, R = h->R, NS = h->NS;
+    DALLOC(P.x, N); DALLOC(P.y, N); DALLOC(P.z, N);
+    DALLOC(P.vx, N); DALLOC(P.vy, N); DALLOC(P.vz, N);
+    DALLOC(P.species, N); DALLOC(P.q, N); DALLOC(P.h, N);
+    DALLOC(P.frag, N); DALLOC(P.rep, N); DALLOC(P.local_id, N); DALLOC(P.slot_of, N);
+    DALLOC(P.atom_cell, N); DALLOC(P.atom_rank, N);
+    double *d_hdtm, *d_mass, *d_auger, *d_sigma, *d_kci, *d_krec, *d_etab, *d_inv;
+    int *d_z, *d_tsoff;
+    long long *d_ip, *d_epi, *d_eaug;
+    float2* d_ljf;
+    double2* d_ljd;
+    DALLOC(d_hdtm, NS); DALLOC(d_mass, NS); DALLOC(d_z, NS); DALLOC(d_tsoff, NS + 1); DALLOC(d_auger, NS);
+    DALLOC(d_sigma, 2 * nts); DALLOC(d_kci, (size_t)nts * h->NTE); DALLOC(d_krec, (size_t)nts * h->NTE);
+    DALLOC(d_ip, nts); DALLOC(d_epi, 2 * nts); DALLOC(d_eaug, NS);
+    DALLOC(d_etab, kNEtab); DALLOC(d_inv, 13);
+    DALLOC(d_ljf, (size_t)nts * nts); DALLOC(d_ljd, (size_t)nts * nts);
+    P.hdtm = d_hdtm; P.mass = d_mass; P.zs = d_z; P.ts_off = d_tsoff; P.auger_dt = d_auger;
+    P.sigma_pi = d_sigma; P.k_ci = d_kci; P.k_rec = d_krec; P.ip_mev = d_ip; P.e_pi_mev = d_epi;
+    P.e_auger_mev = d_eaug; P.etab = d_etab; P.inv12 = d_inv; P.lj_f = d_ljf; P.lj_d = d_ljd;
+    unsigned long long* d_seed;
+    double *d_dF, *d_pne, *d_pte, *d_vol;
+    int* d_repoff;
+    DALLOC(P.grid, R); DALLOC(P.rs, R); DALLOC(P.acc, (size_t)R * 16);
+    DALLOC(d_seed, R); DALLOC(d_dF, (size_t)R * c.max_steps);
+    DALLOC(d_pne, (size_t)R * (c.max_steps + 1)); DALLOC(d_pte, (size_t)R * (c.max_steps + 1));
+    DALLOC(d_vol, R); DALLOC(d_repoff, R + 1);
+    P.seed = d_seed; P.dF = d_dF; P.pres_ne = d_pne; P.pres_te = d_pte; P.volume = d_vol; P.rep_off = d_repoff;
+    DALLOC(P.cell_count, C); DALLOC(P.cell_start, C + 1); DALLOC(P.cell_pstart, C + 1);
+    DALLOC(P.tmp_key, N);
+    DALLOC(P.sc_cell, P.sc_cap); DALLOC(P.sc_first, P.sc_cap); DALLOC(P.sc_ncl, P.sc_cap);
+    DALLOC(P.counters, 8);
+    if (c.precision == MD_PREC_MIXED) { DALLOC(P.xq, P.slot_cap); P.xq64 = nullptr; }
+    else { DALLOC(P.xq64, P.slot_cap); P.xq = nullptr; }
+    DALLOC(P.tf, P.slot_cap); DALLOC(P.atom_of, P.slot_cap);
+    DALLOC(P.bb_lo, P.cluster_cap); DALLOC(P.bb_hi, P.cluster_cap); DALLOC(P.bb_frag, P.cluster_cap);
+    P.cl_cell = nullptr;
+    DALLOC(P.fx, P.slot_cap); DALLOC(P.fy, P.slot_cap); DALLOC(P.fz, P.slot_cap); DALLOC(P.epot, P.slot_cap);
+    DALLOC(P.pair_count, 1);
+    DALLOC(P.err, 1); DALLOC(P.step, 1); DALLOC(P.kick_full, 1);
+    DALLOC(h->d_scratch, 3 * (size_t)N);
+    DALLOC(h->d_ekin, R); DALLOC(h->d_epot, R);
+
+    // ---- uploads (synchronous, init only) ----
+    {
+        std::vector<double> tmp(N);
+        double* dst[6] = {P.x, P.y, P.z, P.vx, P.vy, P.vz};
+        for (int k = 0; k < 6; ++k) {
+            const double* src = k < 3 ? sys->x : sys->v;
+            for (int i = 0; i < N; ++i) tmp[i] = src[3 * i + (k % 3)];
+            CU(cudaMemcpy(dst[k], tmp.data(), N * sizeof(double), cudaMemcpyHostToDevice));
+        }
+        CU(cudaMemcpy(P.species, sys->species, N, cudaMemcpyHostToDevice));
+        std::vector<uint8_t> q0(N, 0);
+        if (sys->q0) std::copy(sys->q0, sys->q0 + N, q0.begin());
+        CU(cudaMemcpy(P.q, q0.data(), N, cudaMemcpyHostToDevice));
+        CU(cudaMemset(P.h, 0, N));
+        CU(cudaMemcpy(P.frag, sys->fragment, N * sizeof(int), cudaMemcpyHostToDevice));
+        std::vector<int> rep(N), loc(N);
+        std::vector<RepState> rs(R);
+        for (int r = 0; r < R; ++r) {
+            rs[r] = RepState{};
+            for (int i = h->rep_off[r]; i < h->rep_off[r + 1]; ++i) {
+                rep[i] = r;
+                loc[i] = i - h->rep_off[r];
+                rs[r].n_e += q0[i];
+            }
+        }
+        CU(cudaMemcpy(P.rep, rep.data(), N * sizeof(int), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(P.local_id, loc.data(), N * sizeof(int), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(P.rs, rs.data(), R * sizeof(RepState), cudaMemcpyHostToDevice));
+        std::vector<RepAccum> acc((size_t)R * 16);
+        for (auto& a : acc) {
+            a = RepAccum{};
+            for (int d = 0; d < 3; ++d) { a.bmin[d] = ~0ull; a.bmax[d] = 0ull; }
+        }
+        CU(cudaMemcpy(P.acc, acc.data(), acc.size() * sizeof(RepAccum), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(P.grid, h->grid0.data(), R * sizeof(Grid), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(d_seed, sys->seed, R * sizeof(unsigned long long), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(d_vol, sys->volume, R * sizeof(double), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(d_repoff, h->rep_off.data(), (R + 1) * sizeof(int), cudaMemcpyHostToDevice));
+        CU(cudaMemset(d_dF, 0, (size_t)R * c.max_steps * sizeof(double)));
+        CU(cudaMemset(d_pne, 0, (size_t)R * (c.max_steps + 1) * sizeof(double)));
+        CU(cudaMemset(d_pte, 0, (size_t)R * (c.max_steps + 1) * sizeof(double)));
+        CU(cudaMemcpy(d_hdtm, hdtm.data(), NS * sizeof(double), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(d_mass, mass.data(), NS * sizeof(double), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(d_z, h->z.data(), NS * sizeof(int), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(d_tsoff, h->ts_off.data(), (NS + 1) * sizeof(int), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(d_auger, auger_dt.data(), NS * sizeof(double), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(d_sigma, c.sigma_pi, 2 * nts * sizeof(double), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(d_kci, c.k_ci, (size_t)nts * h->NTE * sizeof(double), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(d_krec, c.k_rec, (size_t)nts * h->NTE * sizeof(double), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(d_ip, c.ip_mev, nts * sizeof(long long), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(d_epi, c.e_pi_mev, 2 * nts * sizeof(long long), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(d_eaug, c.e_auger_mev, NS * sizeof(long long), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(d_etab, etab.data(), kNEtab * sizeof(double), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(d_inv, inv12.data(), 13 * sizeof(double), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(d_ljf, lj_f.data(), lj_f.size() * sizeof(float2), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(d_ljd, lj_d.data(), lj_d.size() * sizeof(double2), cudaMemcpyHostToDevice));
+        CU(cudaMemset(P.cell_count, 0, C * sizeof(int)));
+        CU(cudaMemset(P.counters, 0, 8 * sizeof(int)));
+        CU(cudaMemset(P.err, 0, sizeof(unsigned)));
+        CU(cudaMemset(P.step, 0, sizeof(long long)));
+        CU(cudaMemset(P.kick_full, 0, sizeof(int)));
+        CU(cudaMemset(P.slot_of, 0, N * sizeof(int)));
+        CU(cudaMemset(P.fx, 0, P.slot_cap * sizeof(long long)));
+        CU(cudaMemset(P.fy, 0, P.slot_cap * sizeof(long long)));
+        CU(cudaMemset(P.fz, 0, P.slot_cap * sizeof(long long)));
+        CU(cudaMemset(P.pair_count, 0, sizeof(long long)));
+    }
+    h->grid_atoms = (N + 255) / 256;
+    h->grid_cells = std::max(1, std::min((C + 7) / 8, h->n_sm * 16));
+    h->pair_warps = 8;
+    h->pair_nsplit = 14;
+    h->pair_blocks = h->n_sm * pair_max_blocks_per_sm(c.precision == MD_PREC_FP64, false, 8, nts);
+    CU(cudaDeviceSynchronize());
+
+    // ---- initial cell list and forces F_0 ----
+    enqueue_rebuild(h, h->stream, false);
+    CU(cudaGetLastError());
+    md_status st = check_device_flags(h);
+    if (st != MD_OK) return st;
+    if (c.autotune) {
+        st = autotune(h);
+        if (st != MD_OK) return st;
+        enqueue_rebuild(h, h->stream, false);
+        st = check_device_flags(h);
+        if (st != MD_OK) return st;
+    }
+    return capture_graph(h);
+}
+
+void md_finalize(md_handle* h)
+{
+    if (!h) return;
+    cudaDeviceSynchronize();
+    if (h->exec) cudaGraphExecDestroy(h->exec);
+    for (void* p : h->allocs) {
+        if (h->cfg.dev_free) h->cfg.dev_free(p, h->cfg.alloc_ctx);
+        else cudaFree(p);
+    }
+    if (h->ev_pair0) cudaEventDestroy(h->ev_pair0);
+    if (h->ev_pair1) cudaEventDestroy(h->ev_pair1);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->h_err) cudaFreeHost(h->h_err);
+    delete h;
+}
+
+md_status md_set_stream(md_handle* h, void* stream)
+{
+    if (!h) return fail(nullptr, MD_ERR_INVALID_ARG, "null handle");
+    h->stream = static_cast<cudaStream_t>(stream);
+    return MD_OK;
+}
+
+static md_status check_replica(md_handle* h, int replica)
+{
+    if (!h) return fail(nullptr, MD_ERR_INVALID_ARG, "null handle");
+    if (h->poisoned) return fail(h, MD_ERR_BAD_STATE, "handle is in an error state: " + h->err);
+    if (replica < -1 || replica >= h->R) return fail(h, MD_ERR_INVALID_ARG, "replica out of range");
+    return MD_OK;
+}
+
+md_status md_set_pulse(md_handle* h, int replica, const md_pulse* p, int n_pulses)
+{
+    md_status st = check_replica(h, replica);
+    if (st != MD_OK) return st;
+    if (n_pulses < 0 || (n_pulses > 0 && !p)) return fail(h, MD_ERR_INVALID_ARG, "bad pulse list");
+    for (int k = 0; k < n_pulses; ++k) {
+        if (std::fabs(p[k].photon_kev - h->cfg.photon_kev) > 1e-9 * std::max(1.0, h->cfg.photon_kev))
+            return fail(h, MD_ERR_INVALID_ARG, "pulse photon energy differs from the cross-section table");
+        if (!(p[k].fwhm_fs > 0) || !(p[k].fluence_ph_um2 >= 0) ||
+            (p[k].shape != MD_PULSE_GAUSSIAN && p[k].shape != MD_PULSE_FLAT_TOP))
+            return fail(h, MD_ERR_INVALID_ARG, "bad pulse parameters");
+    }
+    std::vector<double> tab(h->cfg.max_steps);
+    pulse_table_host(p, n_pulses, h->cfg.t_start_fs, h->cfg.dt_ps * 1000.0, h->cfg.max_steps, tab.data());
+    return md_set_pulse_table(h, replica, tab.data(), h->cfg.max_steps);
+}
+
+md_status md_set_pulse_table(md_handle* h, int replica, const double* dF, int n_steps)
+{
+    md_status st = check_replica(h, replica);
+    if (st != MD_OK) return st;
+    if (n_steps < 0 || n_steps > h->cfg.max_steps || (n_steps > 0 && !dF))
+        return fail(h, MD_ERR_INVALID_ARG, "n_steps must be in [0, max_steps]");
+    for (int n = 0; n < n_steps; ++n)
+        if (!(dF[n] >= 0) || !std::isfinite(dF[n])) return fail(h, MD_ERR_INVALID_ARG, "fluence must be finite and >= 0");
+    const int r0 = replica < 0 ? 0 : replica, r1 = replica < 0 ? h->R : replica + 1;
+    for (int r = r0; r < r1; ++r) {
+        double* dst = const_cast<double*>(h->P.dF) + (size_t)r * h->cfg.max_steps;
+        CU(cudaMemcpyAsync(dst, dF, n_steps * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        if (n_steps < h->cfg.max_steps)
+            CU(cudaMemsetAsync(dst + n_steps, 0, (h->cfg.max_steps - n_steps) * sizeof(double), h->stream));
+    }
+    CU(cudaStreamSynchronize(h->stream));
+    return MD_OK;
+}
+
+md_status md_set_pulse_table_at(md_handle* h, int replica, int first_step, const double* dF, int n)
+{
+    md_status st = check_replica(h, replica);
+    if (st != MD_OK) return st;
+    if (first_step < 0 || n < 0 || first_step + n > h->cfg.max_steps || (n > 0 && !dF))
+        return fail(h, MD_ERR_INVALID_ARG, "range outside [0, max_steps)");
+    for (int k = 0; k < n; ++k)
+        if (!(dF[k] >= 0) || !std::isfinite(dF[k])) return fail(h, MD_ERR_INVALID_ARG, "fluence must be finite and >= 0");
+    const int r0 = replica < 0 ? 0 : replica, r1 = replica < 0 ? h->R : replica + 1;
+    for (int r = r0; r < r1; ++r) {
+        double* dst = const_cast<double*>(h->P.dF) + (size_t)r * h->cfg.max_steps + first_step;
+        CU(cudaMemcpyAsync(dst, dF, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    }
+    return MD_OK;
+}
+
+md_status md_set_plasma_table(md_handle* h, int replica, const double* ne, const double* te, int n_steps)
+{
+    md_status st = check_replica(h, replica);
+    if (st != MD_OK) return st;
+    if (n_steps < 1 || n_steps > h->cfg.max_steps + 1 || !ne || !te)
+        return fail(h, MD_ERR_INVALID_ARG, "n_steps must be in [1, max_steps + 1]");
+    const int r0 = replica < 0 ? 0 : replica, r1 = replica < 0 ? h->R : replica + 1;
+    const size_t stride = (size_t)h->cfg.max_steps + 1;
+    for (int r = r0; r < r1; ++r) {
+        CU(cudaMemcpyAsync(const_cast<double*>(h->P.pres_ne) + r * stride, ne, n_steps * sizeof(double),
+                           cudaMemcpyHostToDevice, h->stream));
+        CU(cudaMemcpyAsync(const_cast<double*>(h->P.pres_te) + r * stride, te, n_steps * sizeof(double),
+                           cudaMemcpyHostToDevice, h->stream));
+    }
+    // the scalars of the current step change with the table: recompute them
+    launch_step_a(h->P, 0, h->stream, h->grid_atoms);
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(h->stream));
+    return MD_OK;
+}
+
+md_status md_step(md_handle* h, int n_steps)
+{
+    if (!h) return fail(nullptr, MD_ERR_INVALID_ARG, "null handle");
+    if (h->poisoned) return fail(h, MD_ERR_BAD_STATE, "handle is in an error state: " + h->err);
+    if (n_steps < 0) return fail(h, MD_ERR_INVALID_ARG, "n_steps must be >= 0");
+    if (h->host_step + n_steps > h->cfg.max_steps)
+        return fail(h, MD_ERR_TABLE_END, "step " + std::to_string(h->host_step + n_steps) +
+                                             " is past max_steps = " + std::to_string(h->cfg.max_steps));
+    for (int k = 0; k < n_steps; ++k) {
+        CU(cudaGraphLaunch(h->exec, h->stream));
+        if (h->cfg.profile) {
+            CU(cudaEventSynchronize(h->ev_pair1));
+            float ms = 0.0f;
+            CU(cudaEventElapsedTime(&ms, h->ev_pair0, h->ev_pair1));
+            h->pair_ms += ms;
+            h->pair_launches += 1;
+        }
+    }
+    h->host_step += n_steps;
+    h->steps += n_steps;
+    return check_device_flags(h);
+}
+
+md_status md_get_state(md_handle* h, md_state* out, unsigned fields)
+{
+    if (!h) return fail(nullptr, MD_ERR_INVALID_ARG, "null handle");
+    if (!out) return fail(h, MD_ERR_INVALID_ARG, "null state");
+    const int N = h->N, R = h->R;
+    CU(cudaStreamSynchronize(h->stream));
+    std::vector<double> tmp;
+    if (fields & MD_FIELD_X) {
+        if (!out->x) return fail(h, MD_ERR_INVALID_ARG, "x buffer missing");
+        tmp.resize(N);
+        double* src[3] = {h->P.x, h->P.y, h->P.z};
+        for (int d = 0; d < 3; ++d) {
+            CU(cudaMemcpy(tmp.data(), src[d], N * sizeof(double), cudaMemcpyDeviceToHost));
+            for (int i = 0; i < N; ++i) out->x[3 * i + d] = tmp[i];
+        }
+    }
+    if (fields & MD_FIELD_V) {
+        if (!out->v) return fail(h, MD_ERR_INVALID_ARG, "v buffer missing");
+        launch_velocity_out(h->P, h->d_scratch, h->stream);
+        CU(cudaMemcpyAsync(out->v, h->d_scratch, 3 * (size_t)N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    }
+    if (fields & MD_FIELD_F) {
+        if (!out->f) return fail(h, MD_ERR_INVALID_ARG, "f buffer missing");
+        launch_force_out(h->P, h->d_scratch, h->stream);
+        CU(cudaMemcpyAsync(out->f, h->d_scratch, 3 * (size_t)N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    }
+    if (fields & MD_FIELD_Q) {
+        if (!out->q) return fail(h, MD_ERR_INVALID_ARG, "q buffer missing");
+        CU(cudaMemcpyAsync(out->q, h->P.q, N, cudaMemcpyDeviceToHost, h->stream));
+    }
+    if (fields & MD_FIELD_H) {
+        if (!out->h) return fail(h, MD_ERR_INVALID_ARG, "h buffer missing");
+        CU(cudaMemcpyAsync(out->h, h->P.h, N, cudaMemcpyDeviceToHost, h->stream));
+    }
+    if (fields & (MD_FIELD_PLASMA | MD_FIELD_COUNTS)) {
+        std::vector<RepState> rs(R);
+        CU(cudaMemcpyAsync(rs.data(), h->P.rs, R * sizeof(RepState), cudaMemcpyDeviceToHost, h->stream));
+        CU(cudaStreamSynchronize(h->stream));
+        for (int r = 0; r < R; ++r) {
+            if (fields & MD_FIELD_PLASMA) {
+                if (out->n_e) out->n_e[r] = rs[r].n_e;
+                if (out->e_gas_mev) out->e_gas_mev[r] = rs[r].e_gas;
+                if (out->te_ev) out->te_ev[r] = rs[r].te_ev;
+                if (out->kappa) out->kappa[r] = rs[r].kappa;
+            }
+            if ((fields & MD_FIELD_COUNTS) && out->event_counts)
+                for (int k = 0; k < 4; ++k) out->event_counts[4 * r + k] = rs[r].counts[k];
+        }
+    }
+    if (fields & MD_FIELD_STEP) out->step = h->host_step;
+    CU(cudaStreamSynchronize(h->stream));
+    return MD_OK;
+}
+
+md_status md_set_state(md_handle* h, const md_state* in, unsigned fields)
+{
+    if (!h) return fail(nullptr, MD_ERR_INVALID_ARG, "null handle");
+    if (!in) return fail(h, MD_ERR_INVALID_ARG, "null state");
+    const int N = h->N, R = h->R;
+    CU(cudaStreamSynchronize(h->stream));
+    // bring velocities to the integer step with the current forces first
+    launch_velocity_out(h->P, h->d_scratch, h->stream);
+    {
+        std::vector<double> v(3 * (size_t)N), tmp(N);
+        CU(cudaMemcpyAsync(v.data(), h->d_scratch, v.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        CU(cudaStreamSynchronize(h->stream));
+        const double* vs = (fields & MD_FIELD_V) ? in->v : v.data();
+        if ((fields & MD_FIELD_V) && !in->v) return fail(h, MD_ERR_INVALID_ARG, "v buffer missing");
+        double* dst[3] = {h->P.vx, h->P.vy, h->P.vz};
+        for (int d = 0; d < 3; ++d) {
+            for (int i = 0; i < N; ++i) {
+                tmp[i] = vs[3 * i + d];
+                if (!std::isfinite(tmp[i])) return fail(h, MD_ERR_INVALID_ARG, "non-finite velocity");
+            }
+            CU(cudaMemcpy(dst[d], tmp.data(), N * sizeof(double), cudaMemcpyHostToDevice));
+        }
+    }
+    if (fields & MD_FIELD_X) {
+        if (!in->x) return fail(h, MD_ERR_INVALID_ARG, "x buffer missing");
+        std::vector<double> tmp(N);
+        double* dst[3] = {h->P.x, h->P.y, h->P.z};
+        for (int d = 0; d < 3; ++d) {
+            for (int i = 0; i < N; ++i) {
+                tmp[i] = in->x[3 * i + d];
+                if (!std::isfinite(tmp[i])) return fail(h, MD_ERR_INVALID_ARG, "non-finite position");
+            }
+            CU(cudaMemcpy(dst[d], tmp.data(), N * sizeof(double), cudaMemcpyHostToDevice));
+        }
+    }
+    if (fields & MD_FIELD_Q) {
+        if (!in->q) return fail(h, MD_ERR_INVALID_ARG, "q buffer missing");
+        std::vector<uint8_t> sp(N);
+        CU(cudaMemcpy(sp.data(), h->P.species, N, cudaMemcpyDeviceToHost));
+        for (int i = 0; i < N; ++i)
+            if (in->q[i] > h->z[sp[i]]) return fail(h, MD_ERR_INVALID_ARG, "q above Z");
+        CU(cudaMemcpy(h->P.q, in->q, N, cudaMemcpyHostToDevice));
+    }
+    if (fields & MD_FIELD_H) {
+        if (!in->h) return fail(h, MD_ERR_INVALID_ARG, "h buffer missing");
+        for (int i = 0; i < N; ++i)
+            if (in->h[i] > 1) return fail(h, MD_ERR_INVALID_ARG, "h must be 0 or 1");
+        CU(cudaMemcpy(h->P.h, in->h, N, cudaMemcpyHostToDevice));
+    }
+    if (fields & (MD_FIELD_PLASMA | MD_FIELD_COUNTS)) {
+        std::vector<RepState> rs(R);
+        CU(cudaMemcpy(rs.data(), h->P.rs, R * sizeof(RepState), cudaMemcpyDeviceToHost));
+        for (int r = 0; r < R; ++r) {
+            if (fields & MD_FIELD_PLASMA) {
+                if (!in->n_e || !in->e_gas_mev) return fail(h, MD_ERR_INVALID_ARG, "plasma buffers missing");
+                if (in->n_e[r] < 0 || in->e_gas_mev[r] < 0) return fail(h, MD_ERR_INVALID_ARG, "negative plasma counter");
+                rs[r].n_e = in->n_e[r];
+                rs[r].e_gas = in->e_gas_mev[r];
+            }
+            if ((fields & MD_FIELD_COUNTS) && in->event_counts)
+                for (int k = 0; k < 4; ++k) rs[r].counts[k] = in->event_counts[4 * r + k];
+        }
+        CU(cudaMemcpy(h->P.rs, rs.data(), R * sizeof(RepState), cudaMemcpyHostToDevice));
+    }
+    if (fields & MD_FIELD_STEP) {
+        if (in->step < 0 || in->step > h->cfg.max_steps) return fail(h, MD_ERR_INVALID_ARG, "step out of range");
+        h->host_step = in->step;
+        CU(cudaMemcpy(h->P.step, &in->step, sizeof(long long), cudaMemcpyHostToDevice));
+    }
+    CU(cudaMemset(h->P.kick_full, 0, sizeof(int)));
+    CU(cudaMemset(h->P.err, 0, sizeof(unsigned)));
+    h->poisoned = false;
+    enqueue_rebuild(h, h->stream, false);
+    CU(cudaGetLastError());
+    return check_device_flags(h);
+}
+
+md_status md_get_energies(md_handle* h, double* e_kin, double* e_pot, int64_t* n_pairs)
+{
+    if (!h) return fail(nullptr, MD_ERR_INVALID_ARG, "null handle");
+    if (h->poisoned) return fail(h, MD_ERR_BAD_STATE, "handle is in an error state: " + h->err);
+    const int R = h->R;
+    CU(cudaMemsetAsync(h->P.pair_count, 0, sizeof(long long), h->stream));
+    // same cell list and decomposition -> the forces come out bit-identical
+    launch_cells(h->P, h->stream, h->grid_atoms, h->grid_cells);
+    launch_pair(h->P, h->stream, true, h->pair_blocks, h->pair_warps, h->pair_nsplit);
+    launch_energy(h->P, h->d_ekin, h->d_epot, h->stream);
+    CU(cudaGetLastError());
+    std::vector<double> ek(R);
+    std::vector<long long> ep(R);
+    long long np = 0;
+    CU(cudaMemcpyAsync(ek.data(), h->d_ekin, R * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaMemcpyAsync(ep.data(), h->d_epot, R * sizeof(long long), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaMemcpyAsync(&np, h->P.pair_count, sizeof(long long), cudaMemcpyDeviceToHost, h->stream));
+    md_status st = check_device_flags(h);
+    if (st != MD_OK) return st;
+    for (int r = 0; r < R; ++r) {
+        if (e_kin) e_kin[r] = ek[r];
+        if (e_pot) e_pot[r] = (double)ep[r] * kFixInv;
+    }
+    if (n_pairs) *n_pairs = np;
+    h->last_pairs = np;
+    return MD_OK;
+}
+
+md_status md_get_timing(md_handle* h, md_timing* out)
+{
+    if (!h || !out) return fail(h, MD_ERR_INVALID_ARG, "null argument");
+    out->pair_ms = h->pair_ms;
+    out->pair_launches = h->pair_launches;
+    out->steps = h->steps;
+    out->pair_count_last = h->last_pairs;
+    out->tile_warps = h->pair_warps;
+    out->tile_blocks_per_sm = h->pair_blocks / std::max(1, h->n_sm);
+    return MD_OK;
+}
+
+md_status md_reset_timing(md_handle* h)
+{
+    if (!h) return fail(nullptr, MD_ERR_INVALID_ARG, "null handle");
+    h->pair_ms = 0.0;
+    h->pair_launches = 0;
+    h->steps = 0;
+    return MD_OK;
+}
+
+md_status md_philox(uint64_t seed, const uint32_t* d_ctr4, int64_t n, uint32_t* d_out, void* stream)
+{
+    md_handle* h = nullptr;
+    if (n < 0 || (n > 0 && (!d_ctr4 || !d_out))) return fail(h, MD_ERR_INVALID_ARG, "md_philox: bad arguments");
+    launch_philox(seed, d_ctr4, n, d_out, static_cast<cudaStream_t>(stream));
+    CU(cudaGetLastError());
+    return MD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,189 @@
+// Internal device-side definitions of the GB300 ionising-MD library.
+// Not part of the C ABI (include/md.h is).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mdg {
+
+// Atoms are grouped in clusters of 8 consecutive slots of the cell-sorted
+// order; a warp processes one super-cluster of up to K_SC i-clusters against
+// one neighbour cell at a time.
+constexpr int kClusterSize = 8;
+constexpr int kSuperClusters = 8;     // K_SC
+constexpr int kHalfShell = 14;        // self cell + 13 neighbour cells
+constexpr int kMaxSpecies = 8;
+constexpr int kMaxTS = 128;
+constexpr int kNEtab = 16 * 40;       // e^{-k/16} table, lambda < 40
+constexpr int kRepWindow = 8;         // replicas per CTA kept in shared memory
+constexpr double kFixScale = 4294967296.0;        // 2^32
+constexpr double kFixInv = 1.0 / 4294967296.0;
+constexpr double kFixLimit = 4.611686018427388e18;  // 2^62 (overflow guard)
+constexpr double kEvKJmol = 96.48533212;          // kJ/mol per eV
+constexpr float kBBoxMargin = 1e-4f;               // nm, slack of the cluster prefilter
+
+// device error bits (mirrored to md_status by the host)
+enum : unsigned {
+    ERR_OVERFLOW = 1u,
+    ERR_NONFINITE = 2u,
+    ERR_CELL = 4u,
+    ERR_TABLE_END = 8u,
+};
+
+struct Grid {                // cell grid of one replica (rebuilt every step)
+    double origin[3];        // lower corner (nm)
+    double edge[3];          // cell edge per dimension, >= r_cut
+    double inv_edge[3];
+    double box[3];           // periodic box lengths (0 for vacuum)
+    float edge_f[3];
+    int dims[3];
+    int cell_off;            // first global cell index of the replica
+    int cell_cap;            // cells reserved for the replica
+    int periodic;
+};
+
+struct RepState {            // plasma and bookkeeping of one replica
+    long long n_e;           // free electrons
+    long long e_gas;         // gas energy, meV
+    long long counts[4];     // PI, Auger, CI, REC events so far
+    double te_ev;            // T_e used by the rate tables
+    double n_dens;           // n_e (nm^-3)
+    double kappa;            // 1/lambda_D (nm^-1) from Eq. 3
+    double ne_dt;            // n_e * dt
+    double wt;               // Te-grid interpolation weight
+    int it0;                 // Te-grid interval
+    float kappa_f;           // screening used by the pair forces
+    double kappa_force;      // same in double
+};
+
+struct RepAccum {            // per-step sums of one replica
+    long long dNe;
+    long long dE;
+    long long counts[4];
+    unsigned long long bmin[3];  // ordered encodings of doubles
+    unsigned long long bmax[3];
+};
+
+// Everything a kernel may touch.  Passed by value.
+struct Params {
+    int n_atoms, n_rep, n_species, n_ts, n_te, max_steps;
+    int cell_cap_total, slot_cap, cluster_cap, sc_cap;
+    int precision, cr_enabled, plasma_mode;
+    double dt, r_cut, rc2, kappa_fixed, te_floor, four_pi_f, coulomb_f, inv_dte;
+    float rc2_f, rc_f;
+
+    // atoms, original order
+    double *x, *y, *z, *vx, *vy, *vz;
+    uint8_t *species, *q, *h;
+    int *frag, *rep, *local_id, *slot_of, *atom_cell, *atom_rank;
+
+    // species / type-state tables
+    const double* hdtm;      // [n_species] 0.5 dt / m
+    const double* mass;      // [n_species]
+    const int* zs;           // [n_species]
+    const int* ts_off;       // [n_species + 1]
+    const double* auger_dt;  // [n_species]
+    const double* sigma_pi;  // [n_ts][2]
+    const double* k_ci;      // [n_ts][n_te]
+    const double* k_rec;     // [n_ts][n_te]
+    const long long* ip_mev;     // [n_ts]
+    const long long* e_pi_mev;   // [n_ts][2]
+    const long long* e_auger_mev;// [n_species]
+    const double* etab;      // [kNEtab]
+    const double* inv12;     // [13] 1/m
+    const float2* lj_f;      // [n_ts][n_ts] (c6, c12)
+    const double2* lj_d;
+
+    // replicas
+    Grid* grid;
+    RepState* rs;
+    RepAccum* acc;
+    const unsigned long long* seed;
+    const double* dF;        // [n_rep][max_steps]
+    const double* pres_ne;   // [n_rep][max_steps + 1]
+    const double* pres_te;
+    const double* volume;
+    const int* rep_off;      // [n_rep + 1]
+
+    // cell list
+    int* cell_count;         // [cell_cap_total]
+    int* cell_start;         // [cell_cap_total + 1] unpadded
+    int* cell_pstart;        // [cell_cap_total + 1] padded (multiples of 8)
+    unsigned long long* tmp_key;  // [n_atoms] (sub-cell key << 32 | atom)
+    int* sc_cell;            // [sc_cap]
+    int* sc_first;           // [sc_cap] first cluster
+    int* sc_ncl;             // [sc_cap] clusters in the super-cluster
+    int* counters;           // [0] n_sc, [1] n_slots, [2] work, [3] ticket, [4] ticket2
+
+    // packed, cell-sorted arrays (slot order)
+    float4* xq;              // (x, y, z) relative to the cell centre, q
+    double4_32a* xq64;
+    int2* tf;                // (type state, fragment)
+    int* atom_of;            // slot -> atom (-1: padding)
+    float4* bb_lo;           // per cluster, relative to its cell centre
+    float4* bb_hi;
+    int2* bb_frag;           // min/max fragment of the cluster
+    int* cl_cell;            // cluster -> cell
+    long long *fx, *fy, *fz, *epot;   // fixed-point sums per slot
+    long long* pair_count;   // in-cutoff pairs (energy pass)
+
+    // run state
+    unsigned* err;
+    long long* step;
+    int* kick_full;
+};
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long ordered_bits(double v)
+{
+    unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double from_ordered(unsigned long long u)
+{
+    u = (u & 0x8000000000000000ull) ? (u & 0x7fffffffffffffffull) : ~u;
+    return __longlong_as_double((long long)u);
+}
+__host__ __device__ __forceinline__ unsigned long long ordered_bits_host(double v)
+{
+    union { double d; unsigned long long u; } c;
+    c.d = v;
+    unsigned long long u = c.u;
+    return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
+}
+
+// The 13 half-shell neighbour offsets plus the cell itself (index 0).
+__host__ __device__ __forceinline__ void half_shell(int nb, int& dx, int& dy, int& dz)
+{
+    // enumerate (dx,dy,dz) with dz>0, or dz==0 && dy>0, or dz==dy==0 && dx>0
+    if (nb == 0) { dx = dy = dz = 0; return; }
+    int k = nb - 1;               // 0..12
+    if (k < 1) { dx = 1; dy = 0; dz = 0; return; }
+    k -= 1;                       // 0..11
+    if (k < 3) { dx = k - 1; dy = 1; dz = 0; return; }
+    k -= 3;                       // 0..8
+    dx = k % 3 - 1; dy = k / 3 - 1; dz = 1;
+}
+
+// Launch helpers implemented in the .cu files.
+void launch_step_a(const Params& p, int mode, cudaStream_t s, int grid_atoms);
+void launch_cells(const Params& p, cudaStream_t s, int grid_atoms, int grid_cells);
+void launch_pair(const Params& p, cudaStream_t s, bool energy, int blocks, int warps, int nsplit);
+void launch_velocity_out(const Params& p, double* d_v_out, cudaStream_t s);
+void launch_energy(const Params& p, double* d_ekin, long long* d_epot, cudaStream_t s);
+void launch_philox(unsigned long long seed, const uint32_t* ctr, long long n, uint32_t* out,
+                   cudaStream_t s);
+void launch_force_out(const Params& p, double* d_f_out, cudaStream_t s);
+int pair_max_blocks_per_sm(bool fp64, bool energy, int warps, int n_ts);
+
+// modes of launch_step_a
+enum : int {
+    STEP_KICK_DRIFT = 1,     // velocity kick + position drift
+    STEP_CR = 2,             // collisional-radiative charge update
+    STEP_ADVANCE = 4,        // bump the step counter at the end
+};
+
+}  // namespace mdg

@@ -1,0 +1,361 @@
+"""Thin Python binding of the C ABI in include/md.h (ctypes).
+
+Argument marshalling only: every step of the method runs in libmdgb.so's
+CUDA kernels.  The module-level functions carry the C names (md_init,
+md_set_pulse, md_step, md_get_state, ...); ``IonisingMD`` wraps them for
+convenience.  PyTorch provides device memory (through the library's
+allocation hooks) and the current CUDA stream.  There is no CPU fallback:
+if libmdgb.so is missing or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+MD_OK, MD_ERR_INVALID_ARG, MD_ERR_BAD_STATE, MD_ERR_OOM, MD_ERR_CUDA = 0, 1, 2, 3, 4
+MD_ERR_FIXED_OVERFLOW, MD_ERR_TIMEOUT, MD_ERR_NONFINITE, MD_ERR_CELL_OVERFLOW, MD_ERR_TABLE_END = 5, 6, 7, 8, 9
+MD_PREC_MIXED, MD_PREC_FP64 = 0, 1
+MD_PLASMA_BOOKKEEPING, MD_PLASMA_PRESCRIBED = 0, 1
+MD_FIELD_X, MD_FIELD_V, MD_FIELD_F, MD_FIELD_Q, MD_FIELD_H = 1, 2, 4, 8, 16
+MD_FIELD_PLASMA, MD_FIELD_COUNTS, MD_FIELD_STEP, MD_FIELD_ALL = 32, 64, 128, 255
+MD_MAX_SPECIES = 8
+COULOMB_F = 138.935458
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+_S = MD_MAX_SPECIES
+
+
+class MDConfig(C.Structure):
+    _fields_ = [("dt_ps", C.c_double), ("r_cut", C.c_double), ("precision", C.c_int),
+                ("cr_enabled", C.c_int), ("plasma_mode", C.c_int), ("max_steps", C.c_int),
+                ("kappa_fixed", C.c_double), ("t_start_fs", C.c_double), ("te_floor_ev", C.c_double),
+                ("coulomb_f", C.c_double), ("photon_kev", C.c_double), ("n_species", C.c_int),
+                ("z", C.c_int * _S), ("mass", C.c_double * _S), ("lj_sigma0", C.c_double * _S),
+                ("lj_eps0", C.c_double * _S), ("tau_auger_ps", C.c_double * _S),
+                ("sigma_pi", C.c_void_p), ("k_ci", C.c_void_p), ("k_rec", C.c_void_p),
+                ("ip_mev", C.c_void_p), ("e_pi_mev", C.c_void_p), ("e_auger_mev", C.c_void_p),
+                ("n_te", C.c_int), ("dte_ev", C.c_double), ("dev_alloc", ALLOC_FN),
+                ("dev_free", FREE_FN), ("alloc_ctx", C.c_void_p), ("autotune", C.c_int),
+                ("profile", C.c_int)]
+
+
+class MDSystem(C.Structure):
+    _fields_ = [("n_atoms", C.c_int), ("x", C.c_void_p), ("v", C.c_void_p), ("species", C.c_void_p),
+                ("fragment", C.c_void_p), ("q0", C.c_void_p), ("n_replicas", C.c_int),
+                ("replica_offset", C.c_void_p), ("seed", C.c_void_p), ("box", C.c_void_p),
+                ("volume", C.c_void_p)]
+
+
+class MDPulse(C.Structure):
+    _fields_ = [("photon_kev", C.c_double), ("fwhm_fs", C.c_double), ("fluence_ph_um2", C.c_double),
+                ("t_center_fs", C.c_double), ("shape", C.c_int)]
+
+
+class MDState(C.Structure):
+    _fields_ = [("x", C.c_void_p), ("v", C.c_void_p), ("f", C.c_void_p), ("q", C.c_void_p),
+                ("h", C.c_void_p), ("n_e", C.c_void_p), ("e_gas_mev", C.c_void_p), ("te_ev", C.c_void_p),
+                ("kappa", C.c_void_p), ("event_counts", C.c_void_p), ("step", C.c_int64)]
+
+
+class MDTiming(C.Structure):
+    _fields_ = [("pair_ms", C.c_double), ("pair_launches", C.c_int64), ("steps", C.c_int64),
+                ("pair_count_last", C.c_int64), ("tile_warps", C.c_int), ("tile_blocks_per_sm", C.c_int)]
+
+
+class MDError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"md status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libmdgb.so (built in-tree); raise if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                                   "(no CPU fallback exists)")
+            L = C.CDLL(path)
+            P = C.c_void_p
+            L.md_init.argtypes = [C.POINTER(MDConfig), C.POINTER(MDSystem), C.POINTER(C.c_void_p)]
+            L.md_set_stream.argtypes = [P, P]
+            L.md_set_pulse.argtypes = [P, C.c_int, C.POINTER(MDPulse), C.c_int]
+            L.md_set_pulse_table.argtypes = [P, C.c_int, P, C.c_int]
+            L.md_set_pulse_table_at.argtypes = [P, C.c_int, C.c_int, P, C.c_int]
+            L.md_set_plasma_table.argtypes = [P, C.c_int, P, P, C.c_int]
+            L.md_step.argtypes = [P, C.c_int]
+            L.md_get_state.argtypes = [P, C.POINTER(MDState), C.c_uint]
+            L.md_set_state.argtypes = [P, C.POINTER(MDState), C.c_uint]
+            L.md_get_energies.argtypes = [P, P, P, P]
+            L.md_get_timing.argtypes = [P, C.POINTER(MDTiming)]
+            L.md_reset_timing.argtypes = [P]
+            L.md_last_error.argtypes = [P]
+            L.md_last_error.restype = C.c_char_p
+            L.md_finalize.argtypes = [P]
+            L.md_finalize.restype = None
+            L.md_pulse_table.argtypes = [C.POINTER(MDPulse), C.c_int, C.c_double, C.c_double, C.c_int, P]
+            L.md_philox.argtypes = [C.c_uint64, P, C.c_int64, P, P]
+            L.md_version.restype = C.c_char_p
+            _lib = L
+    return _lib
+
+
+def _check(status, handle=None):
+    if status != MD_OK:
+        msg = lib().md_last_error(handle).decode(errors="replace")
+        raise MDError(status, msg)
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _pulses(pulses):
+    arr = (MDPulse * max(len(pulses), 1))()
+    for k, p in enumerate(pulses):
+        arr[k] = MDPulse(p.photon_kev, p.fwhm_fs, p.fluence_ph_um2, p.t_center_fs, int(p.shape))
+    return arr
+
+
+# ---------------------------------------------------------------------------
+# C-named functions (marshalling only)
+# ---------------------------------------------------------------------------
+def md_init(config: MDConfig, system: MDSystem) -> C.c_void_p:
+    h = C.c_void_p()
+    _check(lib().md_init(C.byref(config), C.byref(system), C.byref(h)))
+    return h
+
+
+def md_set_stream(h, stream_ptr: int):
+    _check(lib().md_set_stream(h, C.c_void_p(stream_ptr)), h)
+
+
+def md_set_pulse(h, replica: int, pulses):
+    arr = _pulses(pulses)
+    _check(lib().md_set_pulse(h, int(replica), arr, len(pulses)), h)
+
+
+def md_set_pulse_table(h, replica: int, dF):
+    dF = _c(dF, np.float64)
+    _check(lib().md_set_pulse_table(h, int(replica), _p(dF), len(dF)), h)
+
+
+def md_set_pulse_table_at(h, replica: int, first_step: int, dF):
+    dF = _c(dF, np.float64)
+    _check(lib().md_set_pulse_table_at(h, int(replica), int(first_step), _p(dF), len(dF)), h)
+
+
+def md_set_plasma_table(h, replica: int, ne, te_ev):
+    ne = _c(ne, np.float64); te = _c(te_ev, np.float64)
+    _check(lib().md_set_plasma_table(h, int(replica), _p(ne), _p(te), len(ne)), h)
+
+
+def md_step(h, n_steps: int):
+    _check(lib().md_step(h, int(n_steps)), h)
+
+
+def md_get_state(h, state: MDState, fields: int):
+    _check(lib().md_get_state(h, C.byref(state), int(fields)), h)
+
+
+def md_set_state(h, state: MDState, fields: int):
+    _check(lib().md_set_state(h, C.byref(state), int(fields)), h)
+
+
+def md_get_energies(h, e_kin, e_pot):
+    n = C.c_int64()
+    _check(lib().md_get_energies(h, _p(e_kin), _p(e_pot), C.byref(n)), h)
+    return int(n.value)
+
+
+def md_get_timing(h) -> MDTiming:
+    t = MDTiming()
+    _check(lib().md_get_timing(h, C.byref(t)), h)
+    return t
+
+
+def md_reset_timing(h):
+    _check(lib().md_reset_timing(h), h)
+
+
+def md_last_error(h=None) -> str:
+    return lib().md_last_error(h).decode(errors="replace")
+
+
+def md_finalize(h):
+    lib().md_finalize(h)
+
+
+def md_pulse_table(pulses, t_start_fs: float, dt_fs: float, n_steps: int) -> np.ndarray:
+    out = np.empty(n_steps)
+    arr = _pulses(pulses)
+    _check(lib().md_pulse_table(arr, len(pulses), float(t_start_fs), float(dt_fs), int(n_steps), _p(out)))
+    return out
+
+
+def md_philox(seed: int, d_ctr4_ptr: int, n: int, d_out_ptr: int, stream_ptr: int = 0):
+    _check(lib().md_philox(C.c_uint64(seed), C.c_void_p(d_ctr4_ptr), C.c_int64(n), C.c_void_p(d_out_ptr),
+                           C.c_void_p(stream_ptr)))
+
+
+def md_version() -> str:
+    return lib().md_version().decode()
+
+
+# ---------------------------------------------------------------------------
+# Torch-backed device allocator for the library's hooks
+# ---------------------------------------------------------------------------
+class TorchAllocator:
+    def __init__(self):
+        import torch
+        self._torch = torch
+        self._live = {}
+        self.alloc_fn = ALLOC_FN(self._alloc)
+        self.free_fn = FREE_FN(self._free)
+
+    def _alloc(self, nbytes, ctx):
+        t = self._torch.empty(int(nbytes), dtype=self._torch.uint8, device="cuda")
+        ptr = t.data_ptr()
+        self._live[ptr] = t
+        return ptr
+
+    def _free(self, ptr, ctx):
+        self._live.pop(ptr, None)
+
+
+# ---------------------------------------------------------------------------
+# Convenience wrapper
+# ---------------------------------------------------------------------------
+class IonisingMD:
+    """One handle of the GB300 hot path for a Sample and its atomic data."""
+
+    def __init__(self, sample, atomic, *, dt_ps=5e-5, r_cut=1.2, precision="mixed", cr_enabled=True,
+                 plasma_mode=MD_PLASMA_BOOKKEEPING, max_steps=1000, kappa_fixed=-1.0, t_start_fs=0.0,
+                 te_floor_ev=1.0, coulomb_f=COULOMB_F, autotune=False, profile=False,
+                 torch_allocator=True, sigma0=None, eps0=None, mass=None):
+        import torch
+        from . import workloads as W
+        if not torch.cuda.is_available():
+            raise RuntimeError("IonisingMD needs a CUDA GPU (no CPU fallback)")
+        self.n = sample.n_atoms
+        self.R = sample.n_replicas
+        ns = len(atomic.z)
+        cfg = MDConfig()
+        cfg.dt_ps, cfg.r_cut = float(dt_ps), float(r_cut)
+        cfg.precision = MD_PREC_FP64 if precision == "fp64" else MD_PREC_MIXED
+        cfg.cr_enabled, cfg.plasma_mode, cfg.max_steps = int(bool(cr_enabled)), int(plasma_mode), int(max_steps)
+        cfg.kappa_fixed, cfg.t_start_fs, cfg.te_floor_ev = float(kappa_fixed), float(t_start_fs), float(te_floor_ev)
+        cfg.coulomb_f, cfg.photon_kev, cfg.n_species = float(coulomb_f), float(atomic.photon_kev), ns
+        mass = W.MASS if mass is None else mass
+        sigma0 = W.LJ_SIGMA0 if sigma0 is None else sigma0
+        eps0 = W.LJ_EPS0 if eps0 is None else eps0
+        for k in range(ns):
+            cfg.z[k] = int(atomic.z[k]); cfg.mass[k] = float(mass[k])
+            cfg.lj_sigma0[k] = float(sigma0[k]); cfg.lj_eps0[k] = float(eps0[k])
+            cfg.tau_auger_ps[k] = float(atomic.tau_auger_ps[k])
+        self._keep = [_c(atomic.sigma_pi, np.float64), _c(atomic.k_ci, np.float64), _c(atomic.k_rec, np.float64),
+                      _c(atomic.ip_mev, np.int64), _c(atomic.e_pi_mev, np.int64), _c(atomic.e_auger_mev, np.int64)]
+        (cfg.sigma_pi, cfg.k_ci, cfg.k_rec, cfg.ip_mev, cfg.e_pi_mev,
+         cfg.e_auger_mev) = [a.ctypes.data for a in self._keep]
+        cfg.n_te, cfg.dte_ev = int(atomic.n_te), float(atomic.dte_ev)
+        self._alloc = TorchAllocator() if torch_allocator else None
+        if self._alloc is not None:
+            cfg.dev_alloc, cfg.dev_free = self._alloc.alloc_fn, self._alloc.free_fn
+        cfg.autotune, cfg.profile = int(bool(autotune)), int(bool(profile))
+        s = sample
+        arrs = [_c(s.x, np.float64), _c(s.v, np.float64), _c(s.species, np.uint8), _c(s.fragment, np.int32),
+                _c(s.q0, np.uint8), _c(s.replica_offset, np.int32), _c(s.seed, np.uint64),
+                _c(s.box, np.float64), _c(s.volume, np.float64)]
+        sysd = MDSystem(self.n, *[a.ctypes.data for a in arrs[:5]], self.R, *[a.ctypes.data for a in arrs[5:]])
+        self.config = cfg
+        self.stream = torch.cuda.current_stream().cuda_stream
+        self.h = md_init(cfg, sysd)
+        md_set_stream(self.h, self.stream)
+
+    # pass-throughs ---------------------------------------------------------
+    def set_pulse(self, pulses, replica=-1):
+        md_set_pulse(self.h, replica, pulses)
+
+    def set_pulse_table(self, dF, replica=-1):
+        md_set_pulse_table(self.h, replica, dF)
+
+    def set_plasma_table(self, ne, te_ev, replica=-1):
+        md_set_plasma_table(self.h, replica, ne, te_ev)
+
+    def step(self, n=1):
+        md_step(self.h, n)
+
+    def get_state(self, fields=MD_FIELD_ALL, out=None):
+        o = out or {}
+        n, R = self.n, self.R
+        spec = [("x", MD_FIELD_X, (n, 3), np.float64), ("v", MD_FIELD_V, (n, 3), np.float64),
+                ("f", MD_FIELD_F, (n, 3), np.float64), ("q", MD_FIELD_Q, (n,), np.uint8),
+                ("h", MD_FIELD_H, (n,), np.uint8), ("n_e", MD_FIELD_PLASMA, (R,), np.int64),
+                ("e_gas_mev", MD_FIELD_PLASMA, (R,), np.int64), ("te_ev", MD_FIELD_PLASMA, (R,), np.float64),
+                ("kappa", MD_FIELD_PLASMA, (R,), np.float64),
+                ("event_counts", MD_FIELD_COUNTS, (R, 4), np.int64)]
+        st = MDState()
+        for name, bit, shape, dt in spec:
+            if fields & bit:
+                if name not in o:
+                    o[name] = np.empty(shape, dtype=dt)
+                setattr(st, name, o[name].ctypes.data)
+        md_get_state(self.h, st, fields)
+        if fields & MD_FIELD_STEP:
+            o["step"] = int(st.step)
+        return o
+
+    def set_state(self, fields, **arrays):
+        st = MDState()
+        keep = []
+        for name, dt in [("x", np.float64), ("v", np.float64), ("q", np.uint8), ("h", np.uint8),
+                         ("n_e", np.int64), ("e_gas_mev", np.int64), ("event_counts", np.int64)]:
+            if name in arrays and arrays[name] is not None:
+                a = _c(arrays[name], dt)
+                keep.append(a)
+                setattr(st, name, a.ctypes.data)
+        st.step = int(arrays.get("step", 0))
+        md_set_state(self.h, st, fields)
+
+    def energies(self):
+        ek = np.zeros(self.R); ep = np.zeros(self.R)
+        n = md_get_energies(self.h, ek, ep)
+        return ek, ep, n
+
+    def timing(self):
+        return md_get_timing(self.h)
+
+    def reset_timing(self):
+        md_reset_timing(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            md_finalize(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

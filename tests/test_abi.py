@@ -1,0 +1,98 @@
+"""The C-ABI library without a GPU: it builds, loads, exports every function
+include/md.h declares, and its ctypes mirror has the C struct layout.  The
+one host-only entry point (md_pulse_table) is compared with the oracle."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2401_03180_gb300 import build as B
+from paper_2401_03180_gb300 import md as M
+from paper_2401_03180_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "md.h")
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    return B.build()
+
+
+def _declared():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:md_status|void|const char\*)\s+(md_\w+)\s*\(", text, re.M)))
+
+
+def test_exports_every_declared_symbol(libpath):
+    names = _declared()
+    assert len(names) >= 15
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (md_\w+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    lib = ctypes.CDLL(libpath)
+    for n in names:
+        assert hasattr(lib, n)
+    assert M.md_version().startswith("gb300")
+
+
+def test_struct_layout_matches_c(tmp_path):
+    src = tmp_path / "layout.c"
+    fields = {
+        "md_config": [f[0] for f in M.MDConfig._fields_],
+        "md_system": [f[0] for f in M.MDSystem._fields_],
+        "md_pulse": [f[0] for f in M.MDPulse._fields_],
+        "md_state": [f[0] for f in M.MDState._fields_],
+        "md_timing": [f[0] for f in M.MDTiming._fields_],
+    }
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void){"]
+    for st, fs in fields.items():
+        lines.append(f'printf("{st} %zu\\n", sizeof({st}));')
+        for f in fs:
+            lines.append(f'printf("{st}.{f} %zu\\n", offsetof({st}, {f}));')
+    lines.append("return 0;}")
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-o", str(exe), str(src)])
+    got = dict(l.split() for l in subprocess.check_output([str(exe)], text=True).splitlines())
+    pys = {"md_config": M.MDConfig, "md_system": M.MDSystem, "md_pulse": M.MDPulse,
+           "md_state": M.MDState, "md_timing": M.MDTiming}
+    for st, cls in pys.items():
+        assert int(got[st]) == ctypes.sizeof(cls), st
+        for f in fields[st]:
+            assert int(got[f"{st}.{f}"]) == getattr(cls, f).offset, (st, f)
+
+
+def test_host_pulse_table_bit_exact_vs_oracle(libpath, oracle_mod):
+    cases = [
+        ([W.Pulse(8.0, 10.0, 1e12, 0.0)], -10.0, 400),
+        ([W.Pulse(6.0, 25.0, 5e12, 0.0)], -25.0, 1000),
+        ([W.Pulse(9.0, 10.0, 1e13, 0.0), W.Pulse(9.0, 10.0, 1e13, 50.0)], -10.0, 1400),
+        ([W.Pulse(8.0, 15.0, 1e13, 3.0, W.FLAT_TOP)], -20.0, 900),
+        ([W.Pulse(8.0, 0.3, 2e12, 0.01)], -1.0, 60),
+    ]
+    for pulses, t0, n in cases:
+        a = M.md_pulse_table(pulses, t0, 0.05, n)
+        b = oracle_mod.pulse_table(pulses, t0, 0.05, n)
+        assert np.array_equal(a.view(np.uint64), b.view(np.uint64))
+
+
+def test_host_pulse_table_rejects_bad_input(libpath):
+    with pytest.raises(M.MDError) as e:
+        M.md_pulse_table([W.Pulse(8.0, -1.0, 1e12, 0.0)], 0.0, 0.05, 10)
+    assert e.value.status == M.MD_ERR_INVALID_ARG
+    with pytest.raises(M.MDError):
+        M.md_pulse_table([W.Pulse(8.0, 10.0, 1e12, 0.0)], 0.0, 0.0, 10)
+
+
+def test_binding_fails_loudly_without_gpu(libpath):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    wl = W.workload("c1_methane_1500", scale=0.02)
+    with pytest.raises(RuntimeError):
+        M.IonisingMD(wl.sample, W.atomic_data(8.0))
