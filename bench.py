@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="minimal run for ncu: default launch shape, W + K steps, no baselines")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     return ap.parse_args()
 
 
@@ -369,9 +372,33 @@ def run_reference(args, rank, world):
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_profile_case(args):
+    """Kernels launched: init 6 (step_a, 4 cell kernels, k_pair), then 6 per step."""
+    import torch
+    from paper_2401_03180_gb300 import build as B
+    from paper_2401_03180_gb300 import md as M
+    B.build()
+    wl, atom = make_workload(args.workload, args.scale, 0)
+    s = wl.sample
+    g = M.IonisingMD(s, atom, precision=args.precision, r_cut=1.2, max_steps=max(wl.n_steps, args.warmup + args.steps + 1),
+                     t_start_fs=wl.t_start_fs, autotune=False)
+    g.set_pulse(wl.pulses[0])
+    g.step(args.warmup)
+    g.step(args.steps)
+    torch.cuda.synchronize()
+    t = g.timing()
+    g.close()
+    return {"profile_case": args.workload, "n_atoms": s.n_atoms, "precision": args.precision,
+            "warmup": args.warmup, "steps": args.steps, "tile_warps": t.tile_warps,
+            "tile_blocks_per_sm": t.tile_blocks_per_sm}
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.profile_case:
+        print(json.dumps(run_profile_case(args)), flush=True)
+        return
     if args.impl == "reference":
         out = run_reference(args, rank, world)
     else:

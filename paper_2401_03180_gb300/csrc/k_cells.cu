@@ -11,8 +11,8 @@
 namespace mdg {
 
 constexpr int kScanThreads = 1024;
-constexpr int kSortWarps = 8;
-constexpr int kSortMax = 512;        // keys per cell kept in shared memory
+constexpr int kSortThreads = 1024;
+constexpr int kKdMax = 1024;         // atoms per cell ordered in shared memory
 
 __device__ __forceinline__ int cell_coord(double x, double origin, double inv_edge, int n)
 {
@@ -26,17 +26,30 @@ __device__ __forceinline__ unsigned spread3(unsigned v)   // 3 bits -> every thi
     return (v & 1u) | ((v & 2u) << 2) | ((v & 4u) << 4);
 }
 
+// Atoms are visited in the previous step's slot order, so neighbouring
+// threads mostly share a cell and one atomic per (warp, cell) suffices.
 __global__ void __launch_bounds__(256) k_cell_assign(Params p)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= p.n_atoms) return;
-    const Grid& g = p.grid[p.rep[i]];
-    const int cx = cell_coord(p.x[i], g.origin[0], g.inv_edge[0], g.dims[0]);
-    const int cy = cell_coord(p.y[i], g.origin[1], g.inv_edge[1], g.dims[1]);
-    const int cz = cell_coord(p.z[i], g.origin[2], g.inv_edge[2], g.dims[2]);
-    const int c = g.cell_off + cx + g.dims[0] * (cy + g.dims[1] * cz);
-    p.atom_cell[i] = c;
-    p.atom_rank[i] = atomicAdd(&p.cell_count[c], 1);
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int i = s < p.counters[1] ? p.atom_of[s] : -1;
+    int c = -1;
+    if (i >= 0) {
+        const Grid& g = p.grid[p.rep[i]];
+        const int cx = cell_coord(p.x[i], g.origin[0], g.inv_edge[0], g.dims[0]);
+        const int cy = cell_coord(p.y[i], g.origin[1], g.inv_edge[1], g.dims[1]);
+        const int cz = cell_coord(p.z[i], g.origin[2], g.inv_edge[2], g.dims[2]);
+        c = g.cell_off + cx + g.dims[0] * (cy + g.dims[1] * cz);
+    }
+    const unsigned grp = __match_any_sync(0xffffffffu, c);
+    const int leader = __ffs(grp) - 1;
+    int base = 0;
+    if (c >= 0 && lane == leader) base = atomicAdd(&p.cell_count[c], __popc(grp));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (c >= 0) {
+        p.atom_cell[i] = c;
+        p.atom_rank[i] = base + __popc(grp & ((1u << lane) - 1u));
+    }
 }
 
 // Single-CTA scan over all cells: unpadded starts, padded starts, and the
@@ -119,20 +132,45 @@ __global__ void __launch_bounds__(256) k_cell_scatter(Params p)
     p.tmp_key[p.cell_start[c] + p.atom_rank[i]] = ((unsigned long long)key << 32) | (unsigned)i;
 }
 
-// One warp per cell: rank sort of the cell's keys, pack, bounding boxes.
-__global__ void __launch_bounds__(kSortWarps * 32) k_cell_sort_pack(Params p)
+// Segment of position e at bisection level `level` for a cell of n atoms:
+// every segment longer than one cluster splits into a left part of
+// ceil(len/16)*8 atoms (a whole number of clusters) and the rest.
+__device__ __forceinline__ void kd_segment(int n, int level, int e, int& s, int& len)
 {
-    __shared__ unsigned long long s_key[kSortWarps][kSortMax];
+    s = 0;
+    len = n;
+    for (int l = 0; l < level && len > kClusterSize; ++l) {
+        const int left = (len + 2 * kClusterSize - 1) / (2 * kClusterSize) * kClusterSize;
+        if (e < s + left) len = left;
+        else { s += left; len -= left; }
+    }
+}
+
+__device__ __forceinline__ int kd_levels(int n)
+{
+    int l = 0;
+    for (int len = n; len > kClusterSize; len = (len + 2 * kClusterSize - 1) / (2 * kClusterSize) * kClusterSize) ++l;
+    return l;
+}
+
+// One CTA per cell.  Atoms are ordered by recursive bisection (split each
+// segment at a multiple of 8 along an axis that cycles through the cell's
+// edges, longest first; ties broken by atom index) so that every run of 8
+// slots is a compact, near-cubic cluster; then the packed arrays and the
+// cluster bounding boxes are written.  Cells with
+// more than kKdMax atoms fall back to a rank sort on (Morton sub-cell, atom).
+__global__ void __launch_bounds__(kSortThreads) k_cell_sort_pack(Params p)
+{
+    __shared__ int s_idx[2][kKdMax];
+    __shared__ float s_pos[2][3][kKdMax];
     if (*p.err & ERR_CELL) return;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n_warps = gridDim.x * kSortWarps;
-    for (int c = blockIdx.x * kSortWarps + warp; c < p.cell_cap_total; c += n_warps) {
+    const int tid = threadIdx.x;
+    for (int c = blockIdx.x; c < p.cell_cap_total; c += gridDim.x) {
         const int b = p.cell_start[c];
         const int n = p.cell_start[c + 1] - b;
         const int ps = p.cell_pstart[c];
         const int npad = p.cell_pstart[c + 1] - ps;
-        if (npad == 0) continue;
-        // which replica / grid cell is this
+        if (npad == 0) continue;                      // uniform across the CTA
         int rr = 0;
         {
             // replicas own contiguous cell ranges; search by cell offset
@@ -151,28 +189,82 @@ __global__ void __launch_bounds__(kSortWarps * 32) k_cell_sort_pack(Params p)
         const double cen[3] = {g.origin[0] + (cx + 0.5) * g.edge[0],
                                g.origin[1] + (cy + 0.5) * g.edge[1],
                                g.origin[2] + (cz + 0.5) * g.edge[2]};
-        const bool in_smem = n <= kSortMax;
-        const unsigned long long* keys = in_smem ? s_key[warp] : p.tmp_key + b;
-        if (in_smem)
-            for (int e = lane; e < n; e += 32) s_key[warp][e] = p.tmp_key[b + e];
-        __syncwarp();
-        for (int e = lane; e < n; e += 32) {
-            const unsigned long long ke = keys[e];
-            int rank = 0;
-            for (int f = 0; f < n; ++f) rank += keys[f] < ke;
-            const int i = (int)(ke & 0xffffffffu);
-            const int slot = ps + rank;
+        int cur = 0;
+        if (n <= kKdMax) {
+            for (int e = tid; e < n; e += kSortThreads) {
+                const int i = (int)(p.tmp_key[b + e] & 0xffffffffu);
+                s_idx[0][e] = i;
+                s_pos[0][0][e] = (float)(p.x[i] - cen[0]);
+                s_pos[0][1][e] = (float)(p.y[i] - cen[1]);
+                s_pos[0][2][e] = (float)(p.z[i] - cen[2]);
+            }
+            __syncthreads();
+            // split axes cycle through the cell's edges, longest first
+            int a0 = 0, a1 = 1, a2 = 2;
+            if (g.edge[a1] > g.edge[a0]) { const int t = a0; a0 = a1; a1 = t; }
+            if (g.edge[a2] > g.edge[a1]) { const int t = a1; a1 = a2; a2 = t; }
+            if (g.edge[a1] > g.edge[a0]) { const int t = a0; a0 = a1; a1 = t; }
+            // tpe threads share the rank count of one element
+            int tpe = 1;
+            while (tpe < 8 && 2 * tpe * n <= kSortThreads) tpe *= 2;
+            const int per_pass = kSortThreads / tpe;
+            const int sub = tid & (tpe - 1);
+            const int levels = kd_levels(n);
+            for (int level = 0; level < levels; ++level) {
+                const int lm = level % 3;
+                const int ax = lm == 0 ? a0 : (lm == 1 ? a1 : a2);
+                const float* pa = s_pos[cur][ax];
+                const int* ia = s_idx[cur];
+                for (int base = 0; base < n; base += per_pass) {
+                    const int e = base + tid / tpe;
+                    int s0 = 0, len = 0, rank = 0;
+                    if (e < n) {
+                        kd_segment(n, level, e, s0, len);
+                        if (len > kClusterSize) {
+                            const float ve = pa[e];
+                            const int ie = ia[e];
+                            for (int f = s0 + sub; f < s0 + len; f += tpe) {
+                                const float vf = pa[f];
+                                rank += (vf < ve) || (vf == ve && ia[f] < ie);
+                            }
+                        }
+                    }
+                    for (int o = 1; o < tpe; o <<= 1) rank += __shfl_xor_sync(0xffffffffu, rank, o);
+                    if (e < n && sub == 0) {
+                        const int dst = len > kClusterSize ? s0 + rank : e;
+                        s_idx[cur ^ 1][dst] = ia[e];
+                        s_pos[cur ^ 1][0][dst] = s_pos[cur][0][e];
+                        s_pos[cur ^ 1][1][dst] = s_pos[cur][1][e];
+                        s_pos[cur ^ 1][2][dst] = s_pos[cur][2][e];
+                    }
+                }
+                __syncthreads();
+                cur ^= 1;
+            }
+        }
+        for (int e = tid; e < n; e += kSortThreads) {
+            int i, pos = e;
+            if (n <= kKdMax) {
+                i = s_idx[cur][e];
+            } else {   // fallback: rank by (Morton sub-cell, atom index) in global memory
+                const unsigned long long ke = p.tmp_key[b + e];
+                int rank = 0;
+                for (int f = 0; f < n; ++f) rank += p.tmp_key[b + f] < ke;
+                i = (int)(ke & 0xffffffffu);
+                pos = rank;
+            }
+            const int slot = ps + pos;
             p.atom_of[slot] = i;
             p.slot_of[i] = slot;
-            const int s = p.species[i];
+            const int sp = p.species[i];
             const int qi = p.q[i];
             const double dx = p.x[i] - cen[0], dy = p.y[i] - cen[1], dz = p.z[i] - cen[2];
             if (p.precision == 0) p.xq[slot] = make_float4((float)dx, (float)dy, (float)dz, (float)qi);
             else p.xq64[slot] = make_double4_32a(dx, dy, dz, (double)qi);
-            p.tf[slot] = make_int2(p.ts_off[s] + qi, p.frag[i]);
+            p.tf[slot] = make_int2(p.ts_off[sp] + qi, p.frag[i]);
             p.fx[slot] = 0; p.fy[slot] = 0; p.fz[slot] = 0; p.epot[slot] = 0;
         }
-        for (int e = n + lane; e < npad; e += 32) {     // padding: far away, no charge
+        for (int e = n + tid; e < npad; e += kSortThreads) {     // padding: far away, no charge
             const int slot = ps + e;
             const double far = 1.0e6 + 1024.0 * (double)slot;
             p.atom_of[slot] = -1;
@@ -181,46 +273,45 @@ __global__ void __launch_bounds__(kSortWarps * 32) k_cell_sort_pack(Params p)
             p.tf[slot] = make_int2(0, -1 - slot);
             p.fx[slot] = 0; p.fy[slot] = 0; p.fz[slot] = 0; p.epot[slot] = 0;
         }
-        __syncwarp();
-        __threadfence_block();
+        __syncthreads();
         // cluster bounding boxes (real atoms only) and fragment ranges
         const int ncl = npad / kClusterSize;
-        for (int k = lane; k < ncl; k += 32) {
-            float lo[3] = {3.0e38f, 3.0e38f, 3.0e38f}, hi[3] = {-3.0e38f, -3.0e38f, -3.0e38f};
+        for (int k = tid; k < ncl; k += kSortThreads) {
+            float lx = 3.0e38f, ly = 3.0e38f, lz = 3.0e38f, hx = -3.0e38f, hy = -3.0e38f, hz = -3.0e38f;
             int fmin = 0x7fffffff, fmax = (int)0x80000000;
             for (int a = 0; a < kClusterSize; ++a) {
                 const int slot = ps + k * kClusterSize + a;
                 if (a + k * kClusterSize >= n) break;
-                float v[3];
+                float vx, vy, vz;
                 if (p.precision == 0) {
                     const float4 t = p.xq[slot];
-                    v[0] = t.x; v[1] = t.y; v[2] = t.z;
+                    vx = t.x; vy = t.y; vz = t.z;
                 } else {
                     const double4_32a t = p.xq64[slot];
-                    v[0] = (float)t.x; v[1] = (float)t.y; v[2] = (float)t.z;
+                    vx = (float)t.x; vy = (float)t.y; vz = (float)t.z;
                 }
-                for (int d = 0; d < 3; ++d) {
-                    lo[d] = fminf(lo[d], v[d]);
-                    hi[d] = fmaxf(hi[d], v[d]);
-                }
+                lx = fminf(lx, vx); hx = fmaxf(hx, vx);
+                ly = fminf(ly, vy); hy = fmaxf(hy, vy);
+                lz = fminf(lz, vz); hz = fmaxf(hz, vz);
                 const int fr = p.tf[slot].y;
                 fmin = min(fmin, fr);
                 fmax = max(fmax, fr);
             }
             const int cl = ps / kClusterSize + k;
-            p.bb_lo[cl] = make_float4(lo[0], lo[1], lo[2], 0.0f);
-            p.bb_hi[cl] = make_float4(hi[0], hi[1], hi[2], 0.0f);
+            p.bb_lo[cl] = make_float4(lx, ly, lz, 0.0f);
+            p.bb_hi[cl] = make_float4(hx, hy, hz, 0.0f);
             p.bb_frag[cl] = make_int2(fmin, fmax);
         }
+        __syncthreads();
     }
 }
 
 void launch_cells(const Params& p, cudaStream_t s, int grid_atoms, int grid_cells)
 {
-    k_cell_assign<<<grid_atoms, 256, 0, s>>>(p);
+    k_cell_assign<<<(p.slot_cap + 255) / 256, 256, 0, s>>>(p);
     k_cell_scan<<<1, kScanThreads, 0, s>>>(p);
     k_cell_scatter<<<grid_atoms, 256, 0, s>>>(p);
-    k_cell_sort_pack<<<grid_cells, kSortWarps * 32, 0, s>>>(p);
+    k_cell_sort_pack<<<grid_cells, kSortThreads, 0, s>>>(p);
 }
 
 }  // namespace mdg

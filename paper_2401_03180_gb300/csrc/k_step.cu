@@ -12,6 +12,7 @@
 namespace mdg {
 
 constexpr int kAccCopies = 16;   // accumulator copies per replica (spread contention)
+constexpr int kStepThreads = 128;
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11): 10 rounds, multipliers M0, M1 on
@@ -101,20 +102,15 @@ __device__ void plasma_scalars(const Params& p, int r, long long step, RepState&
     st.kappa_f = (float)kf;
 }
 
-__device__ void make_grid(const Params& p, int r, const RepAccum* acc)
+__device__ void make_grid(const Params& p, int r, const unsigned long long* mn,
+                          const unsigned long long* mx)
 {
     Grid& g = p.grid[r];
     if (g.periodic) return;   // periodic grids are fixed at init
     double lo[3], hi[3];
     for (int d = 0; d < 3; ++d) {
-        unsigned long long mn = ~0ull, mx = 0ull;
-        for (int c = 0; c < kAccCopies; ++c) {
-            unsigned long long a = acc[c].bmin[d], b = acc[c].bmax[d];
-            mn = a < mn ? a : mn;
-            mx = b > mx ? b : mx;
-        }
-        lo[d] = mn == ~0ull ? 0.0 : from_ordered(mn);
-        hi[d] = mx == 0ull ? 0.0 : from_ordered(mx);
+        lo[d] = mn[d] == ~0ull ? 0.0 : from_ordered(mn[d]);
+        hi[d] = mx[d] == 0ull ? 0.0 : from_ordered(mx[d]);
         if (!(hi[d] >= lo[d])) { lo[d] = 0.0; hi[d] = 0.0; }
     }
     double f = 1.0;
@@ -140,10 +136,30 @@ __device__ void make_grid(const Params& p, int r, const RepAccum* acc)
     }
 }
 
+// Velocity increment of a half kick, (dt/2m) F.  The mixed path forms it in
+// FP32 (it is ~1e-4 of v, so its rounding is far below the FP32 force error);
+// the FP64 path in FP64.  Every kernel that applies or reports a half kick
+// uses this function, so stepping and state read-out round identically.
+__device__ __forceinline__ void half_kick(const Params& p, int s, int slot, double& ax, double& ay,
+                                          double& az)
+{
+    const double c = p.hdtm[s];
+    if (p.precision == 0) {
+        const float cf = (float)(c * kFixInv);
+        ax = (double)(cf * (float)p.fx[slot]);
+        ay = (double)(cf * (float)p.fy[slot]);
+        az = (double)(cf * (float)p.fz[slot]);
+    } else {
+        ax = c * ((double)p.fx[slot] * kFixInv);
+        ay = c * ((double)p.fy[slot] * kFixInv);
+        az = c * ((double)p.fz[slot] * kFixInv);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // k_step_a: one thread per atom (original order).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_step_a(Params p, int mode)
+__global__ void __launch_bounds__(kStepThreads) k_step_a(Params p, int mode)
 {
     __shared__ long long s_acc[kRepWindow][6];
     __shared__ unsigned long long s_bmin[kRepWindow][3], s_bmax[kRepWindow][3];
@@ -171,27 +187,29 @@ __global__ void __launch_bounds__(256) k_step_a(Params p, int mode)
         const int s = p.species[i];
         double x = p.x[i], y = p.y[i], z = p.z[i];
         if (mode & STEP_KICK_DRIFT) {
-            const int slot = p.slot_of[i];
-            const double c = kick_full ? 2.0 * p.hdtm[s] : p.hdtm[s];
-            double vx = p.vx[i] + c * ((double)p.fx[slot] * kFixInv);
-            double vy = p.vy[i] + c * ((double)p.fy[slot] * kFixInv);
-            double vz = p.vz[i] + c * ((double)p.fz[slot] * kFixInv);
+            // the state holds v_{n-1/2} once stepping has started: finish the
+            // previous step's half kick, then this step's (two separate adds,
+            // exactly as velocity Verlet rounds them)
+            double ax, ay, az;
+            half_kick(p, s, p.slot_of[i], ax, ay, az);
+            double vx = p.vx[i], vy = p.vy[i], vz = p.vz[i];
+            if (kick_full) { vx = vx + ax; vy = vy + ay; vz = vz + az; }
+            vx = vx + ax; vy = vy + ay; vz = vz + az;
             x += p.dt * vx;
             y += p.dt * vy;
             z += p.dt * vz;
             const Grid& g = p.grid[r];
             if (g.periodic) {
+                // wrap only atoms that left the box (FP64 division is slow)
                 const double L0 = g.box[0], L1 = g.box[1], L2 = g.box[2];
-                x -= L0 * floor(x / L0);
-                y -= L1 * floor(y / L1);
-                z -= L2 * floor(z / L2);
-                // floor rounding may leave x == L; fold back to 0
-                if (x >= L0) x -= L0;
-                if (y >= L1) y -= L1;
-                if (z >= L2) z -= L2;
+                if (x < 0.0 || x >= L0) { x -= L0 * floor(x / L0); if (x >= L0) x -= L0; }
+                if (y < 0.0 || y >= L1) { y -= L1 * floor(y / L1); if (y >= L1) y -= L1; }
+                if (z < 0.0 || z >= L2) { z -= L2 * floor(z / L2); if (z >= L2) z -= L2; }
             }
-            if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(vx) && isfinite(vy) &&
-                  isfinite(vz)))
+            // finite check on the exponent bits (integer ops; FP64 compares are slow here)
+            if (((__double2hiint(x) & 0x7ff00000) == 0x7ff00000) || ((__double2hiint(y) & 0x7ff00000) == 0x7ff00000) ||
+                ((__double2hiint(z) & 0x7ff00000) == 0x7ff00000) || ((__double2hiint(vx) & 0x7ff00000) == 0x7ff00000) ||
+                ((__double2hiint(vy) & 0x7ff00000) == 0x7ff00000) || ((__double2hiint(vz) & 0x7ff00000) == 0x7ff00000))
                 atomicOr(p.err, ERR_NONFINITE);
             p.vx[i] = vx; p.vy[i] = vy; p.vz[i] = vz;
             p.x[i] = x; p.y[i] = y; p.z[i] = z;
@@ -351,36 +369,46 @@ __global__ void __launch_bounds__(256) k_step_a(Params p, int mode)
     if (!s_last) return;
     __threadfence();
     const long long next = (mode & STEP_ADVANCE) ? step + 1 : step;
-    for (int rr = tid; rr < p.n_rep; rr += blockDim.x) {
+    const int warp = tid >> 5, n_warps = blockDim.x >> 5;
+    for (int rr = warp; rr < p.n_rep; rr += n_warps) {
+        // lane c reads accumulator copy c, then the warp reduces
         RepAccum* a = p.acc + (size_t)rr * kAccCopies;
-        RepState st = p.rs[rr];
-        long long dNe = 0, dE = 0, cnt[4] = {0, 0, 0, 0};
-        for (int c = 0; c < kAccCopies; ++c) {
-            dNe += __ldcg(&a[c].dNe);
-            dE += __ldcg(&a[c].dE);
-            for (int k = 0; k < 4; ++k) cnt[k] += __ldcg(&a[c].counts[k]);
+        long long v[6] = {0, 0, 0, 0, 0, 0};
+        unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0ull, 0ull, 0ull};
+        if (lane < kAccCopies) {
+            v[0] = __ldcg(&a[lane].dNe);
+            v[1] = __ldcg(&a[lane].dE);
+            for (int k = 0; k < 4; ++k) v[2 + k] = __ldcg(&a[lane].counts[k]);
+            for (int d = 0; d < 3; ++d) {
+                mn[d] = __ldcg(&a[lane].bmin[d]);
+                mx[d] = __ldcg(&a[lane].bmax[d]);
+            }
+            a[lane].dNe = 0;
+            a[lane].dE = 0;
+            for (int k = 0; k < 4; ++k) a[lane].counts[k] = 0;
+            for (int d = 0; d < 3; ++d) {
+                a[lane].bmin[d] = ~0ull;
+                a[lane].bmax[d] = 0ull;
+            }
         }
-        st.n_e += dNe;
-        st.e_gas += dE;
-        if (st.e_gas < 0) st.e_gas = 0;
-        for (int k = 0; k < 4; ++k) st.counts[k] += cnt[k];
-        plasma_scalars(p, rr, next, st);
-        p.rs[rr] = st;
-        RepAccum bb[kAccCopies];
-        for (int c = 0; c < kAccCopies; ++c)
+        for (int o = 16; o; o >>= 1) {
+            for (int k = 0; k < 6; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
             for (int d = 0; d < 3; ++d) {
-                bb[c].bmin[d] = __ldcg(&a[c].bmin[d]);
-                bb[c].bmax[d] = __ldcg(&a[c].bmax[d]);
+                const unsigned long long x = __shfl_xor_sync(0xffffffffu, mn[d], o);
+                const unsigned long long y = __shfl_xor_sync(0xffffffffu, mx[d], o);
+                mn[d] = x < mn[d] ? x : mn[d];
+                mx[d] = y > mx[d] ? y : mx[d];
             }
-        make_grid(p, rr, bb);
-        for (int c = 0; c < kAccCopies; ++c) {
-            a[c].dNe = 0;
-            a[c].dE = 0;
-            for (int k = 0; k < 4; ++k) a[c].counts[k] = 0;
-            for (int d = 0; d < 3; ++d) {
-                a[c].bmin[d] = ~0ull;
-                a[c].bmax[d] = 0ull;
-            }
+        }
+        if (lane == 0) {
+            RepState st = p.rs[rr];
+            st.n_e += v[0];
+            st.e_gas += v[1];
+            if (st.e_gas < 0) st.e_gas = 0;
+            for (int k = 0; k < 4; ++k) st.counts[k] += v[2 + k];
+            plasma_scalars(p, rr, next, st);
+            p.rs[rr] = st;
+            make_grid(p, rr, mn, mx);
         }
     }
     if (tid == 0) {
@@ -392,7 +420,8 @@ __global__ void __launch_bounds__(256) k_step_a(Params p, int mode)
 
 void launch_step_a(const Params& p, int mode, cudaStream_t s, int grid_atoms)
 {
-    k_step_a<<<grid_atoms, 256, 0, s>>>(p, mode);
+    (void)grid_atoms;
+    k_step_a<<<(p.n_atoms + kStepThreads - 1) / kStepThreads, kStepThreads, 0, s>>>(p, mode);
 }
 
 // ---------------------------------------------------------------------------
@@ -406,11 +435,9 @@ __global__ void k_velocity_out(Params p, double* out)
     const int full = *p.kick_full;
     double vx = p.vx[i], vy = p.vy[i], vz = p.vz[i];
     if (full) {
-        const int slot = p.slot_of[i];
-        const double c = p.hdtm[p.species[i]];
-        vx += c * ((double)p.fx[slot] * kFixInv);
-        vy += c * ((double)p.fy[slot] * kFixInv);
-        vz += c * ((double)p.fz[slot] * kFixInv);
+        double ax, ay, az;
+        half_kick(p, p.species[i], p.slot_of[i], ax, ay, az);
+        vx = vx + ax; vy = vy + ay; vz = vz + az;
     }
     out[3 * i + 0] = vx;
     out[3 * i + 1] = vy;
@@ -442,10 +469,9 @@ __global__ void k_energy(Params p, double* ekin, long long* epot)
         const int s = p.species[i];
         double vx = p.vx[i], vy = p.vy[i], vz = p.vz[i];
         if (full) {
-            const double c = p.hdtm[s];
-            vx += c * ((double)p.fx[slot] * kFixInv);
-            vy += c * ((double)p.fy[slot] * kFixInv);
-            vz += c * ((double)p.fz[slot] * kFixInv);
+            double ax, ay, az;
+            half_kick(p, s, slot, ax, ay, az);
+            vx = vx + ax; vy = vy + ay; vz = vz + az;
         }
         k += 0.5 * p.mass[s] * (vx * vx + vy * vy + vz * vz);
         u += p.epot[slot];

@@ -143,9 +143,10 @@ void enqueue_step(md_handle* h, cudaStream_t s)
     int mode = STEP_KICK_DRIFT | STEP_ADVANCE | (h->cfg.cr_enabled ? STEP_CR : 0);
     launch_step_a(h->P, mode, s, h->grid_atoms);
     launch_cells(h->P, s, h->grid_atoms, h->grid_cells);
-    if (h->cfg.profile) cudaEventRecord(h->ev_pair0, s);
+    // external event nodes: the events are recorded on every graph replay
+    if (h->cfg.profile) cudaEventRecordWithFlags(h->ev_pair0, s, cudaEventRecordExternal);
     launch_pair(h->P, s, false, h->pair_blocks, h->pair_warps, h->pair_nsplit);
-    if (h->cfg.profile) cudaEventRecord(h->ev_pair1, s);
+    if (h->cfg.profile) cudaEventRecordWithFlags(h->ev_pair1, s, cudaEventRecordExternal);
 }
 
 md_status capture_graph(md_handle* h)
@@ -533,6 +534,13 @@ static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* 
         CU(cudaMemcpy(d_ljd, lj_d.data(), lj_d.size() * sizeof(double2), cudaMemcpyHostToDevice));
         CU(cudaMemset(P.cell_count, 0, C * sizeof(int)));
         CU(cudaMemset(P.counters, 0, 8 * sizeof(int)));
+        {
+            // the first cell assignment walks atoms in input order
+            std::vector<int> ident(P.slot_cap, -1);
+            for (int i = 0; i < N; ++i) ident[i] = i;
+            CU(cudaMemcpy(P.atom_of, ident.data(), P.slot_cap * sizeof(int), cudaMemcpyHostToDevice));
+            CU(cudaMemcpy(P.counters + 1, &N, sizeof(int), cudaMemcpyHostToDevice));
+        }
         CU(cudaMemset(P.err, 0, sizeof(unsigned)));
         CU(cudaMemset(P.step, 0, sizeof(long long)));
         CU(cudaMemset(P.kick_full, 0, sizeof(int)));
@@ -543,7 +551,7 @@ static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* 
         CU(cudaMemset(P.pair_count, 0, sizeof(long long)));
     }
     h->grid_atoms = (N + 255) / 256;
-    h->grid_cells = std::max(1, std::min((C + 7) / 8, h->n_sm * 16));
+    h->grid_cells = std::max(1, std::min(C, h->n_sm * 8));
     h->pair_warps = 8;
     h->pair_nsplit = 14;
     h->pair_blocks = h->n_sm * pair_max_blocks_per_sm(c.precision == MD_PREC_FP64, false, 8, nts);

