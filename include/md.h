@@ -237,7 +237,8 @@ md_status md_get_energies(md_handle* h, double* e_kin, double* e_pot, int64_t* n
 md_status md_get_timing(md_handle* h, md_timing* out);
 md_status md_reset_timing(md_handle* h);
 
-/* Last error message of the handle (or of the last failed md_init when h is NULL). */
+/* Last error message of the handle (or, when h is NULL, of the last failed
+ * md_init, md_pulse_table, md_philox or md_forces_noalloc on this thread). */
 const char* md_last_error(const md_handle* h);
 
 /* Release the handle and its device memory.  NULL is a no-op. */
@@ -253,6 +254,56 @@ md_status md_pulse_table(const md_pulse* p, int n_pulses, double t_start_fs, dou
  * device buffers d_ctr4/d_out (n blocks) and the given stream. */
 md_status md_philox(uint64_t seed, const uint32_t* d_ctr4, int64_t n, uint32_t* d_out,
                     void* cuda_stream);
+
+/*
+ * Allocation-free force evaluation (the paper has no counterpart; this is a
+ * convenience of the library).  For callers that cannot allocate device
+ * memory -- a plug-in inside a host program that owns the device memory
+ * budget, a memory-capped process, an inner loop that must keep the device
+ * footprint fixed -- it computes the screened Coulomb + screened LJ forces of
+ * one configuration using only a fixed scratch area compiled into the
+ * library (a file-scope __device__ array of about 5 MB, held by every GPU
+ * that loads the library until the process exits).  It calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *
+ * Limits: n_atoms <= MD_NOALLOC_MAX_ATOMS; a periodic box needs at most
+ * MD_NOALLOC_MAX_CELLS cells of edge >= r_cut; larger inputs are rejected
+ * with MD_ERR_INVALID_ARG (message in md_last_error(NULL)).
+ * Inputs: device pointers d_x [3n] AoS positions (nm), d_species [n],
+ * d_q [n] charges, d_fragment [n] (LJ excluded within a fragment); the screening
+ * kappa = 1/lambda_D (nm^-1, 0 = bare Coulomb) and the species tables on the host.
+ * species[i] < n_species and q[i] <= z[species[i]] are preconditions (the
+ * device arrays are not inspected on the host).
+ * Output: d_f [3n] AoS forces (kJ/mol/nm), device memory owned by the caller.
+ * The result equals md_init (same sample, kappa_fixed = kappa, charges
+ * frozen) followed by md_get_state(MD_FIELD_F).
+ * The first call on a device looks up the scratch area's device address
+ * (once per device, with that device current); make that first call before
+ * any stream capture.  All calls share the one scratch area, which keeps the
+ * last call's contents: every call resets what must start at zero, and calls
+ * that overlap on the GPU (different streams or threads) race -- serialise
+ * them.  The call is synchronous with respect to `cuda_stream` (it reads a
+ * 4-byte status back).
+ */
+#define MD_NOALLOC_MAX_ATOMS 16384
+#define MD_NOALLOC_MAX_CELLS 4096
+typedef struct md_forces_input {
+    int n_atoms;
+    const double* d_x;
+    const uint8_t* d_species;
+    const uint8_t* d_q;
+    const int32_t* d_fragment;
+    double box[3];               /* periodic box (all zero: vacuum)          */
+    double kappa;
+    double r_cut;
+    double coulomb_f;
+    int precision;               /* MD_PREC_MIXED or MD_PREC_FP64            */
+    int n_species;
+    int z[MD_MAX_SPECIES];
+    double lj_sigma0[MD_MAX_SPECIES];
+    double lj_eps0[MD_MAX_SPECIES];
+} md_forces_input;
+md_status md_forces_noalloc(const md_forces_input* in, double* d_f, void* cuda_stream);
 
 /* Library version string. */
 const char* md_version(void);

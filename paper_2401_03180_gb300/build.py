@@ -25,6 +25,7 @@ SOURCES = {
     "k_step.cu": ["-fmad=false"],
     "k_cells.cu": [],
     "k_pair.cu": [],
+    "md_noalloc.cu": [],
 }
 
 

@@ -270,6 +270,8 @@ md_status validate(const md_config* c, const md_system* s)
 
 }  // namespace
 
+void mdg::set_global_error(const std::string& msg) { g_init_error = msg; }
+
 // ============================================================================
 // C ABI
 // ============================================================================

@@ -3,6 +3,8 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
+
 #include <cuda_runtime.h>
 
 namespace mdg {
@@ -178,6 +180,8 @@ void launch_philox(unsigned long long seed, const uint32_t* ctr, long long n, ui
                    cudaStream_t s);
 void launch_force_out(const Params& p, double* d_f_out, cudaStream_t s);
 int pair_max_blocks_per_sm(bool fp64, bool energy, int warps, int n_ts);
+// message returned by md_last_error(NULL) (host side)
+void set_global_error(const std::string& msg);
 
 // modes of launch_step_a
 enum : int {

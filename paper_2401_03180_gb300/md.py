@@ -24,6 +24,7 @@ MD_PLASMA_BOOKKEEPING, MD_PLASMA_PRESCRIBED = 0, 1
 MD_FIELD_X, MD_FIELD_V, MD_FIELD_F, MD_FIELD_Q, MD_FIELD_H = 1, 2, 4, 8, 16
 MD_FIELD_PLASMA, MD_FIELD_COUNTS, MD_FIELD_STEP, MD_FIELD_ALL = 32, 64, 128, 255
 MD_MAX_SPECIES = 8
+MD_NOALLOC_MAX_ATOMS = 16384
 COULOMB_F = 138.935458
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -69,6 +70,14 @@ class MDTiming(C.Structure):
                 ("pair_count_last", C.c_int64), ("tile_warps", C.c_int), ("tile_blocks_per_sm", C.c_int)]
 
 
+class MDForcesInput(C.Structure):
+    _fields_ = [("n_atoms", C.c_int), ("d_x", C.c_void_p), ("d_species", C.c_void_p), ("d_q", C.c_void_p),
+                ("d_fragment", C.c_void_p), ("box", C.c_double * 3), ("kappa", C.c_double),
+                ("r_cut", C.c_double), ("coulomb_f", C.c_double), ("precision", C.c_int),
+                ("n_species", C.c_int), ("z", C.c_int * _S), ("lj_sigma0", C.c_double * _S),
+                ("lj_eps0", C.c_double * _S)]
+
+
 class MDError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"md status {status}: {msg}")
@@ -112,6 +121,7 @@ def lib():
             L.md_finalize.restype = None
             L.md_pulse_table.argtypes = [C.POINTER(MDPulse), C.c_int, C.c_double, C.c_double, C.c_int, P]
             L.md_philox.argtypes = [C.c_uint64, P, C.c_int64, P, P]
+            L.md_forces_noalloc.argtypes = [C.POINTER(MDForcesInput), P, P]
             L.md_version.restype = C.c_char_p
             _lib = L
     return _lib
@@ -217,6 +227,12 @@ def md_pulse_table(pulses, t_start_fs: float, dt_fs: float, n_steps: int) -> np.
 def md_philox(seed: int, d_ctr4_ptr: int, n: int, d_out_ptr: int, stream_ptr: int = 0):
     _check(lib().md_philox(C.c_uint64(seed), C.c_void_p(d_ctr4_ptr), C.c_int64(n), C.c_void_p(d_out_ptr),
                            C.c_void_p(stream_ptr)))
+
+
+def md_forces_noalloc(inp: MDForcesInput, d_f_ptr: int, stream_ptr: int = 0):
+    """Forces of one configuration from device buffers, with no device
+    allocation inside the library (fixed scratch compiled into it)."""
+    _check(lib().md_forces_noalloc(C.byref(inp), C.c_void_p(d_f_ptr), C.c_void_p(stream_ptr)))
 
 
 def md_version() -> str:

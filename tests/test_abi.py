@@ -38,6 +38,8 @@ def test_exports_every_declared_symbol(libpath):
     for n in names:
         assert hasattr(lib, n)
     assert M.md_version().startswith("gb300")
+    hdr = open(HEADER).read()
+    assert int(re.search(r"#define MD_NOALLOC_MAX_ATOMS (\d+)", hdr).group(1)) == M.MD_NOALLOC_MAX_ATOMS
 
 
 def test_struct_layout_matches_c(tmp_path):
@@ -48,6 +50,7 @@ def test_struct_layout_matches_c(tmp_path):
         "md_pulse": [f[0] for f in M.MDPulse._fields_],
         "md_state": [f[0] for f in M.MDState._fields_],
         "md_timing": [f[0] for f in M.MDTiming._fields_],
+        "md_forces_input": [f[0] for f in M.MDForcesInput._fields_],
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void){"]
     for st, fs in fields.items():
@@ -60,7 +63,7 @@ def test_struct_layout_matches_c(tmp_path):
     subprocess.check_call(["gcc", "-o", str(exe), str(src)])
     got = dict(l.split() for l in subprocess.check_output([str(exe)], text=True).splitlines())
     pys = {"md_config": M.MDConfig, "md_system": M.MDSystem, "md_pulse": M.MDPulse,
-           "md_state": M.MDState, "md_timing": M.MDTiming}
+           "md_state": M.MDState, "md_timing": M.MDTiming, "md_forces_input": M.MDForcesInput}
     for st, cls in pys.items():
         assert int(got[st]) == ctypes.sizeof(cls), st
         for f in fields[st]:
