@@ -1,8 +1,10 @@
 // Cell-list neighbour build (one per step).  The paper's cutoff is chosen
 // from the screening (Sec. II.B); here every replica gets a grid of cells of
 // edge >= r_cut, atoms are counted per cell, the cells are scanned, and each
-// cell is sorted deterministically (sub-cell Morton key, then atom index) into
-// a padded slot range that is a multiple of the 8-atom cluster size.  The
+// cell is sorted deterministically (3D Hilbert index of a 16^3 sub-grid, then
+// atom index) into a padded slot range that is a multiple of the 8-atom
+// cluster size; runs of 8 consecutive atoms along the Hilbert curve are
+// compact, near-cubic clusters.  The
 // packed arrays hold FP32 (or FP64) coordinates relative to the cell centre,
 // the charge, the type state and the fragment, plus one bounding box per
 // cluster for the pair kernel's prefilter.
@@ -12,7 +14,7 @@ namespace mdg {
 
 constexpr int kScanThreads = 1024;
 constexpr int kSortThreads = 1024;
-constexpr int kKdMax = 1024;         // atoms per cell ordered in shared memory
+constexpr int kSortMax = 4096;       // keys per cell kept in shared memory
 
 __device__ __forceinline__ int cell_coord(double x, double origin, double inv_edge, int n)
 {
@@ -21,9 +23,40 @@ __device__ __forceinline__ int cell_coord(double x, double origin, double inv_ed
     return c < n ? c : n - 1;
 }
 
-__device__ __forceinline__ unsigned spread3(unsigned v)   // 3 bits -> every third bit
+// Index of cell (x, y, z) of a 2^kHilBits grid along the 3D Hilbert curve
+// (Skilling's transpose algorithm, "Programming the Hilbert curve", AIP Conf.
+// Proc. 707, 2004: undo the excess work, Gray-encode, interleave the bits).
+constexpr int kHilBits = 4;
+__device__ __forceinline__ unsigned hilbert3(unsigned x0, unsigned x1, unsigned x2)
 {
-    return (v & 1u) | ((v & 2u) << 2) | ((v & 4u) << 4);
+    unsigned X[3] = {x0, x1, x2};
+#pragma unroll
+    for (unsigned Q = 1u << (kHilBits - 1); Q > 1; Q >>= 1) {
+        const unsigned P = Q - 1;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            if (X[i] & Q) {
+                X[0] ^= P;
+            } else {
+                const unsigned t = (X[0] ^ X[i]) & P;
+                X[0] ^= t;
+                X[i] ^= t;
+            }
+        }
+    }
+    X[1] ^= X[0];
+    X[2] ^= X[1];
+    unsigned t = 0;
+#pragma unroll
+    for (unsigned Q = 1u << (kHilBits - 1); Q > 1; Q >>= 1)
+        if (X[2] & Q) t ^= Q - 1;
+    X[0] ^= t; X[1] ^= t; X[2] ^= t;
+    unsigned key = 0;
+#pragma unroll
+    for (int b = kHilBits - 1; b >= 0; --b)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) key = (key << 1) | ((X[i] >> b) & 1u);
+    return key;
 }
 
 // Atoms are visited in the previous step's slot order, so neighbouring
@@ -119,50 +152,25 @@ __global__ void __launch_bounds__(256) k_cell_scatter(Params p)
     const int cx = local % g.dims[0];
     const int cy = (local / g.dims[0]) % g.dims[1];
     const int cz = local / (g.dims[0] * g.dims[1]);
-    // sub-cell (8 per edge) Morton key: spatially compact 8-atom clusters
+    // Hilbert index of the atom's sub-cell (16 per edge)
     unsigned sub[3];
     const double xs[3] = {p.x[i], p.y[i], p.z[i]};
     const int cc[3] = {cx, cy, cz};
     for (int d = 0; d < 3; ++d) {
-        double u = (xs[d] - (g.origin[d] + cc[d] * g.edge[d])) * g.inv_edge[d] * 8.0;
-        int s = u >= 0.0 ? (int)u : 0;
-        sub[d] = (unsigned)(s < 7 ? s : 7);
+        const double u = (xs[d] - (g.origin[d] + cc[d] * g.edge[d])) * g.inv_edge[d] * (double)(1 << kHilBits);
+        const int sv = u >= 0.0 ? (int)u : 0;
+        sub[d] = (unsigned)(sv < (1 << kHilBits) - 1 ? sv : (1 << kHilBits) - 1);
     }
-    const unsigned key = spread3(sub[0]) | (spread3(sub[1]) << 1) | (spread3(sub[2]) << 2);
+    const unsigned key = hilbert3(sub[0], sub[1], sub[2]);
     p.tmp_key[p.cell_start[c] + p.atom_rank[i]] = ((unsigned long long)key << 32) | (unsigned)i;
 }
 
-// Segment of position e at bisection level `level` for a cell of n atoms:
-// every segment longer than one cluster splits into a left part of
-// ceil(len/16)*8 atoms (a whole number of clusters) and the rest.
-__device__ __forceinline__ void kd_segment(int n, int level, int e, int& s, int& len)
-{
-    s = 0;
-    len = n;
-    for (int l = 0; l < level && len > kClusterSize; ++l) {
-        const int left = (len + 2 * kClusterSize - 1) / (2 * kClusterSize) * kClusterSize;
-        if (e < s + left) len = left;
-        else { s += left; len -= left; }
-    }
-}
-
-__device__ __forceinline__ int kd_levels(int n)
-{
-    int l = 0;
-    for (int len = n; len > kClusterSize; len = (len + 2 * kClusterSize - 1) / (2 * kClusterSize) * kClusterSize) ++l;
-    return l;
-}
-
-// One CTA per cell.  Atoms are ordered by recursive bisection (split each
-// segment at a multiple of 8 along an axis that cycles through the cell's
-// edges, longest first; ties broken by atom index) so that every run of 8
-// slots is a compact, near-cubic cluster; then the packed arrays and the
-// cluster bounding boxes are written.  Cells with
-// more than kKdMax atoms fall back to a rank sort on (Morton sub-cell, atom).
+// One CTA per cell: rank sort of the cell's keys (Hilbert index, atom), with
+// up to 8 threads sharing the count of one element; then the packed arrays
+// and the cluster bounding boxes.
 __global__ void __launch_bounds__(kSortThreads) k_cell_sort_pack(Params p)
 {
-    __shared__ int s_idx[2][kKdMax];
-    __shared__ float s_pos[2][3][kKdMax];
+    __shared__ unsigned long long s_key[kSortMax];
     if (*p.err & ERR_CELL) return;
     const int tid = threadIdx.x;
     for (int c = blockIdx.x; c < p.cell_cap_total; c += gridDim.x) {
@@ -189,80 +197,37 @@ __global__ void __launch_bounds__(kSortThreads) k_cell_sort_pack(Params p)
         const double cen[3] = {g.origin[0] + (cx + 0.5) * g.edge[0],
                                g.origin[1] + (cy + 0.5) * g.edge[1],
                                g.origin[2] + (cz + 0.5) * g.edge[2]};
-        int cur = 0;
-        if (n <= kKdMax) {
-            for (int e = tid; e < n; e += kSortThreads) {
-                const int i = (int)(p.tmp_key[b + e] & 0xffffffffu);
-                s_idx[0][e] = i;
-                s_pos[0][0][e] = (float)(p.x[i] - cen[0]);
-                s_pos[0][1][e] = (float)(p.y[i] - cen[1]);
-                s_pos[0][2][e] = (float)(p.z[i] - cen[2]);
+        const bool in_smem = n <= kSortMax;
+        const unsigned long long* keys = in_smem ? s_key : p.tmp_key + b;
+        if (in_smem)
+            for (int e = tid; e < n; e += kSortThreads) s_key[e] = p.tmp_key[b + e];
+        __syncthreads();
+        int tpe = 1;
+        while (tpe < 8 && 2 * tpe * n <= kSortThreads) tpe *= 2;
+        const int per_pass = kSortThreads / tpe;
+        const int sub = tid & (tpe - 1);
+        for (int base = 0; base < n; base += per_pass) {
+            const int e = base + tid / tpe;
+            unsigned long long ke = 0;
+            int rank = 0;
+            if (e < n) {
+                ke = keys[e];
+                for (int f = sub; f < n; f += tpe) rank += keys[f] < ke;
             }
-            __syncthreads();
-            // split axes cycle through the cell's edges, longest first
-            int a0 = 0, a1 = 1, a2 = 2;
-            if (g.edge[a1] > g.edge[a0]) { const int t = a0; a0 = a1; a1 = t; }
-            if (g.edge[a2] > g.edge[a1]) { const int t = a1; a1 = a2; a2 = t; }
-            if (g.edge[a1] > g.edge[a0]) { const int t = a0; a0 = a1; a1 = t; }
-            // tpe threads share the rank count of one element
-            int tpe = 1;
-            while (tpe < 8 && 2 * tpe * n <= kSortThreads) tpe *= 2;
-            const int per_pass = kSortThreads / tpe;
-            const int sub = tid & (tpe - 1);
-            const int levels = kd_levels(n);
-            for (int level = 0; level < levels; ++level) {
-                const int lm = level % 3;
-                const int ax = lm == 0 ? a0 : (lm == 1 ? a1 : a2);
-                const float* pa = s_pos[cur][ax];
-                const int* ia = s_idx[cur];
-                for (int base = 0; base < n; base += per_pass) {
-                    const int e = base + tid / tpe;
-                    int s0 = 0, len = 0, rank = 0;
-                    if (e < n) {
-                        kd_segment(n, level, e, s0, len);
-                        if (len > kClusterSize) {
-                            const float ve = pa[e];
-                            const int ie = ia[e];
-                            for (int f = s0 + sub; f < s0 + len; f += tpe) {
-                                const float vf = pa[f];
-                                rank += (vf < ve) || (vf == ve && ia[f] < ie);
-                            }
-                        }
-                    }
-                    for (int o = 1; o < tpe; o <<= 1) rank += __shfl_xor_sync(0xffffffffu, rank, o);
-                    if (e < n && sub == 0) {
-                        const int dst = len > kClusterSize ? s0 + rank : e;
-                        s_idx[cur ^ 1][dst] = ia[e];
-                        s_pos[cur ^ 1][0][dst] = s_pos[cur][0][e];
-                        s_pos[cur ^ 1][1][dst] = s_pos[cur][1][e];
-                        s_pos[cur ^ 1][2][dst] = s_pos[cur][2][e];
-                    }
-                }
-                __syncthreads();
-                cur ^= 1;
+            for (int o = 1; o < tpe; o <<= 1) rank += __shfl_xor_sync(0xffffffffu, rank, o);
+            if (e < n && sub == 0) {
+                const int i = (int)(ke & 0xffffffffu);
+                const int slot = ps + rank;
+                p.atom_of[slot] = i;
+                p.slot_of[i] = slot;
+                const int sp = p.species[i];
+                const int qi = p.q[i];
+                const double dx = p.x[i] - cen[0], dy = p.y[i] - cen[1], dz = p.z[i] - cen[2];
+                if (p.precision == 0) p.xq[slot] = make_float4((float)dx, (float)dy, (float)dz, (float)qi);
+                else p.xq64[slot] = make_double4_32a(dx, dy, dz, (double)qi);
+                p.tf[slot] = make_int2(p.ts_off[sp] + qi, p.frag[i]);
+                p.fx[slot] = 0; p.fy[slot] = 0; p.fz[slot] = 0; p.epot[slot] = 0;
             }
-        }
-        for (int e = tid; e < n; e += kSortThreads) {
-            int i, pos = e;
-            if (n <= kKdMax) {
-                i = s_idx[cur][e];
-            } else {   // fallback: rank by (Morton sub-cell, atom index) in global memory
-                const unsigned long long ke = p.tmp_key[b + e];
-                int rank = 0;
-                for (int f = 0; f < n; ++f) rank += p.tmp_key[b + f] < ke;
-                i = (int)(ke & 0xffffffffu);
-                pos = rank;
-            }
-            const int slot = ps + pos;
-            p.atom_of[slot] = i;
-            p.slot_of[i] = slot;
-            const int sp = p.species[i];
-            const int qi = p.q[i];
-            const double dx = p.x[i] - cen[0], dy = p.y[i] - cen[1], dz = p.z[i] - cen[2];
-            if (p.precision == 0) p.xq[slot] = make_float4((float)dx, (float)dy, (float)dz, (float)qi);
-            else p.xq64[slot] = make_double4_32a(dx, dy, dz, (double)qi);
-            p.tf[slot] = make_int2(p.ts_off[sp] + qi, p.frag[i]);
-            p.fx[slot] = 0; p.fy[slot] = 0; p.fz[slot] = 0; p.epot[slot] = 0;
         }
         for (int e = n + tid; e < npad; e += kSortThreads) {     // padding: far away, no charge
             const int slot = ps + e;
