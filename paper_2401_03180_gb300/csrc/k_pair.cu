@@ -6,15 +6,16 @@
 // Work decomposition (Newton's third law, every unordered pair once):
 //   * atoms are cell-sorted into clusters of 8; up to 8 consecutive clusters
 //     of one cell form a super-cluster (SC);
-//   * a work item is (SC, a range of the 14 half-shell cells); a warp owns one
-//     item at a time (dynamic scheduling through an atomic counter);
+//   * a work item is (SC, a range of the 14 half-shell cells, each cut in four
+//     parts of its j-cluster range); a warp owns one item at a time (dynamic
+//     scheduling through an atomic counter);
 //   * the SC's atoms and per-lane i-force partials live in shared memory;
 //     lane (tx = lane & 7, ty = lane >> 3) takes atom tx of an i-cluster and
 //     atoms ty, ty+4 of the current j-cluster;
 //   * j-clusters are pre-filtered per i-cluster by bounding-box distance, and
 //     only the i-clusters whose boxes are in range are visited (a loop over
 //     the set bits of a mask, so the code stays small);
-//   * forces are summed in FP32 (or FP64) within one (SC, cell) item for the
+//   * forces are summed in FP32 (or FP64) within one (SC, cell, part) for the
 //     i side and one (SC, j-cluster) visit for the j side, then converted
 //     once to 64-bit fixed point (2^-32 kJ/mol/nm): the per-atom totals are
 //     exact integer sums, identical for every launch shape and schedule.
@@ -49,6 +50,7 @@ struct Prec<false> {
     static __device__ __forceinline__ bool fix_ok(T v) { return fabsf(v) < 1.0737418e9f; }
     static __device__ __forceinline__ const C2* table(const Params& p) { return p.lj_f; }
     static __device__ __forceinline__ S4 mk(T a, T b, T c, T d) { return make_float4(a, b, c, d); }
+    static __device__ __forceinline__ T fma(T a, T b, T c) { return __fmaf_rn(a, b, c); }
 };
 
 template <>
@@ -64,13 +66,14 @@ struct Prec<true> {
     static __device__ __forceinline__ bool fix_ok(T v) { return fabs(v) < 1.073741824e9; }
     static __device__ __forceinline__ const C2* table(const Params& p) { return p.lj_d; }
     static __device__ __forceinline__ S4 mk(T a, T b, T c, T d) { S4 s; s.x = a; s.y = b; s.z = c; s.w = d; return s; }
+    static __device__ __forceinline__ T fma(T a, T b, T c) { return __fma_rn(a, b, c); }
 };
 
 // per-warp shared-memory layout
 template <bool FP64>
 struct WarpSmem {
     typename Prec<FP64>::S4 ix[kSuperClusters * kClusterSize];   // x, y, z, f*q of the SC atoms
-    int2 it[kSuperClusters * kClusterSize];                      // LJ row (ts * n_ts), fragment
+    int2 it[kSuperClusters * kClusterSize];                      // LJ row byte offset, fragment
     typename Prec<FP64>::S4 fi[kSuperClusters * 32];             // per (i-cluster, lane) force (+energy)
     float4 lo[kSuperClusters], hi[kSuperClusters];               // i-cluster boxes (cell frame)
     int2 fr[kSuperClusters];                                     // i-cluster fragment ranges
@@ -87,14 +90,17 @@ __device__ __forceinline__ void red_fix(long long* dst, typename Prec<FP64>::T v
     if (q != 0) atomicAdd((unsigned long long*)dst, (unsigned long long)q);
 }
 
-// One pair, d = x_i - x_j.  ok: the pair is not a duplicate (self-cluster
-// diagonal).  Accumulates the force on i (f*) and on j (fj*) and, with
-// ENERGY, the cutoff-shifted pair energy.
+// One pair, d = x_i - x_j.  `ok` drops the duplicates of the self-cluster
+// diagonal; equal fragments drop the LJ part.  qjk = q_j * kappa.  The force
+// on i is accumulated into (fx, fy, fz), the force on j into (fjx, fjy, fjz);
+// with ENERGY the cutoff-shifted pair energy into u.  Multiply-adds are
+// written out so that each accumulation is one fused operation.
 template <bool FP64, bool ENERGY>
-__device__ __forceinline__ void pair(const typename Prec<FP64>::S4& xi, int rowi, int fri,
+__device__ __forceinline__ void pair(const typename Prec<FP64>::S4& xi, int row_off, int fri,
                                      typename Prec<FP64>::T xj, typename Prec<FP64>::T yj,
-                                     typename Prec<FP64>::T zj, typename Prec<FP64>::T qj, int tsj,
-                                     int frj, bool ok, const typename Prec<FP64>::C2* __restrict__ lj,
+                                     typename Prec<FP64>::T zj, typename Prec<FP64>::T qj,
+                                     typename Prec<FP64>::T qjk, int tsj_off, int frj, bool ok,
+                                     const unsigned char* __restrict__ lj_bytes,
                                      typename Prec<FP64>::T kap, typename Prec<FP64>::T rc2,
                                      typename Prec<FP64>::T& fx, typename Prec<FP64>::T& fy,
                                      typename Prec<FP64>::T& fz, typename Prec<FP64>::T& fjx,
@@ -105,28 +111,29 @@ __device__ __forceinline__ void pair(const typename Prec<FP64>::S4& xi, int rowi
     using P = Prec<FP64>;
     using T = typename P::T;
     const T dx = xi.x - xj, dy = xi.y - yj, dz = xi.z - zj;
-    const T r2 = dx * dx + dy * dy + dz * dz;
+    const T r2 = P::fma(dz, dz, P::fma(dy, dy, dx * dx));
     const bool in = (r2 < rc2) && ok;
     const T rinv = in ? P::rsq(r2) : T(0);
-    const typename P::C2 c = lj[rowi + tsj];
+    const typename P::C2 c = *reinterpret_cast<const typename P::C2*>(lj_bytes + row_off + tsj_off);
     const T rinv2 = rinv * rinv;
     const T rinv6 = rinv2 * rinv2 * rinv2;
-    const T lj6 = fri == frj ? T(0) : rinv6;   // bonded in the native structure: no LJ
+    const T lj6 = fri == frj ? T(0) : rinv6;    // bonded in the native structure: no LJ
     const T r = r2 * rinv;
     const T kr = kap * r;
     const T e = P::expneg(kr);
     const T A = c.y * rinv6;                    // c12 / r^12
     const T B = A - c.x;                        // c12/r^12 - c6/r^6
     const T D6 = T(6) * (A + B);                // 12 c12/r^12 - 6 c6/r^6
-    const T E1 = kr * B + D6;
-    const T qq = xi.w * qj;                     // f q_i q_j
-    const T Cc = qq * (rinv + kap);
-    const T S = lj6 * E1 + Cc;
+    const T E1 = P::fma(kr, B, D6);
+    const T Cc = xi.w * P::fma(qj, rinv, qjk);  // f q_i q_j (1/r + kappa)
+    const T S = P::fma(lj6, E1, Cc);
     const T fs = S * (rinv2 * e);               // F(r)/r
-    fx += fs * dx; fy += fs * dy; fz += fs * dz;
-    fjx -= fs * dx; fjy -= fs * dy; fjz -= fs * dz;
+    const T nfs = -fs;
+    fx = P::fma(fs, dx, fx); fy = P::fma(fs, dy, fy); fz = P::fma(fs, dz, fz);
+    fjx = P::fma(nfs, dx, fjx); fjy = P::fma(nfs, dy, fjy); fjz = P::fma(nfs, dz, fjz);
     if (ENERGY) {
         if (in) {
+            const T qq = xi.w * qj;
             const T irc6 = irc * irc * irc * irc * irc * irc;
             const T lj_on = fri == frj ? T(0) : T(1);
             const T ush = erc * (qq * irc + lj_on * (c.y * irc6 - c.x) * irc6);
@@ -148,6 +155,7 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p, int nsplit
     extern __shared__ __align__(16) unsigned char smem[];
     const int nts = p.n_ts;
     C2* s_lj = reinterpret_cast<C2*>(smem);
+    const unsigned char* lj_bytes = smem;
     const size_t tab = ((size_t)nts * nts * sizeof(C2) + 127) / 128 * 128;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WS& w = reinterpret_cast<WS*>(smem + tab)[warp];
@@ -170,8 +178,10 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p, int nsplit
         if (lane == 0) item = atomicAdd(&p.counters[2], 1);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= n_items) break;
+        // sub-items of a super-cluster: (half-shell cell, part of its j range),
+        // kSubItems of them, grouped nsplit ways into work items
         const int sc = item / nsplit, part = item - sc * nsplit;
-        const int nb0 = part * kHalfShell / nsplit, nb1 = (part + 1) * kHalfShell / nsplit;
+        const int sub0 = part * kSubItems / nsplit, sub1 = (part + 1) * kSubItems / nsplit;
         const int c = p.sc_cell[sc], fc = p.sc_first[sc], ncl = p.sc_ncl[sc];
         int rr;
         {
@@ -198,7 +208,7 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p, int nsplit
                 const T4 v = P::pos(p, slot);
                 const int2 t = p.tf[slot];
                 w.ix[a] = P::mk(v.x, v.y, v.z, coulf * v.w);
-                w.it[a] = make_int2(t.x * nts, t.y);
+                w.it[a] = make_int2(t.x * nts * (int)sizeof(C2), t.y);   // byte offset of the LJ row
             }
         }
         if (lane < ncl) {
@@ -208,7 +218,8 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p, int nsplit
         }
         __syncwarp();
 
-        for (int nb = nb0; nb < nb1; ++nb) {
+        for (int sub = sub0; sub < sub1; ++sub) {
+            const int nb = sub / kJParts, part_j = sub - nb * kJParts;
             int dx, dy, dz;
             half_shell(nb, dx, dy, dz);
             int ncx = cx + dx, ncy = cy + dy, ncz = cz + dz;
@@ -221,9 +232,12 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p, int nsplit
                 continue;
             }
             const int c2 = g.cell_off + ncx + g.dims[0] * (ncy + g.dims[1] * ncz);
-            const int j_end = p.cell_pstart[c2 + 1] / kClusterSize;
             const bool self = nb == 0;
-            const int j_beg = self ? fc : p.cell_pstart[c2] / kClusterSize;
+            const int jr0 = self ? fc : p.cell_pstart[c2] / kClusterSize;
+            const int jr1 = p.cell_pstart[c2 + 1] / kClusterSize;
+            const int jn = jr1 - jr0;
+            const int j_beg = jr0 + (jn * part_j) / kJParts, j_end = jr0 + (jn * (part_j + 1)) / kJParts;
+            if (j_beg >= j_end) continue;
             const float Dfx = (float)dx * g.edge_f[0], Dfy = (float)dy * g.edge_f[1],
                         Dfz = (float)dz * g.edge_f[2];
             const T Dx = FP64 ? T(dx * g.edge[0]) : T(Dfx);
@@ -263,6 +277,8 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p, int nsplit
                     const int2 t0 = p.tf[s0], t1 = p.tf[s1];
                     const T x0 = a0.x + Dx, y0 = a0.y + Dy, z0 = a0.z + Dz;
                     const T x1 = a1.x + Dx, y1 = a1.y + Dy, z1 = a1.z + Dz;
+                    const T q0k = a0.w * kap, q1k = a1.w * kap;
+                    const int j0off = t0.x * (int)sizeof(C2), j1off = t1.x * (int)sizeof(C2);
                     const int kdiag = self ? jcl - fc : -1;   // i-cluster equal to this j-cluster
                     T fj0x = 0, fj0y = 0, fj0z = 0, fj1x = 0, fj1y = 0, fj1z = 0;
                     while (mk) {
@@ -271,14 +287,11 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p, int nsplit
                         const S4 xi = w.ix[k * kClusterSize + tx];
                         const int2 ti = w.it[k * kClusterSize + tx];
                         const bool dg = k == kdiag;
-                        T fx = 0, fy = 0, fz = 0, u = 0;
-                        pair<FP64, ENERGY>(xi, ti.x, ti.y, x0, y0, z0, a0.w, t0.x, t0.y, !dg || gt0, s_lj,
-                                           kap, rc2, fx, fy, fz, fj0x, fj0y, fj0z, u, npair, erc, irc);
-                        pair<FP64, ENERGY>(xi, ti.x, ti.y, x1, y1, z1, a1.w, t1.x, t1.y, !dg || gt1, s_lj,
-                                           kap, rc2, fx, fy, fz, fj1x, fj1y, fj1z, u, npair, erc, irc);
                         S4 acc = w.fi[k * 32 + lane];
-                        acc.x += fx; acc.y += fy; acc.z += fz;
-                        if (ENERGY) acc.w += u;
+                        pair<FP64, ENERGY>(xi, ti.x, ti.y, x0, y0, z0, a0.w, q0k, j0off, t0.y, !dg || gt0, lj_bytes,
+                                           kap, rc2, acc.x, acc.y, acc.z, fj0x, fj0y, fj0z, acc.w, npair, erc, irc);
+                        pair<FP64, ENERGY>(xi, ti.x, ti.y, x1, y1, z1, a1.w, q1k, j1off, t1.y, !dg || gt1, lj_bytes,
+                                           kap, rc2, acc.x, acc.y, acc.z, fj1x, fj1y, fj1z, acc.w, npair, erc, irc);
                         w.fi[k * 32 + lane] = acc;
                     }
                     // j forces: sum over the 8 i-lanes of each ty group.  Lanes tx < 4 keep

@@ -10,7 +10,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/md.h"
+#include "md.h"
 #include "md_internal.cuh"
 
 using namespace mdg;
@@ -29,7 +29,7 @@ struct md_handle {
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t ev_pair0 = nullptr, ev_pair1 = nullptr;
     int grid_atoms = 1, grid_cells = 1;
-    int pair_blocks = 1, pair_warps = 8, pair_nsplit = 14;
+    int pair_blocks = 1, pair_warps = 8, pair_nsplit = kSubItems;
     long long host_step = 0;
     bool poisoned = false;
     unsigned* h_err = nullptr;           // pinned
@@ -176,7 +176,7 @@ md_status autotune(md_handle* h)
     float best = 1e30f;
     int bw = h->pair_warps, bb = h->pair_blocks, bn = h->pair_nsplit;
     const int warps_c[] = {4, 8};
-    const int split_c[] = {1, 2, 7, 14};
+    const int split_c[] = {4, 7, 14, 28, 56};
     for (int w : warps_c) {
         int maxb = pair_max_blocks_per_sm(fp64, false, w, h->NTS);
         for (int bps = 1; bps <= maxb; ++bps) {
@@ -555,7 +555,7 @@ static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* 
     h->grid_atoms = (N + 255) / 256;
     h->grid_cells = std::max(1, std::min(C, h->n_sm * 8));
     h->pair_warps = 8;
-    h->pair_nsplit = 14;
+    h->pair_nsplit = kSubItems;
     h->pair_blocks = h->n_sm * pair_max_blocks_per_sm(c.precision == MD_PREC_FP64, false, 8, nts);
     CU(cudaDeviceSynchronize());
 

@@ -15,6 +15,8 @@ namespace mdg {
 constexpr int kClusterSize = 8;
 constexpr int kSuperClusters = 8;     // K_SC
 constexpr int kHalfShell = 14;        // self cell + 13 neighbour cells
+constexpr int kJParts = 4;                 // a neighbour cell's j-cluster range is cut in 4
+constexpr int kSubItems = kJParts * kHalfShell;   // (cell, part of its j range) per super-cluster
 constexpr int kMaxSpecies = 8;
 constexpr int kMaxTS = 128;
 constexpr int kNEtab = 16 * 40;       // e^{-k/16} table, lambda < 40

@@ -20,7 +20,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/md.h"
+#include "md.h"
 #include "md_internal.cuh"
 
 using namespace mdg;
@@ -273,7 +273,7 @@ extern "C" md_status md_forces_noalloc(const md_forces_input* in, double* d_f, v
     const int blocks = n_sm * pair_max_blocks_per_sm(in->precision == MD_PREC_FP64, false, warps, nts);
     launch_step_a(P, 0, s, (n + 255) / 256);                           // grid and screening
     launch_cells(P, s, (n + 255) / 256, std::max(1, std::min(g.cell_cap, n_sm * 8)));
-    launch_pair(P, s, false, blocks, warps, 14);
+    launch_pair(P, s, false, blocks, warps, kSubItems);
     launch_force_out(P, d_f, s);
     NA_CU(cudaGetLastError());
     unsigned h_err = 0;
