@@ -287,7 +287,7 @@ def run_gpu(args, rank, world, local):
                      "flops_per_pair": FLOPS_PER_PAIR, "pair_kernel_ms": pair_ms,
                      "pair_kernel_share": pair_ms / (ms / K)},
         "e2e": e2e,
-        "gpu_launches": 6 * K,
+        "gpu_launches": 7 * K,
         "clocks": clk.summary(),
         "charge_state": {"n_e": [int(v) for v in state["n_e"]], "te_ev": [float(v) for v in state["te_ev"]],
                          "events_pi_auger_ci_rec": [int(v) for v in state["event_counts"][0]]},

@@ -51,7 +51,7 @@ enum {
     MD_ERR_FIXED_OVERFLOW = 5, /* a force/energy exceeded the fixed-point range */
     MD_ERR_TIMEOUT = 6,        /* a bounded device wait gave up             */
     MD_ERR_NONFINITE = 7,      /* NaN/Inf in positions or velocities        */
-    MD_ERR_CELL_OVERFLOW = 8,  /* cell-list capacity exceeded               */
+    MD_ERR_CELL_OVERFLOW = 8,  /* cell-list or pair-list capacity exceeded  */
     MD_ERR_TABLE_END = 9       /* stepped past the per-step pulse table     */
 };
 
@@ -217,8 +217,12 @@ md_status md_set_plasma_table(md_handle* h, int replica, const double* ne,
                               const double* te_ev, int n_steps);
 
 /* Advance every replica by n_steps timesteps (asynchronous on the handle's
- * stream except for a final 4-byte status read).  Errors: BAD_STATE,
- * TABLE_END, FIXED_OVERFLOW, NONFINITE, CELL_OVERFLOW, CUDA. */
+ * stream except for a final 4-byte status read).  When the atoms crowd
+ * together beyond what the cluster-pair list was sized for, the steps stop
+ * after the one that needs more room, the list grows (through dev_alloc when
+ * given) and the remaining steps follow: the trajectory is the same as with a
+ * larger list from the start.  Errors: BAD_STATE, TABLE_END, FIXED_OVERFLOW,
+ * NONFINITE, CELL_OVERFLOW, OOM, CUDA. */
 md_status md_step(md_handle* h, int n_steps);
 
 /* Copy the requested fields (MD_FIELD_* mask) to caller buffers, in the
@@ -262,13 +266,15 @@ md_status md_philox(uint64_t seed, const uint32_t* d_ctr4, int64_t n, uint32_t* 
  * budget, a memory-capped process, an inner loop that must keep the device
  * footprint fixed -- it computes the screened Coulomb + screened LJ forces of
  * one configuration using only a fixed scratch area compiled into the
- * library (a file-scope __device__ array of about 5 MB, held by every GPU
+ * library (a file-scope __device__ array of about 8 MB, held by every GPU
  * that loads the library until the process exits).  It calls no cudaMalloc,
  * cudaFree or other allocating routine.
  *
  * Limits: n_atoms <= MD_NOALLOC_MAX_ATOMS; a periodic box needs at most
  * MD_NOALLOC_MAX_CELLS cells of edge >= r_cut; larger inputs are rejected
- * with MD_ERR_INVALID_ARG (message in md_last_error(NULL)).
+ * with MD_ERR_INVALID_ARG (message in md_last_error(NULL)).  The cluster-pair
+ * list holds 48 entries per cluster (liquid water at r_cut = 1.2 nm needs
+ * about 31); a denser configuration returns MD_ERR_CELL_OVERFLOW.
  * Inputs: device pointers d_x [3n] AoS positions (nm), d_species [n],
  * d_q [n] charges, d_fragment [n] (LJ excluded within a fragment); the screening
  * kappa = 1/lambda_D (nm^-1, 0 = bare Coulomb) and the species tables on the host.

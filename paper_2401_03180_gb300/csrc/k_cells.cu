@@ -139,6 +139,8 @@ __global__ void __launch_bounds__(kScanThreads) k_cell_scan(Params p)
         p.counters[0] = over ? 0 : os;
         p.counters[1] = over ? 0 : op;
         p.counters[2] = 0;
+        p.counters[6] = 0;
+        p.counters[7] = 0;
     }
 }
 
@@ -225,7 +227,7 @@ __global__ void __launch_bounds__(kSortThreads) k_cell_sort_pack(Params p)
                 const double dx = p.x[i] - cen[0], dy = p.y[i] - cen[1], dz = p.z[i] - cen[2];
                 if (p.precision == 0) p.xq[slot] = make_float4((float)dx, (float)dy, (float)dz, (float)qi);
                 else p.xq64[slot] = make_double4_32a(dx, dy, dz, (double)qi);
-                p.tf[slot] = make_int2(p.ts_off[sp] + qi, p.frag[i]);
+                p.tf[slot] = make_int2(p.lj_ts_off[sp] + qi, p.frag[i]);
                 p.fx[slot] = 0; p.fy[slot] = 0; p.fz[slot] = 0; p.epot[slot] = 0;
             }
         }

@@ -6,17 +6,19 @@
 // Work decomposition (Newton's third law, every unordered pair once):
 //   * atoms are cell-sorted into clusters of 8; up to 8 consecutive clusters
 //     of one cell form a super-cluster (SC);
-//   * a work item is (SC, a range of the 14 half-shell cells, each cut in four
-//     parts of its j-cluster range); a warp owns one item at a time (dynamic
-//     scheduling through an atomic counter);
+//   * a list kernel tests, per SC and half-shell cell, every j-cluster's
+//     bounding box against the SC's 8 i-cluster boxes and writes the pairs in
+//     range as (j-cluster, shift, i-cluster mask) entries, contiguous per SC
+//     and cut into chunks of kChunk entries;
+//   * a warp of the force kernel owns one chunk at a time (dynamic scheduling
+//     through an atomic counter);
 //   * the SC's atoms and per-lane i-force partials live in shared memory;
 //     lane (tx = lane & 7, ty = lane >> 3) takes atom tx of an i-cluster and
 //     atoms ty, ty+4 of the current j-cluster;
-//   * j-clusters are pre-filtered per i-cluster by bounding-box distance, and
-//     only the i-clusters whose boxes are in range are visited (a loop over
-//     the set bits of a mask, so the code stays small);
-//   * forces are summed in FP32 (or FP64) within one (SC, cell, part) for the
-//     i side and one (SC, j-cluster) visit for the j side, then converted
+//   * only the i-clusters of an entry's mask are visited (a loop over the set
+//     bits, so the code stays small);
+//   * forces are summed in FP32 (or FP64) within one chunk for the i side
+//     and one (SC, j-cluster) entry for the j side, then converted
 //     once to 64-bit fixed point (2^-32 kJ/mol/nm): the per-atom totals are
 //     exact integer sums, identical for every launch shape and schedule.
 #include "md_internal.cuh"
@@ -31,7 +33,7 @@ struct Prec<false> {
     using T = float;
     using T4 = float4;         // global packed position + charge
     using S4 = float4;         // shared-memory copy
-    using C2 = float2;         // c6, c12
+    using C2 = float2;         // -c6, c12
     static __device__ __forceinline__ T4 pos(const Params& p, int slot) { return p.xq[slot]; }
     // single MUFU operations (arguments are far from the denormal range)
     static __device__ __forceinline__ T rsq(T x)
@@ -58,7 +60,7 @@ struct Prec<true> {
     using T = double;
     using T4 = double4_32a;
     using S4 = double4_16a;
-    using C2 = double2;        // c6, c12
+    using C2 = double2;        // -c6, c12
     static __device__ __forceinline__ T4 pos(const Params& p, int slot) { return p.xq64[slot]; }
     static __device__ __forceinline__ T rsq(T x) { return 1.0 / sqrt(x); }
     static __device__ __forceinline__ T expneg(T x) { return exp(-x); }
@@ -75,8 +77,6 @@ struct WarpSmem {
     typename Prec<FP64>::S4 ix[kSuperClusters * kClusterSize];   // x, y, z, f*q of the SC atoms
     int2 it[kSuperClusters * kClusterSize];                      // LJ row byte offset, fragment
     typename Prec<FP64>::S4 fi[kSuperClusters * 32];             // per (i-cluster, lane) force (+energy)
-    float4 lo[kSuperClusters], hi[kSuperClusters];               // i-cluster boxes (cell frame)
-    int2 fr[kSuperClusters];                                     // i-cluster fragment ranges
 };
 
 template <bool FP64>
@@ -121,8 +121,8 @@ __device__ __forceinline__ void pair(const typename Prec<FP64>::S4& xi, int row_
     const T r = r2 * rinv;
     const T kr = kap * r;
     const T e = P::expneg(kr);
-    const T A = c.y * rinv6;                    // c12 / r^12
-    const T B = A - c.x;                        // c12/r^12 - c6/r^6
+    const T A = c.y * rinv6;                    // c12 / r^6
+    const T B = A + c.x;                        // c12/r^6 - c6 (table holds -c6)
     const T D6 = T(6) * (A + B);                // 12 c12/r^12 - 6 c6/r^6
     const T E1 = P::fma(kr, B, D6);
     const T Cc = xi.w * P::fma(qj, rinv, qjk);  // f q_i q_j (1/r + kappa)
@@ -136,53 +136,35 @@ __device__ __forceinline__ void pair(const typename Prec<FP64>::S4& xi, int row_
             const T qq = xi.w * qj;
             const T irc6 = irc * irc * irc * irc * irc * irc;
             const T lj_on = fri == frj ? T(0) : T(1);
-            const T ush = erc * (qq * irc + lj_on * (c.y * irc6 - c.x) * irc6);
+            const T ush = erc * (qq * irc + lj_on * (c.y * irc6 + c.x) * irc6);
             u += e * (qq * rinv + lj6 * B) - ush;
             npair += 1;
         }
     }
 }
 
-template <bool FP64, bool ENERGY>
-__global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p, int nsplit)
+// Cluster-pair list (one block per super-cluster, one warp per half-shell
+// cell): every j-cluster whose bounding box comes within r_cut of at least one
+// of the SC's i-cluster boxes gets an entry (j-cluster, half-shell index,
+// mask of those i-clusters).  An SC's entries are contiguous and cut into
+// chunks of kChunk, the work items of the force kernel.  A first pass counts,
+// the second repeats the box tests and writes, so no cell size limit applies.
+__global__ void __launch_bounds__(kHalfShell * 32) k_pair_list(Params p)
 {
-    using P = Prec<FP64>;
-    using T = typename P::T;
-    using T4 = typename P::T4;
-    using S4 = typename P::S4;
-    using C2 = typename P::C2;
-    using WS = WarpSmem<FP64>;
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int nts = p.n_ts;
-    C2* s_lj = reinterpret_cast<C2*>(smem);
-    const unsigned char* lj_bytes = smem;
-    const size_t tab = ((size_t)nts * nts * sizeof(C2) + 127) / 128 * 128;
+    __shared__ float4 s_lo[kSuperClusters], s_hi[kSuperClusters];
+    __shared__ int s_cnt[kHalfShell];
+    __shared__ int s_base, s_tot, s_cbase;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WS& w = reinterpret_cast<WS*>(smem + tab)[warp];
-
-    for (int k = threadIdx.x; k < nts * nts; k += blockDim.x) s_lj[k] = P::table(p)[k];
-    __syncthreads();
     if (*p.err & ERR_CELL) return;
-
-    const int tx = lane & 7, ty = lane >> 3;
-    const bool gt0 = ty > tx, gt1 = ty + 4 > tx;   // j index above i index (diagonal blocks)
-    const int n_items = p.counters[0] * nsplit;
+    const int n_sc = p.counters[0];
     const float rcb = p.rc_f + kBBoxMargin;
     const float rcb2 = rcb * rcb;
-    const T rc2 = FP64 ? T(p.rc2) : T(p.rc2_f);
-    const T irc = T(1.0 / p.r_cut);
-    const T coulf = T(p.coulomb_f);
-
-    while (true) {
-        int item = 0;
-        if (lane == 0) item = atomicAdd(&p.counters[2], 1);
-        item = __shfl_sync(0xffffffffu, item, 0);
-        if (item >= n_items) break;
-        // sub-items of a super-cluster: (half-shell cell, part of its j range),
-        // kSubItems of them, grouped nsplit ways into work items
-        const int sc = item / nsplit, part = item - sc * nsplit;
-        const int sub0 = part * kSubItems / nsplit, sub1 = (part + 1) * kSubItems / nsplit;
+    for (int sc = blockIdx.x; sc < n_sc; sc += gridDim.x) {
         const int c = p.sc_cell[sc], fc = p.sc_first[sc], ncl = p.sc_ncl[sc];
+        if (threadIdx.x < ncl) {
+            s_lo[threadIdx.x] = p.bb_lo[fc + threadIdx.x];
+            s_hi[threadIdx.x] = p.bb_hi[fc + threadIdx.x];
+        }
         int rr;
         {
             int lo = 0, hi = p.n_rep - 1;
@@ -197,10 +179,139 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p, int nsplit
         const int cx = local % g.dims[0];
         const int cy = (local / g.dims[0]) % g.dims[1];
         const int cz = local / (g.dims[0] * g.dims[1]);
+        const int nb = warp;
+        int dx, dy, dz;
+        half_shell(nb, dx, dy, dz);
+        int ncx = cx + dx, ncy = cy + dy, ncz = cz + dz;
+        bool valid = true;
+        if (g.periodic) {
+            ncx = ncx < 0 ? ncx + g.dims[0] : (ncx >= g.dims[0] ? ncx - g.dims[0] : ncx);
+            ncy = ncy < 0 ? ncy + g.dims[1] : (ncy >= g.dims[1] ? ncy - g.dims[1] : ncy);
+            ncz = ncz < 0 ? ncz + g.dims[2] : (ncz >= g.dims[2] ? ncz - g.dims[2] : ncz);
+        } else {
+            valid = ncx >= 0 && ncy >= 0 && ncz >= 0 && ncx < g.dims[0] && ncy < g.dims[1] && ncz < g.dims[2];
+        }
+        int jr0 = 0, jr1 = 0;
+        if (valid) {
+            const int c2 = g.cell_off + ncx + g.dims[0] * (ncy + g.dims[1] * ncz);
+            jr0 = nb == 0 ? fc : p.cell_pstart[c2] / kClusterSize;
+            jr1 = p.cell_pstart[c2 + 1] / kClusterSize;
+        }
+        const float Dfx = (float)dx * g.edge_f[0], Dfy = (float)dy * g.edge_f[1], Dfz = (float)dz * g.edge_f[2];
+        __syncthreads();   // boxes staged
+
+        // mask of the SC's i-clusters in range of j-cluster jc (0 when out of range);
+        // explicit roundings, so that both passes reach the same masks
+        auto test = [&](int jc) -> unsigned {
+            unsigned m = 0;
+            if (jc < jr1) {
+                const float4 lo = p.bb_lo[jc], hi = p.bb_hi[jc];
+                const float jlx = lo.x + Dfx, jly = lo.y + Dfy, jlz = lo.z + Dfz;
+                const float jhx = hi.x + Dfx, jhy = hi.y + Dfy, jhz = hi.z + Dfz;
+                const int kmax = nb == 0 ? min(ncl, jc - fc + 1) : ncl;
+#pragma unroll 2
+                for (int k = 0; k < kmax; ++k) {
+                    const float4 il = s_lo[k], ih = s_hi[k];
+                    const float gx = fmaxf(0.0f, fmaxf(il.x - jhx, jlx - ih.x));
+                    const float gy = fmaxf(0.0f, fmaxf(il.y - jhy, jly - ih.y));
+                    const float gz = fmaxf(0.0f, fmaxf(il.z - jhz, jlz - ih.z));
+                    if (__fmaf_rn(gz, gz, __fmaf_rn(gy, gy, __fmul_rn(gx, gx))) < rcb2) m |= 1u << k;
+                }
+            }
+            return m;
+        };
+        int cnt = 0;
+        unsigned m_first = 0;   // masks of the first 32 j-clusters, kept for the write pass
+        for (int base = jr0; base < jr1; base += 32) {
+            const unsigned m = test(base + lane);
+            if (base == jr0) m_first = m;
+            cnt += __popc(__ballot_sync(0xffffffffu, m != 0));
+        }
+        if (lane == 0) s_cnt[warp] = cnt;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int tot = 0;
+            for (int w = 0; w < kHalfShell; ++w) {
+                const int t = s_cnt[w];
+                s_cnt[w] = tot;
+                tot += t;
+            }
+            const unsigned long long nch = (unsigned long long)((tot + kChunk - 1) / kChunk);
+            // one reservation for both: entries in the low word, chunks in the high word
+            const unsigned long long old =
+                atomicAdd(reinterpret_cast<unsigned long long*>(p.counters + 6), (nch << 32) | (unsigned)tot);
+            int base = (int)(unsigned)old;
+            const int cbase = (int)(old >> 32);
+            if ((long long)base + tot > p.pl_cap || (long long)cbase + (long long)nch > p.chunk_cap) {
+                atomicOr(p.err, ERR_LIST);
+                base = -1;
+            }
+            s_base = base;
+            s_tot = tot;
+            s_cbase = cbase;
+        }
+        __syncthreads();
+        const int base_sc = s_base, tot = s_tot, cbase = s_cbase;
+        if (base_sc >= 0) {
+            int off = base_sc + s_cnt[warp];
+            const int end = base_sc + tot;
+            for (int base = jr0; base < jr1; base += 32) {
+                const unsigned m = base == jr0 ? m_first : test(base + lane);
+                const unsigned bal = __ballot_sync(0xffffffffu, m != 0);
+                const int at = off + __popc(bal & ((1u << lane) - 1u));
+                if (m && at < end) p.pl[at] = make_uint2(base + lane, (nb << 8) | m);
+                off += __popc(bal);
+            }
+            for (int t = threadIdx.x; t * kChunk < tot; t += blockDim.x)
+                p.pl_chunk[cbase + t] = make_int4(sc, base_sc + t * kChunk, min(kChunk, tot - t * kChunk), rr);
+        }
+    }
+}
+
+// Forces over the cluster-pair list.  A warp takes one chunk (up to kChunk
+// entries of one SC) at a time from an atomic counter.
+template <bool FP64, bool ENERGY>
+__global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
+{
+    using P = Prec<FP64>;
+    using T = typename P::T;
+    using T4 = typename P::T4;
+    using S4 = typename P::S4;
+    using C2 = typename P::C2;
+    using WS = WarpSmem<FP64>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int nts = p.n_ts_lj;
+    C2* s_lj = reinterpret_cast<C2*>(smem);
+    const unsigned char* lj_bytes = smem;
+    const size_t tab = ((size_t)nts * nts * sizeof(C2) + 127) / 128 * 128;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WS& w = reinterpret_cast<WS*>(smem + tab)[warp];
+
+    for (int k = threadIdx.x; k < nts * nts; k += blockDim.x) s_lj[k] = P::table(p)[k];
+    __syncthreads();
+    if (*p.err & (ERR_CELL | ERR_LIST)) return;
+
+    const int tx = lane & 7, ty = lane >> 3;
+    const bool gt0 = ty > tx, gt1 = ty + 4 > tx;   // j index above i index (diagonal blocks)
+    const int n_chunks = min(p.counters[7], p.chunk_cap);
+    const T rc2 = FP64 ? T(p.rc2) : T(p.rc2_f);
+    const T irc = T(1.0 / p.r_cut);
+    const T coulf = T(p.coulomb_f);
+
+    while (true) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(&p.counters[2], 1);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= n_chunks) break;
+        const int4 ch = p.pl_chunk[item];          // (sc, first entry, entries, replica)
+        const int sc = ch.x, n_ent = ch.z, rr = ch.w;
+        const uint2 ent = lane < n_ent ? p.pl[ch.y + lane] : make_uint2(0u, 0u);
+        const int fc = p.sc_first[sc], ncl = p.sc_ncl[sc];
+        const Grid& g = p.grid[rr];
         const T kap = FP64 ? T(p.rs[rr].kappa_force) : T(p.rs[rr].kappa_f);
         const T erc = ENERGY ? P::expneg(kap * T(p.r_cut)) : T(0);
 
-        // the super-cluster's atoms and boxes into shared memory
+        // the super-cluster's atoms into shared memory, partial forces cleared
         __syncwarp();
         for (int a = lane; a < kSuperClusters * kClusterSize; a += 32) {
             if ((a >> 3) < ncl) {
@@ -211,137 +322,87 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p, int nsplit
                 w.it[a] = make_int2(t.x * nts * (int)sizeof(C2), t.y);   // byte offset of the LJ row
             }
         }
-        if (lane < ncl) {
-            w.lo[lane] = p.bb_lo[fc + lane];
-            w.hi[lane] = p.bb_hi[fc + lane];
-            w.fr[lane] = p.bb_frag[fc + lane];
-        }
+        for (int k = 0; k < ncl; ++k) w.fi[k * 32 + lane] = P::mk(T(0), T(0), T(0), T(0));
         __syncwarp();
+        int npair = 0;
 
-        for (int sub = sub0; sub < sub1; ++sub) {
-            const int nb = sub / kJParts, part_j = sub - nb * kJParts;
+        for (int v = 0; v < n_ent; ++v) {
+            const int jcl = (int)__shfl_sync(0xffffffffu, ent.x, v);
+            const unsigned code = __shfl_sync(0xffffffffu, ent.y, v);
+            const int nb = (int)(code >> 8);
+            unsigned mk = code & 0xffu;
             int dx, dy, dz;
             half_shell(nb, dx, dy, dz);
-            int ncx = cx + dx, ncy = cy + dy, ncz = cz + dz;
-            if (g.periodic) {
-                ncx = ncx < 0 ? ncx + g.dims[0] : (ncx >= g.dims[0] ? ncx - g.dims[0] : ncx);
-                ncy = ncy < 0 ? ncy + g.dims[1] : (ncy >= g.dims[1] ? ncy - g.dims[1] : ncy);
-                ncz = ncz < 0 ? ncz + g.dims[2] : (ncz >= g.dims[2] ? ncz - g.dims[2] : ncz);
-            } else if (ncx < 0 || ncy < 0 || ncz < 0 || ncx >= g.dims[0] || ncy >= g.dims[1] ||
-                       ncz >= g.dims[2]) {
-                continue;
+            const T Dx = FP64 ? T(dx * g.edge[0]) : T((float)dx * g.edge_f[0]);
+            const T Dy = FP64 ? T(dy * g.edge[1]) : T((float)dy * g.edge_f[1]);
+            const T Dz = FP64 ? T(dz * g.edge[2]) : T((float)dz * g.edge_f[2]);
+            const int s0 = jcl * kClusterSize + ty, s1 = s0 + 4;
+            const T4 a0 = P::pos(p, s0), a1 = P::pos(p, s1);
+            const int2 t0 = p.tf[s0], t1 = p.tf[s1];
+            const T x0 = a0.x + Dx, y0 = a0.y + Dy, z0 = a0.z + Dz;
+            const T x1 = a1.x + Dx, y1 = a1.y + Dy, z1 = a1.z + Dz;
+            const T q0k = a0.w * kap, q1k = a1.w * kap;
+            const int j0off = t0.x * (int)sizeof(C2), j1off = t1.x * (int)sizeof(C2);
+            const int kdiag = nb == 0 ? jcl - fc : -1;   // i-cluster equal to this j-cluster
+            T fj0x = 0, fj0y = 0, fj0z = 0, fj1x = 0, fj1y = 0, fj1z = 0;
+            while (mk) {
+                const int k = __ffs(mk) - 1;
+                mk &= mk - 1;
+                const S4 xi = w.ix[k * kClusterSize + tx];
+                const int2 ti = w.it[k * kClusterSize + tx];
+                const bool dg = k == kdiag;
+                S4 acc = w.fi[k * 32 + lane];
+                pair<FP64, ENERGY>(xi, ti.x, ti.y, x0, y0, z0, a0.w, q0k, j0off, t0.y, !dg || gt0, lj_bytes,
+                                   kap, rc2, acc.x, acc.y, acc.z, fj0x, fj0y, fj0z, acc.w, npair, erc, irc);
+                pair<FP64, ENERGY>(xi, ti.x, ti.y, x1, y1, z1, a1.w, q1k, j1off, t1.y, !dg || gt1, lj_bytes,
+                                   kap, rc2, acc.x, acc.y, acc.z, fj1x, fj1y, fj1z, acc.w, npair, erc, irc);
+                w.fi[k * 32 + lane] = acc;
             }
-            const int c2 = g.cell_off + ncx + g.dims[0] * (ncy + g.dims[1] * ncz);
-            const bool self = nb == 0;
-            const int jr0 = self ? fc : p.cell_pstart[c2] / kClusterSize;
-            const int jr1 = p.cell_pstart[c2 + 1] / kClusterSize;
-            const int jn = jr1 - jr0;
-            const int j_beg = jr0 + (jn * part_j) / kJParts, j_end = jr0 + (jn * (part_j + 1)) / kJParts;
-            if (j_beg >= j_end) continue;
-            const float Dfx = (float)dx * g.edge_f[0], Dfy = (float)dy * g.edge_f[1],
-                        Dfz = (float)dz * g.edge_f[2];
-            const T Dx = FP64 ? T(dx * g.edge[0]) : T(Dfx);
-            const T Dy = FP64 ? T(dy * g.edge[1]) : T(Dfy);
-            const T Dz = FP64 ? T(dz * g.edge[2]) : T(Dfz);
-
-            for (int k = 0; k < ncl; ++k) w.fi[k * 32 + lane] = P::mk(T(0), T(0), T(0), T(0));
-            int npair = 0;
-            bool any = false;
-
-            for (int base = j_beg; base < j_end; base += 32) {
-                const int jc = base + lane;
-                unsigned m = 0;
-                if (jc < j_end) {
-                    const float4 lo = p.bb_lo[jc], hi = p.bb_hi[jc];
-                    const float jlx = lo.x + Dfx, jly = lo.y + Dfy, jlz = lo.z + Dfz;
-                    const float jhx = hi.x + Dfx, jhy = hi.y + Dfy, jhz = hi.z + Dfz;
-                    const int kmax = self ? min(ncl, jc - fc + 1) : ncl;
-#pragma unroll 2
-                    for (int k = 0; k < kmax; ++k) {
-                        const float4 il = w.lo[k], ih = w.hi[k];
-                        const float gx = fmaxf(0.0f, fmaxf(il.x - jhx, jlx - ih.x));
-                        const float gy = fmaxf(0.0f, fmaxf(il.y - jhy, jly - ih.y));
-                        const float gz = fmaxf(0.0f, fmaxf(il.z - jhz, jlz - ih.z));
-                        if (gx * gx + gy * gy + gz * gz < rcb2) m |= 1u << k;
-                    }
-                }
-                unsigned todo = __ballot_sync(0xffffffffu, m != 0);
-                while (todo) {
-                    const int src = __ffs(todo) - 1;
-                    todo &= todo - 1;
-                    unsigned mk = __shfl_sync(0xffffffffu, m, src);
-                    const int jcl = base + src;
-                    any = true;
-                    const int s0 = jcl * kClusterSize + ty, s1 = s0 + 4;
-                    const T4 a0 = P::pos(p, s0), a1 = P::pos(p, s1);
-                    const int2 t0 = p.tf[s0], t1 = p.tf[s1];
-                    const T x0 = a0.x + Dx, y0 = a0.y + Dy, z0 = a0.z + Dz;
-                    const T x1 = a1.x + Dx, y1 = a1.y + Dy, z1 = a1.z + Dz;
-                    const T q0k = a0.w * kap, q1k = a1.w * kap;
-                    const int j0off = t0.x * (int)sizeof(C2), j1off = t1.x * (int)sizeof(C2);
-                    const int kdiag = self ? jcl - fc : -1;   // i-cluster equal to this j-cluster
-                    T fj0x = 0, fj0y = 0, fj0z = 0, fj1x = 0, fj1y = 0, fj1z = 0;
-                    while (mk) {
-                        const int k = __ffs(mk) - 1;
-                        mk &= mk - 1;
-                        const S4 xi = w.ix[k * kClusterSize + tx];
-                        const int2 ti = w.it[k * kClusterSize + tx];
-                        const bool dg = k == kdiag;
-                        S4 acc = w.fi[k * 32 + lane];
-                        pair<FP64, ENERGY>(xi, ti.x, ti.y, x0, y0, z0, a0.w, q0k, j0off, t0.y, !dg || gt0, lj_bytes,
-                                           kap, rc2, acc.x, acc.y, acc.z, fj0x, fj0y, fj0z, acc.w, npair, erc, irc);
-                        pair<FP64, ENERGY>(xi, ti.x, ti.y, x1, y1, z1, a1.w, q1k, j1off, t1.y, !dg || gt1, lj_bytes,
-                                           kap, rc2, acc.x, acc.y, acc.z, fj1x, fj1y, fj1z, acc.w, npair, erc, irc);
-                        w.fi[k * 32 + lane] = acc;
-                    }
-                    // j forces: sum over the 8 i-lanes of each ty group.  Lanes tx < 4 keep
-                    // atom ty (j0), lanes tx >= 4 atom ty + 4 (j1); then each lane holds one
-                    // component of one atom and issues one RED.
-                    {
-                        const bool up = tx >= 4;
-                        T ax = up ? fj1x : fj0x, ay = up ? fj1y : fj0y, az = up ? fj1z : fj0z;
-                        ax += __shfl_xor_sync(0xffffffffu, up ? fj0x : fj1x, 4);
-                        ay += __shfl_xor_sync(0xffffffffu, up ? fj0y : fj1y, 4);
-                        az += __shfl_xor_sync(0xffffffffu, up ? fj0z : fj1z, 4);
+            // j forces: sum over the 8 i-lanes of each ty group.  Lanes tx < 4 keep
+            // atom ty (j0), lanes tx >= 4 atom ty + 4 (j1); then each lane holds one
+            // component of one atom and issues one RED.
+            {
+                const bool up = tx >= 4;
+                T ax = up ? fj1x : fj0x, ay = up ? fj1y : fj0y, az = up ? fj1z : fj0z;
+                ax += __shfl_xor_sync(0xffffffffu, up ? fj0x : fj1x, 4);
+                ay += __shfl_xor_sync(0xffffffffu, up ? fj0y : fj1y, 4);
+                az += __shfl_xor_sync(0xffffffffu, up ? fj0z : fj1z, 4);
 #pragma unroll
-                        for (int o = 1; o < 4; o <<= 1) {
-                            ax += __shfl_xor_sync(0xffffffffu, ax, o);
-                            ay += __shfl_xor_sync(0xffffffffu, ay, o);
-                            az += __shfl_xor_sync(0xffffffffu, az, o);
-                        }
-                        const int comp = tx & 3;
-                        if (comp < 3) {
-                            const T v = comp == 0 ? ax : (comp == 1 ? ay : az);
-                            long long* dst = (comp == 0 ? p.fx : comp == 1 ? p.fy : p.fz) + (up ? s1 : s0);
-                            red_fix<FP64>(dst, v, p.err);
-                        }
-                    }
+                for (int o = 1; o < 4; o <<= 1) {
+                    ax += __shfl_xor_sync(0xffffffffu, ax, o);
+                    ay += __shfl_xor_sync(0xffffffffu, ay, o);
+                    az += __shfl_xor_sync(0xffffffffu, az, o);
+                }
+                const int comp = tx & 3;
+                if (comp < 3) {
+                    const T v3 = comp == 0 ? ax : (comp == 1 ? ay : az);
+                    long long* dst = (comp == 0 ? p.fx : comp == 1 ? p.fy : p.fz) + (up ? s1 : s0);
+                    red_fix<FP64>(dst, v3, p.err);
                 }
             }
-            if (!__any_sync(0xffffffffu, any)) continue;
-            __syncwarp();
-            // i forces of this (SC, cell): sum the 4 ty partials of each atom
-            for (int a = lane; a < ncl * kClusterSize; a += 32) {
-                const int k = a >> 3, t = a & 7;
-                S4 sum = w.fi[k * 32 + t];
+        }
+        __syncwarp();
+        // i forces of this chunk: sum the 4 ty partials of each atom
+        for (int a = lane; a < ncl * kClusterSize; a += 32) {
+            const int k = a >> 3, t = a & 7;
+            S4 sum = w.fi[k * 32 + t];
 #pragma unroll
-                for (int q = 1; q < 4; ++q) {
-                    const S4 v = w.fi[k * 32 + q * 8 + t];
-                    sum.x += v.x; sum.y += v.y; sum.z += v.z;
-                    if (ENERGY) sum.w += v.w;
-                }
-                const int slot = fc * kClusterSize + a;
-                red_fix<FP64>(p.fx + slot, sum.x, p.err);
-                red_fix<FP64>(p.fy + slot, sum.y, p.err);
-                red_fix<FP64>(p.fz + slot, sum.z, p.err);
-                if (ENERGY) red_fix<FP64>(p.epot + slot, sum.w, p.err);
+            for (int q = 1; q < 4; ++q) {
+                const S4 v = w.fi[k * 32 + q * 8 + t];
+                sum.x += v.x; sum.y += v.y; sum.z += v.z;
+                if (ENERGY) sum.w += v.w;
             }
-            __syncwarp();
-            if (ENERGY) {
+            const int slot = fc * kClusterSize + a;
+            red_fix<FP64>(p.fx + slot, sum.x, p.err);
+            red_fix<FP64>(p.fy + slot, sum.y, p.err);
+            red_fix<FP64>(p.fz + slot, sum.z, p.err);
+            if (ENERGY) red_fix<FP64>(p.epot + slot, sum.w, p.err);
+        }
+        __syncwarp();
+        if (ENERGY) {
 #pragma unroll
-                for (int o = 16; o; o >>= 1) npair += __shfl_xor_sync(0xffffffffu, npair, o);
-                if (lane == 0 && npair) atomicAdd((unsigned long long*)p.pair_count, (unsigned long long)npair);
-            }
+            for (int o = 16; o; o >>= 1) npair += __shfl_xor_sync(0xffffffffu, npair, o);
+            if (lane == 0 && npair) atomicAdd((unsigned long long*)p.pair_count, (unsigned long long)npair);
         }
     }
 }
@@ -359,25 +420,32 @@ static void set_smem_attr()
     static bool done = false;   // one per instantiation
     if (!done) {
         cudaFuncSetAttribute(k_pair<FP64, ENERGY>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_pair<FP64, ENERGY>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
         done = true;
     }
 }
 
 template <bool FP64, bool ENERGY>
-static void launch_one(const Params& p, cudaStream_t s, int blocks, int warps, int nsplit)
+static void launch_one(const Params& p, cudaStream_t s, int blocks, int warps)
 {
     set_smem_attr<FP64, ENERGY>();
-    k_pair<FP64, ENERGY><<<blocks, warps * 32, pair_smem<FP64>(p.n_ts, warps), s>>>(p, nsplit);
+    k_pair<FP64, ENERGY><<<blocks, warps * 32, pair_smem<FP64>(p.n_ts_lj, warps), s>>>(p);
 }
 
-void launch_pair(const Params& p, cudaStream_t s, bool energy, int blocks, int warps, int nsplit)
+void launch_pair_list(const Params& p, cudaStream_t s, int blocks)
+{
+    k_pair_list<<<blocks, kHalfShell * 32, 0, s>>>(p);
+}
+
+void launch_pair_forces(const Params& p, cudaStream_t s, bool energy, int blocks, int warps)
 {
     if (p.precision == 0) {
-        if (energy) launch_one<false, true>(p, s, blocks, warps, nsplit);
-        else launch_one<false, false>(p, s, blocks, warps, nsplit);
+        if (energy) launch_one<false, true>(p, s, blocks, warps);
+        else launch_one<false, false>(p, s, blocks, warps);
     } else {
-        if (energy) launch_one<true, true>(p, s, blocks, warps, nsplit);
-        else launch_one<true, false>(p, s, blocks, warps, nsplit);
+        if (energy) launch_one<true, true>(p, s, blocks, warps);
+        else launch_one<true, false>(p, s, blocks, warps);
     }
 }
 

@@ -164,6 +164,9 @@ __global__ void __launch_bounds__(kStepThreads) k_step_a(Params p, int mode)
     __shared__ long long s_acc[kRepWindow][6];
     __shared__ unsigned long long s_bmin[kRepWindow][3], s_bmax[kRepWindow][3];
     __shared__ int s_last;
+    // a cluster-pair list overflow freezes the state at the step whose forces
+    // are missing; the host grows the list, recomputes them and resumes
+    if (*p.err & ERR_LIST) return;
     const int tid = threadIdx.x;
     for (int k = tid; k < kRepWindow * 6; k += blockDim.x) (&s_acc[0][0])[k] = 0;
     for (int k = tid; k < kRepWindow * 3; k += blockDim.x) {

@@ -18,9 +18,9 @@ using namespace mdg;
 struct md_handle {
     md_config cfg{};
     std::string err;
-    int N = 0, R = 0, NS = 0, NTS = 0, NTE = 0;
+    int N = 0, R = 0, NS = 0, NTS = 0, NTS_LJ = 0, NTE = 0;
     int n_sm = 0;
-    std::vector<int> z, ts_off, rep_off;
+    std::vector<int> z, ts_off, lj_ts_off, rep_off;
     std::vector<Grid> grid0;
     Params P{};
     std::vector<void*> allocs;
@@ -29,7 +29,7 @@ struct md_handle {
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t ev_pair0 = nullptr, ev_pair1 = nullptr;
     int grid_atoms = 1, grid_cells = 1;
-    int pair_blocks = 1, pair_warps = 8, pair_nsplit = kSubItems;
+    int pair_blocks = 1, pair_warps = 8, list_blocks = 1;
     long long host_step = 0;
     bool poisoned = false;
     unsigned* h_err = nullptr;           // pinned
@@ -130,12 +130,14 @@ md_status check_device_flags(md_handle* h)
     return fail(h, MD_ERR_CUDA, "unknown device error flag");
 }
 
-// Cell list + forces at the current positions/charges (no time advance).
+// Cell list + cluster-pair list + forces at the current positions/charges
+// (no time advance).
 void enqueue_rebuild(md_handle* h, cudaStream_t s, bool energy)
 {
     launch_step_a(h->P, 0, s, h->grid_atoms);
     launch_cells(h->P, s, h->grid_atoms, h->grid_cells);
-    launch_pair(h->P, s, energy, h->pair_blocks, h->pair_warps, h->pair_nsplit);
+    launch_pair_list(h->P, s, h->list_blocks);
+    launch_pair_forces(h->P, s, energy, h->pair_blocks, h->pair_warps);
 }
 
 void enqueue_step(md_handle* h, cudaStream_t s)
@@ -143,10 +145,69 @@ void enqueue_step(md_handle* h, cudaStream_t s)
     int mode = STEP_KICK_DRIFT | STEP_ADVANCE | (h->cfg.cr_enabled ? STEP_CR : 0);
     launch_step_a(h->P, mode, s, h->grid_atoms);
     launch_cells(h->P, s, h->grid_atoms, h->grid_cells);
+    launch_pair_list(h->P, s, h->list_blocks);
     // external event nodes: the events are recorded on every graph replay
     if (h->cfg.profile) cudaEventRecordWithFlags(h->ev_pair0, s, cudaEventRecordExternal);
-    launch_pair(h->P, s, false, h->pair_blocks, h->pair_warps, h->pair_nsplit);
+    launch_pair_forces(h->P, s, false, h->pair_blocks, h->pair_warps);
     if (h->cfg.profile) cudaEventRecordWithFlags(h->ev_pair1, s, cudaEventRecordExternal);
+}
+
+// Device error flags without acting on them.
+md_status read_flags(md_handle* h, unsigned* e)
+{
+    CU(cudaMemcpyAsync(h->h_err, h->P.err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    *e = *h->h_err;
+    return MD_OK;
+}
+
+void dfree(md_handle* h, void* ptr)
+{
+    for (size_t k = 0; k < h->allocs.size(); ++k)
+        if (h->allocs[k] == ptr) {
+            h->allocs.erase(h->allocs.begin() + (long)k);
+            break;
+        }
+    if (h->cfg.dev_free) h->cfg.dev_free(ptr, h->cfg.alloc_ctx);
+    else cudaFree(ptr);
+}
+
+// (Re)size the cluster-pair list for `entries` entries.
+md_status size_list(md_handle* h, long long entries)
+{
+    Params& P = h->P;
+    if (entries > (1LL << 30)) return fail(h, MD_ERR_INVALID_ARG, "cluster-pair list too large");
+    if (P.pl) dfree(h, P.pl);
+    if (P.pl_chunk) dfree(h, P.pl_chunk);
+    P.pl = nullptr;
+    P.pl_chunk = nullptr;
+    P.pl_cap = (int)entries;
+    P.chunk_cap = P.sc_cap + P.pl_cap / kChunk + 1;
+    md_status st = dalloc(h, &P.pl, (size_t)P.pl_cap);
+    if (st != MD_OK) return st;
+    return dalloc(h, &P.pl_chunk, (size_t)P.chunk_cap);
+}
+
+// Rebuild at the current state.  A cluster-pair list overflow (the system got
+// denser) grows the list to twice the entries needed and rebuilds.
+md_status rebuild_checked(md_handle* h, bool* grown)
+{
+    if (grown) *grown = false;
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        enqueue_rebuild(h, h->stream, false);
+        CU(cudaGetLastError());
+        unsigned e = 0;
+        md_status st = read_flags(h, &e);
+        if (st != MD_OK) return st;
+        if (e != ERR_LIST) return check_device_flags(h);
+        int need[2] = {0, 0};
+        CU(cudaMemcpy(need, h->P.counters + 6, sizeof(need), cudaMemcpyDeviceToHost));
+        st = size_list(h, std::max<long long>(2LL * need[0], 2LL * h->P.pl_cap));
+        if (st != MD_OK) return st;
+        CU(cudaMemset(h->P.err, 0, sizeof(unsigned)));
+        if (grown) *grown = true;
+    }
+    return fail(h, MD_ERR_CELL_OVERFLOW, "cluster-pair list could not be sized");
 }
 
 md_status capture_graph(md_handle* h)
@@ -174,30 +235,27 @@ md_status autotune(md_handle* h)
     CU(cudaEventCreate(&a));
     CU(cudaEventCreate(&b));
     float best = 1e30f;
-    int bw = h->pair_warps, bb = h->pair_blocks, bn = h->pair_nsplit;
+    int bw = h->pair_warps, bb = h->pair_blocks;
     const int warps_c[] = {4, 8};
-    const int split_c[] = {4, 7, 14, 28, 56};
     for (int w : warps_c) {
-        int maxb = pair_max_blocks_per_sm(fp64, false, w, h->NTS);
+        int maxb = pair_max_blocks_per_sm(fp64, false, w, h->NTS_LJ);
         for (int bps = 1; bps <= maxb; ++bps) {
-            for (int ns : split_c) {
-                int blocks = bps * h->n_sm;
-                float tot = 0.0f;
-                for (int rep = 0; rep < 3; ++rep) {
-                    // reset the work counter only (forces are rebuilt afterwards)
-                    CU(cudaMemsetAsync(h->P.counters + 2, 0, sizeof(int), h->stream));
-                    CU(cudaEventRecord(a, h->stream));
-                    launch_pair(h->P, h->stream, false, blocks, w, ns);
-                    CU(cudaEventRecord(b, h->stream));
-                    CU(cudaEventSynchronize(b));
-                    float ms = 0.0f;
-                    CU(cudaEventElapsedTime(&ms, a, b));
-                    if (rep) tot += ms;
-                }
-                if (tot < best) {
-                    best = tot;
-                    bw = w; bb = blocks; bn = ns;
-                }
+            int blocks = bps * h->n_sm;
+            float tot = 0.0f;
+            for (int rep = 0; rep < 4; ++rep) {
+                // reset the work counter only (the list stays; forces are rebuilt afterwards)
+                CU(cudaMemsetAsync(h->P.counters + 2, 0, sizeof(int), h->stream));
+                CU(cudaEventRecord(a, h->stream));
+                launch_pair_forces(h->P, h->stream, false, blocks, w);
+                CU(cudaEventRecord(b, h->stream));
+                CU(cudaEventSynchronize(b));
+                float ms = 0.0f;
+                CU(cudaEventElapsedTime(&ms, a, b));
+                if (rep) tot += ms;
+            }
+            if (tot < best) {
+                best = tot;
+                bw = w; bb = blocks;
             }
         }
     }
@@ -205,7 +263,6 @@ md_status autotune(md_handle* h)
     cudaEventDestroy(b);
     h->pair_warps = bw;
     h->pair_blocks = bb;
-    h->pair_nsplit = bn;
     return MD_OK;
 }
 
@@ -340,23 +397,36 @@ static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* 
     for (int s = 0; s < h->NS; ++s) h->ts_off[s + 1] = h->ts_off[s] + h->z[s] + 1;
     const int nts = h->NTS = h->ts_off[h->NS];
     // LJ per pair of type states: sigma scaled by (1 - q/Z) (Eq. 11), arithmetic-mean
-    // sigma and geometric-mean epsilon, c6 = 4 eps s^6, c12 = c6 s^6
-    std::vector<double> sig_ts(nts), eps_ts(nts);
+    // sigma and geometric-mean epsilon, c6 = 4 eps s^6, c12 = c6 s^6.  The pair
+    // table covers only the species present in the system (it is staged in shared
+    // memory by the pair kernel); absent species map to row 0 and are never read.
+    std::vector<char> present(h->NS, 0);
+    for (int i = 0; i < sys->n_atoms; ++i) present[sys->species[i]] = 1;
+    h->lj_ts_off.assign(h->NS, 0);
+    int nts_lj = 0;
     for (int s = 0; s < h->NS; ++s)
-        for (int q = 0; q <= h->z[s]; ++q) {
-            sig_ts[h->ts_off[s] + q] = c.lj_sigma0[s] * (1.0 - (double)q / (double)h->z[s]);
-            eps_ts[h->ts_off[s] + q] = c.lj_eps0[s];
+        if (present[s]) {
+            h->lj_ts_off[s] = nts_lj;
+            nts_lj += h->z[s] + 1;
         }
-    std::vector<double2> lj_d((size_t)nts * nts);
-    std::vector<float2> lj_f((size_t)nts * nts);
-    for (int a = 0; a < nts; ++a)
-        for (int b = 0; b < nts; ++b) {
+    h->NTS_LJ = nts_lj;
+    std::vector<double> sig_ts(nts_lj), eps_ts(nts_lj);
+    for (int s = 0; s < h->NS; ++s)
+        if (present[s])
+            for (int q = 0; q <= h->z[s]; ++q) {
+                sig_ts[h->lj_ts_off[s] + q] = c.lj_sigma0[s] * (1.0 - (double)q / (double)h->z[s]);
+                eps_ts[h->lj_ts_off[s] + q] = c.lj_eps0[s];
+            }
+    std::vector<double2> lj_d((size_t)nts_lj * nts_lj);
+    std::vector<float2> lj_f((size_t)nts_lj * nts_lj);
+    for (int a = 0; a < nts_lj; ++a)
+        for (int b = 0; b < nts_lj; ++b) {
             double sg = 0.5 * (sig_ts[a] + sig_ts[b]);
             double ep = std::sqrt(eps_ts[a] * eps_ts[b]);
             double s6 = sg * sg * sg * sg * sg * sg;
             double c6 = 4.0 * ep * s6, c12 = c6 * s6;
-            lj_d[(size_t)a * nts + b] = make_double2(c6, c12);
-            lj_f[(size_t)a * nts + b] = make_float2((float)c6, (float)c12);
+            lj_d[(size_t)a * nts_lj + b] = make_double2(-c6, c12);   // pair kernels take (-c6, c12)
+            lj_f[(size_t)a * nts_lj + b] = make_float2(-(float)c6, (float)c12);
         }
     std::vector<double> etab(kNEtab), inv12(13, 0.0);
     for (int k = 0; k < kNEtab; ++k) etab[k] = std::exp(-(double)k / 16.0);
@@ -424,6 +494,7 @@ static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* 
     // ---- device memory ----
     Params& P = h->P;
     P.n_atoms = h->N; P.n_rep = h->R; P.n_species = h->NS; P.n_ts = nts; P.n_te = h->NTE;
+    P.n_ts_lj = h->NTS_LJ;
     P.max_steps = c.max_steps;
     P.cell_cap_total = C;
     P.slot_cap = (int)slot_cap;
@@ -443,16 +514,16 @@ static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* 
     DALLOC(P.frag, N); DALLOC(P.rep, N); DALLOC(P.local_id, N); DALLOC(P.slot_of, N);
     DALLOC(P.atom_cell, N); DALLOC(P.atom_rank, N);
     double *d_hdtm, *d_mass, *d_auger, *d_sigma, *d_kci, *d_krec, *d_etab, *d_inv;
-    int *d_z, *d_tsoff;
+    int *d_z, *d_tsoff, *d_ljtsoff;
     long long *d_ip, *d_epi, *d_eaug;
     float2* d_ljf;
     double2* d_ljd;
-    DALLOC(d_hdtm, NS); DALLOC(d_mass, NS); DALLOC(d_z, NS); DALLOC(d_tsoff, NS + 1); DALLOC(d_auger, NS);
+    DALLOC(d_hdtm, NS); DALLOC(d_mass, NS); DALLOC(d_z, NS); DALLOC(d_tsoff, NS + 1); DALLOC(d_ljtsoff, NS); DALLOC(d_auger, NS);
     DALLOC(d_sigma, 2 * nts); DALLOC(d_kci, (size_t)nts * h->NTE); DALLOC(d_krec, (size_t)nts * h->NTE);
     DALLOC(d_ip, nts); DALLOC(d_epi, 2 * nts); DALLOC(d_eaug, NS);
     DALLOC(d_etab, kNEtab); DALLOC(d_inv, 13);
-    DALLOC(d_ljf, (size_t)nts * nts); DALLOC(d_ljd, (size_t)nts * nts);
-    P.hdtm = d_hdtm; P.mass = d_mass; P.zs = d_z; P.ts_off = d_tsoff; P.auger_dt = d_auger;
+    DALLOC(d_ljf, (size_t)nts_lj * nts_lj); DALLOC(d_ljd, (size_t)nts_lj * nts_lj);
+    P.hdtm = d_hdtm; P.mass = d_mass; P.zs = d_z; P.ts_off = d_tsoff; P.lj_ts_off = d_ljtsoff; P.auger_dt = d_auger;
     P.sigma_pi = d_sigma; P.k_ci = d_kci; P.k_rec = d_krec; P.ip_mev = d_ip; P.e_pi_mev = d_epi;
     P.e_auger_mev = d_eaug; P.etab = d_etab; P.inv12 = d_inv; P.lj_f = d_ljf; P.lj_d = d_ljd;
     unsigned long long* d_seed;
@@ -467,6 +538,12 @@ static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* 
     DALLOC(P.tmp_key, N);
     DALLOC(P.sc_cell, P.sc_cap); DALLOC(P.sc_first, P.sc_cap); DALLOC(P.sc_ncl, P.sc_cap);
     DALLOC(P.counters, 8);
+    P.pl = nullptr;
+    P.pl_chunk = nullptr;
+    {
+        md_status st0 = size_list(h, (long long)kListMinPerCluster * P.cluster_cap);
+        if (st0 != MD_OK) return st0;
+    }
     if (c.precision == MD_PREC_MIXED) { DALLOC(P.xq, P.slot_cap); P.xq64 = nullptr; }
     else { DALLOC(P.xq64, P.slot_cap); P.xq = nullptr; }
     DALLOC(P.tf, P.slot_cap); DALLOC(P.atom_of, P.slot_cap);
@@ -523,6 +600,7 @@ static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* 
         CU(cudaMemcpy(d_mass, mass.data(), NS * sizeof(double), cudaMemcpyHostToDevice));
         CU(cudaMemcpy(d_z, h->z.data(), NS * sizeof(int), cudaMemcpyHostToDevice));
         CU(cudaMemcpy(d_tsoff, h->ts_off.data(), (NS + 1) * sizeof(int), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(d_ljtsoff, h->lj_ts_off.data(), NS * sizeof(int), cudaMemcpyHostToDevice));
         CU(cudaMemcpy(d_auger, auger_dt.data(), NS * sizeof(double), cudaMemcpyHostToDevice));
         CU(cudaMemcpy(d_sigma, c.sigma_pi, 2 * nts * sizeof(double), cudaMemcpyHostToDevice));
         CU(cudaMemcpy(d_kci, c.k_ci, (size_t)nts * h->NTE * sizeof(double), cudaMemcpyHostToDevice));
@@ -555,20 +633,28 @@ static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* 
     h->grid_atoms = (N + 255) / 256;
     h->grid_cells = std::max(1, std::min(C, h->n_sm * 8));
     h->pair_warps = 8;
-    h->pair_nsplit = kSubItems;
-    h->pair_blocks = h->n_sm * pair_max_blocks_per_sm(c.precision == MD_PREC_FP64, false, 8, nts);
+    h->pair_blocks = h->n_sm * pair_max_blocks_per_sm(c.precision == MD_PREC_FP64, false, 8, h->NTS_LJ);
+    h->list_blocks = std::max(1, std::min(P.sc_cap, 4 * h->n_sm));
     CU(cudaDeviceSynchronize());
 
-    // ---- initial cell list and forces F_0 ----
-    enqueue_rebuild(h, h->stream, false);
-    CU(cudaGetLastError());
-    md_status st = check_device_flags(h);
+    // ---- initial cell list, cluster-pair list and forces F_0 ----
+    md_status st = rebuild_checked(h, nullptr);
     if (st != MD_OK) return st;
+    {
+        // headroom: twice the entries the initial configuration needs
+        int need = 0;
+        CU(cudaMemcpy(&need, P.counters + 6, sizeof(int), cudaMemcpyDeviceToHost));
+        if (2LL * need > P.pl_cap) {
+            st = size_list(h, 2LL * need);
+            if (st != MD_OK) return st;
+            st = rebuild_checked(h, nullptr);
+            if (st != MD_OK) return st;
+        }
+    }
     if (c.autotune) {
         st = autotune(h);
         if (st != MD_OK) return st;
-        enqueue_rebuild(h, h->stream, false);
-        st = check_device_flags(h);
+        st = rebuild_checked(h, nullptr);
         if (st != MD_OK) return st;
     }
     return capture_graph(h);
@@ -686,19 +772,44 @@ md_status md_step(md_handle* h, int n_steps)
     if (h->host_step + n_steps > h->cfg.max_steps)
         return fail(h, MD_ERR_TABLE_END, "step " + std::to_string(h->host_step + n_steps) +
                                              " is past max_steps = " + std::to_string(h->cfg.max_steps));
-    for (int k = 0; k < n_steps; ++k) {
-        CU(cudaGraphLaunch(h->exec, h->stream));
-        if (h->cfg.profile) {
-            CU(cudaEventSynchronize(h->ev_pair1));
-            float ms = 0.0f;
-            CU(cudaEventElapsedTime(&ms, h->ev_pair0, h->ev_pair1));
-            h->pair_ms += ms;
-            h->pair_launches += 1;
+    int done = 0;
+    while (done < n_steps) {
+        const int todo = n_steps - done;
+        for (int k = 0; k < todo; ++k) {
+            CU(cudaGraphLaunch(h->exec, h->stream));
+            if (h->cfg.profile) {
+                CU(cudaEventSynchronize(h->ev_pair1));
+                float ms = 0.0f;
+                CU(cudaEventElapsedTime(&ms, h->ev_pair0, h->ev_pair1));
+                h->pair_ms += ms;
+                h->pair_launches += 1;
+            }
         }
+        unsigned e = 0;
+        md_status st = read_flags(h, &e);
+        if (st != MD_OK) return st;
+        if (e != ERR_LIST) {
+            h->host_step += todo;
+            h->steps += todo;
+            return check_device_flags(h);
+        }
+        // The list of some step overflowed: the state stopped after that step's
+        // kick, drift and charge update.  Grow the list, compute its forces, go on.
+        long long dstep = 0;
+        CU(cudaMemcpy(&dstep, h->P.step, sizeof(long long), cudaMemcpyDeviceToHost));
+        const int adv = (int)(dstep - h->host_step);
+        if (adv < 1 || adv > todo) return fail(h, MD_ERR_CUDA, "inconsistent step counter after a list overflow");
+        h->host_step = dstep;
+        h->steps += adv;
+        done += adv;
+        CU(cudaMemset(h->P.err, 0, sizeof(unsigned)));
+        bool grown = false;
+        st = rebuild_checked(h, &grown);
+        if (st != MD_OK) return st;
+        st = capture_graph(h);
+        if (st != MD_OK) return st;
     }
-    h->host_step += n_steps;
-    h->steps += n_steps;
-    return check_device_flags(h);
+    return MD_OK;
 }
 
 md_status md_get_state(md_handle* h, md_state* out, unsigned fields)
@@ -827,9 +938,10 @@ md_status md_set_state(md_handle* h, const md_state* in, unsigned fields)
     CU(cudaMemset(h->P.kick_full, 0, sizeof(int)));
     CU(cudaMemset(h->P.err, 0, sizeof(unsigned)));
     h->poisoned = false;
-    enqueue_rebuild(h, h->stream, false);
-    CU(cudaGetLastError());
-    return check_device_flags(h);
+    bool grown = false;
+    md_status st = rebuild_checked(h, &grown);
+    if (st != MD_OK) return st;
+    return grown ? capture_graph(h) : MD_OK;
 }
 
 md_status md_get_energies(md_handle* h, double* e_kin, double* e_pot, int64_t* n_pairs)
@@ -840,7 +952,8 @@ md_status md_get_energies(md_handle* h, double* e_kin, double* e_pot, int64_t* n
     CU(cudaMemsetAsync(h->P.pair_count, 0, sizeof(long long), h->stream));
     // same cell list and decomposition -> the forces come out bit-identical
     launch_cells(h->P, h->stream, h->grid_atoms, h->grid_cells);
-    launch_pair(h->P, h->stream, true, h->pair_blocks, h->pair_warps, h->pair_nsplit);
+    launch_pair_list(h->P, h->stream, h->list_blocks);
+    launch_pair_forces(h->P, h->stream, true, h->pair_blocks, h->pair_warps);
     launch_energy(h->P, h->d_ekin, h->d_epot, h->stream);
     CU(cudaGetLastError());
     std::vector<double> ek(R);

@@ -15,8 +15,8 @@ namespace mdg {
 constexpr int kClusterSize = 8;
 constexpr int kSuperClusters = 8;     // K_SC
 constexpr int kHalfShell = 14;        // self cell + 13 neighbour cells
-constexpr int kJParts = 4;                 // a neighbour cell's j-cluster range is cut in 4
-constexpr int kSubItems = kJParts * kHalfShell;   // (cell, part of its j range) per super-cluster
+constexpr int kChunk = 8;             // cluster-pair list entries per force work item
+constexpr int kListMinPerCluster = 32;   // initial pair-list entries per cluster
 constexpr int kMaxSpecies = 8;
 constexpr int kMaxTS = 128;
 constexpr int kNEtab = 16 * 40;       // e^{-k/16} table, lambda < 40
@@ -33,6 +33,7 @@ enum : unsigned {
     ERR_NONFINITE = 2u,
     ERR_CELL = 4u,
     ERR_TABLE_END = 8u,
+    ERR_LIST = 16u,             // cluster-pair list capacity exceeded
 };
 
 struct Grid {                // cell grid of one replica (rebuilt every step)
@@ -72,6 +73,7 @@ struct RepAccum {            // per-step sums of one replica
 // Everything a kernel may touch.  Passed by value.
 struct Params {
     int n_atoms, n_rep, n_species, n_ts, n_te, max_steps;
+    int n_ts_lj;             // type states of the species present (LJ table side)
     int cell_cap_total, slot_cap, cluster_cap, sc_cap;
     int precision, cr_enabled, plasma_mode;
     double dt, r_cut, rc2, kappa_fixed, te_floor, four_pi_f, coulomb_f, inv_dte;
@@ -87,6 +89,7 @@ struct Params {
     const double* mass;      // [n_species]
     const int* zs;           // [n_species]
     const int* ts_off;       // [n_species + 1]
+    const int* lj_ts_off;    // [n_species] LJ table row of (species, q = 0)
     const double* auger_dt;  // [n_species]
     const double* sigma_pi;  // [n_ts][2]
     const double* k_ci;      // [n_ts][n_te]
@@ -96,8 +99,8 @@ struct Params {
     const long long* e_auger_mev;// [n_species]
     const double* etab;      // [kNEtab]
     const double* inv12;     // [13] 1/m
-    const float2* lj_f;      // [n_ts][n_ts] (c6, c12)
-    const double2* lj_d;
+    const float2* lj_f;      // [n_ts_lj][n_ts_lj] (-c6, c12)
+    const double2* lj_d;     // [n_ts_lj][n_ts_lj] (-c6, c12)
 
     // replicas
     Grid* grid;
@@ -118,7 +121,10 @@ struct Params {
     int* sc_cell;            // [sc_cap]
     int* sc_first;           // [sc_cap] first cluster
     int* sc_ncl;             // [sc_cap] clusters in the super-cluster
-    int* counters;           // [0] n_sc, [1] n_slots, [2] work, [3] ticket, [4] ticket2
+    int* counters;           // [0] n_sc, [1] n_slots, [2] work, [3] ticket, [6] list entries, [7] chunks
+    uint2* pl;               // [pl_cap] cluster-pair list: (j-cluster, half-shell index << 8 | i mask)
+    int4* pl_chunk;          // [chunk_cap] (SC, first entry, entries, replica)
+    int pl_cap, chunk_cap;
 
     // packed, cell-sorted arrays (slot order)
     float4* xq;              // (x, y, z) relative to the cell centre, q
@@ -175,7 +181,8 @@ __host__ __device__ __forceinline__ void half_shell(int nb, int& dx, int& dy, in
 // Launch helpers implemented in the .cu files.
 void launch_step_a(const Params& p, int mode, cudaStream_t s, int grid_atoms);
 void launch_cells(const Params& p, cudaStream_t s, int grid_atoms, int grid_cells);
-void launch_pair(const Params& p, cudaStream_t s, bool energy, int blocks, int warps, int nsplit);
+void launch_pair_list(const Params& p, cudaStream_t s, int blocks);
+void launch_pair_forces(const Params& p, cudaStream_t s, bool energy, int blocks, int warps);
 void launch_velocity_out(const Params& p, double* d_v_out, cudaStream_t s);
 void launch_energy(const Params& p, double* d_ekin, long long* d_epot, cudaStream_t s);
 void launch_philox(unsigned long long seed, const uint32_t* ctr, long long n, uint32_t* out,

@@ -31,6 +31,8 @@ constexpr int kNaMax = MD_NOALLOC_MAX_ATOMS;
 constexpr int kNcMax = MD_NOALLOC_MAX_CELLS;
 constexpr int kSlotCap = kNaMax + 7 * kNcMax + 8;
 constexpr int kClusterCap = kSlotCap / kClusterSize + 1;
+constexpr int kPlCap = 48 * kClusterCap;                  // cluster-pair list entries
+constexpr int kChunkCap = kClusterCap + kPlCap / kChunk + 1;
 constexpr int kTabMax = MD_MAX_TYPE_STATES * MD_MAX_TYPE_STATES;
 
 constexpr size_t align256(size_t b) { return (b + 255) / 256 * 256; }
@@ -41,6 +43,7 @@ struct Layout {
     size_t zs, ts_off, hdtm, mass, auger, volume, rep_off, lj;
     size_t grid, rs, acc, cell_count, cell_start, cell_pstart, tmp_key, sc_cell, sc_first, sc_ncl;
     size_t counters, xq, tf, atom_of, bb_lo, bb_hi, bb_frag, fx, fy, fz, epot, pair_count, err, step, kick;
+    size_t pl, pl_chunk;
     size_t total;
 };
 
@@ -70,6 +73,7 @@ constexpr Layout make_layout()
     L.fx = take(8 * (size_t)kSlotCap); L.fy = take(8 * (size_t)kSlotCap); L.fz = take(8 * (size_t)kSlotCap);
     L.epot = take(8 * (size_t)kSlotCap);
     L.pair_count = take(8); L.err = take(4); L.step = take(8); L.kick = take(4);
+    L.pl = take(8 * (size_t)kPlCap); L.pl_chunk = take(16 * (size_t)kChunkCap);
     L.total = o;
     return L;
 }
@@ -196,7 +200,7 @@ extern "C" md_status md_forces_noalloc(const md_forces_input* in, double* d_f, v
     unsigned char* B = g_base[dev];
 
     Params P{};
-    P.n_atoms = n; P.n_rep = 1; P.n_species = in->n_species; P.n_ts = nts; P.n_te = 2; P.max_steps = 1;
+    P.n_atoms = n; P.n_rep = 1; P.n_species = in->n_species; P.n_ts = nts; P.n_ts_lj = nts; P.n_te = 2; P.max_steps = 1;
     P.cell_cap_total = g.cell_cap;
     P.slot_cap = n + 7 * g.cell_cap + 8;
     P.cluster_cap = P.slot_cap / kClusterSize + 1;
@@ -210,7 +214,7 @@ extern "C" md_status md_forces_noalloc(const md_forces_input* in, double* d_f, v
     P.species = B + kL.species; P.q = B + kL.q; P.h = B + kL.h;
     P.frag = (int*)(B + kL.frag); P.rep = (int*)(B + kL.rep); P.local_id = (int*)(B + kL.local_id);
     P.slot_of = (int*)(B + kL.slot_of); P.atom_cell = (int*)(B + kL.atom_cell); P.atom_rank = (int*)(B + kL.atom_rank);
-    P.zs = (const int*)(B + kL.zs); P.ts_off = (const int*)(B + kL.ts_off);
+    P.zs = (const int*)(B + kL.zs); P.ts_off = (const int*)(B + kL.ts_off); P.lj_ts_off = P.ts_off;
     P.hdtm = (const double*)(B + kL.hdtm); P.mass = (const double*)(B + kL.mass);
     P.auger_dt = (const double*)(B + kL.auger); P.volume = (const double*)(B + kL.volume);
     P.rep_off = (const int*)(B + kL.rep_off);
@@ -226,6 +230,8 @@ extern "C" md_status md_forces_noalloc(const md_forces_input* in, double* d_f, v
     P.fx = (long long*)(B + kL.fx); P.fy = (long long*)(B + kL.fy); P.fz = (long long*)(B + kL.fz);
     P.epot = (long long*)(B + kL.epot); P.pair_count = (long long*)(B + kL.pair_count);
     P.err = (unsigned*)(B + kL.err); P.step = (long long*)(B + kL.step); P.kick_full = (int*)(B + kL.kick);
+    P.pl = (uint2*)(B + kL.pl); P.pl_chunk = (int4*)(B + kL.pl_chunk);
+    P.pl_cap = kPlCap; P.chunk_cap = kChunkCap;
 
     // host-built tables: LJ per pair of type states (sigma scaled by 1 - q/Z,
     // arithmetic-mean sigma, geometric-mean epsilon), offsets, the grid
@@ -243,8 +249,8 @@ extern "C" md_status md_forces_noalloc(const md_forces_input* in, double* d_f, v
             const double ep = std::sqrt(eps[a] * eps[b]);
             const double s6 = sg * sg * sg * sg * sg * sg;
             const double c6 = 4.0 * ep * s6, c12 = c6 * s6;
-            tab_d[(size_t)a * nts + b] = make_double2(c6, c12);
-            tab_f[(size_t)a * nts + b] = make_float2((float)c6, (float)c12);
+            tab_d[(size_t)a * nts + b] = make_double2(-c6, c12);   // pair kernels take (-c6, c12)
+            tab_f[(size_t)a * nts + b] = make_float2(-(float)c6, (float)c12);
         }
     const int zs[MD_MAX_SPECIES] = {in->z[0], in->z[1], in->z[2], in->z[3], in->z[4], in->z[5], in->z[6], in->z[7]};
     const double one = 1.0;
@@ -273,7 +279,8 @@ extern "C" md_status md_forces_noalloc(const md_forces_input* in, double* d_f, v
     const int blocks = n_sm * pair_max_blocks_per_sm(in->precision == MD_PREC_FP64, false, warps, nts);
     launch_step_a(P, 0, s, (n + 255) / 256);                           // grid and screening
     launch_cells(P, s, (n + 255) / 256, std::max(1, std::min(g.cell_cap, n_sm * 8)));
-    launch_pair(P, s, false, blocks, warps, kSubItems);
+    launch_pair_list(P, s, std::max(1, std::min(P.sc_cap, 4 * n_sm)));
+    launch_pair_forces(P, s, false, blocks, warps);
     launch_force_out(P, d_f, s);
     NA_CU(cudaGetLastError());
     unsigned h_err = 0;
@@ -283,6 +290,7 @@ extern "C" md_status md_forces_noalloc(const md_forces_input* in, double* d_f, v
     if (h_err & ERR_OVERFLOW) return fail(MD_ERR_FIXED_OVERFLOW, "force beyond the 64-bit fixed-point range");
     if (h_err & ERR_NONFINITE) return fail(MD_ERR_NONFINITE, "non-finite input position");
     if (h_err & ERR_CELL) return fail(MD_ERR_CELL_OVERFLOW, "cell-list capacity exceeded");
+    if (h_err & ERR_LIST) return fail(MD_ERR_CELL_OVERFLOW, "cluster-pair list capacity exceeded");
     if (h_err) return fail(MD_ERR_CUDA, "unexpected device error flag");
     return MD_OK;
 }
