@@ -191,13 +191,16 @@ def run_gpu(args, rank, world, local):
         return g
 
     def timed_steps(g, k_steps):
+        # steps are enqueued without a host round trip (their status is read
+        # once at the end), so the events bracket the device work of each step
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(k_steps)]
         for k in range(k_steps):
             flush.zero_()                       # evict the 129 MB L2 between steps
             ev[k][0].record(stream)
-            g.step(1)
+            g.step(1, wait=False)
             ev[k][1].record(stream)
+        g.sync()
         torch.cuda.synchronize()
         return sum(a.elapsed_time(b) for a, b in ev)
 

@@ -118,6 +118,11 @@ typedef struct md_config {
     void* alloc_ctx;
     int autotune;            /* 1: time launch shapes at init and keep the fastest */
     int profile;             /* 1: time the pair kernel with CUDA events in md_step */
+    int list_reserve;        /* cluster-pair list entries per cluster allocated
+                                at init; 0: automatic (32, and at least twice
+                                what the initial configuration needs).  The
+                                list grows whenever a build needs more room
+                                (see md_step)                                  */
 } md_config;
 
 /*
@@ -186,6 +191,9 @@ typedef struct md_timing {
     int64_t pair_count_last; /* in-cutoff pairs of the last evaluated step (md_get_energies) */
     int tile_warps;          /* launch shape in use                         */
     int tile_blocks_per_sm;
+    int64_t list_capacity;   /* cluster-pair list entries allocated         */
+    int64_t list_entries;    /* entries the last list build used            */
+    int64_t list_grows;      /* times the list was enlarged on demand       */
 } md_timing;
 
 typedef struct md_handle md_handle;
@@ -224,6 +232,17 @@ md_status md_set_plasma_table(md_handle* h, int replica, const double* ne,
  * larger list from the start.  Errors: BAD_STATE, TABLE_END, FIXED_OVERFLOW,
  * NONFINITE, CELL_OVERFLOW, OOM, CUDA. */
 md_status md_step(md_handle* h, int n_steps);
+
+/* md_step without the final status read: enqueues n_steps timesteps on the
+ * handle's stream and returns.  Errors of those steps (and the list growth
+ * md_step describes) are handled by the next md_sync, md_step,
+ * md_get_state, md_set_state, md_get_energies or md_get_timing.  Errors:
+ * BAD_STATE, TABLE_END, INVALID_ARG, CUDA. */
+md_status md_step_async(md_handle* h, int n_steps);
+
+/* Wait for the steps enqueued by md_step_async and read their status
+ * (same errors as md_step). */
+md_status md_sync(md_handle* h);
 
 /* Copy the requested fields (MD_FIELD_* mask) to caller buffers, in the
  * original atom order.  Synchronises the handle's stream. */

@@ -27,10 +27,16 @@ struct md_handle {
     cudaStream_t stream = nullptr;       // caller's stream (NULL = legacy default)
     cudaStream_t cap_stream = nullptr;   // private stream used for graph capture
     cudaGraphExec_t exec = nullptr;
-    cudaEvent_t ev_pair0 = nullptr, ev_pair1 = nullptr;
+    cudaEvent_t ev_pair0 = nullptr, ev_pair1 = nullptr;   // captured into the graph
+    cudaGraph_t graph = nullptr;                          // kept for event-node updates
+    cudaGraphNode_t node_ev0 = nullptr, node_ev1 = nullptr;
+    std::vector<cudaEvent_t> prof_pool;                   // [2 * kProfPool] pair-kernel events
+    int prof_next = 0;                                    // pairs in flight
+    long long list_grows = 0;
     int grid_atoms = 1, grid_cells = 1;
     int pair_blocks = 1, pair_warps = 8, list_blocks = 1;
-    long long host_step = 0;
+    long long host_step = 0;             // steps enqueued
+    long long pending = 0;               // enqueued steps whose status is not read yet
     bool poisoned = false;
     unsigned* h_err = nullptr;           // pinned
     double pair_ms = 0.0;
@@ -41,6 +47,8 @@ struct md_handle {
 };
 
 namespace {
+
+constexpr int kProfPool = 256;   // pair-kernel event pairs in flight (profile mode)
 
 thread_local std::string g_init_error;
 
@@ -205,6 +213,7 @@ md_status rebuild_checked(md_handle* h, bool* grown)
         st = size_list(h, std::max<long long>(2LL * need[0], 2LL * h->P.pl_cap));
         if (st != MD_OK) return st;
         CU(cudaMemset(h->P.err, 0, sizeof(unsigned)));
+        h->list_grows += 1;
         if (grown) *grown = true;
     }
     return fail(h, MD_ERR_CELL_OVERFLOW, "cluster-pair list could not be sized");
@@ -216,13 +225,49 @@ md_status capture_graph(md_handle* h)
         cudaGraphExecDestroy(h->exec);
         h->exec = nullptr;
     }
-    cudaGraph_t graph = nullptr;
+    if (h->graph) {
+        cudaGraphDestroy(h->graph);
+        h->graph = nullptr;
+    }
     CU(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
     enqueue_step(h, h->cap_stream);
-    CU(cudaStreamEndCapture(h->cap_stream, &graph));
-    cudaError_t e = cudaGraphInstantiate(&h->exec, graph, 0);
-    cudaGraphDestroy(graph);
+    CU(cudaStreamEndCapture(h->cap_stream, &h->graph));
+    if (h->cfg.profile) {
+        // the two event-record nodes around the pair kernel: each launch points
+        // them at a fresh pair of events from the pool
+        size_t n = 0;
+        CU(cudaGraphGetNodes(h->graph, nullptr, &n));
+        std::vector<cudaGraphNode_t> nodes(n);
+        CU(cudaGraphGetNodes(h->graph, nodes.data(), &n));
+        h->node_ev0 = h->node_ev1 = nullptr;
+        for (cudaGraphNode_t nd : nodes) {
+            cudaGraphNodeType t;
+            CU(cudaGraphNodeGetType(nd, &t));
+            if (t != cudaGraphNodeTypeEventRecord) continue;
+            cudaEvent_t ev = nullptr;
+            CU(cudaGraphEventRecordNodeGetEvent(nd, &ev));
+            if (ev == h->ev_pair0) h->node_ev0 = nd;
+            if (ev == h->ev_pair1) h->node_ev1 = nd;
+        }
+        if (!h->node_ev0 || !h->node_ev1) return fail(h, MD_ERR_CUDA, "profile event nodes not found in the step graph");
+    }
+    cudaError_t e = cudaGraphInstantiate(&h->exec, h->graph, 0);
     if (e != cudaSuccess) return fail(h, MD_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    return MD_OK;
+}
+
+// Pair-kernel times of the launched steps (profile mode).
+md_status drain_profile(md_handle* h)
+{
+    if (h->prof_next == 0) return MD_OK;
+    CU(cudaEventSynchronize(h->prof_pool[2 * (h->prof_next - 1) + 1]));
+    for (int k = 0; k < h->prof_next; ++k) {
+        float ms = 0.0f;
+        CU(cudaEventElapsedTime(&ms, h->prof_pool[2 * k], h->prof_pool[2 * k + 1]));
+        h->pair_ms += ms;
+    }
+    h->pair_launches += h->prof_next;
+    h->prof_next = 0;
     return MD_OK;
 }
 
@@ -295,6 +340,8 @@ md_status validate(const md_config* c, const md_system* s)
         return fail(h, MD_ERR_INVALID_ARG, "CR tables missing");
     if ((c->dev_alloc == nullptr) != (c->dev_free == nullptr))
         return fail(h, MD_ERR_INVALID_ARG, "dev_alloc and dev_free must be given together");
+    if (c->list_reserve < 0 || c->list_reserve > 4096)
+        return fail(h, MD_ERR_INVALID_ARG, "list_reserve must be in [0, 4096]");
     if (s->n_atoms < 1) return fail(h, MD_ERR_INVALID_ARG, "n_atoms must be >= 1");
     if (!s->x || !s->v || !s->species || !s->fragment || !s->replica_offset || !s->seed || !s->box ||
         !s->volume)
@@ -389,6 +436,10 @@ static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* 
     CU(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
     CU(cudaEventCreate(&h->ev_pair0));
     CU(cudaEventCreate(&h->ev_pair1));
+    if (c.profile) {
+        h->prof_pool.assign(2 * kProfPool, nullptr);
+        for (cudaEvent_t& ev : h->prof_pool) CU(cudaEventCreate(&ev));
+    }
     CU(cudaMallocHost(&h->h_err, sizeof(unsigned)));
 
     // ---- type states and tables ----
@@ -541,7 +592,8 @@ static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* 
     P.pl = nullptr;
     P.pl_chunk = nullptr;
     {
-        md_status st0 = size_list(h, (long long)kListMinPerCluster * P.cluster_cap);
+        const int reserve = c.list_reserve > 0 ? c.list_reserve : kListMinPerCluster;
+        md_status st0 = size_list(h, (long long)reserve * P.cluster_cap);
         if (st0 != MD_OK) return st0;
     }
     if (c.precision == MD_PREC_MIXED) { DALLOC(P.xq, P.slot_cap); P.xq64 = nullptr; }
@@ -640,7 +692,7 @@ static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* 
     // ---- initial cell list, cluster-pair list and forces F_0 ----
     md_status st = rebuild_checked(h, nullptr);
     if (st != MD_OK) return st;
-    {
+    if (c.list_reserve == 0) {
         // headroom: twice the entries the initial configuration needs
         int need = 0;
         CU(cudaMemcpy(&need, P.counters + 6, sizeof(int), cudaMemcpyDeviceToHost));
@@ -671,6 +723,9 @@ void md_finalize(md_handle* h)
     }
     if (h->ev_pair0) cudaEventDestroy(h->ev_pair0);
     if (h->ev_pair1) cudaEventDestroy(h->ev_pair1);
+    for (cudaEvent_t ev : h->prof_pool)
+        if (ev) cudaEventDestroy(ev);
+    if (h->graph) cudaGraphDestroy(h->graph);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->h_err) cudaFreeHost(h->h_err);
     delete h;
@@ -764,7 +819,30 @@ md_status md_set_plasma_table(md_handle* h, int replica, const double* ne, const
     return MD_OK;
 }
 
-md_status md_step(md_handle* h, int n_steps)
+namespace {
+
+md_status launch_steps(md_handle* h, int n)
+{
+    for (int k = 0; k < n; ++k) {
+        if (h->cfg.profile) {
+            if (h->prof_next == kProfPool) {
+                md_status st = drain_profile(h);
+                if (st != MD_OK) return st;
+            }
+            const int j = h->prof_next++;
+            CU(cudaGraphExecEventRecordNodeSetEvent(h->exec, h->node_ev0, h->prof_pool[2 * j]));
+            CU(cudaGraphExecEventRecordNodeSetEvent(h->exec, h->node_ev1, h->prof_pool[2 * j + 1]));
+        }
+        CU(cudaGraphLaunch(h->exec, h->stream));
+    }
+    h->host_step += n;
+    h->pending += n;
+    return MD_OK;
+}
+
+}  // namespace
+
+md_status md_step_async(md_handle* h, int n_steps)
 {
     if (!h) return fail(nullptr, MD_ERR_INVALID_ARG, "null handle");
     if (h->poisoned) return fail(h, MD_ERR_BAD_STATE, "handle is in an error state: " + h->err);
@@ -772,50 +850,61 @@ md_status md_step(md_handle* h, int n_steps)
     if (h->host_step + n_steps > h->cfg.max_steps)
         return fail(h, MD_ERR_TABLE_END, "step " + std::to_string(h->host_step + n_steps) +
                                              " is past max_steps = " + std::to_string(h->cfg.max_steps));
-    int done = 0;
-    while (done < n_steps) {
-        const int todo = n_steps - done;
-        for (int k = 0; k < todo; ++k) {
-            CU(cudaGraphLaunch(h->exec, h->stream));
-            if (h->cfg.profile) {
-                CU(cudaEventSynchronize(h->ev_pair1));
-                float ms = 0.0f;
-                CU(cudaEventElapsedTime(&ms, h->ev_pair0, h->ev_pair1));
-                h->pair_ms += ms;
-                h->pair_launches += 1;
-            }
-        }
+    return launch_steps(h, n_steps);
+}
+
+md_status md_sync(md_handle* h)
+{
+    if (!h) return fail(nullptr, MD_ERR_INVALID_ARG, "null handle");
+    if (h->poisoned) return fail(h, MD_ERR_BAD_STATE, "handle is in an error state: " + h->err);
+    while (true) {
         unsigned e = 0;
         md_status st = read_flags(h, &e);
         if (st != MD_OK) return st;
         if (e != ERR_LIST) {
-            h->host_step += todo;
-            h->steps += todo;
-            return check_device_flags(h);
+            h->steps += h->pending;
+            h->pending = 0;
+            st = check_device_flags(h);
+            if (st != MD_OK) return st;
+            return drain_profile(h);
         }
         // The list of some step overflowed: the state stopped after that step's
-        // kick, drift and charge update.  Grow the list, compute its forces, go on.
+        // kick, drift and charge update, and the steps after it did nothing.
+        // Grow the list, compute the forces of that step, launch the rest again.
         long long dstep = 0;
         CU(cudaMemcpy(&dstep, h->P.step, sizeof(long long), cudaMemcpyDeviceToHost));
-        const int adv = (int)(dstep - h->host_step);
-        if (adv < 1 || adv > todo) return fail(h, MD_ERR_CUDA, "inconsistent step counter after a list overflow");
-        h->host_step = dstep;
+        const long long first = h->host_step - h->pending;
+        const long long adv = dstep - first;
+        if (adv < 1 || adv > h->pending) return fail(h, MD_ERR_CUDA, "inconsistent step counter after a list overflow");
+        const int rest = (int)(h->pending - adv);
         h->steps += adv;
-        done += adv;
+        h->host_step = dstep;
+        h->pending = 0;
         CU(cudaMemset(h->P.err, 0, sizeof(unsigned)));
-        bool grown = false;
-        st = rebuild_checked(h, &grown);
+        st = rebuild_checked(h, nullptr);
         if (st != MD_OK) return st;
         st = capture_graph(h);
         if (st != MD_OK) return st;
+        st = launch_steps(h, rest);
+        if (st != MD_OK) return st;
     }
-    return MD_OK;
+}
+
+md_status md_step(md_handle* h, int n_steps)
+{
+    md_status st = md_step_async(h, n_steps);
+    if (st != MD_OK) return st;
+    return md_sync(h);
 }
 
 md_status md_get_state(md_handle* h, md_state* out, unsigned fields)
 {
     if (!h) return fail(nullptr, MD_ERR_INVALID_ARG, "null handle");
     if (!out) return fail(h, MD_ERR_INVALID_ARG, "null state");
+    if (h->pending && !h->poisoned) {
+        md_status st_ = md_sync(h);
+        if (st_ != MD_OK) return st_;
+    }
     const int N = h->N, R = h->R;
     CU(cudaStreamSynchronize(h->stream));
     std::vector<double> tmp;
@@ -870,6 +959,10 @@ md_status md_set_state(md_handle* h, const md_state* in, unsigned fields)
 {
     if (!h) return fail(nullptr, MD_ERR_INVALID_ARG, "null handle");
     if (!in) return fail(h, MD_ERR_INVALID_ARG, "null state");
+    if (h->pending && !h->poisoned) {
+        md_status st_ = md_sync(h);
+        if (st_ != MD_OK) return st_;
+    }
     const int N = h->N, R = h->R;
     CU(cudaStreamSynchronize(h->stream));
     // bring velocities to the integer step with the current forces first
@@ -947,6 +1040,10 @@ md_status md_set_state(md_handle* h, const md_state* in, unsigned fields)
 md_status md_get_energies(md_handle* h, double* e_kin, double* e_pot, int64_t* n_pairs)
 {
     if (!h) return fail(nullptr, MD_ERR_INVALID_ARG, "null handle");
+    if (h->pending && !h->poisoned) {
+        md_status st_ = md_sync(h);
+        if (st_ != MD_OK) return st_;
+    }
     if (h->poisoned) return fail(h, MD_ERR_BAD_STATE, "handle is in an error state: " + h->err);
     const int R = h->R;
     CU(cudaMemsetAsync(h->P.pair_count, 0, sizeof(long long), h->stream));
@@ -976,18 +1073,31 @@ md_status md_get_energies(md_handle* h, double* e_kin, double* e_pot, int64_t* n
 md_status md_get_timing(md_handle* h, md_timing* out)
 {
     if (!h || !out) return fail(h, MD_ERR_INVALID_ARG, "null argument");
+    if (h->pending && !h->poisoned) {
+        md_status st = md_sync(h);
+        if (st != MD_OK) return st;
+    }
     out->pair_ms = h->pair_ms;
     out->pair_launches = h->pair_launches;
     out->steps = h->steps;
     out->pair_count_last = h->last_pairs;
     out->tile_warps = h->pair_warps;
     out->tile_blocks_per_sm = h->pair_blocks / std::max(1, h->n_sm);
+    out->list_capacity = h->P.pl_cap;
+    int used = 0;
+    CU(cudaMemcpy(&used, h->P.counters + 6, sizeof(int), cudaMemcpyDeviceToHost));
+    out->list_entries = used;
+    out->list_grows = h->list_grows;
     return MD_OK;
 }
 
 md_status md_reset_timing(md_handle* h)
 {
     if (!h) return fail(nullptr, MD_ERR_INVALID_ARG, "null handle");
+    if (h->pending && !h->poisoned) {
+        md_status st = md_sync(h);
+        if (st != MD_OK) return st;
+    }
     h->pair_ms = 0.0;
     h->pair_launches = 0;
     h->steps = 0;

@@ -44,7 +44,7 @@ class MDConfig(C.Structure):
                 ("ip_mev", C.c_void_p), ("e_pi_mev", C.c_void_p), ("e_auger_mev", C.c_void_p),
                 ("n_te", C.c_int), ("dte_ev", C.c_double), ("dev_alloc", ALLOC_FN),
                 ("dev_free", FREE_FN), ("alloc_ctx", C.c_void_p), ("autotune", C.c_int),
-                ("profile", C.c_int)]
+                ("profile", C.c_int), ("list_reserve", C.c_int)]
 
 
 class MDSystem(C.Structure):
@@ -67,7 +67,8 @@ class MDState(C.Structure):
 
 class MDTiming(C.Structure):
     _fields_ = [("pair_ms", C.c_double), ("pair_launches", C.c_int64), ("steps", C.c_int64),
-                ("pair_count_last", C.c_int64), ("tile_warps", C.c_int), ("tile_blocks_per_sm", C.c_int)]
+                ("pair_count_last", C.c_int64), ("tile_warps", C.c_int), ("tile_blocks_per_sm", C.c_int),
+                ("list_capacity", C.c_int64), ("list_entries", C.c_int64), ("list_grows", C.c_int64)]
 
 
 class MDForcesInput(C.Structure):
@@ -110,6 +111,8 @@ def lib():
             L.md_set_pulse_table_at.argtypes = [P, C.c_int, C.c_int, P, C.c_int]
             L.md_set_plasma_table.argtypes = [P, C.c_int, P, P, C.c_int]
             L.md_step.argtypes = [P, C.c_int]
+            L.md_step_async.argtypes = [P, C.c_int]
+            L.md_sync.argtypes = [P]
             L.md_get_state.argtypes = [P, C.POINTER(MDState), C.c_uint]
             L.md_set_state.argtypes = [P, C.POINTER(MDState), C.c_uint]
             L.md_get_energies.argtypes = [P, P, P, P]
@@ -183,6 +186,14 @@ def md_set_plasma_table(h, replica: int, ne, te_ev):
 
 def md_step(h, n_steps: int):
     _check(lib().md_step(h, int(n_steps)), h)
+
+
+def md_step_async(h, n_steps: int):
+    _check(lib().md_step_async(h, int(n_steps)), h)
+
+
+def md_sync(h):
+    _check(lib().md_sync(h), h)
 
 
 def md_get_state(h, state: MDState, fields: int):
@@ -268,7 +279,7 @@ class IonisingMD:
 
     def __init__(self, sample, atomic, *, dt_ps=5e-5, r_cut=1.2, precision="mixed", cr_enabled=True,
                  plasma_mode=MD_PLASMA_BOOKKEEPING, max_steps=1000, kappa_fixed=-1.0, t_start_fs=0.0,
-                 te_floor_ev=1.0, coulomb_f=COULOMB_F, autotune=False, profile=False,
+                 te_floor_ev=1.0, coulomb_f=COULOMB_F, autotune=False, profile=False, list_reserve=0,
                  torch_allocator=True, sigma0=None, eps0=None, mass=None):
         import torch
         from . import workloads as W
@@ -299,6 +310,7 @@ class IonisingMD:
         if self._alloc is not None:
             cfg.dev_alloc, cfg.dev_free = self._alloc.alloc_fn, self._alloc.free_fn
         cfg.autotune, cfg.profile = int(bool(autotune)), int(bool(profile))
+        cfg.list_reserve = int(list_reserve)
         s = sample
         arrs = [_c(s.x, np.float64), _c(s.v, np.float64), _c(s.species, np.uint8), _c(s.fragment, np.int32),
                 _c(s.q0, np.uint8), _c(s.replica_offset, np.int32), _c(s.seed, np.uint64),
@@ -319,8 +331,15 @@ class IonisingMD:
     def set_plasma_table(self, ne, te_ev, replica=-1):
         md_set_plasma_table(self.h, replica, ne, te_ev)
 
-    def step(self, n=1):
-        md_step(self.h, n)
+    def step(self, n=1, wait=True):
+        """Advance n steps; wait=False only enqueues them (status read by sync())."""
+        if wait:
+            md_step(self.h, n)
+        else:
+            md_step_async(self.h, n)
+
+    def sync(self):
+        md_sync(self.h)
 
     def get_state(self, fields=MD_FIELD_ALL, out=None):
         o = out or {}
