@@ -123,6 +123,14 @@ typedef struct md_config {
                                 what the initial configuration needs).  The
                                 list grows whenever a build needs more room
                                 (see md_step)                                  */
+    double list_skin_nm;     /* Verlet buffer of the cluster-pair list (nm).
+                                0: cells and list are rebuilt every step.  > 0:
+                                the list is built with r_cut + skin and kept
+                                until some atom has moved more than skin/2 since
+                                the build (then rebuilt within the same step);
+                                the pair set within r_cut is the same, only the
+                                grouping of the FP32 partial sums follows the
+                                build.  Periodic edges need >= 3 (r_cut + skin). */
 } md_config;
 
 /*
@@ -167,7 +175,11 @@ enum {
     MD_FIELD_PLASMA = 32,  /* n_e, e_gas_mev [R]; te_ev, kappa [R] get only  */
     MD_FIELD_COUNTS = 64,  /* event_counts [R][4] (PI, Auger, CI, REC), get only */
     MD_FIELD_STEP = 128,   /* step                                           */
-    MD_FIELD_ALL = 255
+    MD_FIELD_XLIST = 256,  /* x_list [3n] AoS: positions of the last list
+                              build (list_skin_nm > 0; otherwise equal to x).
+                              md_set_state rebuilds the list from them, so a
+                              resumed run groups its sums as the original did */
+    MD_FIELD_ALL = 511
 };
 typedef struct md_state {
     double* x;
@@ -181,6 +193,7 @@ typedef struct md_state {
     double* kappa;
     int64_t* event_counts;
     int64_t step;
+    double* x_list;
 } md_state;
 
 /* Accumulated device time of the pair kernel (md_config.profile = 1). */
@@ -194,6 +207,8 @@ typedef struct md_timing {
     int64_t list_capacity;   /* cluster-pair list entries allocated         */
     int64_t list_entries;    /* entries the last list build used            */
     int64_t list_grows;      /* times the list was enlarged on demand       */
+    int64_t list_builds;     /* cell + list builds in md_step since init or
+                                md_reset_timing (equals steps when the skin is 0) */
 } md_timing;
 
 typedef struct md_handle md_handle;

@@ -1,4 +1,4 @@
-// Cell-list neighbour build (one per step).  The paper's cutoff is chosen
+// Cell-list neighbour build (every step, or when the Verlet skin is used up).  The paper's cutoff is chosen
 // from the screening (Sec. II.B); here every replica gets a grid of cells of
 // edge >= r_cut, atoms are counted per cell, the cells are scanned, and each
 // cell is sorted deterministically (3D Hilbert index of a 16^3 sub-grid, then
@@ -59,6 +59,27 @@ __device__ __forceinline__ unsigned hilbert3(unsigned x0, unsigned x1, unsigned 
     return key;
 }
 
+// Packed record of atom i in a slot of the cell centred at cen: coordinates
+// relative to the centre (minimum image when periodic: between list builds an
+// atom may have been wrapped across the box), charge, LJ type state, fragment;
+// the slot's force sums are cleared.  Used by the build and by the refresh
+// between builds, so both round identically.
+__device__ __forceinline__ void pack_slot(const Params& p, int slot, int i, const double cen[3], const Grid& g)
+{
+    double d[3] = {p.x[i] - cen[0], p.y[i] - cen[1], p.z[i] - cen[2]};
+    if (g.periodic)
+        for (int k = 0; k < 3; ++k) {
+            if (d[k] > 0.5 * g.box[k]) d[k] -= g.box[k];
+            else if (d[k] < -0.5 * g.box[k]) d[k] += g.box[k];
+        }
+    const int sp = p.species[i];
+    const int qi = p.q[i];
+    if (p.precision == 0) p.xq[slot] = make_float4((float)d[0], (float)d[1], (float)d[2], (float)qi);
+    else p.xq64[slot] = make_double4_32a(d[0], d[1], d[2], (double)qi);
+    p.tf[slot] = make_int2(p.lj_ts_off[sp] + qi, p.frag[i]);
+    p.fx[slot] = 0; p.fy[slot] = 0; p.fz[slot] = 0; p.epot[slot] = 0;
+}
+
 // Atoms are visited in the previous step's slot order, so neighbouring
 // threads mostly share a cell and one atomic per (warp, cell) suffices.
 __global__ void __launch_bounds__(256) k_cell_assign(Params p)
@@ -90,6 +111,9 @@ __global__ void __launch_bounds__(256) k_cell_assign(Params p)
 __global__ void __launch_bounds__(kScanThreads) k_cell_scan(Params p)
 {
     __shared__ int s_n[kScanThreads], s_p[kScanThreads], s_s[kScanThreads];
+    // the grid of this build stays with the list until the next build
+    if (p.grid_b != p.grid)
+        for (int r = threadIdx.x; r < p.n_rep; r += blockDim.x) p.grid_b[r] = p.grid[r];
     const int C = p.cell_cap_total;
     const int t = threadIdx.x;
     const int chunk = (C + kScanThreads - 1) / kScanThreads;
@@ -164,6 +188,11 @@ __global__ void __launch_bounds__(256) k_cell_scatter(Params p)
         sub[d] = (unsigned)(sv < (1 << kHilBits) - 1 ? sv : (1 << kHilBits) - 1);
     }
     const unsigned key = hilbert3(sub[0], sub[1], sub[2]);
+    if (p.xr) {   // reference positions of the Verlet-buffered list
+        p.xr[i] = xs[0];
+        p.yr[i] = xs[1];
+        p.zr[i] = xs[2];
+    }
     p.tmp_key[p.cell_start[c] + p.atom_rank[i]] = ((unsigned long long)key << 32) | (unsigned)i;
 }
 
@@ -222,13 +251,7 @@ __global__ void __launch_bounds__(kSortThreads) k_cell_sort_pack(Params p)
                 const int slot = ps + rank;
                 p.atom_of[slot] = i;
                 p.slot_of[i] = slot;
-                const int sp = p.species[i];
-                const int qi = p.q[i];
-                const double dx = p.x[i] - cen[0], dy = p.y[i] - cen[1], dz = p.z[i] - cen[2];
-                if (p.precision == 0) p.xq[slot] = make_float4((float)dx, (float)dy, (float)dz, (float)qi);
-                else p.xq64[slot] = make_double4_32a(dx, dy, dz, (double)qi);
-                p.tf[slot] = make_int2(p.lj_ts_off[sp] + qi, p.frag[i]);
-                p.fx[slot] = 0; p.fy[slot] = 0; p.fz[slot] = 0; p.epot[slot] = 0;
+                pack_slot(p, slot, i, cen, g);
             }
         }
         for (int e = n + tid; e < npad; e += kSortThreads) {     // padding: far away, no charge
@@ -265,12 +288,35 @@ __global__ void __launch_bounds__(kSortThreads) k_cell_sort_pack(Params p)
                 fmax = max(fmax, fr);
             }
             const int cl = ps / kClusterSize + k;
+            p.cl_cen[cl] = make_double4_32a(cen[0], cen[1], cen[2], 0.0);
             p.bb_lo[cl] = make_float4(lx, ly, lz, 0.0f);
             p.bb_hi[cl] = make_float4(hx, hy, hz, 0.0f);
             p.bb_frag[cl] = make_int2(fmin, fmax);
         }
         __syncthreads();
     }
+}
+
+// Between list builds: the packed records of the current positions and
+// charges in the slots of the last build (cell centres and grid of that build).
+__global__ void __launch_bounds__(256) k_refresh(Params p)
+{
+    const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+    if (slot == 0) p.counters[2] = 0;   // work counter of the force kernel that follows
+    if (slot >= p.counters[1]) return;
+    const int i = p.atom_of[slot];
+    if (i < 0) {   // padding keeps its far-away record
+        p.fx[slot] = 0; p.fy[slot] = 0; p.fz[slot] = 0; p.epot[slot] = 0;
+        return;
+    }
+    const double4_32a c = p.cl_cen[slot / kClusterSize];
+    const double cen[3] = {c.x, c.y, c.z};
+    pack_slot(p, slot, i, cen, p.grid_b[p.rep[i]]);
+}
+
+void launch_refresh(const Params& p, cudaStream_t s)
+{
+    k_refresh<<<(p.slot_cap + 255) / 256, 256, 0, s>>>(p);
 }
 
 void launch_cells(const Params& p, cudaStream_t s, int grid_atoms, int grid_cells)

@@ -144,9 +144,9 @@ __device__ __forceinline__ void pair(const typename Prec<FP64>::S4& xi, int row_
 }
 
 // Cluster-pair list (one block per super-cluster, one warp per half-shell
-// cell): every j-cluster whose bounding box comes within r_cut of at least one
-// of the SC's i-cluster boxes gets an entry (j-cluster, half-shell index,
-// mask of those i-clusters).  An SC's entries are contiguous and cut into
+// cell): every j-cluster whose bounding box comes within r_cut + skin of at
+// least one of the SC's i-cluster boxes gets an entry (j-cluster, half-shell
+// index, mask of those i-clusters).  An SC's entries are contiguous and cut into
 // chunks of kChunk, the work items of the force kernel.  A first pass counts,
 // the second repeats the box tests and writes, so no cell size limit applies.
 __global__ void __launch_bounds__(kHalfShell * 32) k_pair_list(Params p)
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(kHalfShell * 32) k_pair_list(Params p)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (*p.err & ERR_CELL) return;
     const int n_sc = p.counters[0];
-    const float rcb = p.rc_f + kBBoxMargin;
+    const float rcb = p.rlist_f + kBBoxMargin;   // r_cut + Verlet skin
     const float rcb2 = rcb * rcb;
     for (int sc = blockIdx.x; sc < n_sc; sc += gridDim.x) {
         const int c = p.sc_cell[sc], fc = p.sc_first[sc], ncl = p.sc_ncl[sc];
@@ -170,11 +170,11 @@ __global__ void __launch_bounds__(kHalfShell * 32) k_pair_list(Params p)
             int lo = 0, hi = p.n_rep - 1;
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
-                if (p.grid[mid].cell_off <= c) lo = mid; else hi = mid - 1;
+                if (p.grid_b[mid].cell_off <= c) lo = mid; else hi = mid - 1;
             }
             rr = lo;
         }
-        const Grid& g = p.grid[rr];
+        const Grid& g = p.grid_b[rr];
         const int local = c - g.cell_off;
         const int cx = local % g.dims[0];
         const int cy = (local / g.dims[0]) % g.dims[1];
@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
         const int sc = ch.x, n_ent = ch.z, rr = ch.w;
         const uint2 ent = lane < n_ent ? p.pl[ch.y + lane] : make_uint2(0u, 0u);
         const int fc = p.sc_first[sc], ncl = p.sc_ncl[sc];
-        const Grid& g = p.grid[rr];
+        const Grid& g = p.grid_b[rr];
         const T kap = FP64 ? T(p.rs[rr].kappa_force) : T(p.rs[rr].kappa_f);
         const T erc = ENERGY ? P::expneg(kap * T(p.r_cut)) : T(0);
 

@@ -118,7 +118,7 @@ __device__ void make_grid(const Params& p, int r, const unsigned long long* mn,
     for (int it = 0; it < 400; ++it) {
         long long prod = 1;
         for (int d = 0; d < 3; ++d) {
-            double m = floor((hi[d] - lo[d]) / (p.r_cut * f));
+            double m = floor((hi[d] - lo[d]) / (p.r_list * f));
             n[d] = m < 1.0 ? 1 : (m > 1.0e6 ? 1000000 : (int)m);
             prod *= n[d];
         }
@@ -127,7 +127,7 @@ __device__ void make_grid(const Params& p, int r, const unsigned long long* mn,
     }
     for (int d = 0; d < 3; ++d) {
         double ext = hi[d] - lo[d];
-        double e = n[d] == 1 ? (ext > p.r_cut ? ext : p.r_cut) : ext / n[d];
+        double e = n[d] == 1 ? (ext > p.r_list ? ext : p.r_list) : ext / n[d];
         g.origin[d] = lo[d];
         g.edge[d] = e;
         g.inv_edge[d] = 1.0 / e;
@@ -164,6 +164,7 @@ __global__ void __launch_bounds__(kStepThreads) k_step_a(Params p, int mode)
     __shared__ long long s_acc[kRepWindow][6];
     __shared__ unsigned long long s_bmin[kRepWindow][3], s_bmax[kRepWindow][3];
     __shared__ int s_last;
+    __shared__ unsigned s_maxd2;
     // a cluster-pair list overflow freezes the state at the step whose forces
     // are missing; the host grows the list, recomputes them and resumes
     if (*p.err & ERR_LIST) return;
@@ -173,6 +174,7 @@ __global__ void __launch_bounds__(kStepThreads) k_step_a(Params p, int mode)
         (&s_bmin[0][0])[k] = ~0ull;
         (&s_bmax[0][0])[k] = 0ull;
     }
+    if (tid == 0) s_maxd2 = 0u;
     __syncthreads();
 
     const long long step = *p.step;
@@ -216,6 +218,18 @@ __global__ void __launch_bounds__(kStepThreads) k_step_a(Params p, int mode)
                 atomicOr(p.err, ERR_NONFINITE);
             p.vx[i] = vx; p.vy[i] = vy; p.vz[i] = vz;
             p.x[i] = x; p.y[i] = y; p.z[i] = z;
+            if (p.xr) {
+                // displacement since the last list build (minimum image)
+                double d[3] = {x - p.xr[i], y - p.yr[i], z - p.zr[i]};
+                if (g.periodic)
+                    for (int k = 0; k < 3; ++k) {
+                        if (d[k] > 0.5 * g.box[k]) d[k] -= g.box[k];
+                        else if (d[k] < -0.5 * g.box[k]) d[k] += g.box[k];
+                    }
+                const float d2 = (float)(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                // non-negative floats order like their bit patterns (NaN sorts high)
+                atomicMax(&s_maxd2, __float_as_uint(d2));
+            }
         }
         pos[0] = x; pos[1] = y; pos[2] = z;
         vac = !p.grid[r].periodic;
@@ -364,6 +378,8 @@ __global__ void __launch_bounds__(kStepThreads) k_step_a(Params p, int mode)
         }
     }
 
+    if (tid == 0 && s_maxd2) atomicMax(p.maxd2, s_maxd2);
+
     // ---- last block: per-replica reduction (Eq. 3) and next grid ----
     __threadfence();
     __syncthreads();
@@ -418,6 +434,16 @@ __global__ void __launch_bounds__(kStepThreads) k_step_a(Params p, int mode)
         p.counters[3] = 0;
         if (mode & STEP_ADVANCE) *p.step = next;
         if (mode & STEP_KICK_DRIFT) *p.kick_full = 1;
+        if (mode & STEP_SETCOND) {
+            // rebuild once some atom may have closed half of the skin: pairs
+            // within r_cut now were within r_cut + skin at the build
+            const unsigned m = __ldcg(p.maxd2);
+            *p.maxd2 = 0u;
+            const int rebuild = m > __float_as_uint(p.half_skin2) ? 1 : 0;
+            p.builds[0] += rebuild;
+            p.builds[1] = rebuild;
+            cudaGraphSetConditional(p.cond, (unsigned)rebuild);
+        }
     }
 }
 

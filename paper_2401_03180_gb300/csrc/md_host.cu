@@ -26,6 +26,7 @@ struct md_handle {
     std::vector<void*> allocs;
     cudaStream_t stream = nullptr;       // caller's stream (NULL = legacy default)
     cudaStream_t cap_stream = nullptr;   // private stream used for graph capture
+    cudaStream_t body_stream = nullptr;  // captures the bodies of the rebuild IF node
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t ev_pair0 = nullptr, ev_pair1 = nullptr;   // captured into the graph
     cudaGraph_t graph = nullptr;                          // kept for event-node updates
@@ -148,6 +149,27 @@ void enqueue_rebuild(md_handle* h, cudaStream_t s, bool energy)
     launch_pair_forces(h->P, s, energy, h->pair_blocks, h->pair_warps);
 }
 
+// Cell + list build at the positions held in xr/yr/zr (a checkpoint's list
+// positions), then the packed records and forces at the current positions.
+void enqueue_rebuild_from_ref(md_handle* h, cudaStream_t s)
+{
+    Params& P = h->P;
+    const size_t nb = (size_t)h->N * sizeof(double);
+    double* cur[3] = {P.x, P.y, P.z};
+    double* ref[3] = {P.xr, P.yr, P.zr};
+    for (int d = 0; d < 3; ++d) {
+        cudaMemcpyAsync(h->d_scratch + (size_t)d * h->N, cur[d], nb, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(cur[d], ref[d], nb, cudaMemcpyDeviceToDevice, s);
+    }
+    launch_step_a(P, 0, s, h->grid_atoms);
+    launch_cells(P, s, h->grid_atoms, h->grid_cells);
+    launch_pair_list(P, s, h->list_blocks);
+    for (int d = 0; d < 3; ++d)
+        cudaMemcpyAsync(cur[d], h->d_scratch + (size_t)d * h->N, nb, cudaMemcpyDeviceToDevice, s);
+    launch_refresh(P, s);
+    launch_pair_forces(P, s, false, h->pair_blocks, h->pair_warps);
+}
+
 void enqueue_step(md_handle* h, cudaStream_t s)
 {
     int mode = STEP_KICK_DRIFT | STEP_ADVANCE | (h->cfg.cr_enabled ? STEP_CR : 0);
@@ -198,11 +220,12 @@ md_status size_list(md_handle* h, long long entries)
 
 // Rebuild at the current state.  A cluster-pair list overflow (the system got
 // denser) grows the list to twice the entries needed and rebuilds.
-md_status rebuild_checked(md_handle* h, bool* grown)
+md_status rebuild_checked(md_handle* h, bool* grown, bool from_ref = false)
 {
     if (grown) *grown = false;
     for (int attempt = 0; attempt < 4; ++attempt) {
-        enqueue_rebuild(h, h->stream, false);
+        if (from_ref) enqueue_rebuild_from_ref(h, h->stream);
+        else enqueue_rebuild(h, h->stream, false);
         CU(cudaGetLastError());
         unsigned e = 0;
         md_status st = read_flags(h, &e);
@@ -219,6 +242,45 @@ md_status rebuild_checked(md_handle* h, bool* grown)
     return fail(h, MD_ERR_CELL_OVERFLOW, "cluster-pair list could not be sized");
 }
 
+// Step with a Verlet-buffered list: the step kernel decides whether the list
+// is used up and sets the condition of an IF node whose bodies are the cell +
+// list build and the refresh of the packed records; the forces follow.
+md_status capture_buffered_step(md_handle* h)
+{
+    cudaStream_t s = h->cap_stream;
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    CU(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+    cudaGraphConditionalHandle hc;
+    CU(cudaGraphConditionalHandleCreate(&hc, g, 1u, cudaGraphCondAssignDefault));
+    h->P.cond = hc;
+    const int mode = STEP_KICK_DRIFT | STEP_ADVANCE | STEP_SETCOND | (h->cfg.cr_enabled ? STEP_CR : 0);
+    launch_step_a(h->P, mode, s, h->grid_atoms);
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    CU(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = hc;
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 2;
+    cudaGraphNode_t cn;
+    CU(cudaGraphAddNode(&cn, g, deps, nullptr, nd, &cp));
+    cudaGraph_t rebuild = cp.conditional.phGraph_out[0], keep = cp.conditional.phGraph_out[1];
+    CU(cudaStreamBeginCaptureToGraph(h->body_stream, rebuild, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    launch_cells(h->P, h->body_stream, h->grid_atoms, h->grid_cells);
+    launch_pair_list(h->P, h->body_stream, h->list_blocks);
+    CU(cudaStreamEndCapture(h->body_stream, &rebuild));
+    CU(cudaStreamBeginCaptureToGraph(h->body_stream, keep, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    launch_refresh(h->P, h->body_stream);
+    CU(cudaStreamEndCapture(h->body_stream, &keep));
+    CU(cudaStreamUpdateCaptureDependencies(s, &cn, nullptr, 1, cudaStreamSetCaptureDependencies));
+    if (h->cfg.profile) cudaEventRecordWithFlags(h->ev_pair0, s, cudaEventRecordExternal);
+    launch_pair_forces(h->P, s, false, h->pair_blocks, h->pair_warps);
+    if (h->cfg.profile) cudaEventRecordWithFlags(h->ev_pair1, s, cudaEventRecordExternal);
+    return MD_OK;
+}
+
 md_status capture_graph(md_handle* h)
 {
     if (h->exec) {
@@ -230,7 +292,17 @@ md_status capture_graph(md_handle* h)
         h->graph = nullptr;
     }
     CU(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-    enqueue_step(h, h->cap_stream);
+    if (h->cfg.list_skin_nm > 0) {
+        md_status st = capture_buffered_step(h);
+        if (st != MD_OK) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(h->cap_stream, &g);
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+    } else {
+        enqueue_step(h, h->cap_stream);
+    }
     CU(cudaStreamEndCapture(h->cap_stream, &h->graph));
     if (h->cfg.profile) {
         // the two event-record nodes around the pair kernel: each launch points
@@ -317,6 +389,8 @@ md_status validate(const md_config* c, const md_system* s)
     if (!c || !s) return fail(h, MD_ERR_INVALID_ARG, "null config or system");
     if (!(c->dt_ps > 0) || !(c->r_cut > 0) || !(c->r_cut < 1e3))
         return fail(h, MD_ERR_INVALID_ARG, "dt_ps and r_cut must be positive");
+    if (!(c->list_skin_nm >= 0) || !(c->list_skin_nm <= c->r_cut))
+        return fail(h, MD_ERR_INVALID_ARG, "list_skin_nm must be in [0, r_cut]");
     if (c->precision != MD_PREC_MIXED && c->precision != MD_PREC_FP64)
         return fail(h, MD_ERR_INVALID_ARG, "precision must be MD_PREC_MIXED or MD_PREC_FP64");
     if (c->plasma_mode != MD_PLASMA_BOOKKEEPING && c->plasma_mode != MD_PLASMA_PRESCRIBED)
@@ -358,8 +432,8 @@ md_status validate(const md_config* c, const md_system* s)
         bool per = L[0] > 0 || L[1] > 0 || L[2] > 0;
         if (per) {
             for (int d = 0; d < 3; ++d)
-                if (!(L[d] >= 3.0 * c->r_cut))
-                    return fail(h, MD_ERR_INVALID_ARG, "periodic box edges must all be >= 3 r_cut");
+                if (!(L[d] >= 3.0 * (c->r_cut + c->list_skin_nm)))
+                    return fail(h, MD_ERR_INVALID_ARG, "periodic box edges must all be >= 3 (r_cut + list_skin_nm)");
         }
     }
     for (int i = 0; i < s->n_atoms; ++i) {
@@ -434,6 +508,7 @@ static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* 
     CU(cudaGetDevice(&dev));
     CU(cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, dev));
     CU(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    CU(cudaStreamCreateWithFlags(&h->body_stream, cudaStreamNonBlocking));
     CU(cudaEventCreate(&h->ev_pair0));
     CU(cudaEventCreate(&h->ev_pair1));
     if (c.profile) {
@@ -492,6 +567,7 @@ static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* 
     // ---- replica grids ----
     h->rep_off.assign(sys->replica_offset, sys->replica_offset + h->R + 1);
     h->grid0.assign(h->R, Grid{});
+    const double r_list = c.r_cut + c.list_skin_nm;   // cell edge and list cutoff
     long long cells_total = 0;
     for (int r = 0; r < h->R; ++r) {
         Grid& g = h->grid0[r];
@@ -500,7 +576,7 @@ static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* 
         if (g.periodic) {
             long long prod = 1;
             for (int d = 0; d < 3; ++d) {
-                int n = (int)std::floor(L[d] / c.r_cut);
+                int n = (int)std::floor(L[d] / r_list);
                 n = std::max(3, std::min(n, 1024));
                 g.dims[d] = n;
                 g.edge[d] = L[d] / n;
@@ -520,12 +596,12 @@ static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* 
                 }
             long long prod = 1;
             for (int d = 0; d < 3; ++d) {
-                long long n = std::max(1LL, (long long)std::floor((hi[d] - lo[d]) / c.r_cut));
+                long long n = std::max(1LL, (long long)std::floor((hi[d] - lo[d]) / r_list));
                 prod *= n;
                 g.dims[d] = 1;
-                g.edge[d] = c.r_cut;
-                g.inv_edge[d] = 1.0 / c.r_cut;
-                g.edge_f[d] = (float)c.r_cut;
+                g.edge[d] = r_list;
+                g.inv_edge[d] = 1.0 / r_list;
+                g.edge_f[d] = (float)r_list;
                 g.origin[d] = lo[d];
                 g.box[d] = 0.0;
             }
@@ -557,6 +633,9 @@ static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* 
     P.four_pi_f = 4.0 * M_PI * c.coulomb_f;
     P.inv_dte = 1.0 / c.dte_ev;
     P.rc_f = (float)c.r_cut;
+    P.r_list = r_list;
+    P.rlist_f = (float)r_list;
+    P.half_skin2 = (float)(0.25 * c.list_skin_nm * c.list_skin_nm);
     P.rc2_f = P.rc_f * P.rc_f;
     const int N = h->N, R = h->R, NS = h->NS;
     DALLOC(P.x, N); DALLOC(P.y, N); DALLOC(P.z, N);
@@ -600,11 +679,21 @@ static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* 
     else { DALLOC(P.xq64, P.slot_cap); P.xq = nullptr; }
     DALLOC(P.tf, P.slot_cap); DALLOC(P.atom_of, P.slot_cap);
     DALLOC(P.bb_lo, P.cluster_cap); DALLOC(P.bb_hi, P.cluster_cap); DALLOC(P.bb_frag, P.cluster_cap);
-    P.cl_cell = nullptr;
     DALLOC(P.fx, P.slot_cap); DALLOC(P.fy, P.slot_cap); DALLOC(P.fz, P.slot_cap); DALLOC(P.epot, P.slot_cap);
     DALLOC(P.pair_count, 1);
     DALLOC(P.err, 1); DALLOC(P.step, 1); DALLOC(P.kick_full, 1);
     DALLOC(h->d_scratch, 3 * (size_t)N);
+    DALLOC(P.cl_cen, P.cluster_cap);
+    DALLOC(P.maxd2, 1);
+    DALLOC(P.builds, 2);
+    if (c.list_skin_nm > 0) {
+        DALLOC(P.grid_b, R);
+        DALLOC(P.xr, N); DALLOC(P.yr, N); DALLOC(P.zr, N);
+    } else {
+        P.grid_b = P.grid;   // rebuilt every step: the build grid is the grid
+        P.xr = P.yr = P.zr = nullptr;
+    }
+    P.cond = 0;
     DALLOC(h->d_ekin, R); DALLOC(h->d_epot, R);
 
     // ---- uploads (synchronous, init only) ----
@@ -642,6 +731,10 @@ static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* 
         }
         CU(cudaMemcpy(P.acc, acc.data(), acc.size() * sizeof(RepAccum), cudaMemcpyHostToDevice));
         CU(cudaMemcpy(P.grid, h->grid0.data(), R * sizeof(Grid), cudaMemcpyHostToDevice));
+        if (P.grid_b != P.grid)
+            CU(cudaMemcpy(P.grid_b, h->grid0.data(), R * sizeof(Grid), cudaMemcpyHostToDevice));
+        CU(cudaMemset(P.maxd2, 0, sizeof(unsigned)));
+        CU(cudaMemset(P.builds, 0, 2 * sizeof(int)));
         CU(cudaMemcpy(d_seed, sys->seed, R * sizeof(unsigned long long), cudaMemcpyHostToDevice));
         CU(cudaMemcpy(d_vol, sys->volume, R * sizeof(double), cudaMemcpyHostToDevice));
         CU(cudaMemcpy(d_repoff, h->rep_off.data(), (R + 1) * sizeof(int), cudaMemcpyHostToDevice));
@@ -727,6 +820,7 @@ void md_finalize(md_handle* h)
         if (ev) cudaEventDestroy(ev);
     if (h->graph) cudaGraphDestroy(h->graph);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->body_stream) cudaStreamDestroy(h->body_stream);
     if (h->h_err) cudaFreeHost(h->h_err);
     delete h;
 }
@@ -951,6 +1045,16 @@ md_status md_get_state(md_handle* h, md_state* out, unsigned fields)
         }
     }
     if (fields & MD_FIELD_STEP) out->step = h->host_step;
+    if (fields & MD_FIELD_XLIST) {
+        if (!out->x_list) return fail(h, MD_ERR_INVALID_ARG, "x_list buffer missing");
+        tmp.resize(N);
+        const bool buffered = h->P.xr != nullptr;
+        double* src[3] = {buffered ? h->P.xr : h->P.x, buffered ? h->P.yr : h->P.y, buffered ? h->P.zr : h->P.z};
+        for (int d = 0; d < 3; ++d) {
+            CU(cudaMemcpy(tmp.data(), src[d], N * sizeof(double), cudaMemcpyDeviceToHost));
+            for (int i = 0; i < N; ++i) out->x_list[3 * i + d] = tmp[i];
+        }
+    }
     CU(cudaStreamSynchronize(h->stream));
     return MD_OK;
 }
@@ -1031,8 +1135,24 @@ md_status md_set_state(md_handle* h, const md_state* in, unsigned fields)
     CU(cudaMemset(h->P.kick_full, 0, sizeof(int)));
     CU(cudaMemset(h->P.err, 0, sizeof(unsigned)));
     h->poisoned = false;
+    bool from_ref = false;
+    if (fields & MD_FIELD_XLIST) {
+        if (!in->x_list) return fail(h, MD_ERR_INVALID_ARG, "x_list buffer missing");
+        if (h->P.xr) {   // buffered list: rebuild it where the checkpointed run built it
+            std::vector<double> tmp(N);
+            double* dst[3] = {h->P.xr, h->P.yr, h->P.zr};
+            for (int d = 0; d < 3; ++d) {
+                for (int i = 0; i < N; ++i) {
+                    tmp[i] = in->x_list[3 * i + d];
+                    if (!std::isfinite(tmp[i])) return fail(h, MD_ERR_INVALID_ARG, "non-finite list position");
+                }
+                CU(cudaMemcpy(dst[d], tmp.data(), N * sizeof(double), cudaMemcpyHostToDevice));
+            }
+            from_ref = true;
+        }
+    }
     bool grown = false;
-    md_status st = rebuild_checked(h, &grown);
+    md_status st = rebuild_checked(h, &grown, from_ref);
     if (st != MD_OK) return st;
     return grown ? capture_graph(h) : MD_OK;
 }
@@ -1047,9 +1167,9 @@ md_status md_get_energies(md_handle* h, double* e_kin, double* e_pot, int64_t* n
     if (h->poisoned) return fail(h, MD_ERR_BAD_STATE, "handle is in an error state: " + h->err);
     const int R = h->R;
     CU(cudaMemsetAsync(h->P.pair_count, 0, sizeof(long long), h->stream));
-    // same cell list and decomposition -> the forces come out bit-identical
-    launch_cells(h->P, h->stream, h->grid_atoms, h->grid_cells);
-    launch_pair_list(h->P, h->stream, h->list_blocks);
+    // the current list and packed records (re-packed from the same state), so
+    // the forces come out bit-identical
+    launch_refresh(h->P, h->stream);
     launch_pair_forces(h->P, h->stream, true, h->pair_blocks, h->pair_warps);
     launch_energy(h->P, h->d_ekin, h->d_epot, h->stream);
     CU(cudaGetLastError());
@@ -1088,6 +1208,13 @@ md_status md_get_timing(md_handle* h, md_timing* out)
     CU(cudaMemcpy(&used, h->P.counters + 6, sizeof(int), cudaMemcpyDeviceToHost));
     out->list_entries = used;
     out->list_grows = h->list_grows;
+    if (h->cfg.list_skin_nm > 0) {
+        int b = 0;
+        CU(cudaMemcpy(&b, h->P.builds, sizeof(int), cudaMemcpyDeviceToHost));
+        out->list_builds = b;
+    } else {
+        out->list_builds = h->steps;
+    }
     return MD_OK;
 }
 
@@ -1101,6 +1228,7 @@ md_status md_reset_timing(md_handle* h)
     h->pair_ms = 0.0;
     h->pair_launches = 0;
     h->steps = 0;
+    CU(cudaMemset(h->P.builds, 0, sizeof(int)));
     return MD_OK;
 }
 

@@ -78,6 +78,9 @@ struct Params {
     int precision, cr_enabled, plasma_mode;
     double dt, r_cut, rc2, kappa_fixed, te_floor, four_pi_f, coulomb_f, inv_dte;
     float rc2_f, rc_f;
+    double r_list;           // r_cut + Verlet skin: cell edge and list cutoff
+    float rlist_f;
+    float half_skin2;        // (skin/2)^2; 0: rebuild every step
 
     // atoms, original order
     double *x, *y, *z, *vx, *vy, *vz;
@@ -103,7 +106,8 @@ struct Params {
     const double2* lj_d;     // [n_ts_lj][n_ts_lj] (-c6, c12)
 
     // replicas
-    Grid* grid;
+    Grid* grid;              // grid for the next cell build (step kernel output)
+    Grid* grid_b;            // grid of the last build (list, forces, refresh); may alias grid
     RepState* rs;
     RepAccum* acc;
     const unsigned long long* seed;
@@ -131,10 +135,14 @@ struct Params {
     double4_32a* xq64;
     int2* tf;                // (type state, fragment)
     int* atom_of;            // slot -> atom (-1: padding)
+    double4_32a* cl_cen;     // per cluster: centre of its cell at the build (x, y, z, -)
+    double *xr, *yr, *zr;    // positions at the last build (Verlet skin only, else null)
+    unsigned* maxd2;         // max over atoms of |x - x_build|^2 this step (float bits)
+    int* builds;             // [0] list builds by the step graph, [1] last step rebuilt
+    cudaGraphConditionalHandle cond;   // IF node of the step graph (Verlet skin only)
     float4* bb_lo;           // per cluster, relative to its cell centre
     float4* bb_hi;
     int2* bb_frag;           // min/max fragment of the cluster
-    int* cl_cell;            // cluster -> cell
     long long *fx, *fy, *fz, *epot;   // fixed-point sums per slot
     long long* pair_count;   // in-cutoff pairs (energy pass)
 
@@ -188,6 +196,7 @@ void launch_energy(const Params& p, double* d_ekin, long long* d_epot, cudaStrea
 void launch_philox(unsigned long long seed, const uint32_t* ctr, long long n, uint32_t* out,
                    cudaStream_t s);
 void launch_force_out(const Params& p, double* d_f_out, cudaStream_t s);
+void launch_refresh(const Params& p, cudaStream_t s);
 int pair_max_blocks_per_sm(bool fp64, bool energy, int warps, int n_ts);
 // message returned by md_last_error(NULL) (host side)
 void set_global_error(const std::string& msg);
@@ -197,6 +206,7 @@ enum : int {
     STEP_KICK_DRIFT = 1,     // velocity kick + position drift
     STEP_CR = 2,             // collisional-radiative charge update
     STEP_ADVANCE = 4,        // bump the step counter at the end
+    STEP_SETCOND = 8,        // decide the rebuild and set the graph condition
 };
 
 }  // namespace mdg

@@ -43,7 +43,7 @@ struct Layout {
     size_t zs, ts_off, hdtm, mass, auger, volume, rep_off, lj;
     size_t grid, rs, acc, cell_count, cell_start, cell_pstart, tmp_key, sc_cell, sc_first, sc_ncl;
     size_t counters, xq, tf, atom_of, bb_lo, bb_hi, bb_frag, fx, fy, fz, epot, pair_count, err, step, kick;
-    size_t pl, pl_chunk;
+    size_t pl, pl_chunk, cl_cen;
     size_t total;
 };
 
@@ -74,6 +74,7 @@ constexpr Layout make_layout()
     L.epot = take(8 * (size_t)kSlotCap);
     L.pair_count = take(8); L.err = take(4); L.step = take(8); L.kick = take(4);
     L.pl = take(8 * (size_t)kPlCap); L.pl_chunk = take(16 * (size_t)kChunkCap);
+    L.cl_cen = take(32 * (size_t)kClusterCap);
     L.total = o;
     return L;
 }
@@ -209,6 +210,7 @@ extern "C" md_status md_forces_noalloc(const md_forces_input* in, double* d_f, v
     P.dt = 0.0; P.r_cut = in->r_cut; P.rc2 = in->r_cut * in->r_cut; P.kappa_fixed = in->kappa;
     P.te_floor = 1.0; P.coulomb_f = in->coulomb_f; P.four_pi_f = 4.0 * M_PI * in->coulomb_f; P.inv_dte = 1.0;
     P.rc_f = (float)in->r_cut; P.rc2_f = P.rc_f * P.rc_f;
+    P.r_list = in->r_cut; P.rlist_f = P.rc_f; P.half_skin2 = 0.0f;
     P.x = (double*)(B + kL.x); P.y = (double*)(B + kL.y); P.z = (double*)(B + kL.z);
     P.vx = (double*)(B + kL.vx); P.vy = (double*)(B + kL.vy); P.vz = (double*)(B + kL.vz);
     P.species = B + kL.species; P.q = B + kL.q; P.h = B + kL.h;
@@ -232,6 +234,10 @@ extern "C" md_status md_forces_noalloc(const md_forces_input* in, double* d_f, v
     P.err = (unsigned*)(B + kL.err); P.step = (long long*)(B + kL.step); P.kick_full = (int*)(B + kL.kick);
     P.pl = (uint2*)(B + kL.pl); P.pl_chunk = (int4*)(B + kL.pl_chunk);
     P.pl_cap = kPlCap; P.chunk_cap = kChunkCap;
+    P.cl_cen = (double4_32a*)(B + kL.cl_cen);
+    P.grid_b = P.grid;                 // one build: the build grid is the grid
+    P.xr = P.yr = P.zr = nullptr;
+    P.maxd2 = nullptr; P.builds = nullptr; P.cond = 0;
 
     // host-built tables: LJ per pair of type states (sigma scaled by 1 - q/Z,
     // arithmetic-mean sigma, geometric-mean epsilon), offsets, the grid

@@ -22,7 +22,7 @@ MD_ERR_FIXED_OVERFLOW, MD_ERR_TIMEOUT, MD_ERR_NONFINITE, MD_ERR_CELL_OVERFLOW, M
 MD_PREC_MIXED, MD_PREC_FP64 = 0, 1
 MD_PLASMA_BOOKKEEPING, MD_PLASMA_PRESCRIBED = 0, 1
 MD_FIELD_X, MD_FIELD_V, MD_FIELD_F, MD_FIELD_Q, MD_FIELD_H = 1, 2, 4, 8, 16
-MD_FIELD_PLASMA, MD_FIELD_COUNTS, MD_FIELD_STEP, MD_FIELD_ALL = 32, 64, 128, 255
+MD_FIELD_PLASMA, MD_FIELD_COUNTS, MD_FIELD_STEP, MD_FIELD_XLIST, MD_FIELD_ALL = 32, 64, 128, 256, 511
 MD_MAX_SPECIES = 8
 MD_NOALLOC_MAX_ATOMS = 16384
 COULOMB_F = 138.935458
@@ -44,7 +44,7 @@ class MDConfig(C.Structure):
                 ("ip_mev", C.c_void_p), ("e_pi_mev", C.c_void_p), ("e_auger_mev", C.c_void_p),
                 ("n_te", C.c_int), ("dte_ev", C.c_double), ("dev_alloc", ALLOC_FN),
                 ("dev_free", FREE_FN), ("alloc_ctx", C.c_void_p), ("autotune", C.c_int),
-                ("profile", C.c_int), ("list_reserve", C.c_int)]
+                ("profile", C.c_int), ("list_reserve", C.c_int), ("list_skin_nm", C.c_double)]
 
 
 class MDSystem(C.Structure):
@@ -62,13 +62,15 @@ class MDPulse(C.Structure):
 class MDState(C.Structure):
     _fields_ = [("x", C.c_void_p), ("v", C.c_void_p), ("f", C.c_void_p), ("q", C.c_void_p),
                 ("h", C.c_void_p), ("n_e", C.c_void_p), ("e_gas_mev", C.c_void_p), ("te_ev", C.c_void_p),
-                ("kappa", C.c_void_p), ("event_counts", C.c_void_p), ("step", C.c_int64)]
+                ("kappa", C.c_void_p), ("event_counts", C.c_void_p), ("step", C.c_int64),
+                ("x_list", C.c_void_p)]
 
 
 class MDTiming(C.Structure):
     _fields_ = [("pair_ms", C.c_double), ("pair_launches", C.c_int64), ("steps", C.c_int64),
                 ("pair_count_last", C.c_int64), ("tile_warps", C.c_int), ("tile_blocks_per_sm", C.c_int),
-                ("list_capacity", C.c_int64), ("list_entries", C.c_int64), ("list_grows", C.c_int64)]
+                ("list_capacity", C.c_int64), ("list_entries", C.c_int64), ("list_grows", C.c_int64),
+                ("list_builds", C.c_int64)]
 
 
 class MDForcesInput(C.Structure):
@@ -280,6 +282,7 @@ class IonisingMD:
     def __init__(self, sample, atomic, *, dt_ps=5e-5, r_cut=1.2, precision="mixed", cr_enabled=True,
                  plasma_mode=MD_PLASMA_BOOKKEEPING, max_steps=1000, kappa_fixed=-1.0, t_start_fs=0.0,
                  te_floor_ev=1.0, coulomb_f=COULOMB_F, autotune=False, profile=False, list_reserve=0,
+                 list_skin_nm=0.0,
                  torch_allocator=True, sigma0=None, eps0=None, mass=None):
         import torch
         from . import workloads as W
@@ -311,6 +314,7 @@ class IonisingMD:
             cfg.dev_alloc, cfg.dev_free = self._alloc.alloc_fn, self._alloc.free_fn
         cfg.autotune, cfg.profile = int(bool(autotune)), int(bool(profile))
         cfg.list_reserve = int(list_reserve)
+        cfg.list_skin_nm = float(list_skin_nm)
         s = sample
         arrs = [_c(s.x, np.float64), _c(s.v, np.float64), _c(s.species, np.uint8), _c(s.fragment, np.int32),
                 _c(s.q0, np.uint8), _c(s.replica_offset, np.int32), _c(s.seed, np.uint64),
@@ -349,7 +353,8 @@ class IonisingMD:
                 ("h", MD_FIELD_H, (n,), np.uint8), ("n_e", MD_FIELD_PLASMA, (R,), np.int64),
                 ("e_gas_mev", MD_FIELD_PLASMA, (R,), np.int64), ("te_ev", MD_FIELD_PLASMA, (R,), np.float64),
                 ("kappa", MD_FIELD_PLASMA, (R,), np.float64),
-                ("event_counts", MD_FIELD_COUNTS, (R, 4), np.int64)]
+                ("event_counts", MD_FIELD_COUNTS, (R, 4), np.int64),
+                ("x_list", MD_FIELD_XLIST, (n, 3), np.float64)]
         st = MDState()
         for name, bit, shape, dt in spec:
             if fields & bit:
@@ -365,7 +370,8 @@ class IonisingMD:
         st = MDState()
         keep = []
         for name, dt in [("x", np.float64), ("v", np.float64), ("q", np.uint8), ("h", np.uint8),
-                         ("n_e", np.int64), ("e_gas_mev", np.int64), ("event_counts", np.int64)]:
+                         ("n_e", np.int64), ("e_gas_mev", np.int64), ("event_counts", np.int64),
+                         ("x_list", np.float64)]:
             if name in arrays and arrays[name] is not None:
                 a = _c(arrays[name], dt)
                 keep.append(a)

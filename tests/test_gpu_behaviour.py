@@ -84,7 +84,7 @@ def test_checkpoint_resume_bit_exact():
     g.close()
     h = M.IonisingMD(s, atom, **kw)
     h.set_pulse(p)
-    h.set_state(ALL, **{k: ck[k] for k in ("x", "v", "q", "h", "n_e", "e_gas_mev", "event_counts")},
+    h.set_state(ALL, **{k: ck[k] for k in ("x", "v", "q", "h", "n_e", "e_gas_mev", "event_counts", "x_list")},
                 step=ck["step"])
     h.step(20)
     resumed = h.get_state(ALL)

@@ -143,3 +143,97 @@ def test_list_growth_on_set_state():
         g.close()
     assert out["tight"][1] >= 1 and out["roomy"][1] == 0
     _same(out["tight"][0], out["roomy"][0])
+
+
+# ---- Verlet-buffered list (list_skin_nm > 0) ----
+SKIN = 0.01   # thermal atoms close half of it in ~15 steps: several builds in 50
+
+
+def _buffered_water():
+    s, _ = water(1000)               # 3.11 nm box: r_cut + skin <= box / 3
+    return s, 0.9
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_buffered_trajectory_matches_oracle(oracle_mod, prec):
+    s, rc = _buffered_water()
+    atom = W.atomic_data(6.0, pi_scale=3000.0)
+    pulses = [W.Pulse(6.0, 5.0, 1e12, 0.0)]
+    gpu = M.IonisingMD(s, atom, precision=prec, r_cut=rc, max_steps=60, t_start_fs=-2.0, list_skin_nm=SKIN)
+    gpu.set_pulse(pulses)
+    ora = oracle_mod.OracleMD(s, atom, r_cut=rc, t_start_fs=-2.0, pulses=[pulses], n_steps_max=60)
+    L = s.box[0]
+    for _ in range(50):
+        gpu.step(1)
+        ora.step()
+    st = gpu.get_state(M.MD_FIELD_X | M.MD_FIELD_V | M.MD_FIELD_Q | M.MD_FIELD_F)
+    t = gpu.timing()
+    gpu.close()
+    assert 1 <= t.list_builds < 50, t.list_builds          # the buffer skipped builds
+    assert np.array_equal(st["q"], ora.q)
+    d = st["x"] - ora.x
+    d -= L * np.round(d / L)
+    rms = float(np.sqrt((d ** 2).sum(1).mean()))
+    assert rms <= {"mixed": 1e-6, "fp64": 1e-9}[prec], rms
+    dv = np.abs(st["v"] - ora.v).max(1)
+    assert np.percentile(dv, 98) <= {"mixed": 2.5e-4, "fp64": 2.5e-11}[prec]
+    # forces at the final state, from the list built some steps earlier
+    F = ora.F
+    rel = np.linalg.norm(st["f"] - F) / np.linalg.norm(F)
+    assert rel <= {"mixed": 1e-5, "fp64": 1e-12}[prec], rel
+
+
+def test_buffered_checkpoint_resume_bit_exact():
+    s, rc = _buffered_water()
+    atom = W.atomic_data(6.0, pi_scale=800.0, ci_scale=20.0)
+    p = [W.Pulse(6.0, 4.0, 3e12, 0.0)]
+    kw = dict(r_cut=rc, max_steps=80, t_start_fs=-1.5, list_skin_nm=SKIN)
+    g = M.IonisingMD(s, atom, **kw)
+    g.set_pulse(p)
+    g.step(60)
+    straight = g.get_state(ALL)
+    g.close()
+    g = M.IonisingMD(s, atom, **kw)
+    g.set_pulse(p)
+    g.step(23)                       # mid-way between two list builds
+    ck = g.get_state(ALL)
+    g.close()
+    assert not np.array_equal(ck["x_list"], ck["x"])
+    h = M.IonisingMD(s, atom, **kw)
+    h.set_pulse(p)
+    h.set_state(ALL, **{k: ck[k] for k in ("x", "v", "q", "h", "n_e", "e_gas_mev", "event_counts", "x_list")},
+                step=ck["step"])
+    h.step(37)
+    resumed = h.get_state(ALL)
+    h.close()
+    _same(straight, resumed)
+    assert np.array_equal(straight["x_list"], resumed["x_list"])
+
+
+def test_buffered_energy_pass_changes_nothing():
+    s, rc = _buffered_water()
+    atom = W.atomic_data(6.0, pi_scale=800.0)
+    p = [W.Pulse(6.0, 4.0, 3e12, 0.0)]
+    kw = dict(r_cut=rc, max_steps=50, t_start_fs=-1.5, list_skin_nm=SKIN)
+    out = []
+    for with_energy in (False, True):
+        g = M.IonisingMD(s, atom, **kw)
+        g.set_pulse(p)
+        g.step(17)
+        if with_energy:
+            f0 = g.get_state(M.MD_FIELD_F)["f"]
+            _, _, n = g.energies()
+            assert n > 0
+            assert np.array_equal(f0, g.get_state(M.MD_FIELD_F)["f"])
+        g.step(13)
+        out.append(g.get_state(ALL))
+        g.close()
+    _same(out[0], out[1])
+
+
+def test_unbuffered_list_builds_every_step():
+    s, rc = water(300)
+    g = M.IonisingMD(s, W.atomic_data(6.0), r_cut=rc, max_steps=20)
+    g.step(7)
+    assert g.timing().list_builds == 7
+    g.close()
