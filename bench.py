@@ -37,6 +37,7 @@ METRIC = "atom-steps/s (pair forces + ionisation) on 1 GB300, mixed vs FP64 at s
 UNIT = "atom-steps/s"
 FLOPS_PER_PAIR = 41          # FP32 operations per in-cutoff pair in the pair kernel (FMA = 2)
 L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
+SKIN_NM = 0.04               # Verlet buffer of the pair list (measured choice for the water box)
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_pair_c2_water_30k.md")
 
 
@@ -55,6 +56,8 @@ def parse():
     ap.add_argument("--profile-case", action="store_true",
                     help="minimal run for ncu: default launch shape, W + K steps, no baselines")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--skin", type=float, default=SKIN_NM,
+                    help="Verlet buffer of the cluster-pair list (nm); 0 rebuilds every step")
     return ap.parse_args()
 
 
@@ -185,7 +188,8 @@ def run_gpu(args, rank, world, local):
 
     def make(prec, profile):
         g = M.IonisingMD(s, atom, precision=prec, r_cut=1.2, dt_ps=5e-5, max_steps=max_steps,
-                         t_start_fs=wl.t_start_fs, autotune=(prec == "mixed"), profile=profile)
+                         t_start_fs=wl.t_start_fs, autotune=(prec == "mixed"), profile=profile,
+                         list_skin_nm=args.skin)
         for r in range(s.n_replicas):
             g.set_pulse(wl.pulses[r], replica=r)
         return g
@@ -279,6 +283,7 @@ def run_gpu(args, rank, world, local):
                    "pulse": [vars(p) for p in wl.pulses[0]], "t_start_fs": wl.t_start_fs,
                    "l2": "flushed between steps (256 MB write, untimed)",
                    "pair_tile": {"warps": tim.tile_warps, "blocks_per_sm": tim.tile_blocks_per_sm},
+                   "list_skin_nm": args.skin,
                    "parallelism": f"replicas{world}"},
         "pair_interactions_per_s": world * pairs * K / (ms / 1e3),
         "pairs_per_step": pairs,
@@ -290,7 +295,11 @@ def run_gpu(args, rank, world, local):
                      "flops_per_pair": FLOPS_PER_PAIR, "pair_kernel_ms": pair_ms,
                      "pair_kernel_share": pair_ms / (ms / K)},
         "e2e": e2e,
-        "gpu_launches": 7 * K,
+        # per step: step kernel + force kernel, and 5 more (4 cell kernels + list)
+        # in the steps whose list is rebuilt
+        "gpu_launches": 2 * K + 5 * int(tim.list_builds),
+        "pair_list": {"skin_nm": args.skin, "builds": int(tim.list_builds), "steps": K,
+                      "entries_last_build": int(tim.list_entries), "capacity": int(tim.list_capacity)},
         "clocks": clk.summary(),
         "charge_state": {"n_e": [int(v) for v in state["n_e"]], "te_ev": [float(v) for v in state["te_ev"]],
                          "events_pi_auger_ci_rec": [int(v) for v in state["event_counts"][0]]},
@@ -376,7 +385,8 @@ def run_reference(args, rank, world):
 
 
 def run_profile_case(args):
-    """Kernels launched: init 6 (step_a, 4 cell kernels, k_pair), then 6 per step."""
+    """Kernels launched: init 7 (step kernel, 4 cell kernels, list, forces), then
+    per step the step kernel and the forces, plus 5 when the list is rebuilt."""
     import torch
     from paper_2401_03180_gb300 import build as B
     from paper_2401_03180_gb300 import md as M
@@ -384,7 +394,7 @@ def run_profile_case(args):
     wl, atom = make_workload(args.workload, args.scale, 0)
     s = wl.sample
     g = M.IonisingMD(s, atom, precision=args.precision, r_cut=1.2, max_steps=max(wl.n_steps, args.warmup + args.steps + 1),
-                     t_start_fs=wl.t_start_fs, autotune=False)
+                     t_start_fs=wl.t_start_fs, autotune=False, list_skin_nm=args.skin)
     g.set_pulse(wl.pulses[0])
     g.step(args.warmup)
     g.step(args.steps)
@@ -393,7 +403,7 @@ def run_profile_case(args):
     g.close()
     return {"profile_case": args.workload, "n_atoms": s.n_atoms, "precision": args.precision,
             "warmup": args.warmup, "steps": args.steps, "tile_warps": t.tile_warps,
-            "tile_blocks_per_sm": t.tile_blocks_per_sm}
+            "tile_blocks_per_sm": t.tile_blocks_per_sm, "skin_nm": args.skin, "list_builds": t.list_builds}
 
 
 def main():

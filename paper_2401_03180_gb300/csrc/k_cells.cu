@@ -59,27 +59,6 @@ __device__ __forceinline__ unsigned hilbert3(unsigned x0, unsigned x1, unsigned 
     return key;
 }
 
-// Packed record of atom i in a slot of the cell centred at cen: coordinates
-// relative to the centre (minimum image when periodic: between list builds an
-// atom may have been wrapped across the box), charge, LJ type state, fragment;
-// the slot's force sums are cleared.  Used by the build and by the refresh
-// between builds, so both round identically.
-__device__ __forceinline__ void pack_slot(const Params& p, int slot, int i, const double cen[3], const Grid& g)
-{
-    double d[3] = {p.x[i] - cen[0], p.y[i] - cen[1], p.z[i] - cen[2]};
-    if (g.periodic)
-        for (int k = 0; k < 3; ++k) {
-            if (d[k] > 0.5 * g.box[k]) d[k] -= g.box[k];
-            else if (d[k] < -0.5 * g.box[k]) d[k] += g.box[k];
-        }
-    const int sp = p.species[i];
-    const int qi = p.q[i];
-    if (p.precision == 0) p.xq[slot] = make_float4((float)d[0], (float)d[1], (float)d[2], (float)qi);
-    else p.xq64[slot] = make_double4_32a(d[0], d[1], d[2], (double)qi);
-    p.tf[slot] = make_int2(p.lj_ts_off[sp] + qi, p.frag[i]);
-    p.fx[slot] = 0; p.fy[slot] = 0; p.fz[slot] = 0; p.epot[slot] = 0;
-}
-
 // Atoms are visited in the previous step's slot order, so neighbouring
 // threads mostly share a cell and one atomic per (warp, cell) suffices.
 __global__ void __launch_bounds__(256) k_cell_assign(Params p)

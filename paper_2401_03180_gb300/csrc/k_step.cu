@@ -352,6 +352,15 @@ __global__ void __launch_bounds__(kStepThreads) k_step_a(Params p, int mode)
             }
         }
     }
+    // ---- Verlet-buffered list: the packed record of this atom for the forces
+    // of this step, in the slot of the last build (a build, if one follows,
+    // rewrites all records); the force sums are cleared after the kick read them
+    if (live && p.xr && (mode & STEP_KICK_DRIFT)) {
+        const int slot = p.slot_of[i];
+        const double4_32a c = p.cl_cen[slot / kClusterSize];
+        const double cen[3] = {c.x, c.y, c.z};
+        pack_slot(p, slot, i, cen, p.grid_b[r]);
+    }
     __syncthreads();
 
     // ---- flush block partials ----
@@ -435,6 +444,7 @@ __global__ void __launch_bounds__(kStepThreads) k_step_a(Params p, int mode)
         if (mode & STEP_ADVANCE) *p.step = next;
         if (mode & STEP_KICK_DRIFT) *p.kick_full = 1;
         if (mode & STEP_SETCOND) {
+            p.counters[2] = 0;   // work counter of the force kernel (also reset by a build)
             // rebuild once some atom may have closed half of the skin: pairs
             // within r_cut now were within r_cut + skin at the build
             const unsigned m = __ldcg(p.maxd2);

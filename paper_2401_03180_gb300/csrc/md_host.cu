@@ -242,9 +242,10 @@ md_status rebuild_checked(md_handle* h, bool* grown, bool from_ref = false)
     return fail(h, MD_ERR_CELL_OVERFLOW, "cluster-pair list could not be sized");
 }
 
-// Step with a Verlet-buffered list: the step kernel decides whether the list
-// is used up and sets the condition of an IF node whose bodies are the cell +
-// list build and the refresh of the packed records; the forces follow.
+// Step with a Verlet-buffered list: the step kernel re-packs every atom's
+// record in its slot, decides whether the list is used up and sets the
+// condition of an IF node whose body is the cell + list build; the forces
+// follow.
 md_status capture_buffered_step(md_handle* h)
 {
     cudaStream_t s = h->cap_stream;
@@ -263,17 +264,14 @@ md_status capture_buffered_step(md_handle* h)
     cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = hc;
     cp.conditional.type = cudaGraphCondTypeIf;
-    cp.conditional.size = 2;
+    cp.conditional.size = 1;
     cudaGraphNode_t cn;
     CU(cudaGraphAddNode(&cn, g, deps, nullptr, nd, &cp));
-    cudaGraph_t rebuild = cp.conditional.phGraph_out[0], keep = cp.conditional.phGraph_out[1];
+    cudaGraph_t rebuild = cp.conditional.phGraph_out[0];
     CU(cudaStreamBeginCaptureToGraph(h->body_stream, rebuild, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     launch_cells(h->P, h->body_stream, h->grid_atoms, h->grid_cells);
     launch_pair_list(h->P, h->body_stream, h->list_blocks);
     CU(cudaStreamEndCapture(h->body_stream, &rebuild));
-    CU(cudaStreamBeginCaptureToGraph(h->body_stream, keep, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    launch_refresh(h->P, h->body_stream);
-    CU(cudaStreamEndCapture(h->body_stream, &keep));
     CU(cudaStreamUpdateCaptureDependencies(s, &cn, nullptr, 1, cudaStreamSetCaptureDependencies));
     if (h->cfg.profile) cudaEventRecordWithFlags(h->ev_pair0, s, cudaEventRecordExternal);
     launch_pair_forces(h->P, s, false, h->pair_blocks, h->pair_warps);

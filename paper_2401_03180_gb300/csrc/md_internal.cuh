@@ -186,6 +186,27 @@ __host__ __device__ __forceinline__ void half_shell(int nb, int& dx, int& dy, in
     dx = k % 3 - 1; dy = k / 3 - 1; dz = 1;
 }
 
+// Packed record of atom i in a slot of the cell centred at cen: coordinates
+// relative to the centre (minimum image when periodic: between list builds an
+// atom may have been wrapped across the box), charge, LJ type state, fragment;
+// the slot's force sums are cleared.  Used by the build and by the refresh
+// between builds, so both round identically.
+__device__ __forceinline__ void pack_slot(const Params& p, int slot, int i, const double cen[3], const Grid& g)
+{
+    double d[3] = {p.x[i] - cen[0], p.y[i] - cen[1], p.z[i] - cen[2]};
+    if (g.periodic)
+        for (int k = 0; k < 3; ++k) {
+            if (d[k] > 0.5 * g.box[k]) d[k] -= g.box[k];
+            else if (d[k] < -0.5 * g.box[k]) d[k] += g.box[k];
+        }
+    const int sp = p.species[i];
+    const int qi = p.q[i];
+    if (p.precision == 0) p.xq[slot] = make_float4((float)d[0], (float)d[1], (float)d[2], (float)qi);
+    else p.xq64[slot] = make_double4_32a(d[0], d[1], d[2], (double)qi);
+    p.tf[slot] = make_int2(p.lj_ts_off[sp] + qi, p.frag[i]);
+    p.fx[slot] = 0; p.fy[slot] = 0; p.fz[slot] = 0; p.epot[slot] = 0;
+}
+
 // Launch helpers implemented in the .cu files.
 void launch_step_a(const Params& p, int mode, cudaStream_t s, int grid_atoms);
 void launch_cells(const Params& p, cudaStream_t s, int grid_atoms, int grid_cells);
