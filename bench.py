@@ -80,6 +80,22 @@ def make_workload(name, scale, rank):
     return wl, atom
 
 
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's time: the job is done when its last rank is."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, n_atoms, steps, ms):
+    """Whole-job atom-steps/s: each of the `world` ranks advances its own
+    replica of n_atoms atoms by `steps` steps in `ms` milliseconds."""
+    return world * n_atoms * steps / (ms / 1e3)
+
+
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
@@ -220,17 +236,14 @@ def run_gpu(args, rank, world, local):
     with ClockSampler(local) as clk:
         ms = timed_steps(g, K)
     torch.cuda.synchronize()
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     tim = g.timing()
     _, _, pairs1 = g.energies()
     state = g.get_state(M.MD_FIELD_PLASMA | M.MD_FIELD_COUNTS | M.MD_FIELD_Q)
     g.close()
     pair_ms = tim.pair_ms / max(tim.pair_launches, 1)
     pairs = 0.5 * (pairs0 + pairs1)
-    value = world * n_atoms * K / (ms / 1e3)
+    value = job_throughput(world, n_atoms, K, ms)
     peak, sms, max_mhz = fp32_peak_tflops(torch)
     achieved = FLOPS_PER_PAIR * pairs / (pair_ms / 1e3) / 1e12
     traffic, _ = profiled_traffic()
