@@ -159,6 +159,10 @@ __device__ __forceinline__ void half_kick(const Params& p, int s, int slot, doub
 // ---------------------------------------------------------------------------
 // k_step_a: one thread per atom (original order).
 // ---------------------------------------------------------------------------
+// SETCOND: the Verlet-buffered variant that decides the rebuild and sets the
+// graph condition (ncu does not profile kernels that can set one, so the
+// every-step variant is a separate instantiation).
+template <bool SETCOND>
 __global__ void __launch_bounds__(kStepThreads) k_step_a(Params p, int mode)
 {
     __shared__ long long s_acc[kRepWindow][6];
@@ -443,7 +447,7 @@ __global__ void __launch_bounds__(kStepThreads) k_step_a(Params p, int mode)
         p.counters[3] = 0;
         if (mode & STEP_ADVANCE) *p.step = next;
         if (mode & STEP_KICK_DRIFT) *p.kick_full = 1;
-        if (mode & STEP_SETCOND) {
+        if constexpr (SETCOND) {
             p.counters[2] = 0;   // work counter of the force kernel (also reset by a build)
             // rebuild once some atom may have closed half of the skin: pairs
             // within r_cut now were within r_cut + skin at the build
@@ -460,7 +464,9 @@ __global__ void __launch_bounds__(kStepThreads) k_step_a(Params p, int mode)
 void launch_step_a(const Params& p, int mode, cudaStream_t s, int grid_atoms)
 {
     (void)grid_atoms;
-    k_step_a<<<(p.n_atoms + kStepThreads - 1) / kStepThreads, kStepThreads, 0, s>>>(p, mode);
+    const int blocks = (p.n_atoms + kStepThreads - 1) / kStepThreads;
+    if (mode & STEP_SETCOND) k_step_a<true><<<blocks, kStepThreads, 0, s>>>(p, mode);
+    else k_step_a<false><<<blocks, kStepThreads, 0, s>>>(p, mode);
 }
 
 // ---------------------------------------------------------------------------
