@@ -218,6 +218,31 @@ def plasma_scalars(n_e_count: int, e_gas_mev: int, volume: float, *, dt_ps: floa
 # ---------------------------------------------------------------------------
 # Whole-system oracle
 # ---------------------------------------------------------------------------
+def forces_of_atoms(sample, atomic, idx, *, r_cut, kappa, coulomb_f=COULOMB_F, sigma0=None, eps0=None):
+    """Forces on the atoms `idx` of `sample` (at its positions and charges q0),
+    each summed over every other atom of its replica (all pairs, FP64), with a
+    fixed screening kappa per replica.  Costs len(idx) * n_atoms pair terms,
+    so it checks or times a sample of a system too large for all pairs."""
+    from paper_2401_03180_gb300 import workloads as W
+    md = OracleMD.__new__(OracleMD)
+    md.n, md.R = sample.n_atoms, sample.n_replicas
+    md.rc, md.f = float(r_cut), float(coulomb_f)
+    md.kappa_fixed = -1.0
+    md.z = np.ascontiguousarray(atomic.z, np.int32)
+    md.off = np.concatenate([[0], np.cumsum(md.z + 1)]).astype(np.int32)
+    md.c6, md.c12 = lj_table(md.z, W.LJ_SIGMA0 if sigma0 is None else sigma0, W.LJ_EPS0 if eps0 is None else eps0)
+    md.nts = md.c6.shape[0]
+    md.x = np.ascontiguousarray(sample.x, np.float64)
+    md.q = np.ascontiguousarray(sample.q0, np.uint8)
+    md.sp = np.ascontiguousarray(sample.species, np.uint8)
+    md.frag = np.ascontiguousarray(sample.fragment, np.int32)
+    md.rep_off = np.ascontiguousarray(sample.replica_offset, np.int32)
+    md.rep_of = np.repeat(np.arange(md.R, dtype=np.int32), np.diff(md.rep_off))
+    md.box = np.ascontiguousarray(sample.box, np.float64).reshape(md.R, 3)
+    kap = np.broadcast_to(np.asarray(kappa, np.float64), (md.R,))
+    return md.forces_subset(np.asarray(idx), kappa=np.ascontiguousarray(kap))
+
+
 class OracleMD:
     """The full step of the method on the CPU, in FP64.
 

@@ -177,18 +177,4 @@ def test_full_size_droplet_sampled(oracle_mod):
 
 
 def _subset_forces(oracle_mod, s, atom, rc, kappa, idx):
-    md = oracle_mod.OracleMD.__new__(oracle_mod.OracleMD)
-    md.n, md.R = s.n_atoms, s.n_replicas
-    md.rc, md.f, md.kappa_fixed = rc, oracle_mod.COULOMB_F, kappa
-    md.z = np.ascontiguousarray(atom.z, np.int32)
-    md.off = np.concatenate([[0], np.cumsum(md.z + 1)]).astype(np.int32)
-    md.c6, md.c12 = oracle_mod.lj_table(md.z, W.LJ_SIGMA0, W.LJ_EPS0)
-    md.nts = md.c6.shape[0]
-    md.x = np.ascontiguousarray(s.x, np.float64)
-    md.q = np.ascontiguousarray(s.q0, np.uint8)
-    md.sp = np.ascontiguousarray(s.species, np.uint8)
-    md.frag = np.ascontiguousarray(s.fragment, np.int32)
-    md.rep_off = np.ascontiguousarray(s.replica_offset, np.int32)
-    md.rep_of = np.repeat(np.arange(md.R, dtype=np.int32), np.diff(md.rep_off))
-    md.box = np.ascontiguousarray(s.box, np.float64).reshape(md.R, 3)
-    return md.forces_subset(idx, kappa=np.full(md.R, kappa))
+    return oracle_mod.forces_of_atoms(s, atom, idx, r_cut=rc, kappa=kappa)
