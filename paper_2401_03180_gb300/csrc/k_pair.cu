@@ -262,9 +262,17 @@ __global__ void __launch_bounds__(kHalfShell * 32) k_pair_list(Params p)
                 if (m && at < end) p.pl[at] = make_uint2(base + lane, (nb << 8) | m);
                 off += __popc(bal);
             }
+            // both passes see the same boxes and round identically, so `off` ends at
+            // this warp's share; should it fall short, pad with empty entries (a
+            // real cluster, no i-cluster in range) rather than leave slots unwritten
+            for (int at = off + lane; at < min(base_sc + s_cnt[warp] + cnt, end); at += 32)
+                p.pl[at] = make_uint2((unsigned)fc, (unsigned)(nb << 8));
             for (int t = threadIdx.x; t * kChunk < tot; t += blockDim.x)
                 p.pl_chunk[cbase + t] = make_int4(sc, base_sc + t * kChunk, min(kChunk, tot - t * kChunk), rr);
         }
+        // the write pass re-reads the boxes (batches after the first): no warp may
+        // stage the next super-cluster's boxes before every warp is done with these
+        __syncthreads();
     }
 }
 

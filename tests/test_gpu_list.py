@@ -237,3 +237,25 @@ def test_unbuffered_list_builds_every_step():
     g.step(7)
     assert g.timing().list_builds == 7
     g.close()
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_list_blocks_loop_over_super_clusters(oracle_mod, prec):
+    """More super-clusters than list blocks (each block loops over several) and
+    cells of more than 32 clusters (the write pass re-tests the boxes of its
+    later batches): a 60,000-atom protein-crystal box with r_cut + skin = 1.24 nm
+    (1,042 super-clusters, 162 cells above 256 atoms), sampled forces."""
+    from gpu_common import force_errors
+    wl = W.workload("c3_protein_200k", scale=0.3)
+    s = wl.sample
+    rng = np.random.default_rng(21)
+    s.q0[rng.random(s.n_atoms) < 0.2] = 1
+    atom = W.atomic_data(wl.photon_kev)
+    g = M.IonisingMD(s, atom, precision=prec, r_cut=1.2, cr_enabled=False, kappa_fixed=1.5, max_steps=4,
+                     list_skin_nm=0.04)
+    f = g.get_state(M.MD_FIELD_F)["f"]
+    g.close()
+    idx = rng.choice(s.n_atoms, 500, replace=False)
+    ref = oracle_mod.forces_of_atoms(s, atom, idx, r_cut=1.2, kappa=1.5)
+    rms, mx = force_errors(f[idx], ref)
+    assert rms <= {"mixed": 1e-5, "fp64": 1e-12}[prec], (rms, mx)
