@@ -262,7 +262,9 @@ def run_gpu(args, rank, world, local):
     if not args.no_e2e:
         from paper_2401_03180_gb300 import md as M2
         ge = make("mixed", profile=False)
-        dF_all = M2.md_pulse_table([p for p in wl.pulses[0]], wl.t_start_fs, 5e-5 * 1000.0, max_steps)
+        # each replica's own pulse train, streamed one step at a time
+        dF_tab = np.stack([M2.md_pulse_table([p for p in wl.pulses[r]], wl.t_start_fs, 5e-5 * 1000.0, max_steps)
+                           for r in range(s.n_replicas)])
         h_in = torch.empty(s.n_replicas, dtype=torch.float64, pin_memory=True).numpy()
         h_q = torch.empty(n_atoms, dtype=torch.uint8, pin_memory=True).numpy()
         outs = {"q": h_q, "n_e": np.empty(s.n_replicas, np.int64), "e_gas_mev": np.empty(s.n_replicas, np.int64),
@@ -274,9 +276,9 @@ def run_gpu(args, rank, world, local):
             flush.zero_()
             torch.cuda.synchronize()
             step = W_ + k
-            h_in[:] = dF_all[step]
+            h_in[:] = dF_tab[:, step]
             t0 = time.perf_counter()
-            M2.md_set_pulse_table_at(ge.h, -1, step, h_in)          # H2D: this step's fluence
+            M2.md_set_fluence_at(ge.h, step, h_in)                  # H2D: this step's fluence, per replica
             ge.step(1)
             ge.get_state(M2.MD_FIELD_Q | M2.MD_FIELD_PLASMA, out=outs)  # D2H: charges + plasma
             tot += time.perf_counter() - t0

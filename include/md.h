@@ -234,6 +234,14 @@ md_status md_set_pulse_table(md_handle* h, int replica, const double* dF, int n_
  * (e.g. a per-step input streamed from the host); other entries unchanged. */
 md_status md_set_pulse_table_at(md_handle* h, int replica, int first_step, const double* dF, int n);
 
+/* The fluence of one step for every replica at once: dF[r] (photons/nm^2,
+ * finite, >= 0) becomes entry `step` of replica r's table, r < n_replicas,
+ * in one host-to-device copy ordered on the handle's stream (the host array
+ * may be reused when the call returns only if it is pinned and the stream
+ * has passed the copy; pageable memory is staged by the driver).  Errors:
+ * INVALID_ARG (step outside [0, max_steps), null or bad values), CUDA. */
+md_status md_set_fluence_at(md_handle* h, int step, const double* dF);
+
 /* Prescribed plasma (plasma_mode = MD_PLASMA_PRESCRIBED): n_e (nm^-3) and
  * T_e (eV) for steps 0 .. n_steps-1 (n_steps <= max_steps + 1). */
 md_status md_set_plasma_table(md_handle* h, int replica, const double* ne,

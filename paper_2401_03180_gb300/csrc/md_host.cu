@@ -890,6 +890,19 @@ md_status md_set_pulse_table_at(md_handle* h, int replica, int first_step, const
     return MD_OK;
 }
 
+md_status md_set_fluence_at(md_handle* h, int step, const double* dF)
+{
+    if (!h) return fail(nullptr, MD_ERR_INVALID_ARG, "null handle");
+    if (step < 0 || step >= h->cfg.max_steps || !dF) return fail(h, MD_ERR_INVALID_ARG, "step outside [0, max_steps)");
+    for (int r = 0; r < h->R; ++r)
+        if (!(dF[r] >= 0) || !std::isfinite(dF[r])) return fail(h, MD_ERR_INVALID_ARG, "fluence must be finite and >= 0");
+    // column `step` of the [replica][max_steps] table: one strided copy
+    double* dst = const_cast<double*>(h->P.dF) + step;
+    CU(cudaMemcpy2DAsync(dst, (size_t)h->cfg.max_steps * sizeof(double), dF, sizeof(double), sizeof(double),
+                         (size_t)h->R, cudaMemcpyHostToDevice, h->stream));
+    return MD_OK;
+}
+
 md_status md_set_plasma_table(md_handle* h, int replica, const double* ne, const double* te, int n_steps)
 {
     md_status st = check_replica(h, replica);

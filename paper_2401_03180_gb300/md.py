@@ -112,6 +112,7 @@ def lib():
             L.md_set_pulse_table.argtypes = [P, C.c_int, P, C.c_int]
             L.md_set_pulse_table_at.argtypes = [P, C.c_int, C.c_int, P, C.c_int]
             L.md_set_plasma_table.argtypes = [P, C.c_int, P, P, C.c_int]
+            L.md_set_fluence_at.argtypes = [P, C.c_int, P]
             L.md_step.argtypes = [P, C.c_int]
             L.md_step_async.argtypes = [P, C.c_int]
             L.md_sync.argtypes = [P]
@@ -179,6 +180,11 @@ def md_set_pulse_table(h, replica: int, dF):
 def md_set_pulse_table_at(h, replica: int, first_step: int, dF):
     dF = _c(dF, np.float64)
     _check(lib().md_set_pulse_table_at(h, int(replica), int(first_step), _p(dF), len(dF)), h)
+
+
+def md_set_fluence_at(h, step: int, dF):
+    """dF[r]: fluence of `step` for each replica r (float64 array, pinned for overlap)."""
+    _check(lib().md_set_fluence_at(h, int(step), _p(dF)), h)
 
 
 def md_set_plasma_table(h, replica: int, ne, te_ev):

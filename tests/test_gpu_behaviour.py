@@ -153,3 +153,35 @@ def test_errors_are_reported_not_faulted():
     with pytest.raises(M.MDError) as e:
         M.IonisingMD(two, atom, cr_enabled=False, kappa_fixed=0.0, max_steps=3)
     assert e.value.status == M.MD_ERR_FIXED_OVERFLOW
+
+
+def test_fluence_per_step_equals_pulse_tables():
+    """md_set_fluence_at (one step, every replica) reproduces per-replica pulse
+    tables set up front, bit for bit."""
+    wl = W.workload("c4_methane_batch", scale=0.05)
+    s = wl.sample
+    atom = W.atomic_data(wl.photon_kev, pi_scale=3000.0)
+    steps = 30
+    kw = dict(r_cut=1.2, max_steps=steps + 1, t_start_fs=wl.t_start_fs)
+    a = M.IonisingMD(s, atom, **kw)
+    for r in range(s.n_replicas):
+        a.set_pulse(wl.pulses[r], replica=r)
+    a.step(steps)
+    ref = a.get_state(ALL)
+    a.close()
+    tab = np.stack([M.md_pulse_table(wl.pulses[r], wl.t_start_fs, 5e-5 * 1000.0, steps + 1)
+                    for r in range(s.n_replicas)])
+    b = M.IonisingMD(s, atom, **kw)
+    for k in range(steps):
+        M.md_set_fluence_at(b.h, k, np.ascontiguousarray(tab[:, k]))
+        b.step(1)
+    got = b.get_state(ALL)
+    b.close()
+    assert s.n_replicas > 1 and ref["event_counts"].sum() > 0
+    _same(ref, got)
+    with pytest.raises(M.MDError):
+        c = M.IonisingMD(s, atom, **kw)
+        try:
+            M.md_set_fluence_at(c.h, steps + 1, np.ascontiguousarray(tab[:, 0]))
+        finally:
+            c.close()
