@@ -302,6 +302,12 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
     const int tx = lane & 7, ty = lane >> 3;
     const bool gt0 = ty > tx, gt1 = ty + 4 > tx;   // j index above i index (diagonal blocks)
     const int n_chunks = min(p.counters[7], p.chunk_cap);
+    // In the step of a Verlet-buffered build the positions are the build's:
+    // i-clusters with no atom pair within r_cut + skin of the entry's j-cluster
+    // are dropped from its mask for the list's lifetime (they cannot come within
+    // r_cut before the next build; their pairs add exact zeros, so no sum changes).
+    const bool prune = p.builds != nullptr && p.half_skin2 > 0.0f && p.builds[1] != 0;
+    const T rl2 = T(p.rlist_f + kBBoxMargin) * T(p.rlist_f + kBBoxMargin);
     const T rc2 = FP64 ? T(p.rc2) : T(p.rc2_f);
     const T irc = T(1.0 / p.r_cut);
     const T coulf = T(p.coulomb_f);
@@ -339,6 +345,7 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
             const unsigned code = __shfl_sync(0xffffffffu, ent.y, v);
             const int nb = (int)(code >> 8);
             unsigned mk = code & 0xffu;
+            unsigned keep = 0u;
             int dx, dy, dz;
             half_shell(nb, dx, dy, dz);
             const T Dx = FP64 ? T(dx * g.edge[0]) : T((float)dx * g.edge_f[0]);
@@ -364,8 +371,15 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
                                    kap, rc2, acc.x, acc.y, acc.z, fj0x, fj0y, fj0z, acc.w, npair, erc, irc);
                 pair<FP64, ENERGY>(xi, ti.x, ti.y, x1, y1, z1, a1.w, q1k, j1off, t1.y, !dg || gt1, lj_bytes,
                                    kap, rc2, acc.x, acc.y, acc.z, fj1x, fj1y, fj1z, acc.w, npair, erc, irc);
+                if (prune) {
+                    const T ax = xi.x - x0, ay = xi.y - y0, az = xi.z - z0;
+                    const T bx = xi.x - x1, by = xi.y - y1, bz = xi.z - z1;
+                    const bool near = ax * ax + ay * ay + az * az < rl2 || bx * bx + by * by + bz * bz < rl2;
+                    if (__any_sync(0xffffffffu, near)) keep |= 1u << k;
+                }
                 w.fi[k * 32 + lane] = acc;
             }
+            if (prune && lane == 0 && keep != (code & 0xffu)) p.pl[ch.y + v].y = (code & ~0xffu) | keep;
             // j forces: sum over the 8 i-lanes of each ty group.  Lanes tx < 4 keep
             // atom ty (j0), lanes tx >= 4 atom ty + 4 (j1); then each lane holds one
             // component of one atom and issues one RED.

@@ -159,6 +159,74 @@ __device__ __forceinline__ void half_kick(const Params& p, int s, int slot, doub
 // ---------------------------------------------------------------------------
 // k_step_a: one thread per atom (original order).
 // ---------------------------------------------------------------------------
+constexpr int kInlineReps = 4;   // up to this many replicas the step kernel's last block reduces them
+
+// Replica rr's per-step reduction by one warp: lane c reads accumulator copy
+// c and clears it, the warp reduces, lane 0 updates the plasma scalars (Eq. 3)
+// and the next grid.
+__device__ void finalize_replica(const Params& p, int rr, int lane, long long next)
+{
+    RepAccum* a = p.acc + (size_t)rr * kAccCopies;
+    long long v[6] = {0, 0, 0, 0, 0, 0};
+    unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0ull, 0ull, 0ull};
+    if (lane < kAccCopies) {
+        v[0] = __ldcg(&a[lane].dNe);
+        v[1] = __ldcg(&a[lane].dE);
+        for (int k = 0; k < 4; ++k) v[2 + k] = __ldcg(&a[lane].counts[k]);
+        for (int d = 0; d < 3; ++d) {
+            mn[d] = __ldcg(&a[lane].bmin[d]);
+            mx[d] = __ldcg(&a[lane].bmax[d]);
+        }
+        a[lane].dNe = 0;
+        a[lane].dE = 0;
+        for (int k = 0; k < 4; ++k) a[lane].counts[k] = 0;
+        for (int d = 0; d < 3; ++d) {
+            a[lane].bmin[d] = ~0ull;
+            a[lane].bmax[d] = 0ull;
+        }
+    }
+    for (int o = 16; o; o >>= 1) {
+        for (int k = 0; k < 6; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+        for (int d = 0; d < 3; ++d) {
+            const unsigned long long x = __shfl_xor_sync(0xffffffffu, mn[d], o);
+            const unsigned long long y = __shfl_xor_sync(0xffffffffu, mx[d], o);
+            mn[d] = x < mn[d] ? x : mn[d];
+            mx[d] = y > mx[d] ? y : mx[d];
+        }
+    }
+    if (lane == 0) {
+        RepState st = p.rs[rr];
+        st.n_e += v[0];
+        st.e_gas += v[1];
+        if (st.e_gas < 0) st.e_gas = 0;
+        for (int k = 0; k < 4; ++k) st.counts[k] += v[2 + k];
+        plasma_scalars(p, rr, next, st);
+        p.rs[rr] = st;
+        make_grid(p, rr, mn, mx);
+    }
+}
+
+// Once per step, after every replica: counters, step number and, with the
+// Verlet buffer, the rebuild decision and the graph condition.
+template <bool SETCOND>
+__device__ void finalize_step(const Params& p, int mode, long long next)
+{
+    p.counters[3] = 0;
+    if (mode & STEP_ADVANCE) *p.step = next;
+    if (mode & STEP_KICK_DRIFT) *p.kick_full = 1;
+    if constexpr (SETCOND) {
+        p.counters[2] = 0;   // work counter of the force kernel (also reset by a build)
+        // rebuild once some atom may have closed half of the skin: pairs
+        // within r_cut now were within r_cut + skin at the build
+        const unsigned m = __ldcg(p.maxd2);
+        *p.maxd2 = 0u;
+        const int rebuild = m > __float_as_uint(p.half_skin2) ? 1 : 0;
+        p.builds[0] += rebuild;
+        p.builds[1] = rebuild;
+        cudaGraphSetConditional(p.cond, (unsigned)rebuild);
+    }
+}
+
 // SETCOND: the Verlet-buffered variant that decides the rebuild and sets the
 // graph condition (ncu does not profile kernels that can set one, so the
 // every-step variant is a separate instantiation).
@@ -393,7 +461,9 @@ __global__ void __launch_bounds__(kStepThreads) k_step_a(Params p, int mode)
 
     if (tid == 0 && s_maxd2) atomicMax(p.maxd2, s_maxd2);
 
-    // ---- last block: per-replica reduction (Eq. 3) and next grid ----
+    // ---- per-replica reduction (Eq. 3) and next grid: by this kernel's last
+    // block for a few replicas, by k_step_fin (a warp per replica) for more ----
+    if (p.n_rep > kInlineReps) return;
     __threadfence();
     __syncthreads();
     if (tid == 0) s_last = (atomicAdd(&p.counters[3], 1) == (int)gridDim.x - 1);
@@ -402,71 +472,43 @@ __global__ void __launch_bounds__(kStepThreads) k_step_a(Params p, int mode)
     __threadfence();
     const long long next = (mode & STEP_ADVANCE) ? step + 1 : step;
     const int warp = tid >> 5, n_warps = blockDim.x >> 5;
-    for (int rr = warp; rr < p.n_rep; rr += n_warps) {
-        // lane c reads accumulator copy c, then the warp reduces
-        RepAccum* a = p.acc + (size_t)rr * kAccCopies;
-        long long v[6] = {0, 0, 0, 0, 0, 0};
-        unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0ull, 0ull, 0ull};
-        if (lane < kAccCopies) {
-            v[0] = __ldcg(&a[lane].dNe);
-            v[1] = __ldcg(&a[lane].dE);
-            for (int k = 0; k < 4; ++k) v[2 + k] = __ldcg(&a[lane].counts[k]);
-            for (int d = 0; d < 3; ++d) {
-                mn[d] = __ldcg(&a[lane].bmin[d]);
-                mx[d] = __ldcg(&a[lane].bmax[d]);
-            }
-            a[lane].dNe = 0;
-            a[lane].dE = 0;
-            for (int k = 0; k < 4; ++k) a[lane].counts[k] = 0;
-            for (int d = 0; d < 3; ++d) {
-                a[lane].bmin[d] = ~0ull;
-                a[lane].bmax[d] = 0ull;
-            }
-        }
-        for (int o = 16; o; o >>= 1) {
-            for (int k = 0; k < 6; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-            for (int d = 0; d < 3; ++d) {
-                const unsigned long long x = __shfl_xor_sync(0xffffffffu, mn[d], o);
-                const unsigned long long y = __shfl_xor_sync(0xffffffffu, mx[d], o);
-                mn[d] = x < mn[d] ? x : mn[d];
-                mx[d] = y > mx[d] ? y : mx[d];
-            }
-        }
-        if (lane == 0) {
-            RepState st = p.rs[rr];
-            st.n_e += v[0];
-            st.e_gas += v[1];
-            if (st.e_gas < 0) st.e_gas = 0;
-            for (int k = 0; k < 4; ++k) st.counts[k] += v[2 + k];
-            plasma_scalars(p, rr, next, st);
-            p.rs[rr] = st;
-            make_grid(p, rr, mn, mx);
-        }
-    }
-    if (tid == 0) {
-        p.counters[3] = 0;
-        if (mode & STEP_ADVANCE) *p.step = next;
-        if (mode & STEP_KICK_DRIFT) *p.kick_full = 1;
-        if constexpr (SETCOND) {
-            p.counters[2] = 0;   // work counter of the force kernel (also reset by a build)
-            // rebuild once some atom may have closed half of the skin: pairs
-            // within r_cut now were within r_cut + skin at the build
-            const unsigned m = __ldcg(p.maxd2);
-            *p.maxd2 = 0u;
-            const int rebuild = m > __float_as_uint(p.half_skin2) ? 1 : 0;
-            p.builds[0] += rebuild;
-            p.builds[1] = rebuild;
-            cudaGraphSetConditional(p.cond, (unsigned)rebuild);
-        }
-    }
+    for (int rr = warp; rr < p.n_rep; rr += n_warps) finalize_replica(p, rr, lane, next);
+    if (tid == 0) finalize_step<SETCOND>(p, mode, next);
+}
+
+// Per-replica reduction when there are many replicas: one warp each, then the
+// last block finishes the step.
+template <bool SETCOND>
+__global__ void __launch_bounds__(256) k_step_fin(Params p, int mode)
+{
+    __shared__ int s_last;
+    if (*p.err & ERR_LIST) return;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const long long step = *p.step;
+    const long long next = (mode & STEP_ADVANCE) ? step + 1 : step;
+    const int rr = (blockIdx.x * blockDim.x + tid) >> 5;
+    if (rr < p.n_rep) finalize_replica(p, rr, lane, next);
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = (atomicAdd(&p.counters[3], 1) == (int)gridDim.x - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (tid == 0) finalize_step<SETCOND>(p, mode, next);
 }
 
 void launch_step_a(const Params& p, int mode, cudaStream_t s, int grid_atoms)
 {
     (void)grid_atoms;
     const int blocks = (p.n_atoms + kStepThreads - 1) / kStepThreads;
-    if (mode & STEP_SETCOND) k_step_a<true><<<blocks, kStepThreads, 0, s>>>(p, mode);
-    else k_step_a<false><<<blocks, kStepThreads, 0, s>>>(p, mode);
+    const int fin_blocks = (p.n_rep * 32 + 255) / 256;
+    if (mode & STEP_SETCOND) {
+        k_step_a<true><<<blocks, kStepThreads, 0, s>>>(p, mode);
+        if (p.n_rep > kInlineReps) k_step_fin<true><<<fin_blocks, 256, 0, s>>>(p, mode);
+    } else {
+        k_step_a<false><<<blocks, kStepThreads, 0, s>>>(p, mode);
+        if (p.n_rep > kInlineReps) k_step_fin<false><<<fin_blocks, 256, 0, s>>>(p, mode);
+    }
 }
 
 // ---------------------------------------------------------------------------

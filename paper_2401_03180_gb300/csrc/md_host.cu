@@ -139,6 +139,13 @@ md_status check_device_flags(md_handle* h)
     return fail(h, MD_ERR_CUDA, "unknown device error flag");
 }
 
+// Whether the next force evaluation happens at the positions of the list build
+// (then it may drop i-clusters with no pair within r_cut + skin from the list).
+void set_build_step(md_handle* h, cudaStream_t s, bool at_build)
+{
+    cudaMemsetAsync(h->P.builds + 1, at_build ? 0x01 : 0x00, sizeof(int), s);   // nonzero / zero
+}
+
 // Cell list + cluster-pair list + forces at the current positions/charges
 // (no time advance).
 void enqueue_rebuild(md_handle* h, cudaStream_t s, bool energy)
@@ -146,6 +153,7 @@ void enqueue_rebuild(md_handle* h, cudaStream_t s, bool energy)
     launch_step_a(h->P, 0, s, h->grid_atoms);
     launch_cells(h->P, s, h->grid_atoms, h->grid_cells);
     launch_pair_list(h->P, s, h->list_blocks);
+    set_build_step(h, s, true);   // forces at the build positions: the list may be pruned
     launch_pair_forces(h->P, s, energy, h->pair_blocks, h->pair_warps);
 }
 
@@ -167,6 +175,7 @@ void enqueue_rebuild_from_ref(md_handle* h, cudaStream_t s)
     for (int d = 0; d < 3; ++d)
         cudaMemcpyAsync(cur[d], h->d_scratch + (size_t)d * h->N, nb, cudaMemcpyDeviceToDevice, s);
     launch_refresh(P, s);
+    set_build_step(h, s, false);  // forces away from the build positions: no pruning
     launch_pair_forces(P, s, false, h->pair_blocks, h->pair_warps);
 }
 
@@ -1181,6 +1190,7 @@ md_status md_get_energies(md_handle* h, double* e_kin, double* e_pot, int64_t* n
     // the current list and packed records (re-packed from the same state), so
     // the forces come out bit-identical
     launch_refresh(h->P, h->stream);
+    set_build_step(h, h->stream, false);
     launch_pair_forces(h->P, h->stream, true, h->pair_blocks, h->pair_warps);
     launch_energy(h->P, h->d_ekin, h->d_epot, h->stream);
     CU(cudaGetLastError());
