@@ -130,14 +130,18 @@ typedef struct md_config {
                                 the build (then rebuilt within the same step);
                                 the pair set within r_cut is the same, only the
                                 grouping of the FP32 partial sums follows the
-                                build.  Periodic edges need >= 3 (r_cut + skin). */
+                                build (one schedule for all replicas).  Periodic
+                                edges need >= 3 (r_cut + skin).                 */
 } md_config;
 
 /*
  * The sample: n_atoms atoms of n_replicas independent replicas stored
  * back to back (replica r owns atoms replica_offset[r] .. replica_offset[r+1]-1).
  * Replicas share the configuration but have their own RNG seed, box, gas
- * volume and pulses; a replica run alone gives the same result bit for bit.
+ * volume and pulses; a replica run alone gives the same result bit for bit
+ * (with list_skin_nm > 0 the list is rebuilt for all replicas when any of
+ * them needs it, so forces then match a solo run to FP32 rounding of the
+ * block sums, and charges still bit for bit).
  * box[3r..3r+2] > 0: periodic (minimum image; every edge >= 3 r_cut);
  * all zero: vacuum.  volume[r]: electron-gas volume (nm^3) for n_e = N_e/V.
  * fragment: LJ is excluded between atoms with equal fragment id.
