@@ -345,6 +345,7 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
             const unsigned code = __shfl_sync(0xffffffffu, ent.y, v);
             const int nb = (int)(code >> 8);
             unsigned mk = code & 0xffu;
+            if (mk == 0u) continue;   // emptied by the pruning of an earlier step
             unsigned keep = 0u;
             int dx, dy, dz;
             half_shell(nb, dx, dy, dz);
