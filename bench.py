@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile-case", action="store_true",
                     help="minimal run for ncu: default launch shape, W + K steps, no baselines")
+    ap.add_argument("--profile-resume", action="store_true",
+                    help="with --profile-case and --skin > 0: end with a checkpoint round trip, whose "
+                         "last force launch runs outside the step graph over the trimmed list")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--skin", type=float, default=SKIN_NM,
                     help="Verlet buffer of the cluster-pair list (nm); 0 rebuilds every step")
@@ -448,7 +451,9 @@ def run_reference(args, rank, world):
 
 def run_profile_case(args):
     """Kernels launched: init 7 (step kernel, 4 cell kernels, list, forces), then
-    per step the step kernel and the forces, plus 5 when the list is rebuilt."""
+    per step the step kernel and the forces, plus 5 when the list is rebuilt;
+    --profile-resume adds the checkpoint round trip (step kernel, 4 cell kernels,
+    list, two force launches, refresh)."""
     import torch
     from paper_2401_03180_gb300 import build as B
     from paper_2401_03180_gb300 import md as M
@@ -460,6 +465,13 @@ def run_profile_case(args):
     g.set_pulse(wl.pulses[0])
     g.step(args.warmup)
     g.step(args.steps)
+    if args.profile_resume:
+        # set_state rebuilds the list at the checkpoint's list positions, trims it
+        # (one force launch) and evaluates the forces at the current positions (a
+        # second one): the same kernel as a step between builds, launched on its own
+        st = g.get_state(M.MD_FIELD_ALL)
+        g.set_state(M.MD_FIELD_ALL, **{k: st[k] for k in ("x", "v", "q", "h", "n_e", "e_gas_mev",
+                                                         "event_counts", "x_list")}, step=st["step"])
     torch.cuda.synchronize()
     t = g.timing()
     g.close()

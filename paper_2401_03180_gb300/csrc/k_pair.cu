@@ -7,20 +7,28 @@
 //   * atoms are cell-sorted into clusters of 8; up to 8 consecutive clusters
 //     of one cell form a super-cluster (SC);
 //   * a list kernel tests, per SC and half-shell cell, every j-cluster's
-//     bounding box against the SC's 8 i-cluster boxes and writes the pairs in
-//     range as (j-cluster, shift, i-cluster mask) entries, contiguous per SC
-//     and cut into chunks of kChunk entries;
+//     bounding box against the SC's 8 i-cluster boxes, and for the clusters
+//     in range every i-atom against the j-cluster's box; each j-cluster with
+//     an i-atom in range becomes an entry (j-cluster, shift, 64-bit i-atom
+//     mask), contiguous per SC and cut into chunks of kChunk entries;
 //   * a warp of the force kernel owns one chunk at a time (dynamic scheduling
 //     through an atomic counter);
-//   * the SC's atoms and per-lane i-force partials live in shared memory;
-//     lane (tx = lane & 7, ty = lane >> 3) takes atom tx of an i-cluster and
-//     atoms ty, ty+4 of the current j-cluster;
-//   * only the i-clusters of an entry's mask are visited (a loop over the set
-//     bits, so the code stays small);
+//   * the SC's atoms and per-(atom, lane row) i-force partials live in shared
+//     memory; for each entry the warp compacts the mask into a list of i-atoms
+//     and takes them 8 at a time: lane (tx = lane & 7, ty = lane >> 3) pairs
+//     list atom tx with atoms ty, ty+4 of the j-cluster, so lanes only idle in
+//     an entry's last tile of 8;
+//   * at the step of a Verlet-buffered build a distance pass over each entry
+//     drops from its mask the i-atoms with no j-atom within r_cut + skin
+//     (exact for the list's lifetime) and records whether any pair in range
+//     lies within one fragment, before the forces are evaluated, so every
+//     evaluation of the list runs over the same atoms;
 //   * forces are summed in FP32 (or FP64) within one chunk for the i side
 //     and one (SC, j-cluster) entry for the j side, then converted
 //     once to 64-bit fixed point (2^-32 kJ/mol/nm): the per-atom totals are
 //     exact integer sums, identical for every launch shape and schedule.
+#include <type_traits>
+
 #include "md_internal.cuh"
 
 namespace mdg {
@@ -33,7 +41,7 @@ struct Prec<false> {
     using T = float;
     using T4 = float4;         // global packed position + charge
     using S4 = float4;         // shared-memory copy
-    using C2 = float2;         // -c6, c12
+    using C2 = float2;         // -6 c6, c12
     static __device__ __forceinline__ T4 pos(const Params& p, int slot) { return p.xq[slot]; }
     // single MUFU operations (arguments are far from the denormal range)
     static __device__ __forceinline__ T rsq(T x)
@@ -60,7 +68,7 @@ struct Prec<true> {
     using T = double;
     using T4 = double4_32a;
     using S4 = double4_16a;
-    using C2 = double2;        // -c6, c12
+    using C2 = double2;        // -6 c6, c12
     static __device__ __forceinline__ T4 pos(const Params& p, int slot) { return p.xq64[slot]; }
     static __device__ __forceinline__ T rsq(T x) { return 1.0 / sqrt(x); }
     static __device__ __forceinline__ T expneg(T x) { return exp(-x); }
@@ -71,12 +79,15 @@ struct Prec<true> {
     static __device__ __forceinline__ T fma(T a, T b, T c) { return __fma_rn(a, b, c); }
 };
 
-// per-warp shared-memory layout
+// per-warp shared-memory layout; row kSCAtoms is a far-away, uncharged
+// stand-in that idle lanes of an entry's last tile point at
 template <bool FP64>
 struct WarpSmem {
-    typename Prec<FP64>::S4 ix[kSuperClusters * kClusterSize];   // x, y, z, f*q of the SC atoms
-    int2 it[kSuperClusters * kClusterSize];                      // LJ row byte offset, fragment
-    typename Prec<FP64>::S4 fi[kSuperClusters * 32];             // per (i-cluster, lane) force (+energy)
+    typename Prec<FP64>::S4 ix[kSCAtoms + 1];          // x, y, z, f*q of the SC atoms
+    int2 it[kSCAtoms + 1];                             // LJ row byte offset, fragment
+    typename Prec<FP64>::S4 fi[(kSCAtoms + 1) * 4];    // per (atom, ty) force (+energy)
+    typename Prec<FP64>::S4 sh[kHalfShell];            // shift of each half-shell cell
+    unsigned char il[kSCAtoms + 8];                    // compacted i-atoms of an entry
 };
 
 template <bool FP64>
@@ -91,11 +102,13 @@ __device__ __forceinline__ void red_fix(long long* dst, typename Prec<FP64>::T v
 }
 
 // One pair, d = x_i - x_j.  `ok` drops the duplicates of the self-cluster
-// diagonal; equal fragments drop the LJ part.  qjk = q_j * kappa.  The force
-// on i is accumulated into (fx, fy, fz), the force on j into (fjx, fjy, fjz);
-// with ENERGY the cutoff-shifted pair energy into u.  Multiply-adds are
-// written out so that each accumulation is one fused operation.
-template <bool FP64, bool ENERGY>
+// diagonal; with EXCL equal fragments drop the LJ part (entries known to hold
+// no such pair skip the test).  qjk = q_j * kappa.  The LJ table holds
+// (-6 c6, c12).  The force on i is accumulated into (fx, fy, fz), the force on
+// j into (fjx, fjy, fjz); with ENERGY the cutoff-shifted pair energy into u.
+// Multiply-adds are written out so that each accumulation is one fused
+// operation.
+template <bool FP64, bool ENERGY, bool EXCL>
 __device__ __forceinline__ void pair(const typename Prec<FP64>::S4& xi, int row_off, int fri,
                                      typename Prec<FP64>::T xj, typename Prec<FP64>::T yj,
                                      typename Prec<FP64>::T zj, typename Prec<FP64>::T qj,
@@ -117,13 +130,13 @@ __device__ __forceinline__ void pair(const typename Prec<FP64>::S4& xi, int row_
     const typename P::C2 c = *reinterpret_cast<const typename P::C2*>(lj_bytes + row_off + tsj_off);
     const T rinv2 = rinv * rinv;
     const T rinv6 = rinv2 * rinv2 * rinv2;
-    const T lj6 = fri == frj ? T(0) : rinv6;    // bonded in the native structure: no LJ
+    const T lj6 = (EXCL && fri == frj) ? T(0) : rinv6;   // bonded in the native structure: no LJ
     const T r = r2 * rinv;
     const T kr = kap * r;
     const T e = P::expneg(kr);
     const T A = c.y * rinv6;                    // c12 / r^6
-    const T B = A + c.x;                        // c12/r^6 - c6 (table holds -c6)
-    const T D6 = T(6) * (A + B);                // 12 c12/r^12 - 6 c6/r^6
+    const T B = P::fma(c.x, T(1.0 / 6.0), A);   // c12/r^6 - c6
+    const T D6 = P::fma(A, T(12), c.x);         // 12 c12/r^6 - 6 c6
     const T E1 = P::fma(kr, B, D6);
     const T Cc = xi.w * P::fma(qj, rinv, qjk);  // f q_i q_j (1/r + kappa)
     const T S = P::fma(lj6, E1, Cc);
@@ -135,8 +148,8 @@ __device__ __forceinline__ void pair(const typename Prec<FP64>::S4& xi, int row_
         if (in) {
             const T qq = xi.w * qj;
             const T irc6 = irc * irc * irc * irc * irc * irc;
-            const T lj_on = fri == frj ? T(0) : T(1);
-            const T ush = erc * (qq * irc + lj_on * (c.y * irc6 + c.x) * irc6);
+            const T lj_on = (EXCL && fri == frj) ? T(0) : T(1);
+            const T ush = erc * (qq * irc + lj_on * (c.y * irc6 + c.x * T(1.0 / 6.0)) * irc6);
             u += e * (qq * rinv + lj6 * B) - ush;
             npair += 1;
         }
@@ -146,12 +159,15 @@ __device__ __forceinline__ void pair(const typename Prec<FP64>::S4& xi, int row_
 // Cluster-pair list (one block per super-cluster, one warp per half-shell
 // cell): every j-cluster whose bounding box comes within r_cut + skin of at
 // least one of the SC's i-cluster boxes gets an entry (j-cluster, half-shell
-// index, mask of those i-clusters).  An SC's entries are contiguous and cut into
-// chunks of kChunk, the work items of the force kernel.  A first pass counts,
-// the second repeats the box tests and writes, so no cell size limit applies.
+// index, mask of the i-atoms of those clusters that lie within r_cut + skin of
+// the j-cluster's box).  An SC's entries are contiguous and cut into chunks of
+// kChunk, the work items of the force kernel.  A first pass counts, the second
+// repeats the box tests and writes, so no cell size limit applies.
 __global__ void __launch_bounds__(kHalfShell * 32) k_pair_list(Params p)
 {
     __shared__ float4 s_lo[kSuperClusters], s_hi[kSuperClusters];
+    __shared__ float4 s_ip[kSCAtoms];       // the SC's atom positions (cell frame)
+    __shared__ int2 s_fr[kSuperClusters];   // fragment range of each i-cluster
     __shared__ int s_cnt[kHalfShell];
     __shared__ int s_base, s_tot, s_cbase;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -164,6 +180,16 @@ __global__ void __launch_bounds__(kHalfShell * 32) k_pair_list(Params p)
         if (threadIdx.x < ncl) {
             s_lo[threadIdx.x] = p.bb_lo[fc + threadIdx.x];
             s_hi[threadIdx.x] = p.bb_hi[fc + threadIdx.x];
+            s_fr[threadIdx.x] = p.bb_frag[fc + threadIdx.x];
+        }
+        if (threadIdx.x < ncl * kClusterSize) {
+            const int slot = fc * kClusterSize + threadIdx.x;
+            if (p.precision == 0) {
+                s_ip[threadIdx.x] = p.xq[slot];
+            } else {
+                const double4_32a t = p.xq64[slot];
+                s_ip[threadIdx.x] = make_float4((float)t.x, (float)t.y, (float)t.z, 0.0f);
+            }
         }
         int rr;
         {
@@ -259,14 +285,39 @@ __global__ void __launch_bounds__(kHalfShell * 32) k_pair_list(Params p)
                 const unsigned m = base == jr0 ? m_first : test(base + lane);
                 const unsigned bal = __ballot_sync(0xffffffffu, m != 0);
                 const int at = off + __popc(bal & ((1u << lane) - 1u));
-                if (m && at < end) p.pl[at] = make_uint2(base + lane, (nb << 8) | m);
+                if (m && at < end) {
+                    // i-atoms of the clusters in range that lie within r_cut + skin
+                    // of the j-cluster's box (padding slots are far away)
+                    const int jc = base + lane;
+                    const float4 lo = p.bb_lo[jc], hi = p.bb_hi[jc];
+                    const float jlx = lo.x + Dfx, jly = lo.y + Dfy, jlz = lo.z + Dfz;
+                    const float jhx = hi.x + Dfx, jhy = hi.y + Dfy, jhz = hi.z + Dfz;
+                    const int2 jfr = p.bb_frag[jc];
+                    unsigned long long am = 0ull;
+                    bool share = false;   // fragment ranges overlap: LJ exclusions possible
+                    for (unsigned mm = m; mm; mm &= mm - 1u) {
+                        const int k = __ffs(mm) - 1;
+                        share |= !(s_fr[k].y < jfr.x || jfr.y < s_fr[k].x);
+#pragma unroll
+                        for (int a = 0; a < kClusterSize; ++a) {
+                            const float4 xi = s_ip[k * kClusterSize + a];
+                            const float gx = fmaxf(0.0f, fmaxf(xi.x - jhx, jlx - xi.x));
+                            const float gy = fmaxf(0.0f, fmaxf(xi.y - jhy, jly - xi.y));
+                            const float gz = fmaxf(0.0f, fmaxf(xi.z - jhz, jlz - xi.z));
+                            if (__fmaf_rn(gz, gz, __fmaf_rn(gy, gy, __fmul_rn(gx, gx))) < rcb2)
+                                am |= 1ull << (k * kClusterSize + a);
+                        }
+                    }
+                    p.pl[at] = make_uint4((unsigned)jc, (unsigned)nb | (share ? kEntryExcl : 0u), (unsigned)am,
+                                          (unsigned)(am >> 32));
+                }
                 off += __popc(bal);
             }
             // both passes see the same boxes and round identically, so `off` ends at
             // this warp's share; should it fall short, pad with empty entries (a
-            // real cluster, no i-cluster in range) rather than leave slots unwritten
+            // real cluster, no i-atom in range) rather than leave slots unwritten
             for (int at = off + lane; at < min(base_sc + s_cnt[warp] + cnt, end); at += 32)
-                p.pl[at] = make_uint2((unsigned)fc, (unsigned)(nb << 8));
+                p.pl[at] = make_uint4((unsigned)fc, (unsigned)nb, 0u, 0u);
             for (int t = threadIdx.x; t * kChunk < tot; t += blockDim.x)
                 p.pl_chunk[cbase + t] = make_int4(sc, base_sc + t * kChunk, min(kChunk, tot - t * kChunk), rr);
         }
@@ -287,6 +338,7 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
     using S4 = typename P::S4;
     using C2 = typename P::C2;
     using WS = WarpSmem<FP64>;
+    constexpr unsigned kFull = 0xffffffffu;
     extern __shared__ __align__(16) unsigned char smem[];
     const int nts = p.n_ts_lj;
     C2* s_lj = reinterpret_cast<C2*>(smem);
@@ -296,16 +348,20 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
     WS& w = reinterpret_cast<WS*>(smem + tab)[warp];
 
     for (int k = threadIdx.x; k < nts * nts; k += blockDim.x) s_lj[k] = P::table(p)[k];
+    if (lane == 0) {
+        w.ix[kSCAtoms] = P::mk(T(-1.0e6), T(-1.0e6), T(-1.0e6), T(0));
+        w.it[kSCAtoms] = make_int2(0, (int)0x80000000);
+    }
+    if (lane < 4) w.fi[kSCAtoms * 4 + lane] = P::mk(T(0), T(0), T(0), T(0));
     __syncthreads();
     if (*p.err & (ERR_CELL | ERR_LIST)) return;
 
     const int tx = lane & 7, ty = lane >> 3;
-    const bool gt0 = ty > tx, gt1 = ty + 4 > tx;   // j index above i index (diagonal blocks)
     const int n_chunks = min(p.counters[7], p.chunk_cap);
     // In the step of a Verlet-buffered build the positions are the build's:
-    // i-clusters with no atom pair within r_cut + skin of the entry's j-cluster
-    // are dropped from its mask for the list's lifetime (they cannot come within
-    // r_cut before the next build; their pairs add exact zeros, so no sum changes).
+    // i-atoms with no j-atom within r_cut + skin are dropped from an entry's
+    // mask for the list's lifetime (they cannot come within r_cut before the
+    // next build), before the entry's forces are evaluated.
     const bool prune = p.builds != nullptr && p.half_skin2 > 0.0f && p.builds[1] != 0;
     const T rl2 = T(p.rlist_f + kBBoxMargin) * T(p.rlist_f + kBBoxMargin);
     const T rc2 = FP64 ? T(p.rc2) : T(p.rc2_f);
@@ -315,19 +371,20 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
     while (true) {
         int item = 0;
         if (lane == 0) item = atomicAdd(&p.counters[2], 1);
-        item = __shfl_sync(0xffffffffu, item, 0);
+        item = __shfl_sync(kFull, item, 0);
         if (item >= n_chunks) break;
         const int4 ch = p.pl_chunk[item];          // (sc, first entry, entries, replica)
         const int sc = ch.x, n_ent = ch.z, rr = ch.w;
-        const uint2 ent = lane < n_ent ? p.pl[ch.y + lane] : make_uint2(0u, 0u);
+        const PairEntry ent = lane < n_ent ? p.pl[ch.y + lane] : make_uint4(0u, 0u, 0u, 0u);
         const int fc = p.sc_first[sc], ncl = p.sc_ncl[sc];
         const Grid& g = p.grid_b[rr];
         const T kap = FP64 ? T(p.rs[rr].kappa_force) : T(p.rs[rr].kappa_f);
         const T erc = ENERGY ? P::expneg(kap * T(p.r_cut)) : T(0);
 
-        // the super-cluster's atoms into shared memory, partial forces cleared
+        // the super-cluster's atoms into shared memory, partial forces cleared,
+        // the shift of every half-shell cell of this replica's grid
         __syncwarp();
-        for (int a = lane; a < kSuperClusters * kClusterSize; a += 32) {
+        for (int a = lane; a < kSCAtoms; a += 32) {
             if ((a >> 3) < ncl) {
                 const int slot = fc * kClusterSize + a;
                 const T4 v = P::pos(p, slot);
@@ -336,65 +393,128 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
                 w.it[a] = make_int2(t.x * nts * (int)sizeof(C2), t.y);   // byte offset of the LJ row
             }
         }
-        for (int k = 0; k < ncl; ++k) w.fi[k * 32 + lane] = P::mk(T(0), T(0), T(0), T(0));
+        for (int k = lane; k < ncl * kClusterSize * 4; k += 32) w.fi[k] = P::mk(T(0), T(0), T(0), T(0));
+        if (lane < kHalfShell) {
+            int dx, dy, dz;
+            half_shell(lane, dx, dy, dz);
+            w.sh[lane] = FP64 ? P::mk(T(dx * g.edge[0]), T(dy * g.edge[1]), T(dz * g.edge[2]), T(0))
+                              : P::mk(T((float)dx * g.edge_f[0]), T((float)dy * g.edge_f[1]),
+                                      T((float)dz * g.edge_f[2]), T(0));
+        }
         __syncwarp();
         int npair = 0;
 
         for (int v = 0; v < n_ent; ++v) {
-            const int jcl = (int)__shfl_sync(0xffffffffu, ent.x, v);
-            const unsigned code = __shfl_sync(0xffffffffu, ent.y, v);
-            const int nb = (int)(code >> 8);
-            unsigned mk = code & 0xffu;
-            if (mk == 0u) continue;   // emptied by the pruning of an earlier step
-            unsigned keep = 0u;
-            int dx, dy, dz;
-            half_shell(nb, dx, dy, dz);
-            const T Dx = FP64 ? T(dx * g.edge[0]) : T((float)dx * g.edge_f[0]);
-            const T Dy = FP64 ? T(dy * g.edge[1]) : T((float)dy * g.edge_f[1]);
-            const T Dz = FP64 ? T(dz * g.edge[2]) : T((float)dz * g.edge_f[2]);
+            const int jcl = (int)__shfl_sync(kFull, ent.x, v);
+            const unsigned code = __shfl_sync(kFull, ent.y, v);
+            const int nb = (int)(code & 0xffu);
+            bool excl = (code & kEntryExcl) != 0u;
+            const unsigned mlo0 = __shfl_sync(kFull, ent.z, v), mhi0 = __shfl_sync(kFull, ent.w, v);
+            if ((mlo0 | mhi0) == 0u) continue;   // no i-atom in range (or emptied by pruning)
+            const S4 D = w.sh[nb];
             const int s0 = jcl * kClusterSize + ty, s1 = s0 + 4;
             const T4 a0 = P::pos(p, s0), a1 = P::pos(p, s1);
             const int2 t0 = p.tf[s0], t1 = p.tf[s1];
-            const T x0 = a0.x + Dx, y0 = a0.y + Dy, z0 = a0.z + Dz;
-            const T x1 = a1.x + Dx, y1 = a1.y + Dy, z1 = a1.z + Dz;
+            const T x0 = a0.x + D.x, y0 = a0.y + D.y, z0 = a0.z + D.z;
+            const T x1 = a1.x + D.x, y1 = a1.y + D.y, z1 = a1.z + D.z;
             const T q0k = a0.w * kap, q1k = a1.w * kap;
             const int j0off = t0.x * (int)sizeof(C2), j1off = t1.x * (int)sizeof(C2);
             const int kdiag = nb == 0 ? jcl - fc : -1;   // i-cluster equal to this j-cluster
-            T fj0x = 0, fj0y = 0, fj0z = 0, fj1x = 0, fj1y = 0, fj1z = 0;
-            while (mk) {
-                const int k = __ffs(mk) - 1;
-                mk &= mk - 1;
-                const S4 xi = w.ix[k * kClusterSize + tx];
-                const int2 ti = w.it[k * kClusterSize + tx];
-                const bool dg = k == kdiag;
-                S4 acc = w.fi[k * 32 + lane];
-                pair<FP64, ENERGY>(xi, ti.x, ti.y, x0, y0, z0, a0.w, q0k, j0off, t0.y, !dg || gt0, lj_bytes,
-                                   kap, rc2, acc.x, acc.y, acc.z, fj0x, fj0y, fj0z, acc.w, npair, erc, irc);
-                pair<FP64, ENERGY>(xi, ti.x, ti.y, x1, y1, z1, a1.w, q1k, j1off, t1.y, !dg || gt1, lj_bytes,
-                                   kap, rc2, acc.x, acc.y, acc.z, fj1x, fj1y, fj1z, acc.w, npair, erc, irc);
-                if (prune) {
-                    const T ax = xi.x - x0, ay = xi.y - y0, az = xi.z - z0;
-                    const T bx = xi.x - x1, by = xi.y - y1, bz = xi.z - z1;
-                    const bool near = ax * ax + ay * ay + az * az < rl2 || bx * bx + by * by + bz * bz < rl2;
-                    if (__any_sync(0xffffffffu, near)) keep |= 1u << k;
+
+            // the entry's i-atoms in slot order; the last tile is padded with the stand-in
+            unsigned mlo = mlo0, mhi = mhi0;
+            int n_i = 0;
+            auto compact = [&]() {
+                const int nlo = __popc(mlo);
+                n_i = nlo + __popc(mhi);
+                const unsigned below = (1u << lane) - 1u;
+                __syncwarp();   // earlier readers of the list are done
+                if ((mlo >> lane) & 1u) w.il[__popc(mlo & below)] = (unsigned char)lane;
+                if ((mhi >> lane) & 1u) w.il[nlo + __popc(mhi & below)] = (unsigned char)(lane + 32);
+                if (lane < 8) w.il[n_i + lane] = (unsigned char)kSCAtoms;
+                __syncwarp();
+            };
+            compact();
+            if (prune) {
+                // keep the i-atoms with a j-atom within r_cut + skin (distances
+                // only), so that every evaluation of the list, this one included,
+                // runs over the same atoms
+                unsigned keep_lo = 0u, keep_hi = 0u;
+                bool share = false;   // a pair in range within one fragment
+                for (int t = 0; t < n_i; t += 8) {
+                    const int ia = w.il[t + tx];
+                    const S4 xi = w.ix[ia];
+                    const int fri = w.it[ia].y;
+                    const bool dg = (ia >> 3) == kdiag;
+                    const T dx0 = xi.x - x0, dy0 = xi.y - y0, dz0 = xi.z - z0;
+                    const T dx1 = xi.x - x1, dy1 = xi.y - y1, dz1 = xi.z - z1;
+                    const T r20 = P::fma(dz0, dz0, P::fma(dy0, dy0, dx0 * dx0));
+                    const T r21 = P::fma(dz1, dz1, P::fma(dy1, dy1, dx1 * dx1));
+                    const bool n0 = (!dg || (ia & 7) < ty) && r20 < rl2;
+                    const bool n1 = (!dg || (ia & 7) < ty + 4) && r21 < rl2;
+                    const unsigned b = __ballot_sync(kFull, n0 || n1);
+                    share |= __any_sync(kFull, (n0 && fri == t0.y) || (n1 && fri == t1.y));
+                    const bool mine = ty == 0 && (((b | (b >> 8) | (b >> 16) | (b >> 24)) >> tx) & 1u) && ia < kSCAtoms;
+                    keep_lo |= __reduce_or_sync(kFull, mine && ia < 32 ? 1u << ia : 0u);
+                    keep_hi |= __reduce_or_sync(kFull, mine && ia >= 32 ? 1u << (ia & 31) : 0u);
                 }
-                w.fi[k * 32 + lane] = acc;
+                if (lane == 0) {
+                    if (keep_lo != mlo || keep_hi != mhi)
+                        *reinterpret_cast<uint2*>(&p.pl[ch.y + v].z) = make_uint2(keep_lo, keep_hi);
+                    if (share != excl) p.pl[ch.y + v].y = (unsigned)nb | (share ? kEntryExcl : 0u);
+                }
+                excl = share;
+                if ((keep_lo | keep_hi) == 0u) continue;
+                if (keep_lo != mlo || keep_hi != mhi) {
+                    mlo = keep_lo;
+                    mhi = keep_hi;
+                    compact();
+                }
             }
-            if (prune && lane == 0 && keep != (code & 0xffu)) p.pl[ch.y + v].y = (code & ~0xffu) | keep;
+
+            T fj0x = 0, fj0y = 0, fj0z = 0, fj1x = 0, fj1y = 0, fj1z = 0;
+            // DIAG: the self-cluster diagonal (i < j inside the cluster); EXCL:
+            // pairs within one fragment are possible; other entries take the
+            // plain tile loop
+            auto tiles = [&](auto diag, auto ex) {
+                constexpr bool DIAG = decltype(diag)::value;
+                constexpr bool EXCL = DIAG || decltype(ex)::value;
+                for (int t = 0; t < n_i; t += 8) {
+                    const int ia = w.il[t + tx];
+                    const S4 xi = w.ix[ia];
+                    const int2 ti = w.it[ia];
+                    S4 acc = w.fi[ia * 4 + ty];
+                    bool ok0 = true, ok1 = true;
+                    if (DIAG) {
+                        const bool dg = (ia >> 3) == kdiag;
+                        ok0 = !dg || (ia & 7) < ty;
+                        ok1 = !dg || (ia & 7) < ty + 4;
+                    }
+                    pair<FP64, ENERGY, EXCL>(xi, ti.x, ti.y, x0, y0, z0, a0.w, q0k, j0off, t0.y, ok0, lj_bytes, kap,
+                                             rc2, acc.x, acc.y, acc.z, fj0x, fj0y, fj0z, acc.w, npair, erc, irc);
+                    pair<FP64, ENERGY, EXCL>(xi, ti.x, ti.y, x1, y1, z1, a1.w, q1k, j1off, t1.y, ok1, lj_bytes, kap,
+                                             rc2, acc.x, acc.y, acc.z, fj1x, fj1y, fj1z, acc.w, npair, erc, irc);
+                    w.fi[ia * 4 + ty] = acc;
+                }
+            };
+            if ((unsigned)kdiag < (unsigned)ncl) tiles(std::true_type{}, std::true_type{});
+            else if (excl) tiles(std::false_type{}, std::true_type{});
+            else tiles(std::false_type{}, std::false_type{});
+            __syncwarp();   // the next entry rewrites the i-atom list
             // j forces: sum over the 8 i-lanes of each ty group.  Lanes tx < 4 keep
             // atom ty (j0), lanes tx >= 4 atom ty + 4 (j1); then each lane holds one
             // component of one atom and issues one RED.
             {
                 const bool up = tx >= 4;
                 T ax = up ? fj1x : fj0x, ay = up ? fj1y : fj0y, az = up ? fj1z : fj0z;
-                ax += __shfl_xor_sync(0xffffffffu, up ? fj0x : fj1x, 4);
-                ay += __shfl_xor_sync(0xffffffffu, up ? fj0y : fj1y, 4);
-                az += __shfl_xor_sync(0xffffffffu, up ? fj0z : fj1z, 4);
+                ax += __shfl_xor_sync(kFull, up ? fj0x : fj1x, 4);
+                ay += __shfl_xor_sync(kFull, up ? fj0y : fj1y, 4);
+                az += __shfl_xor_sync(kFull, up ? fj0z : fj1z, 4);
 #pragma unroll
                 for (int o = 1; o < 4; o <<= 1) {
-                    ax += __shfl_xor_sync(0xffffffffu, ax, o);
-                    ay += __shfl_xor_sync(0xffffffffu, ay, o);
-                    az += __shfl_xor_sync(0xffffffffu, az, o);
+                    ax += __shfl_xor_sync(kFull, ax, o);
+                    ay += __shfl_xor_sync(kFull, ay, o);
+                    az += __shfl_xor_sync(kFull, az, o);
                 }
                 const int comp = tx & 3;
                 if (comp < 3) {
@@ -407,11 +527,10 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
         __syncwarp();
         // i forces of this chunk: sum the 4 ty partials of each atom
         for (int a = lane; a < ncl * kClusterSize; a += 32) {
-            const int k = a >> 3, t = a & 7;
-            S4 sum = w.fi[k * 32 + t];
+            S4 sum = w.fi[a * 4];
 #pragma unroll
             for (int q = 1; q < 4; ++q) {
-                const S4 v = w.fi[k * 32 + q * 8 + t];
+                const S4 v = w.fi[a * 4 + q];
                 sum.x += v.x; sum.y += v.y; sum.z += v.z;
                 if (ENERGY) sum.w += v.w;
             }
@@ -424,7 +543,7 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
         __syncwarp();
         if (ENERGY) {
 #pragma unroll
-            for (int o = 16; o; o >>= 1) npair += __shfl_xor_sync(0xffffffffu, npair, o);
+            for (int o = 16; o; o >>= 1) npair += __shfl_xor_sync(kFull, npair, o);
             if (lane == 0 && npair) atomicAdd((unsigned long long*)p.pair_count, (unsigned long long)npair);
         }
     }

@@ -172,6 +172,10 @@ void enqueue_rebuild_from_ref(md_handle* h, cudaStream_t s)
     launch_step_a(P, 0, s, h->grid_atoms);
     launch_cells(P, s, h->grid_atoms, h->grid_cells);
     launch_pair_list(P, s, h->list_blocks);
+    // a force pass at the build positions trims the entries' i-atom masks
+    // exactly as the step of the original build did (its forces are discarded)
+    set_build_step(h, s, true);
+    launch_pair_forces(P, s, false, h->pair_blocks, h->pair_warps);
     for (int d = 0; d < 3; ++d)
         cudaMemcpyAsync(cur[d], h->d_scratch + (size_t)d * h->N, nb, cudaMemcpyDeviceToDevice, s);
     launch_refresh(P, s);
@@ -558,8 +562,8 @@ static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* 
             double ep = std::sqrt(eps_ts[a] * eps_ts[b]);
             double s6 = sg * sg * sg * sg * sg * sg;
             double c6 = 4.0 * ep * s6, c12 = c6 * s6;
-            lj_d[(size_t)a * nts_lj + b] = make_double2(-c6, c12);   // pair kernels take (-c6, c12)
-            lj_f[(size_t)a * nts_lj + b] = make_float2(-(float)c6, (float)c12);
+            lj_d[(size_t)a * nts_lj + b] = make_double2(-6.0 * c6, c12);   // pair kernels take (-6 c6, c12)
+            lj_f[(size_t)a * nts_lj + b] = make_float2((float)(-6.0 * c6), (float)c12);
         }
     std::vector<double> etab(kNEtab), inv12(13, 0.0);
     for (int k = 0; k < kNEtab; ++k) etab[k] = std::exp(-(double)k / 16.0);

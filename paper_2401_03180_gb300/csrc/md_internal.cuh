@@ -15,6 +15,7 @@ namespace mdg {
 constexpr int kClusterSize = 8;
 constexpr int kSuperClusters = 8;     // K_SC
 constexpr int kHalfShell = 14;        // self cell + 13 neighbour cells
+constexpr int kSCAtoms = kSuperClusters * kClusterSize;   // atom slots of a super-cluster
 constexpr int kChunk = 8;             // cluster-pair list entries per force work item
 constexpr int kListMinPerCluster = 32;   // initial pair-list entries per cluster
 constexpr int kMaxSpecies = 8;
@@ -35,6 +36,13 @@ enum : unsigned {
     ERR_TABLE_END = 8u,
     ERR_LIST = 16u,             // cluster-pair list capacity exceeded
 };
+
+// Cluster-pair list entry: x = j-cluster, y = half-shell index of the
+// j-cluster's cell | kEntryExcl when an i-atom and a j-atom may share a
+// fragment, (z, w) = 64-bit mask of the super-cluster's atom slots (bit
+// k*8 + a: atom a of i-cluster k) that may interact with the j-cluster.
+using PairEntry = uint4;
+constexpr unsigned kEntryExcl = 0x100u;
 
 struct Grid {                // cell grid of one replica (rebuilt every step)
     double origin[3];        // lower corner (nm)
@@ -102,8 +110,8 @@ struct Params {
     const long long* e_auger_mev;// [n_species]
     const double* etab;      // [kNEtab]
     const double* inv12;     // [13] 1/m
-    const float2* lj_f;      // [n_ts_lj][n_ts_lj] (-c6, c12)
-    const double2* lj_d;     // [n_ts_lj][n_ts_lj] (-c6, c12)
+    const float2* lj_f;      // [n_ts_lj][n_ts_lj] (-6 c6, c12)
+    const double2* lj_d;     // [n_ts_lj][n_ts_lj] (-6 c6, c12)
 
     // replicas
     Grid* grid;              // grid for the next cell build (step kernel output)
@@ -126,7 +134,7 @@ struct Params {
     int* sc_first;           // [sc_cap] first cluster
     int* sc_ncl;             // [sc_cap] clusters in the super-cluster
     int* counters;           // [0] n_sc, [1] n_slots, [2] work, [3] ticket, [6] list entries, [7] chunks
-    uint2* pl;               // [pl_cap] cluster-pair list: (j-cluster, half-shell index << 8 | i mask)
+    PairEntry* pl;           // [pl_cap] cluster-pair list (j-cluster, half-shell index, i-atom mask)
     int4* pl_chunk;          // [chunk_cap] (SC, first entry, entries, replica)
     int pl_cap, chunk_cap;
 

@@ -8,7 +8,7 @@
 // entry point serves them: all the scratch it needs (cell list, packed
 // coordinates, fixed-point force sums, grid and screening bookkeeping) lives
 // in one file-scope __device__ array of a fixed, modest size
-// (MD_NOALLOC_MAX_ATOMS atoms, MD_NOALLOC_MAX_CELLS cells; about 5 MB) that
+// (MD_NOALLOC_MAX_ATOMS atoms, MD_NOALLOC_MAX_CELLS cells; about 10.5 MB) that
 // every GPU loading the library holds until the process exits.  The caller
 // passes inputs and the output buffer; nothing is allocated.
 //
@@ -73,7 +73,7 @@ constexpr Layout make_layout()
     L.fx = take(8 * (size_t)kSlotCap); L.fy = take(8 * (size_t)kSlotCap); L.fz = take(8 * (size_t)kSlotCap);
     L.epot = take(8 * (size_t)kSlotCap);
     L.pair_count = take(8); L.err = take(4); L.step = take(8); L.kick = take(4);
-    L.pl = take(8 * (size_t)kPlCap); L.pl_chunk = take(16 * (size_t)kChunkCap);
+    L.pl = take(sizeof(PairEntry) * (size_t)kPlCap); L.pl_chunk = take(16 * (size_t)kChunkCap);
     L.cl_cen = take(32 * (size_t)kClusterCap);
     L.total = o;
     return L;
@@ -232,7 +232,7 @@ extern "C" md_status md_forces_noalloc(const md_forces_input* in, double* d_f, v
     P.fx = (long long*)(B + kL.fx); P.fy = (long long*)(B + kL.fy); P.fz = (long long*)(B + kL.fz);
     P.epot = (long long*)(B + kL.epot); P.pair_count = (long long*)(B + kL.pair_count);
     P.err = (unsigned*)(B + kL.err); P.step = (long long*)(B + kL.step); P.kick_full = (int*)(B + kL.kick);
-    P.pl = (uint2*)(B + kL.pl); P.pl_chunk = (int4*)(B + kL.pl_chunk);
+    P.pl = (PairEntry*)(B + kL.pl); P.pl_chunk = (int4*)(B + kL.pl_chunk);
     P.pl_cap = kPlCap; P.chunk_cap = kChunkCap;
     P.cl_cen = (double4_32a*)(B + kL.cl_cen);
     P.grid_b = P.grid;                 // one build: the build grid is the grid
@@ -255,8 +255,8 @@ extern "C" md_status md_forces_noalloc(const md_forces_input* in, double* d_f, v
             const double ep = std::sqrt(eps[a] * eps[b]);
             const double s6 = sg * sg * sg * sg * sg * sg;
             const double c6 = 4.0 * ep * s6, c12 = c6 * s6;
-            tab_d[(size_t)a * nts + b] = make_double2(-c6, c12);   // pair kernels take (-c6, c12)
-            tab_f[(size_t)a * nts + b] = make_float2(-(float)c6, (float)c12);
+            tab_d[(size_t)a * nts + b] = make_double2(-6.0 * c6, c12);   // pair kernels take (-6 c6, c12)
+            tab_f[(size_t)a * nts + b] = make_float2((float)(-6.0 * c6), (float)c12);
         }
     const int zs[MD_MAX_SPECIES] = {in->z[0], in->z[1], in->z[2], in->z[3], in->z[4], in->z[5], in->z[6], in->z[7]};
     const double one = 1.0;
