@@ -14,15 +14,15 @@
 //   * a warp of the force kernel owns one chunk at a time (dynamic scheduling
 //     through an atomic counter);
 //   * the SC's atoms and per-(atom, lane row) i-force partials live in shared
-//     memory; for each entry the warp compacts the mask into a list of i-atoms
-//     and takes them 8 at a time: lane (tx = lane & 7, ty = lane >> 3) pairs
-//     list atom tx with atoms ty, ty+4 of the j-cluster, so lanes only idle in
-//     an entry's last tile of 8;
-//   * at the step of a Verlet-buffered build a distance pass over each entry
-//     drops from its mask the i-atoms with no j-atom within r_cut + skin
-//     (exact for the list's lifetime) and records whether any pair in range
-//     lies within one fragment, before the forces are evaluated, so every
-//     evaluation of the list runs over the same atoms;
+//     memory; lane (tx = lane & 7, ty = lane >> 3) takes atoms ty, ty+4 of the
+//     entry's j-cluster and, tile by tile, the next i-cluster whose atom tx
+//     is in the mask (its own queue), so a lane column always sees the same
+//     slots in the same order and the shared-memory rows it touches never
+//     share a bank with another column's;
+//   * at the step of a Verlet-buffered build the evaluation also tests every
+//     pair against r_cut + skin and drops from the mask the i-atoms with no
+//     j-atom in range (exact for the list's lifetime), and clears the entry's
+//     fragment flag when no pair in range lies within one fragment;
 //   * forces are summed in FP32 (or FP64) within one chunk for the i side
 //     and one (SC, j-cluster) entry for the j side, then converted
 //     once to 64-bit fixed point (2^-32 kJ/mol/nm): the per-atom totals are
@@ -79,15 +79,15 @@ struct Prec<true> {
     static __device__ __forceinline__ T fma(T a, T b, T c) { return __fma_rn(a, b, c); }
 };
 
-// per-warp shared-memory layout; row kSCAtoms is a far-away, uncharged
-// stand-in that idle lanes of an entry's last tile point at
+// per-warp shared-memory layout; rows kSCAtoms + tx are far-away, uncharged
+// stand-ins for lane column tx once its queue of i-clusters is used up
+constexpr int kFiRow = kSCAtoms + kClusterSize;   // rows per lane row of the i-force partials
 template <bool FP64>
 struct WarpSmem {
-    typename Prec<FP64>::S4 ix[kSCAtoms + 1];          // x, y, z, f*q of the SC atoms
-    int2 it[kSCAtoms + 1];                             // LJ row byte offset, fragment
-    typename Prec<FP64>::S4 fi[(kSCAtoms + 1) * 4];    // per (atom, ty) force (+energy)
-    typename Prec<FP64>::S4 sh[kHalfShell];            // shift of each half-shell cell
-    unsigned char il[kSCAtoms + 8];                    // compacted i-atoms of an entry
+    typename Prec<FP64>::S4 ix[kFiRow];        // x, y, z, f*q of the SC atoms
+    int2 it[kFiRow];                           // LJ row byte offset, fragment
+    typename Prec<FP64>::S4 fi[4 * kFiRow];    // [ty][atom] force (+energy)
+    typename Prec<FP64>::S4 sh[kHalfShell];    // shift of each half-shell cell
 };
 
 template <bool FP64>
@@ -106,8 +106,8 @@ __device__ __forceinline__ void red_fix(long long* dst, typename Prec<FP64>::T v
 // no such pair skip the test).  qjk = q_j * kappa.  The LJ table holds
 // (-6 c6, c12).  The force on i is accumulated into (fx, fy, fz), the force on
 // j into (fjx, fjy, fjz); with ENERGY the cutoff-shifted pair energy into u.
-// Multiply-adds are written out so that each accumulation is one fused
-// operation.
+// r2o returns |d|^2.  Multiply-adds are written out so that each accumulation
+// is one fused operation.
 template <bool FP64, bool ENERGY, bool EXCL>
 __device__ __forceinline__ void pair(const typename Prec<FP64>::S4& xi, int row_off, int fri,
                                      typename Prec<FP64>::T xj, typename Prec<FP64>::T yj,
@@ -119,12 +119,13 @@ __device__ __forceinline__ void pair(const typename Prec<FP64>::S4& xi, int row_
                                      typename Prec<FP64>::T& fz, typename Prec<FP64>::T& fjx,
                                      typename Prec<FP64>::T& fjy, typename Prec<FP64>::T& fjz,
                                      typename Prec<FP64>::T& u, int& npair, typename Prec<FP64>::T erc,
-                                     typename Prec<FP64>::T irc)
+                                     typename Prec<FP64>::T irc, typename Prec<FP64>::T& r2o)
 {
     using P = Prec<FP64>;
     using T = typename P::T;
     const T dx = xi.x - xj, dy = xi.y - yj, dz = xi.z - zj;
     const T r2 = P::fma(dz, dz, P::fma(dy, dy, dx * dx));
+    r2o = r2;
     const bool in = (r2 < rc2) && ok;
     const T rinv = in ? P::rsq(r2) : T(0);
     const typename P::C2 c = *reinterpret_cast<const typename P::C2*>(lj_bytes + row_off + tsj_off);
@@ -285,32 +286,42 @@ __global__ void __launch_bounds__(kHalfShell * 32) k_pair_list(Params p)
                 const unsigned m = base == jr0 ? m_first : test(base + lane);
                 const unsigned bal = __ballot_sync(0xffffffffu, m != 0);
                 const int at = off + __popc(bal & ((1u << lane) - 1u));
-                if (m && at < end) {
-                    // i-atoms of the clusters in range that lie within r_cut + skin
-                    // of the j-cluster's box (padding slots are far away)
-                    const int jc = base + lane;
+                // i-atoms of the clusters in range that lie within r_cut + skin of the
+                // j-cluster's box (padding slots are far away), one entry at a time
+                // across the warp: lane l tests slots l and l + 32
+                unsigned my_lo = 0u, my_hi = 0u;
+                bool my_share = false;
+                for (unsigned pend = bal; pend; pend &= pend - 1u) {
+                    const int L = __ffs(pend) - 1;
+                    const int jc = base + L;
+                    const unsigned mL = __shfl_sync(0xffffffffu, m, L);
                     const float4 lo = p.bb_lo[jc], hi = p.bb_hi[jc];
                     const float jlx = lo.x + Dfx, jly = lo.y + Dfy, jlz = lo.z + Dfz;
                     const float jhx = hi.x + Dfx, jhy = hi.y + Dfy, jhz = hi.z + Dfz;
+                    auto near = [&](float4 xi) {
+                        const float gx = fmaxf(0.0f, fmaxf(xi.x - jhx, jlx - xi.x));
+                        const float gy = fmaxf(0.0f, fmaxf(xi.y - jhy, jly - xi.y));
+                        const float gz = fmaxf(0.0f, fmaxf(xi.z - jhz, jlz - xi.z));
+                        return __fmaf_rn(gz, gz, __fmaf_rn(gy, gy, __fmul_rn(gx, gx))) < rcb2;
+                    };
+                    const bool in0 = ((mL >> (lane >> 3)) & 1u) && near(s_ip[lane]);
+                    const bool in1 = ((mL >> ((lane >> 3) + 4)) & 1u) && near(s_ip[lane + 32]);
+                    const unsigned alo = __ballot_sync(0xffffffffu, in0);
+                    const unsigned ahi = __ballot_sync(0xffffffffu, in1);
+                    // fragment ranges of the i-clusters in range against the j-cluster's
                     const int2 jfr = p.bb_frag[jc];
-                    unsigned long long am = 0ull;
-                    bool share = false;   // fragment ranges overlap: LJ exclusions possible
-                    for (unsigned mm = m; mm; mm &= mm - 1u) {
-                        const int k = __ffs(mm) - 1;
-                        share |= !(s_fr[k].y < jfr.x || jfr.y < s_fr[k].x);
-#pragma unroll
-                        for (int a = 0; a < kClusterSize; ++a) {
-                            const float4 xi = s_ip[k * kClusterSize + a];
-                            const float gx = fmaxf(0.0f, fmaxf(xi.x - jhx, jlx - xi.x));
-                            const float gy = fmaxf(0.0f, fmaxf(xi.y - jhy, jly - xi.y));
-                            const float gz = fmaxf(0.0f, fmaxf(xi.z - jhz, jlz - xi.z));
-                            if (__fmaf_rn(gz, gz, __fmaf_rn(gy, gy, __fmul_rn(gx, gx))) < rcb2)
-                                am |= 1ull << (k * kClusterSize + a);
-                        }
+                    const bool ov = lane < kSuperClusters && ((mL >> lane) & 1u) &&
+                                    !(s_fr[lane].y < jfr.x || jfr.y < s_fr[lane].x);
+                    const bool share = __any_sync(0xffffffffu, ov);
+                    if (lane == L) {
+                        my_lo = alo;
+                        my_hi = ahi;
+                        my_share = share;
                     }
-                    p.pl[at] = make_uint4((unsigned)jc, (unsigned)nb | (share ? kEntryExcl : 0u), (unsigned)am,
-                                          (unsigned)(am >> 32));
                 }
+                if (m && at < end)
+                    p.pl[at] = make_uint4((unsigned)(base + lane), (unsigned)nb | (my_share ? kEntryExcl : 0u), my_lo,
+                                          my_hi);
                 off += __popc(bal);
             }
             // both passes see the same boxes and round identically, so `off` ends at
@@ -348,11 +359,10 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
     WS& w = reinterpret_cast<WS*>(smem + tab)[warp];
 
     for (int k = threadIdx.x; k < nts * nts; k += blockDim.x) s_lj[k] = P::table(p)[k];
-    if (lane == 0) {
-        w.ix[kSCAtoms] = P::mk(T(-1.0e6), T(-1.0e6), T(-1.0e6), T(0));
-        w.it[kSCAtoms] = make_int2(0, (int)0x80000000);
+    if (lane < kClusterSize) {
+        w.ix[kSCAtoms + lane] = P::mk(T(-1.0e6), T(-1.0e6), T(-1.0e6), T(0));
+        w.it[kSCAtoms + lane] = make_int2(0, (int)0x80000000);
     }
-    if (lane < 4) w.fi[kSCAtoms * 4 + lane] = P::mk(T(0), T(0), T(0), T(0));
     __syncthreads();
     if (*p.err & (ERR_CELL | ERR_LIST)) return;
 
@@ -361,7 +371,10 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
     // In the step of a Verlet-buffered build the positions are the build's:
     // i-atoms with no j-atom within r_cut + skin are dropped from an entry's
     // mask for the list's lifetime (they cannot come within r_cut before the
-    // next build), before the entry's forces are evaluated.
+    // next build), and so is the fragment flag of an entry with no pair in
+    // range inside one fragment.  Lane column tx always takes the atoms tx of
+    // the entry's i-clusters in cluster order, so the dropped atoms only ever
+    // added exact zeros: every sum comes out bit-identical with either mask.
     const bool prune = p.builds != nullptr && p.half_skin2 > 0.0f && p.builds[1] != 0;
     const T rl2 = T(p.rlist_f + kBBoxMargin) * T(p.rlist_f + kBBoxMargin);
     const T rc2 = FP64 ? T(p.rc2) : T(p.rc2_f);
@@ -393,7 +406,7 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
                 w.it[a] = make_int2(t.x * nts * (int)sizeof(C2), t.y);   // byte offset of the LJ row
             }
         }
-        for (int k = lane; k < ncl * kClusterSize * 4; k += 32) w.fi[k] = P::mk(T(0), T(0), T(0), T(0));
+        for (int k = lane; k < 4 * kFiRow; k += 32) w.fi[k] = P::mk(T(0), T(0), T(0), T(0));
         if (lane < kHalfShell) {
             int dx, dy, dz;
             half_shell(lane, dx, dy, dz);
@@ -408,9 +421,9 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
             const int jcl = (int)__shfl_sync(kFull, ent.x, v);
             const unsigned code = __shfl_sync(kFull, ent.y, v);
             const int nb = (int)(code & 0xffu);
-            bool excl = (code & kEntryExcl) != 0u;
-            const unsigned mlo0 = __shfl_sync(kFull, ent.z, v), mhi0 = __shfl_sync(kFull, ent.w, v);
-            if ((mlo0 | mhi0) == 0u) continue;   // no i-atom in range (or emptied by pruning)
+            const bool excl = (code & kEntryExcl) != 0u;
+            const unsigned mlo = __shfl_sync(kFull, ent.z, v), mhi = __shfl_sync(kFull, ent.w, v);
+            if ((mlo | mhi) == 0u) continue;   // no i-atom in range (or emptied by pruning)
             const S4 D = w.sh[nb];
             const int s0 = jcl * kClusterSize + ty, s1 = s0 + 4;
             const T4 a0 = P::pos(p, s0), a1 = P::pos(p, s1);
@@ -421,86 +434,66 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
             const int j0off = t0.x * (int)sizeof(C2), j1off = t1.x * (int)sizeof(C2);
             const int kdiag = nb == 0 ? jcl - fc : -1;   // i-cluster equal to this j-cluster
 
-            // the entry's i-atoms in slot order; the last tile is padded with the stand-in
-            unsigned mlo = mlo0, mhi = mhi0;
-            int n_i = 0;
-            auto compact = [&]() {
-                const int nlo = __popc(mlo);
-                n_i = nlo + __popc(mhi);
-                const unsigned below = (1u << lane) - 1u;
-                __syncwarp();   // earlier readers of the list are done
-                if ((mlo >> lane) & 1u) w.il[__popc(mlo & below)] = (unsigned char)lane;
-                if ((mhi >> lane) & 1u) w.il[nlo + __popc(mhi & below)] = (unsigned char)(lane + 32);
-                if (lane < 8) w.il[n_i + lane] = (unsigned char)kSCAtoms;
-                __syncwarp();
-            };
-            compact();
-            if (prune) {
-                // keep the i-atoms with a j-atom within r_cut + skin (distances
-                // only), so that every evaluation of the list, this one included,
-                // runs over the same atoms
-                unsigned keep_lo = 0u, keep_hi = 0u;
-                bool share = false;   // a pair in range within one fragment
-                for (int t = 0; t < n_i; t += 8) {
-                    const int ia = w.il[t + tx];
-                    const S4 xi = w.ix[ia];
-                    const int fri = w.it[ia].y;
-                    const bool dg = (ia >> 3) == kdiag;
-                    const T dx0 = xi.x - x0, dy0 = xi.y - y0, dz0 = xi.z - z0;
-                    const T dx1 = xi.x - x1, dy1 = xi.y - y1, dz1 = xi.z - z1;
-                    const T r20 = P::fma(dz0, dz0, P::fma(dy0, dy0, dx0 * dx0));
-                    const T r21 = P::fma(dz1, dz1, P::fma(dy1, dy1, dx1 * dx1));
-                    const bool n0 = (!dg || (ia & 7) < ty) && r20 < rl2;
-                    const bool n1 = (!dg || (ia & 7) < ty + 4) && r21 < rl2;
-                    const unsigned b = __ballot_sync(kFull, n0 || n1);
-                    share |= __any_sync(kFull, (n0 && fri == t0.y) || (n1 && fri == t1.y));
-                    const bool mine = ty == 0 && (((b | (b >> 8) | (b >> 16) | (b >> 24)) >> tx) & 1u) && ia < kSCAtoms;
-                    keep_lo |= __reduce_or_sync(kFull, mine && ia < 32 ? 1u << ia : 0u);
-                    keep_hi |= __reduce_or_sync(kFull, mine && ia >= 32 ? 1u << (ia & 31) : 0u);
-                }
-                if (lane == 0) {
-                    if (keep_lo != mlo || keep_hi != mhi)
-                        *reinterpret_cast<uint2*>(&p.pl[ch.y + v].z) = make_uint2(keep_lo, keep_hi);
-                    if (share != excl) p.pl[ch.y + v].y = (unsigned)nb | (share ? kEntryExcl : 0u);
-                }
-                excl = share;
-                if ((keep_lo | keep_hi) == 0u) continue;
-                if (keep_lo != mlo || keep_hi != mhi) {
-                    mlo = keep_lo;
-                    mhi = keep_hi;
-                    compact();
-                }
-            }
+            // this lane column's i-clusters: bit k when atom tx of i-cluster k is in
+            // the mask; a tile takes the next one of every column
+            const unsigned clo = (mlo >> tx) & 0x01010101u, chi = (mhi >> tx) & 0x01010101u;
+            const unsigned col0 = ((clo * 0x01020408u) >> 24) | (((chi * 0x01020408u) >> 24) << 4);
+            const int n_t = (int)__reduce_max_sync(kFull, (unsigned)__popc(col0));
 
             T fj0x = 0, fj0y = 0, fj0z = 0, fj1x = 0, fj1y = 0, fj1z = 0;
+            unsigned keep = 0u;   // PRUNE: this column's i-clusters with a j-atom in range
+            bool share = false;   // PRUNE: a pair in range within one fragment
             // DIAG: the self-cluster diagonal (i < j inside the cluster); EXCL:
-            // pairs within one fragment are possible; other entries take the
-            // plain tile loop
-            auto tiles = [&](auto diag, auto ex) {
+            // pairs within one fragment are possible; PRUNE: build step
+            auto tiles = [&](auto diag, auto ex, auto pr) {
                 constexpr bool DIAG = decltype(diag)::value;
                 constexpr bool EXCL = DIAG || decltype(ex)::value;
-                for (int t = 0; t < n_i; t += 8) {
-                    const int ia = w.il[t + tx];
+                constexpr bool PRUNE = decltype(pr)::value;
+                unsigned col = col0;
+                for (int t = 0; t < n_t; ++t) {
+                    const int k = col ? __ffs(col) - 1 : -1;
+                    col &= col - 1u;
+                    const int ia = k >= 0 ? k * kClusterSize + tx : kSCAtoms + tx;   // idle: stand-in
                     const S4 xi = w.ix[ia];
                     const int2 ti = w.it[ia];
-                    S4 acc = w.fi[ia * 4 + ty];
+                    S4 acc = w.fi[ty * kFiRow + ia];
                     bool ok0 = true, ok1 = true;
                     if (DIAG) {
-                        const bool dg = (ia >> 3) == kdiag;
-                        ok0 = !dg || (ia & 7) < ty;
-                        ok1 = !dg || (ia & 7) < ty + 4;
+                        const bool dg = k == kdiag;
+                        ok0 = !dg || tx < ty;
+                        ok1 = !dg || tx < ty + 4;
                     }
+                    T r20, r21;
                     pair<FP64, ENERGY, EXCL>(xi, ti.x, ti.y, x0, y0, z0, a0.w, q0k, j0off, t0.y, ok0, lj_bytes, kap,
-                                             rc2, acc.x, acc.y, acc.z, fj0x, fj0y, fj0z, acc.w, npair, erc, irc);
+                                             rc2, acc.x, acc.y, acc.z, fj0x, fj0y, fj0z, acc.w, npair, erc, irc, r20);
                     pair<FP64, ENERGY, EXCL>(xi, ti.x, ti.y, x1, y1, z1, a1.w, q1k, j1off, t1.y, ok1, lj_bytes, kap,
-                                             rc2, acc.x, acc.y, acc.z, fj1x, fj1y, fj1z, acc.w, npair, erc, irc);
-                    w.fi[ia * 4 + ty] = acc;
+                                             rc2, acc.x, acc.y, acc.z, fj1x, fj1y, fj1z, acc.w, npair, erc, irc, r21);
+                    w.fi[ty * kFiRow + ia] = acc;
+                    if (PRUNE) {
+                        const bool n0 = ok0 && r20 < rl2, n1 = ok1 && r21 < rl2;
+                        const unsigned b = __ballot_sync(kFull, n0 || n1);
+                        if (k >= 0 && (((b | (b >> 8) | (b >> 16) | (b >> 24)) >> tx) & 1u)) keep |= 1u << k;
+                        if (EXCL) share |= __any_sync(kFull, (n0 && ti.y == t0.y) || (n1 && ti.y == t1.y));
+                    }
                 }
             };
-            if ((unsigned)kdiag < (unsigned)ncl) tiles(std::true_type{}, std::true_type{});
-            else if (excl) tiles(std::false_type{}, std::true_type{});
-            else tiles(std::false_type{}, std::false_type{});
-            __syncwarp();   // the next entry rewrites the i-atom list
+            if (prune) {
+                if ((unsigned)kdiag < (unsigned)ncl) tiles(std::true_type{}, std::true_type{}, std::true_type{});
+                else if (excl) tiles(std::false_type{}, std::true_type{}, std::true_type{});
+                else tiles(std::false_type{}, std::false_type{}, std::true_type{});
+                // columns back to the 64-bit atom mask (bit k*8 + tx)
+                const unsigned klo = __reduce_or_sync(kFull, (((keep & 0xfu) * 0x00204081u) & 0x01010101u) << tx);
+                const unsigned khi = __reduce_or_sync(kFull, (((keep >> 4) * 0x00204081u) & 0x01010101u) << tx);
+                if (lane == 0) {
+                    if (klo != mlo || khi != mhi)
+                        *reinterpret_cast<uint2*>(&p.pl[ch.y + v].z) = make_uint2(klo, khi);
+                    if (share != excl) p.pl[ch.y + v].y = (unsigned)nb | (share ? kEntryExcl : 0u);
+                }
+            } else {
+                if ((unsigned)kdiag < (unsigned)ncl) tiles(std::true_type{}, std::true_type{}, std::false_type{});
+                else if (excl) tiles(std::false_type{}, std::true_type{}, std::false_type{});
+                else tiles(std::false_type{}, std::false_type{}, std::false_type{});
+            }
             // j forces: sum over the 8 i-lanes of each ty group.  Lanes tx < 4 keep
             // atom ty (j0), lanes tx >= 4 atom ty + 4 (j1); then each lane holds one
             // component of one atom and issues one RED.
@@ -527,10 +520,10 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
         __syncwarp();
         // i forces of this chunk: sum the 4 ty partials of each atom
         for (int a = lane; a < ncl * kClusterSize; a += 32) {
-            S4 sum = w.fi[a * 4];
+            S4 sum = w.fi[a];
 #pragma unroll
             for (int q = 1; q < 4; ++q) {
-                const S4 v = w.fi[a * 4 + q];
+                const S4 v = w.fi[q * kFiRow + a];
                 sum.x += v.x; sum.y += v.y; sum.z += v.z;
                 if (ENERGY) sum.w += v.w;
             }

@@ -277,11 +277,12 @@ __global__ void __launch_bounds__(kStepThreads) k_step_a(Params p, int mode)
             z += p.dt * vz;
             const Grid& g = p.grid[r];
             if (g.periodic) {
-                // wrap only atoms that left the box (FP64 division is slow)
+                // wrap only atoms that left the box (FP64 division is slow); the
+                // tests run on the bit patterns
                 const double L0 = g.box[0], L1 = g.box[1], L2 = g.box[2];
-                if (x < 0.0 || x >= L0) { x -= L0 * floor(x / L0); if (x >= L0) x -= L0; }
-                if (y < 0.0 || y >= L1) { y -= L1 * floor(y / L1); if (y >= L1) y -= L1; }
-                if (z < 0.0 || z >= L2) { z -= L2 * floor(z / L2); if (z >= L2) z -= L2; }
+                if (below_zero(x) || at_or_above(x, L0)) { x -= L0 * floor(x / L0); if (x >= L0) x -= L0; }
+                if (below_zero(y) || at_or_above(y, L1)) { y -= L1 * floor(y / L1); if (y >= L1) y -= L1; }
+                if (below_zero(z) || at_or_above(z, L2)) { z -= L2 * floor(z / L2); if (z >= L2) z -= L2; }
             }
             // finite check on the exponent bits (integer ops; FP64 compares are slow here)
             if (((__double2hiint(x) & 0x7ff00000) == 0x7ff00000) || ((__double2hiint(y) & 0x7ff00000) == 0x7ff00000) ||
@@ -291,14 +292,17 @@ __global__ void __launch_bounds__(kStepThreads) k_step_a(Params p, int mode)
             p.vx[i] = vx; p.vy[i] = vy; p.vz[i] = vz;
             p.x[i] = x; p.y[i] = y; p.z[i] = z;
             if (p.xr) {
-                // displacement since the last list build (minimum image)
+                // displacement since the last list build (minimum image), squared
+                // in FP32: it only decides the rebuild, against half the skin
                 double d[3] = {x - p.xr[i], y - p.yr[i], z - p.zr[i]};
                 if (g.periodic)
                     for (int k = 0; k < 3; ++k) {
-                        if (d[k] > 0.5 * g.box[k]) d[k] -= g.box[k];
-                        else if (d[k] < -0.5 * g.box[k]) d[k] += g.box[k];
+                        const int o = beyond_half(d[k], g.box[k]);
+                        if (o > 0) d[k] -= g.box[k];
+                        else if (o < 0) d[k] += g.box[k];
                     }
-                const float d2 = (float)(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                const float e0 = (float)d[0], e1 = (float)d[1], e2 = (float)d[2];
+                const float d2 = e0 * e0 + e1 * e1 + e2 * e2;
                 // non-negative floats order like their bit patterns (NaN sorts high)
                 atomicMax(&s_maxd2, __float_as_uint(d2));
             }

@@ -181,6 +181,29 @@ __host__ __device__ __forceinline__ unsigned long long ordered_bits_host(double 
     return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
 }
 
+// Comparisons of doubles on their bit patterns, in the integer pipe (FP64
+// issues at 2 lanes per SM per clock on GB300).  For non-NaN operands they
+// give exactly the FP64 comparisons; -0.0 counts as zero.
+//
+// beyond_half(d, L), L > 0 normal: +1 when d > L/2, -1 when d < -L/2, else 0.
+__device__ __forceinline__ int beyond_half(double d, double L)
+{
+    const long long b = __double_as_longlong(d);
+    const long long half = __double_as_longlong(L) - (1ll << 52);   // bits of L/2
+    if ((b & 0x7fffffffffffffffll) <= half) return 0;
+    return b < 0 ? -1 : 1;
+}
+// x < 0 (x not -0.0) and x >= L for L > 0.
+__device__ __forceinline__ bool below_zero(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b < 0 && (b << 1) != 0;
+}
+__device__ __forceinline__ bool at_or_above(double x, double L)
+{
+    return __double_as_longlong(x) >= __double_as_longlong(L);
+}
+
 // The 13 half-shell neighbour offsets plus the cell itself (index 0).
 __host__ __device__ __forceinline__ void half_shell(int nb, int& dx, int& dy, int& dz)
 {
@@ -204,8 +227,9 @@ __device__ __forceinline__ void pack_slot(const Params& p, int slot, int i, cons
     double d[3] = {p.x[i] - cen[0], p.y[i] - cen[1], p.z[i] - cen[2]};
     if (g.periodic)
         for (int k = 0; k < 3; ++k) {
-            if (d[k] > 0.5 * g.box[k]) d[k] -= g.box[k];
-            else if (d[k] < -0.5 * g.box[k]) d[k] += g.box[k];
+            const int o = beyond_half(d[k], g.box[k]);
+            if (o > 0) d[k] -= g.box[k];
+            else if (o < 0) d[k] += g.box[k];
         }
     const int sp = p.species[i];
     const int qi = p.q[i];
