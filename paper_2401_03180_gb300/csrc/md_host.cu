@@ -172,6 +172,11 @@ void enqueue_rebuild_from_ref(md_handle* h, cudaStream_t s)
     launch_step_a(P, 0, s, h->grid_atoms);
     launch_cells(P, s, h->grid_atoms, h->grid_cells);
     launch_pair_list(P, s, h->list_blocks);
+    // a force pass at the build positions trims the entries' masks as the step
+    // of the original build did (its forces are discarded; the trimmed atoms
+    // only add exact zeros, so the forces below are the same either way)
+    set_build_step(h, s, true);
+    launch_pair_forces(P, s, false, h->pair_blocks, h->pair_warps);
     for (int d = 0; d < 3; ++d)
         cudaMemcpyAsync(cur[d], h->d_scratch + (size_t)d * h->N, nb, cudaMemcpyDeviceToDevice, s);
     launch_refresh(P, s);
