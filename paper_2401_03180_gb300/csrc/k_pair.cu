@@ -87,7 +87,8 @@ struct WarpSmem {
     typename Prec<FP64>::S4 ix[kFiRow];        // x, y, z, f*q of the SC atoms
     int2 it[kFiRow];                           // LJ row byte offset, fragment
     typename Prec<FP64>::S4 fi[4 * kFiRow];    // [ty][atom] force (+energy)
-    typename Prec<FP64>::S4 sh[kHalfShell];    // shift of each half-shell cell
+    typename Prec<FP64>::S4 jx[kChunk * kClusterSize];   // the chunk's j-atoms, shifted: x, y, z, q
+    int2 jt[kChunk * kClusterSize];                      // their LJ column byte offset, fragment
 };
 
 template <bool FP64>
@@ -368,6 +369,10 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
 
     const int tx = lane & 7, ty = lane >> 3;
     const int n_chunks = min(p.counters[7], p.chunk_cap);
+    // after the j-force reduction lane (tx, ty) holds component tx & 3 of atom
+    // ty (tx < 4) or ty + 4 (tx >= 4) of the entry's j-cluster
+    const int comp = tx & 3;
+    long long* const jdst = comp == 0 ? p.fx : (comp == 1 ? p.fy : p.fz);
     // In the step of a Verlet-buffered build the positions are the build's:
     // i-atoms with no j-atom within r_cut + skin are dropped from an entry's
     // mask for the list's lifetime (they cannot come within r_cut before the
@@ -394,8 +399,9 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
         const T kap = FP64 ? T(p.rs[rr].kappa_force) : T(p.rs[rr].kappa_f);
         const T erc = ENERGY ? P::expneg(kap * T(p.r_cut)) : T(0);
 
-        // the super-cluster's atoms into shared memory, partial forces cleared,
-        // the shift of every half-shell cell of this replica's grid
+        // the super-cluster's atoms and the chunk's j-atoms (shifted into the
+        // SC's cell frame) into shared memory, partial forces cleared: one load
+        // latency per chunk instead of one per entry
         __syncwarp();
         for (int a = lane; a < kSCAtoms; a += 32) {
             if ((a >> 3) < ncl) {
@@ -406,14 +412,23 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
                 w.it[a] = make_int2(t.x * nts * (int)sizeof(C2), t.y);   // byte offset of the LJ row
             }
         }
-        for (int k = lane; k < 4 * kFiRow; k += 32) w.fi[k] = P::mk(T(0), T(0), T(0), T(0));
-        if (lane < kHalfShell) {
-            int dx, dy, dz;
-            half_shell(lane, dx, dy, dz);
-            w.sh[lane] = FP64 ? P::mk(T(dx * g.edge[0]), T(dy * g.edge[1]), T(dz * g.edge[2]), T(0))
-                              : P::mk(T((float)dx * g.edge_f[0]), T((float)dy * g.edge_f[1]),
-                                      T((float)dz * g.edge_f[2]), T(0));
+        for (int a0 = 0; a0 < kChunk * kClusterSize; a0 += 32) {
+            const int a = a0 + lane, e = a >> 3;                 // entry e, atom a & 7
+            const unsigned jc = __shfl_sync(kFull, ent.x, e);
+            const unsigned cd = __shfl_sync(kFull, ent.y, e);
+            if (e < n_ent) {
+                int dx, dy, dz;
+                half_shell((int)(cd & 0xffu), dx, dy, dz);
+                const int slot = (int)jc * kClusterSize + (a & 7);
+                const T4 v = P::pos(p, slot);
+                const int2 t = p.tf[slot];
+                if (FP64) w.jx[a] = P::mk(v.x + T(dx * g.edge[0]), v.y + T(dy * g.edge[1]), v.z + T(dz * g.edge[2]), v.w);
+                else w.jx[a] = P::mk(v.x + T((float)dx * g.edge_f[0]), v.y + T((float)dy * g.edge_f[1]),
+                                     v.z + T((float)dz * g.edge_f[2]), v.w);
+                w.jt[a] = make_int2(t.x * (int)sizeof(C2), t.y);   // byte offset of the LJ column
+            }
         }
+        for (int k = lane; k < 4 * kFiRow; k += 32) w.fi[k] = P::mk(T(0), T(0), T(0), T(0));
         __syncwarp();
         int npair = 0;
 
@@ -424,14 +439,13 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
             const bool excl = (code & kEntryExcl) != 0u;
             const unsigned mlo = __shfl_sync(kFull, ent.z, v), mhi = __shfl_sync(kFull, ent.w, v);
             if ((mlo | mhi) == 0u) continue;   // no i-atom in range (or emptied by pruning)
-            const S4 D = w.sh[nb];
             const int s0 = jcl * kClusterSize + ty, s1 = s0 + 4;
-            const T4 a0 = P::pos(p, s0), a1 = P::pos(p, s1);
-            const int2 t0 = p.tf[s0], t1 = p.tf[s1];
-            const T x0 = a0.x + D.x, y0 = a0.y + D.y, z0 = a0.z + D.z;
-            const T x1 = a1.x + D.x, y1 = a1.y + D.y, z1 = a1.z + D.z;
+            const S4 a0 = w.jx[v * kClusterSize + ty], a1 = w.jx[v * kClusterSize + ty + 4];
+            const int2 t0 = w.jt[v * kClusterSize + ty], t1 = w.jt[v * kClusterSize + ty + 4];
+            const T x0 = a0.x, y0 = a0.y, z0 = a0.z;
+            const T x1 = a1.x, y1 = a1.y, z1 = a1.z;
             const T q0k = a0.w * kap, q1k = a1.w * kap;
-            const int j0off = t0.x * (int)sizeof(C2), j1off = t1.x * (int)sizeof(C2);
+            const int j0off = t0.x, j1off = t1.x;
             const int kdiag = nb == 0 ? jcl - fc : -1;   // i-cluster equal to this j-cluster
 
             // this lane column's i-clusters: bit k when atom tx of i-cluster k is in
@@ -509,11 +523,9 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
                     ay += __shfl_xor_sync(kFull, ay, o);
                     az += __shfl_xor_sync(kFull, az, o);
                 }
-                const int comp = tx & 3;
                 if (comp < 3) {
                     const T v3 = comp == 0 ? ax : (comp == 1 ? ay : az);
-                    long long* dst = (comp == 0 ? p.fx : comp == 1 ? p.fy : p.fz) + (up ? s1 : s0);
-                    red_fix<FP64>(dst, v3, p.err);
+                    red_fix<FP64>(jdst + (up ? s1 : s0), v3, p.err);
                 }
             }
         }
