@@ -289,16 +289,26 @@ __global__ void __launch_bounds__(kHalfShell * 32) k_pair_list(Params p)
                 const int at = off + __popc(bal & ((1u << lane) - 1u));
                 // i-atoms of the clusters in range that lie within r_cut + skin of the
                 // j-cluster's box (padding slots are far away), one entry at a time
-                // across the warp: lane l tests slots l and l + 32
+                // across the warp: lane l tests slots l and l + 32.  Each lane loads
+                // its own j-cluster's box once; the entry loop shuffles it.
                 unsigned my_lo = 0u, my_hi = 0u;
                 bool my_share = false;
+                float4 blo = make_float4(0.f, 0.f, 0.f, 0.f), bhi = blo;
+                int2 bfr = make_int2(0, 0);
+                if (m) {
+                    blo = p.bb_lo[base + lane];
+                    bhi = p.bb_hi[base + lane];
+                    bfr = p.bb_frag[base + lane];
+                }
                 for (unsigned pend = bal; pend; pend &= pend - 1u) {
                     const int L = __ffs(pend) - 1;
-                    const int jc = base + L;
                     const unsigned mL = __shfl_sync(0xffffffffu, m, L);
-                    const float4 lo = p.bb_lo[jc], hi = p.bb_hi[jc];
-                    const float jlx = lo.x + Dfx, jly = lo.y + Dfy, jlz = lo.z + Dfz;
-                    const float jhx = hi.x + Dfx, jhy = hi.y + Dfy, jhz = hi.z + Dfz;
+                    const float jlx = __shfl_sync(0xffffffffu, blo.x, L) + Dfx;
+                    const float jly = __shfl_sync(0xffffffffu, blo.y, L) + Dfy;
+                    const float jlz = __shfl_sync(0xffffffffu, blo.z, L) + Dfz;
+                    const float jhx = __shfl_sync(0xffffffffu, bhi.x, L) + Dfx;
+                    const float jhy = __shfl_sync(0xffffffffu, bhi.y, L) + Dfy;
+                    const float jhz = __shfl_sync(0xffffffffu, bhi.z, L) + Dfz;
                     auto near = [&](float4 xi) {
                         const float gx = fmaxf(0.0f, fmaxf(xi.x - jhx, jlx - xi.x));
                         const float gy = fmaxf(0.0f, fmaxf(xi.y - jhy, jly - xi.y));
@@ -310,7 +320,7 @@ __global__ void __launch_bounds__(kHalfShell * 32) k_pair_list(Params p)
                     const unsigned alo = __ballot_sync(0xffffffffu, in0);
                     const unsigned ahi = __ballot_sync(0xffffffffu, in1);
                     // fragment ranges of the i-clusters in range against the j-cluster's
-                    const int2 jfr = p.bb_frag[jc];
+                    const int2 jfr = make_int2(__shfl_sync(0xffffffffu, bfr.x, L), __shfl_sync(0xffffffffu, bfr.y, L));
                     const bool ov = lane < kSuperClusters && ((mL >> lane) & 1u) &&
                                     !(s_fr[lane].y < jfr.x || jfr.y < s_fr[lane].x);
                     const bool share = __any_sync(0xffffffffu, ov);
