@@ -12,7 +12,8 @@
 namespace mdg {
 
 constexpr int kAccCopies = 16;   // accumulator copies per replica (spread contention)
-constexpr int kStepThreads = 128;
+constexpr int kStepAtoms = 128;     // atoms per block of the step kernel
+constexpr int kStepThreads = 256;   // two threads per atom: kick/drift and charge update
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11): 10 rounds, multipliers M0, M1 on
@@ -167,6 +168,8 @@ constexpr int kInlineReps = 4;   // up to this many replicas the step kernel's l
 __device__ void finalize_replica(const Params& p, int rr, int lane, long long next)
 {
     RepAccum* a = p.acc + (size_t)rr * kAccCopies;
+    RepState st;
+    if (lane == 0) st = p.rs[rr];   // issued before the accumulators are read and cleared
     long long v[6] = {0, 0, 0, 0, 0, 0};
     unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0ull, 0ull, 0ull};
     if (lane < kAccCopies) {
@@ -185,7 +188,7 @@ __device__ void finalize_replica(const Params& p, int rr, int lane, long long ne
             a[lane].bmax[d] = 0ull;
         }
     }
-    for (int o = 16; o; o >>= 1) {
+    for (int o = kAccCopies / 2; o; o >>= 1) {   // lanes 0..kAccCopies-1 hold the copies
         for (int k = 0; k < 6; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
         for (int d = 0; d < 3; ++d) {
             const unsigned long long x = __shfl_xor_sync(0xffffffffu, mn[d], o);
@@ -195,7 +198,6 @@ __device__ void finalize_replica(const Params& p, int rr, int lane, long long ne
         }
     }
     if (lane == 0) {
-        RepState st = p.rs[rr];
         st.n_e += v[0];
         st.e_gas += v[1];
         if (st.e_gas < 0) st.e_gas = 0;
@@ -209,7 +211,7 @@ __device__ void finalize_replica(const Params& p, int rr, int lane, long long ne
 // Once per step, after every replica: counters, step number and, with the
 // Verlet buffer, the rebuild decision and the graph condition.
 template <bool SETCOND>
-__device__ void finalize_step(const Params& p, int mode, long long next)
+__device__ void finalize_step(const Params& p, int mode, long long next, unsigned maxd2)
 {
     p.counters[3] = 0;
     if (mode & STEP_ADVANCE) *p.step = next;
@@ -218,9 +220,8 @@ __device__ void finalize_step(const Params& p, int mode, long long next)
         p.counters[2] = 0;   // work counter of the force kernel (also reset by a build)
         // rebuild once some atom may have closed half of the skin: pairs
         // within r_cut now were within r_cut + skin at the build
-        const unsigned m = __ldcg(p.maxd2);
         *p.maxd2 = 0u;
-        const int rebuild = m > __float_as_uint(p.half_skin2) ? 1 : 0;
+        const int rebuild = maxd2 > __float_as_uint(p.half_skin2) ? 1 : 0;
         p.builds[0] += rebuild;
         p.builds[1] = rebuild;
         cudaGraphSetConditional(p.cond, (unsigned)rebuild);
@@ -251,16 +252,19 @@ __global__ void __launch_bounds__(kStepThreads) k_step_a(Params p, int mode)
 
     const long long step = *p.step;
     const int kick_full = *p.kick_full;
-    const int first = blockIdx.x * blockDim.x;
+    // warps 0-3 kick, drift and re-pack atoms first..first+127; warps 4-7 run
+    // the charge update of the same atoms (independent until the re-pack)
+    const bool cr_role = tid >= kStepAtoms;
+    const int first = blockIdx.x * kStepAtoms;
     const int r0 = p.rep[first < p.n_atoms ? first : p.n_atoms - 1];
-    const int i = first + tid;
+    const int i = first + (tid & (kStepAtoms - 1));
     const bool live = i < p.n_atoms;
     const int lane = tid & 31;
     int r = live ? p.rep[i] : -1;
     double pos[3] = {0.0, 0.0, 0.0};
     bool vac = false;
 
-    if (live) {
+    if (live && !cr_role) {
         const int s = p.species[i];
         double x = p.x[i], y = p.y[i], z = p.z[i];
         if (mode & STEP_KICK_DRIFT) {
@@ -359,7 +363,7 @@ __global__ void __launch_bounds__(kStepThreads) k_step_a(Params p, int mode)
     }
 
     // ---- collisional-radiative update (reading of Sec. II.A) ----
-    if (live && (mode & STEP_CR)) {
+    if (live && cr_role && (mode & STEP_CR)) {
         const int s = p.species[i];
         const int Z = p.zs[s];
         const int qi = p.q[i], hi = p.h[i];
@@ -431,7 +435,8 @@ __global__ void __launch_bounds__(kStepThreads) k_step_a(Params p, int mode)
     // ---- Verlet-buffered list: the packed record of this atom for the forces
     // of this step, in the slot of the last build (a build, if one follows,
     // rewrites all records); the force sums are cleared after the kick read them
-    if (live && p.xr && (mode & STEP_KICK_DRIFT)) {
+    __syncthreads();   // the charges of this step are written
+    if (live && !cr_role && p.xr && (mode & STEP_KICK_DRIFT)) {
         const int slot = p.slot_of[i];
         const double4_32a c = p.cl_cen[slot / kClusterSize];
         const double cen[3] = {c.x, c.y, c.z};
@@ -441,7 +446,7 @@ __global__ void __launch_bounds__(kStepThreads) k_step_a(Params p, int mode)
 
     // ---- flush block partials ----
     {
-        const int last_atom = min(first + (int)blockDim.x, p.n_atoms) - 1;
+        const int last_atom = min(first + kStepAtoms, p.n_atoms) - 1;
         const int r_last = p.rep[last_atom];
         const int nw = min(r_last - r0 + 1, kRepWindow);
         for (int k = tid; k < nw * 12; k += blockDim.x) {
@@ -474,10 +479,11 @@ __global__ void __launch_bounds__(kStepThreads) k_step_a(Params p, int mode)
     __syncthreads();
     if (!s_last) return;
     __threadfence();
+    const unsigned m2 = (SETCOND && tid == 0) ? __ldcg(p.maxd2) : 0u;   // issued early
     const long long next = (mode & STEP_ADVANCE) ? step + 1 : step;
     const int warp = tid >> 5, n_warps = blockDim.x >> 5;
     for (int rr = warp; rr < p.n_rep; rr += n_warps) finalize_replica(p, rr, lane, next);
-    if (tid == 0) finalize_step<SETCOND>(p, mode, next);
+    if (tid == 0) finalize_step<SETCOND>(p, mode, next, m2);
 }
 
 // Per-replica reduction when there are many replicas: one warp each, then the
@@ -498,13 +504,13 @@ __global__ void __launch_bounds__(256) k_step_fin(Params p, int mode)
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    if (tid == 0) finalize_step<SETCOND>(p, mode, next);
+    if (tid == 0) finalize_step<SETCOND>(p, mode, next, SETCOND ? __ldcg(p.maxd2) : 0u);
 }
 
 void launch_step_a(const Params& p, int mode, cudaStream_t s, int grid_atoms)
 {
     (void)grid_atoms;
-    const int blocks = (p.n_atoms + kStepThreads - 1) / kStepThreads;
+    const int blocks = (p.n_atoms + kStepAtoms - 1) / kStepAtoms;
     const int fin_blocks = (p.n_rep * 32 + 255) / 256;
     if (mode & STEP_SETCOND) {
         k_step_a<true><<<blocks, kStepThreads, 0, s>>>(p, mode);
