@@ -41,7 +41,7 @@ struct Prec<false> {
     using T = float;
     using T4 = float4;         // global packed position + charge
     using S4 = float4;         // shared-memory copy
-    using C2 = float2;         // -6 c6, c12
+    using C2 = float2;         // -6 c6, -ln2 c12
     static __device__ __forceinline__ T4 pos(const Params& p, int slot) { return p.xq[slot]; }
     // single MUFU operations (arguments are far from the denormal range)
     static __device__ __forceinline__ T rsq(T x)
@@ -56,6 +56,12 @@ struct Prec<false> {
         asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x * -1.4426950408889634f));
         return y;
     }
+    static __device__ __forceinline__ T exp2_(T x)
+    {
+        T y;
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+        return y;
+    }
     static __device__ __forceinline__ long long fix(T v) { return __float2ll_rn(v * 4294967296.0f); }
     static __device__ __forceinline__ bool fix_ok(T v) { return fabsf(v) < 1.0737418e9f; }
     static __device__ __forceinline__ const C2* table(const Params& p) { return p.lj_f; }
@@ -68,10 +74,11 @@ struct Prec<true> {
     using T = double;
     using T4 = double4_32a;
     using S4 = double4_16a;
-    using C2 = double2;        // -6 c6, c12
+    using C2 = double2;        // -6 c6, -ln2 c12
     static __device__ __forceinline__ T4 pos(const Params& p, int slot) { return p.xq64[slot]; }
     static __device__ __forceinline__ T rsq(T x) { return 1.0 / sqrt(x); }
     static __device__ __forceinline__ T expneg(T x) { return exp(-x); }
+    static __device__ __forceinline__ T exp2_(T x) { return exp2(x); }
     static __device__ __forceinline__ long long fix(T v) { return __double2ll_rn(v * 4294967296.0); }
     static __device__ __forceinline__ bool fix_ok(T v) { return fabs(v) < 1.073741824e9; }
     static __device__ __forceinline__ const C2* table(const Params& p) { return p.lj_d; }
@@ -98,24 +105,25 @@ __device__ __forceinline__ void red_fix(long long* dst, typename Prec<FP64>::T v
         atomicOr(err, ERR_OVERFLOW);
         return;
     }
-    const long long q = Prec<FP64>::fix(v);
-    if (q != 0) atomicAdd((unsigned long long*)dst, (unsigned long long)q);
+    atomicAdd((unsigned long long*)dst, (unsigned long long)Prec<FP64>::fix(v));
 }
 
 // One pair, d = x_i - x_j.  `ok` drops the duplicates of the self-cluster
 // diagonal; with EXCL equal fragments drop the LJ part (entries known to hold
-// no such pair skip the test).  qjk = q_j * kappa.  The LJ table holds
-// (-6 c6, c12).  The force on i is accumulated into (fx, fy, fz), the force on
-// j into (fjx, fjy, fjz); with ENERGY the cutoff-shifted pair energy into u.
-// r2o returns |d|^2.  Multiply-adds are written out so that each accumulation
-// is one fused operation.
+// no such pair skip the test).  qjk = q_j * kappa, kl = -kappa log2(e).  The
+// LJ table holds (-6 c6, -ln2 c12), so that t = kl r serves both the
+// screening factor e^{-kappa r} = 2^t and the kappa r term of the LJ force
+// (kappa r = -ln2 t).  The force on i is accumulated into (fx, fy, fz), the
+// force on j into (fjx, fjy, fjz); with ENERGY the cutoff-shifted pair
+// energy into u.  r2o returns |d|^2.  Multiply-adds are written out so that
+// each accumulation is one fused operation.
 template <bool FP64, bool ENERGY, bool EXCL>
 __device__ __forceinline__ void pair(const typename Prec<FP64>::S4& xi, int row_off, int fri,
                                      typename Prec<FP64>::T xj, typename Prec<FP64>::T yj,
                                      typename Prec<FP64>::T zj, typename Prec<FP64>::T qj,
                                      typename Prec<FP64>::T qjk, int tsj_off, int frj, bool ok,
                                      const unsigned char* __restrict__ lj_bytes,
-                                     typename Prec<FP64>::T kap, typename Prec<FP64>::T rc2,
+                                     typename Prec<FP64>::T kl, typename Prec<FP64>::T rc2,
                                      typename Prec<FP64>::T& fx, typename Prec<FP64>::T& fy,
                                      typename Prec<FP64>::T& fz, typename Prec<FP64>::T& fjx,
                                      typename Prec<FP64>::T& fjy, typename Prec<FP64>::T& fjz,
@@ -124,6 +132,7 @@ __device__ __forceinline__ void pair(const typename Prec<FP64>::S4& xi, int row_
 {
     using P = Prec<FP64>;
     using T = typename P::T;
+    constexpr T kLn2 = T(0.69314718055994530942);
     const T dx = xi.x - xj, dy = xi.y - yj, dz = xi.z - zj;
     const T r2 = P::fma(dz, dz, P::fma(dy, dy, dx * dx));
     r2o = r2;
@@ -134,12 +143,12 @@ __device__ __forceinline__ void pair(const typename Prec<FP64>::S4& xi, int row_
     const T rinv6 = rinv2 * rinv2 * rinv2;
     const T lj6 = (EXCL && fri == frj) ? T(0) : rinv6;   // bonded in the native structure: no LJ
     const T r = r2 * rinv;
-    const T kr = kap * r;
-    const T e = P::expneg(kr);
-    const T A = c.y * rinv6;                    // c12 / r^6
-    const T B = P::fma(c.x, T(1.0 / 6.0), A);   // c12/r^6 - c6
-    const T D6 = P::fma(A, T(12), c.x);         // 12 c12/r^6 - 6 c6
-    const T E1 = P::fma(kr, B, D6);
+    const T t = kl * r;                         // -kappa r log2(e)
+    const T e = P::exp2_(t);                    // e^{-kappa r}
+    const T An = c.y * rinv6;                   // -ln2 c12/r^6
+    const T Bn = P::fma(c.x, T(-kLn2 / 6), An); // -ln2 (c12/r^6 - c6)
+    const T D6 = P::fma(An, T(-12 / kLn2), c.x);  // 12 c12/r^6 - 6 c6
+    const T E1 = P::fma(t, Bn, D6);             // D6 + kappa r (c12/r^6 - c6)
     const T Cc = xi.w * P::fma(qj, rinv, qjk);  // f q_i q_j (1/r + kappa)
     const T S = P::fma(lj6, E1, Cc);
     const T fs = S * (rinv2 * e);               // F(r)/r
@@ -151,8 +160,8 @@ __device__ __forceinline__ void pair(const typename Prec<FP64>::S4& xi, int row_
             const T qq = xi.w * qj;
             const T irc6 = irc * irc * irc * irc * irc * irc;
             const T lj_on = (EXCL && fri == frj) ? T(0) : T(1);
-            const T ush = erc * (qq * irc + lj_on * (c.y * irc6 + c.x * T(1.0 / 6.0)) * irc6);
-            u += e * (qq * rinv + lj6 * B) - ush;
+            const T ush = erc * (qq * irc + lj_on * (c.y * T(-1 / kLn2) * irc6 + c.x * T(1.0 / 6.0)) * irc6);
+            u += e * (qq * rinv + lj6 * (Bn * T(-1 / kLn2))) - ush;
             npair += 1;
         }
     }
@@ -289,8 +298,10 @@ __global__ void __launch_bounds__(kHalfShell * 32) k_pair_list(Params p)
                 const int at = off + __popc(bal & ((1u << lane) - 1u));
                 // i-atoms of the clusters in range that lie within r_cut + skin of the
                 // j-cluster's box (padding slots are far away), one entry at a time
-                // across the warp: lane l tests slots l and l + 32.  Each lane loads
-                // its own j-cluster's box once; the entry loop shuffles it.
+                // across the warp.  The mask is column-major (bit a*8 + k: atom a of
+                // i-cluster k): lane l tests atom l >> 3 (low word) and 4 + (l >> 3)
+                // (high word) of i-cluster l & 7.  Each lane loads its own j-cluster's
+                // box once; the entry loop shuffles it.
                 unsigned my_lo = 0u, my_hi = 0u;
                 bool my_share = false;
                 float4 blo = make_float4(0.f, 0.f, 0.f, 0.f), bhi = blo;
@@ -315,8 +326,9 @@ __global__ void __launch_bounds__(kHalfShell * 32) k_pair_list(Params p)
                         const float gz = fmaxf(0.0f, fmaxf(xi.z - jhz, jlz - xi.z));
                         return __fmaf_rn(gz, gz, __fmaf_rn(gy, gy, __fmul_rn(gx, gx))) < rcb2;
                     };
-                    const bool in0 = ((mL >> (lane >> 3)) & 1u) && near(s_ip[lane]);
-                    const bool in1 = ((mL >> ((lane >> 3) + 4)) & 1u) && near(s_ip[lane + 32]);
+                    const bool kin = (mL >> (lane & 7)) & 1u;
+                    const bool in0 = kin && near(s_ip[(lane & 7) * kClusterSize + (lane >> 3)]);
+                    const bool in1 = kin && near(s_ip[(lane & 7) * kClusterSize + 4 + (lane >> 3)]);
                     const unsigned alo = __ballot_sync(0xffffffffu, in0);
                     const unsigned ahi = __ballot_sync(0xffffffffu, in1);
                     // fragment ranges of the i-clusters in range against the j-cluster's
@@ -407,6 +419,7 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
         const int fc = p.sc_first[sc], ncl = p.sc_ncl[sc];
         const Grid& g = p.grid_b[rr];
         const T kap = FP64 ? T(p.rs[rr].kappa_force) : T(p.rs[rr].kappa_f);
+        const T kl = kap * T(-1.4426950408889634);   // -kappa log2(e)
         const T erc = ENERGY ? P::expneg(kap * T(p.r_cut)) : T(0);
 
         // the super-cluster's atoms and the chunk's j-atoms (shifted into the
@@ -458,10 +471,9 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
             const int j0off = t0.x, j1off = t1.x;
             const int kdiag = nb == 0 ? jcl - fc : -1;   // i-cluster equal to this j-cluster
 
-            // this lane column's i-clusters: bit k when atom tx of i-cluster k is in
-            // the mask; a tile takes the next one of every column
-            const unsigned clo = (mlo >> tx) & 0x01010101u, chi = (mhi >> tx) & 0x01010101u;
-            const unsigned col0 = ((clo * 0x01020408u) >> 24) | (((chi * 0x01020408u) >> 24) << 4);
+            // this lane column's i-clusters (byte tx of the column-major mask: bit k
+            // when atom tx of i-cluster k is in); a tile takes the next one of every column
+            const unsigned col0 = ((tx < 4 ? mlo : mhi) >> ((tx & 3) * 8)) & 0xffu;
             const int n_t = (int)__reduce_max_sync(kFull, (unsigned)__popc(col0));
 
             T fj0x = 0, fj0y = 0, fj0z = 0, fj1x = 0, fj1y = 0, fj1z = 0;
@@ -488,9 +500,9 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
                         ok1 = !dg || tx < ty + 4;
                     }
                     T r20, r21;
-                    pair<FP64, ENERGY, EXCL>(xi, ti.x, ti.y, x0, y0, z0, a0.w, q0k, j0off, t0.y, ok0, lj_bytes, kap,
+                    pair<FP64, ENERGY, EXCL>(xi, ti.x, ti.y, x0, y0, z0, a0.w, q0k, j0off, t0.y, ok0, lj_bytes, kl,
                                              rc2, acc.x, acc.y, acc.z, fj0x, fj0y, fj0z, acc.w, npair, erc, irc, r20);
-                    pair<FP64, ENERGY, EXCL>(xi, ti.x, ti.y, x1, y1, z1, a1.w, q1k, j1off, t1.y, ok1, lj_bytes, kap,
+                    pair<FP64, ENERGY, EXCL>(xi, ti.x, ti.y, x1, y1, z1, a1.w, q1k, j1off, t1.y, ok1, lj_bytes, kl,
                                              rc2, acc.x, acc.y, acc.z, fj1x, fj1y, fj1z, acc.w, npair, erc, irc, r21);
                     w.fi[ty * kFiRow + ia] = acc;
                     if (PRUNE) {
@@ -505,9 +517,9 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
                 if ((unsigned)kdiag < (unsigned)ncl) tiles(std::true_type{}, std::true_type{}, std::true_type{});
                 else if (excl) tiles(std::false_type{}, std::true_type{}, std::true_type{});
                 else tiles(std::false_type{}, std::false_type{}, std::true_type{});
-                // columns back to the 64-bit atom mask (bit k*8 + tx)
-                const unsigned klo = __reduce_or_sync(kFull, (((keep & 0xfu) * 0x00204081u) & 0x01010101u) << tx);
-                const unsigned khi = __reduce_or_sync(kFull, (((keep >> 4) * 0x00204081u) & 0x01010101u) << tx);
+                // columns back to the column-major mask (byte tx)
+                const unsigned klo = __reduce_or_sync(kFull, tx < 4 ? keep << ((tx & 3) * 8) : 0u);
+                const unsigned khi = __reduce_or_sync(kFull, tx >= 4 ? keep << ((tx & 3) * 8) : 0u);
                 if (lane == 0) {
                     if (klo != mlo || khi != mhi)
                         *reinterpret_cast<uint2*>(&p.pl[ch.y + v].z) = make_uint2(klo, khi);

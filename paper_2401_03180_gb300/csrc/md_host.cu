@@ -563,8 +563,8 @@ static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* 
             double ep = std::sqrt(eps_ts[a] * eps_ts[b]);
             double s6 = sg * sg * sg * sg * sg * sg;
             double c6 = 4.0 * ep * s6, c12 = c6 * s6;
-            lj_d[(size_t)a * nts_lj + b] = make_double2(-6.0 * c6, c12);   // pair kernels take (-6 c6, c12)
-            lj_f[(size_t)a * nts_lj + b] = make_float2((float)(-6.0 * c6), (float)c12);
+            lj_d[(size_t)a * nts_lj + b] = make_double2(-6.0 * c6, -kLn2 * c12);   // pair kernels take (-6 c6, -ln2 c12)
+            lj_f[(size_t)a * nts_lj + b] = make_float2((float)(-6.0 * c6), (float)(-kLn2 * c12));
         }
     std::vector<double> etab(kNEtab), inv12(13, 0.0);
     for (int k = 0; k < kNEtab; ++k) etab[k] = std::exp(-(double)k / 16.0);

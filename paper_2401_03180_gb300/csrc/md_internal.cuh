@@ -26,6 +26,7 @@ constexpr double kFixScale = 4294967296.0;        // 2^32
 constexpr double kFixInv = 1.0 / 4294967296.0;
 constexpr double kFixLimit = 4.611686018427388e18;  // 2^62 (overflow guard)
 constexpr double kEvKJmol = 96.48533212;          // kJ/mol per eV
+constexpr double kLn2 = 0.69314718055994530942;   // ln 2 (scales the LJ table's c12 column)
 constexpr float kBBoxMargin = 1e-4f;               // nm, slack of the cluster prefilter
 
 // device error bits (mirrored to md_status by the host)
@@ -39,8 +40,9 @@ enum : unsigned {
 
 // Cluster-pair list entry: x = j-cluster, y = half-shell index of the
 // j-cluster's cell | kEntryExcl when an i-atom and a j-atom may share a
-// fragment, (z, w) = 64-bit mask of the super-cluster's atom slots (bit
-// k*8 + a: atom a of i-cluster k) that may interact with the j-cluster.
+// fragment, (z, w) = column-major 64-bit mask of the super-cluster's atom
+// slots (bit a*8 + k: atom a of i-cluster k) that may interact with the
+// j-cluster.
 using PairEntry = uint4;
 constexpr unsigned kEntryExcl = 0x100u;
 
@@ -110,8 +112,8 @@ struct Params {
     const long long* e_auger_mev;// [n_species]
     const double* etab;      // [kNEtab]
     const double* inv12;     // [13] 1/m
-    const float2* lj_f;      // [n_ts_lj][n_ts_lj] (-6 c6, c12)
-    const double2* lj_d;     // [n_ts_lj][n_ts_lj] (-6 c6, c12)
+    const float2* lj_f;      // [n_ts_lj][n_ts_lj] (-6 c6, -ln2 c12)
+    const double2* lj_d;     // [n_ts_lj][n_ts_lj] (-6 c6, -ln2 c12)
 
     // replicas
     Grid* grid;              // grid for the next cell build (step kernel output)

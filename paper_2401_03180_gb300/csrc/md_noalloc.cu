@@ -255,8 +255,8 @@ extern "C" md_status md_forces_noalloc(const md_forces_input* in, double* d_f, v
             const double ep = std::sqrt(eps[a] * eps[b]);
             const double s6 = sg * sg * sg * sg * sg * sg;
             const double c6 = 4.0 * ep * s6, c12 = c6 * s6;
-            tab_d[(size_t)a * nts + b] = make_double2(-6.0 * c6, c12);   // pair kernels take (-6 c6, c12)
-            tab_f[(size_t)a * nts + b] = make_float2((float)(-6.0 * c6), (float)c12);
+            tab_d[(size_t)a * nts + b] = make_double2(-6.0 * c6, -kLn2 * c12);   // pair kernels take (-6 c6, -ln2 c12)
+            tab_f[(size_t)a * nts + b] = make_float2((float)(-6.0 * c6), (float)(-kLn2 * c12));
         }
     const int zs[MD_MAX_SPECIES] = {in->z[0], in->z[1], in->z[2], in->z[3], in->z[4], in->z[5], in->z[6], in->z[7]};
     const double one = 1.0;
