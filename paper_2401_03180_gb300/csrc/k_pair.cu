@@ -378,10 +378,23 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
     C2* s_lj = reinterpret_cast<C2*>(smem);
     const unsigned char* lj_bytes = smem;
     const size_t tab = ((size_t)nts * nts * sizeof(C2) + 127) / 128 * 128;
+    // s_kq[c]: the set bits of the 8-bit column mask c as 4-bit cluster indices,
+    // lowest first, the unused nibbles 8 (a column's stand-in row)
+    unsigned* s_kq = reinterpret_cast<unsigned*>(smem + tab);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WS& w = reinterpret_cast<WS*>(smem + tab)[warp];
+    WS& w = reinterpret_cast<WS*>(smem + tab + 256 * sizeof(unsigned))[warp];
 
     for (int k = threadIdx.x; k < nts * nts; k += blockDim.x) s_lj[k] = P::table(p)[k];
+    for (int c = threadIdx.x; c < 256; c += blockDim.x) {
+        unsigned q = 0x88888888u;
+        int n = 0;
+        for (int k = 0; k < 8; ++k)
+            if ((c >> k) & 1) {
+                q = (q & ~(0xfu << (4 * n))) | ((unsigned)k << (4 * n));
+                ++n;
+            }
+        s_kq[c] = q;
+    }
     if (lane < kClusterSize) {
         w.ix[kSCAtoms + lane] = P::mk(T(-1.0e6), T(-1.0e6), T(-1.0e6), T(0));
         w.it[kSCAtoms + lane] = make_int2(0, (int)0x80000000);
@@ -485,11 +498,11 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
                 constexpr bool DIAG = decltype(diag)::value;
                 constexpr bool EXCL = DIAG || decltype(ex)::value;
                 constexpr bool PRUNE = decltype(pr)::value;
-                unsigned col = col0;
+                unsigned kq = s_kq[col0];
                 for (int t = 0; t < n_t; ++t) {
-                    const int k = col ? __ffs(col) - 1 : -1;
-                    col &= col - 1u;
-                    const int ia = k >= 0 ? k * kClusterSize + tx : kSCAtoms + tx;   // idle: stand-in
+                    const int k = (int)(kq & 0xfu);   // 8 once the column is used up
+                    kq >>= 4;
+                    const int ia = k * kClusterSize + tx;   // k = 8: the stand-in row
                     const S4 xi = w.ix[ia];
                     const int2 ti = w.it[ia];
                     S4 acc = w.fi[ty * kFiRow + ia];
@@ -508,7 +521,7 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
                     if (PRUNE) {
                         const bool n0 = ok0 && r20 < rl2, n1 = ok1 && r21 < rl2;
                         const unsigned b = __ballot_sync(kFull, n0 || n1);
-                        if (k >= 0 && (((b | (b >> 8) | (b >> 16) | (b >> 24)) >> tx) & 1u)) keep |= 1u << k;
+                        if (k < 8 && (((b | (b >> 8) | (b >> 16) | (b >> 24)) >> tx) & 1u)) keep |= 1u << k;
                         if (EXCL) share |= __any_sync(kFull, (n0 && ti.y == t0.y) || (n1 && ti.y == t1.y));
                     }
                 }
@@ -580,7 +593,7 @@ template <bool FP64>
 static size_t pair_smem(int n_ts, int warps)
 {
     const size_t tab = ((size_t)n_ts * n_ts * sizeof(typename Prec<FP64>::C2) + 127) / 128 * 128;
-    return tab + (size_t)warps * sizeof(WarpSmem<FP64>);
+    return tab + 256 * sizeof(unsigned) + (size_t)warps * sizeof(WarpSmem<FP64>);
 }
 
 template <bool FP64, bool ENERGY>
