@@ -312,7 +312,7 @@ md_status md_philox(uint64_t seed, const uint32_t* d_ctr4, int64_t n, uint32_t* 
  * budget, a memory-capped process, an inner loop that must keep the device
  * footprint fixed -- it computes the screened Coulomb + screened LJ forces of
  * one configuration using only a fixed scratch area compiled into the
- * library (a file-scope __device__ array of about 11.7 MB, held by every GPU
+ * library (a file-scope __device__ array of about 10.5 MB, held by every GPU
  * that loads the library until the process exits).  It calls no cudaMalloc,
  * cudaFree or other allocating routine.
  *

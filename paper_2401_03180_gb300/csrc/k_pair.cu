@@ -10,7 +10,7 @@
 //     bounding box against the SC's 8 i-cluster boxes, and for the clusters
 //     in range every i-atom against the j-cluster's box; each j-cluster with
 //     an i-atom in range becomes an entry (j-cluster, shift, 64-bit i-atom
-//     mask), contiguous per (SC, cell) and cut into chunks of up to kChunk;
+//     mask), contiguous per SC and cut into chunks of kChunk entries;
 //   * a warp of the force kernel owns one chunk at a time (dynamic scheduling
 //     through an atomic counter);
 //   * the SC's atoms and per-(atom, lane row) i-force partials live in shared
@@ -171,16 +171,16 @@ __device__ __forceinline__ void pair(const typename Prec<FP64>::S4& xi, int row_
 // cell): every j-cluster whose bounding box comes within r_cut + skin of at
 // least one of the SC's i-cluster boxes gets an entry (j-cluster, half-shell
 // index, mask of the i-atoms of those clusters that lie within r_cut + skin of
-// the j-cluster's box).  The entries of one (SC, cell) are contiguous and cut
-// into chunks of up to kChunk, the work items of the force kernel; each warp
-// reserves its own range, so the warps of a block never wait on each other.
-// A first pass counts, the second repeats the box tests and writes, so no cell
-// size limit applies.
+// the j-cluster's box).  An SC's entries are contiguous and cut into chunks of
+// kChunk, the work items of the force kernel.  A first pass counts, the second
+// repeats the box tests and writes, so no cell size limit applies.
 __global__ void __launch_bounds__(kHalfShell * 32) k_pair_list(Params p)
 {
     __shared__ float4 s_lo[kSuperClusters], s_hi[kSuperClusters];
     __shared__ float4 s_ip[kSCAtoms];       // the SC's atom positions (cell frame)
     __shared__ int2 s_fr[kSuperClusters];   // fragment range of each i-cluster
+    __shared__ int s_cnt[kHalfShell];
+    __shared__ int s_base, s_tot, s_cbase;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (*p.err & ERR_CELL) return;
     const int n_sc = p.counters[0];
@@ -264,23 +264,34 @@ __global__ void __launch_bounds__(kHalfShell * 32) k_pair_list(Params p)
             if (base == jr0) m_first = m;
             cnt += __popc(__ballot_sync(0xffffffffu, m != 0));
         }
-        // this warp's range of entries and chunks: one reservation for both
-        // (entries in the low word, chunks in the high word)
-        const int nch = (cnt + kChunk - 1) / kChunk;
-        unsigned long long old = 0ull;
-        if (lane == 0 && cnt > 0)
-            old = atomicAdd(reinterpret_cast<unsigned long long*>(p.counters + 6),
-                            ((unsigned long long)nch << 32) | (unsigned)cnt);
-        old = __shfl_sync(0xffffffffu, old, 0);
-        int base_w = (int)(unsigned)old;
-        const int cbase = (int)(old >> 32);
-        if (cnt > 0 && ((long long)base_w + cnt > p.pl_cap || (long long)cbase + nch > p.chunk_cap)) {
-            if (lane == 0) atomicOr(p.err, ERR_LIST);
-            base_w = -1;
+        if (lane == 0) s_cnt[warp] = cnt;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int tot = 0;
+            for (int w = 0; w < kHalfShell; ++w) {
+                const int t = s_cnt[w];
+                s_cnt[w] = tot;
+                tot += t;
+            }
+            const unsigned long long nch = (unsigned long long)((tot + kChunk - 1) / kChunk);
+            // one reservation for both: entries in the low word, chunks in the high word
+            const unsigned long long old =
+                atomicAdd(reinterpret_cast<unsigned long long*>(p.counters + 6), (nch << 32) | (unsigned)tot);
+            int base = (int)(unsigned)old;
+            const int cbase = (int)(old >> 32);
+            if ((long long)base + tot > p.pl_cap || (long long)cbase + (long long)nch > p.chunk_cap) {
+                atomicOr(p.err, ERR_LIST);
+                base = -1;
+            }
+            s_base = base;
+            s_tot = tot;
+            s_cbase = cbase;
         }
-        if (cnt > 0 && base_w >= 0) {
-            int off = base_w;
-            const int end = base_w + cnt;
+        __syncthreads();
+        const int base_sc = s_base, tot = s_tot, cbase = s_cbase;
+        if (base_sc >= 0) {
+            int off = base_sc + s_cnt[warp];
+            const int end = base_sc + tot;
             for (int base = jr0; base < jr1; base += 32) {
                 const unsigned m = base == jr0 ? m_first : test(base + lane);
                 const unsigned bal = __ballot_sync(0xffffffffu, m != 0);
@@ -339,10 +350,10 @@ __global__ void __launch_bounds__(kHalfShell * 32) k_pair_list(Params p)
             // both passes see the same boxes and round identically, so `off` ends at
             // this warp's share; should it fall short, pad with empty entries (a
             // real cluster, no i-atom in range) rather than leave slots unwritten
-            for (int at = off + lane; at < end; at += 32)
+            for (int at = off + lane; at < min(base_sc + s_cnt[warp] + cnt, end); at += 32)
                 p.pl[at] = make_uint4((unsigned)fc, (unsigned)nb, 0u, 0u);
-            for (int t = lane; t * kChunk < cnt; t += 32)
-                p.pl_chunk[cbase + t] = make_int4(sc, base_w + t * kChunk, min(kChunk, cnt - t * kChunk), rr);
+            for (int t = threadIdx.x; t * kChunk < tot; t += blockDim.x)
+                p.pl_chunk[cbase + t] = make_int4(sc, base_sc + t * kChunk, min(kChunk, tot - t * kChunk), rr);
         }
         // the write pass re-reads the boxes (batches after the first): no warp may
         // stage the next super-cluster's boxes before every warp is done with these

@@ -226,7 +226,7 @@ md_status size_list(md_handle* h, long long entries)
     P.pl = nullptr;
     P.pl_chunk = nullptr;
     P.pl_cap = (int)entries;
-    P.chunk_cap = kHalfShell * P.sc_cap + P.pl_cap / kChunk + 1;   // a partial chunk per (SC, cell)
+    P.chunk_cap = P.sc_cap + P.pl_cap / kChunk + 1;
     md_status st = dalloc(h, &P.pl, (size_t)P.pl_cap);
     if (st != MD_OK) return st;
     return dalloc(h, &P.pl_chunk, (size_t)P.chunk_cap);

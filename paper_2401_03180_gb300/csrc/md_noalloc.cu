@@ -8,7 +8,7 @@
 // entry point serves them: all the scratch it needs (cell list, packed
 // coordinates, fixed-point force sums, grid and screening bookkeeping) lives
 // in one file-scope __device__ array of a fixed, modest size
-// (MD_NOALLOC_MAX_ATOMS atoms, MD_NOALLOC_MAX_CELLS cells; about 11.7 MB) that
+// (MD_NOALLOC_MAX_ATOMS atoms, MD_NOALLOC_MAX_CELLS cells; about 10.5 MB) that
 // every GPU loading the library holds until the process exits.  The caller
 // passes inputs and the output buffer; nothing is allocated.
 //
@@ -32,7 +32,7 @@ constexpr int kNcMax = MD_NOALLOC_MAX_CELLS;
 constexpr int kSlotCap = kNaMax + 7 * kNcMax + 8;
 constexpr int kClusterCap = kSlotCap / kClusterSize + 1;
 constexpr int kPlCap = 48 * kClusterCap;                  // cluster-pair list entries
-constexpr int kChunkCap = kHalfShell * kClusterCap + kPlCap / kChunk + 1;   // a partial chunk per (SC, cell)
+constexpr int kChunkCap = kClusterCap + kPlCap / kChunk + 1;
 constexpr int kTabMax = MD_MAX_TYPE_STATES * MD_MAX_TYPE_STATES;
 
 constexpr size_t align256(size_t b) { return (b + 255) / 256 * 256; }
