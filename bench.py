@@ -37,7 +37,7 @@ METRIC = "atom-steps/s (pair forces + ionisation) on 1 GB300, mixed vs FP64 at s
 UNIT = "atom-steps/s"
 FLOPS_PER_PAIR = 41          # FP32 operations per in-cutoff pair in the pair kernel (FMA = 2)
 L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
-SKIN_NM = 0.04               # Verlet buffer of the pair list (measured choice for the water box)
+SKIN_NM = 0.08               # Verlet buffer of the pair list (measured choice for the water box)
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_pair_c2_water_30k.md")
 
 
