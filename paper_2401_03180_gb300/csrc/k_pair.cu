@@ -177,7 +177,7 @@ __device__ __forceinline__ void pair(const typename Prec<FP64>::S4& xi, int row_
 __global__ void __launch_bounds__(kHalfShell * 32) k_pair_list(Params p)
 {
     __shared__ float4 s_lo[kSuperClusters], s_hi[kSuperClusters];
-    __shared__ float4 s_ip[kSCAtoms];       // the SC's atom positions (cell frame)
+    __shared__ float4 s_ip[kSCAtoms];       // the SC's atom positions (cell frame), [atom a][cluster k]
     __shared__ int2 s_fr[kSuperClusters];   // fragment range of each i-cluster
     __shared__ int s_cnt[kHalfShell];
     __shared__ int s_base, s_tot, s_cbase;
@@ -194,12 +194,14 @@ __global__ void __launch_bounds__(kHalfShell * 32) k_pair_list(Params p)
             s_fr[threadIdx.x] = p.bb_frag[fc + threadIdx.x];
         }
         if (threadIdx.x < ncl * kClusterSize) {
+            // column-major, like the entries' masks: row a * 8 + k holds atom a of i-cluster k
             const int slot = fc * kClusterSize + threadIdx.x;
+            const int row = (threadIdx.x & 7) * kClusterSize + (threadIdx.x >> 3);
             if (p.precision == 0) {
-                s_ip[threadIdx.x] = p.xq[slot];
+                s_ip[row] = p.xq[slot];
             } else {
                 const double4_32a t = p.xq64[slot];
-                s_ip[threadIdx.x] = make_float4((float)t.x, (float)t.y, (float)t.z, 0.0f);
+                s_ip[row] = make_float4((float)t.x, (float)t.y, (float)t.z, 0.0f);
             }
         }
         int rr;
@@ -327,8 +329,8 @@ __global__ void __launch_bounds__(kHalfShell * 32) k_pair_list(Params p)
                         return __fmaf_rn(gz, gz, __fmaf_rn(gy, gy, __fmul_rn(gx, gx))) < rcb2;
                     };
                     const bool kin = (mL >> (lane & 7)) & 1u;
-                    const bool in0 = kin && near(s_ip[(lane & 7) * kClusterSize + (lane >> 3)]);
-                    const bool in1 = kin && near(s_ip[(lane & 7) * kClusterSize + 4 + (lane >> 3)]);
+                    const bool in0 = kin && near(s_ip[lane]);
+                    const bool in1 = kin && near(s_ip[lane + 32]);
                     const unsigned alo = __ballot_sync(0xffffffffu, in0);
                     const unsigned ahi = __ballot_sync(0xffffffffu, in1);
                     // fragment ranges of the i-clusters in range against the j-cluster's
