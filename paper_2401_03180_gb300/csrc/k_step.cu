@@ -238,6 +238,7 @@ __global__ void __launch_bounds__(kStepThreads) k_step_a(Params p, int mode)
     __shared__ unsigned long long s_bmin[kRepWindow][3], s_bmax[kRepWindow][3];
     __shared__ int s_last;
     __shared__ unsigned s_maxd2;
+    __shared__ uint8_t s_q[kStepAtoms];   // charges after this step's update (charge-update warps)
     // a cluster-pair list overflow freezes the state at the step whose forces
     // are missing; the host grows the list, recomputes them and resumes
     if (*p.err & ERR_LIST) return;
@@ -263,10 +264,26 @@ __global__ void __launch_bounds__(kStepThreads) k_step_a(Params p, int mode)
     int r = live ? p.rep[i] : -1;
     double pos[3] = {0.0, 0.0, 0.0};
     bool vac = false;
+    // inputs of this atom's re-pack (Verlet-buffered list), loaded before the
+    // charge update is waited for
+    const bool repack = live && !cr_role && p.xr && (mode & STEP_KICK_DRIFT);
+    int pk_slot = 0, pk_sp = 0, pk_fr = 0, pk_q = 0, pk_per = 0;
+    double pk_cen[3] = {0.0, 0.0, 0.0}, pk_box[3] = {0.0, 0.0, 0.0};
 
     if (live && !cr_role) {
         const int s = p.species[i];
         double x = p.x[i], y = p.y[i], z = p.z[i];
+        if (repack) {
+            pk_slot = p.slot_of[i];
+            const double4_32a c = p.cl_cen[pk_slot / kClusterSize];
+            pk_cen[0] = c.x; pk_cen[1] = c.y; pk_cen[2] = c.z;
+            const Grid& gb = p.grid_b[r];
+            pk_per = gb.periodic;
+            pk_box[0] = gb.box[0]; pk_box[1] = gb.box[1]; pk_box[2] = gb.box[2];
+            pk_sp = s;
+            pk_fr = p.frag[i];
+            pk_q = p.q[i];
+        }
         if (mode & STEP_KICK_DRIFT) {
             // the state holds v_{n-1/2} once stepping has started: finish the
             // previous step's half kick, then this step's (two separate adds,
@@ -367,6 +384,7 @@ __global__ void __launch_bounds__(kStepThreads) k_step_a(Params p, int mode)
         const int s = p.species[i];
         const int Z = p.zs[s];
         const int qi = p.q[i], hi = p.h[i];
+        s_q[i - first] = (uint8_t)qi;   // replaced below if an event changes it
         const int ts = p.ts_off[s] + qi;
         const RepState st = p.rs[r];
         double dF = 0.0;
@@ -419,6 +437,7 @@ __global__ void __launch_bounds__(kStepThreads) k_step_a(Params p, int mode)
             }
             p.q[i] = (uint8_t)qn;
             p.h[i] = (uint8_t)hn;
+            s_q[i - first] = (uint8_t)qn;
             const int w = r - r0;
             if (w < kRepWindow) {
                 atomicAdd((unsigned long long*)&s_acc[w][0], (unsigned long long)(ch == 3 ? -1ll : 1ll));
@@ -436,11 +455,9 @@ __global__ void __launch_bounds__(kStepThreads) k_step_a(Params p, int mode)
     // of this step, in the slot of the last build (a build, if one follows,
     // rewrites all records); the force sums are cleared after the kick read them
     __syncthreads();   // the charges of this step are written
-    if (live && !cr_role && p.xr && (mode & STEP_KICK_DRIFT)) {
-        const int slot = p.slot_of[i];
-        const double4_32a c = p.cl_cen[slot / kClusterSize];
-        const double cen[3] = {c.x, c.y, c.z};
-        pack_slot(p, slot, i, cen, p.grid_b[r]);
+    if (repack) {
+        const int qi = (mode & STEP_CR) ? (int)s_q[i - first] : pk_q;
+        pack_record(p, pk_slot, pos, pk_cen, pk_per, pk_box, pk_sp, qi, pk_fr);
     }
     __syncthreads();
 

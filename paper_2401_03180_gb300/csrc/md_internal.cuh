@@ -224,21 +224,25 @@ __host__ __device__ __forceinline__ void half_shell(int nb, int& dx, int& dy, in
 // atom may have been wrapped across the box), charge, LJ type state, fragment;
 // the slot's force sums are cleared.  Used by the build and by the refresh
 // between builds, so both round identically.
-__device__ __forceinline__ void pack_slot(const Params& p, int slot, int i, const double cen[3], const Grid& g)
+__device__ __forceinline__ void pack_record(const Params& p, int slot, const double xi[3], const double cen[3],
+                                            int periodic, const double box[3], int sp, int qi, int fr)
 {
-    double d[3] = {p.x[i] - cen[0], p.y[i] - cen[1], p.z[i] - cen[2]};
-    if (g.periodic)
+    double d[3] = {xi[0] - cen[0], xi[1] - cen[1], xi[2] - cen[2]};
+    if (periodic)
         for (int k = 0; k < 3; ++k) {
-            const int o = beyond_half(d[k], g.box[k]);
-            if (o > 0) d[k] -= g.box[k];
-            else if (o < 0) d[k] += g.box[k];
+            const int o = beyond_half(d[k], box[k]);
+            if (o > 0) d[k] -= box[k];
+            else if (o < 0) d[k] += box[k];
         }
-    const int sp = p.species[i];
-    const int qi = p.q[i];
     if (p.precision == 0) p.xq[slot] = make_float4((float)d[0], (float)d[1], (float)d[2], (float)qi);
     else p.xq64[slot] = make_double4_32a(d[0], d[1], d[2], (double)qi);
-    p.tf[slot] = make_int2(p.lj_ts_off[sp] + qi, p.frag[i]);
+    p.tf[slot] = make_int2(p.lj_ts_off[sp] + qi, fr);
     p.fx[slot] = 0; p.fy[slot] = 0; p.fz[slot] = 0; p.epot[slot] = 0;
+}
+__device__ __forceinline__ void pack_slot(const Params& p, int slot, int i, const double cen[3], const Grid& g)
+{
+    const double xi[3] = {p.x[i], p.y[i], p.z[i]};
+    pack_record(p, slot, xi, cen, g.periodic, g.box, p.species[i], p.q[i], p.frag[i]);
 }
 
 // Launch helpers implemented in the .cu files.
