@@ -163,15 +163,95 @@ void orc_pair(double r, double qi, double qj, double c6, double c12, double kapp
 }
 
 /* ------------------------------------------------------------------------ */
+/* Hybrid ion-sphere / Debye potential of one ion (Sec. II.A, Eqs. 4-7).     */
+/* Reading (the paper prints neither the coefficients nor the pair form):    */
+/*   R  = (3 Q / (4 pi n_e))^{1/3}                          (ion sphere, Eq. 4) */
+/*   r' = lambda ((R/lambda)^3 + 1)^{1/3} - lambda,  lambda = 1/kappa  (Eq. 7) */
+/*   phi(r) = Q/r + c1 - c2 r^2            for r <  r'  (ion-sphere form)      */
+/*   phi(r) = c3 exp(-kappa r) / r         for r >= r'  (Debye form, Eq. 2)    */
+/* with c1, c2, c3 fixed by the continuity of phi, phi' and phi'' at r' (the */
+/* matching the paper describes; Eq. 6 lists the four terms).  Solving the   */
+/* three conditions with x = kappa r' and D = 3 + 3x + x^2:                  */
+/*   c3 = 3 Q e^x / D,  c2 = -Q kappa^2 / (2 r' D),                           */
+/*   c1 = -Q kappa (3 + 3x/2) / D.                                            */
+/* (With Eq. 7, D = kappa^2 R^3 / r', so c2 = -Q/(2R^3) = -2 pi n_e / 3: the  */
+/* inner curvature is the uniform electron background's, as in Eq. 5.)      */
+/* r' is evaluated as lambda s^3 / (t^2 + t + 1), s = R/lambda,              */
+/* t = (1 + s^3)^{1/3}, which equals Eq. 7 without its cancellation.  The    */
+/* Debye amplitude is kept at r' (a = c3 e^{-x} = 3Q/D, phi = a             */
+/* e^{-kappa (r - r')}/r), which does not overflow as lambda -> 0.           */
+/* Without an ion sphere (Q <= 0, n_e <= 0 or kappa <= 0) r' = 0 and        */
+/* phi = Q exp(-kappa r)/r (the Debye form; Coulomb when kappa = 0).         */
+/* co = {r', c1, c2, a}.                                                      */
+/* ------------------------------------------------------------------------ */
+void orc_hybrid_coeffs(double Q, double ne, double kappa, double co[4])
+{
+    if (!(Q > 0.0) || !(ne > 0.0) || !(kappa > 0.0)) {
+        co[0] = 0.0; co[1] = 0.0; co[2] = 0.0; co[3] = Q;
+        return;
+    }
+    double lam = 1.0 / kappa;
+    double R = cbrt(3.0 * Q / (4.0 * 3.14159265358979323846 * ne));
+    double s = R / lam;
+    double s3 = s * s * s;
+    double t = cbrt(1.0 + s3);
+    double rp = lam * s3 / (t * t + t + 1.0);
+    double x = kappa * rp;
+    double D = 3.0 + 3.0 * x + x * x;
+    co[0] = rp;
+    co[1] = -Q * kappa * (3.0 + 1.5 * x) / D;
+    co[2] = -Q * kappa * kappa / (2.0 * rp * D);
+    co[3] = 3.0 * Q / D;
+}
+
+/* phi(r) of one ion and -dphi/dr (coefficients from orc_hybrid_coeffs). */
+void orc_hybrid_phi(double Q, const double co[4], double kappa, double r, double* phi, double* mdphi)
+{
+    if (r < co[0]) {
+        *phi = Q / r + co[1] - co[2] * r * r;
+        *mdphi = Q / (r * r) + 2.0 * co[2] * r;
+    } else {
+        double e = exp(-kappa * (r - co[0]));
+        *phi = co[3] * e / r;
+        *mdphi = co[3] * e * (1.0 + kappa * r) / (r * r);
+    }
+}
+
+/* One pair with the hybrid electrostatics (reading: the pair energy is the  */
+/* mean of the two ions' views, U_C = f (q_j phi_i(r) + q_i phi_j(r)) / 2)   */
+/* plus the screened LJ of Eq. 8; energy shifted to zero at the cutoff.      */
+void orc_pair_hybrid(double r, double qi, double qj, double c6, double c12, double kappa,
+                     double ne, double coulomb_f, double rc, int lj_on, double* fr, double* u)
+{
+    double coi[4], coj[4];
+    orc_hybrid_coeffs(qi, ne, kappa, coi);
+    orc_hybrid_coeffs(qj, ne, kappa, coj);
+    double a6 = lj_on ? c6 : 0.0, a12 = lj_on ? c12 : 0.0;
+    double flj, ulj, flj_c, ulj_c;
+    pair_terms(r, 0.0, a6, a12, kappa, &flj, &ulj);
+    pair_terms(rc, 0.0, a6, a12, kappa, &flj_c, &ulj_c);
+    double pi, mi, pj, mj, pic, mic, pjc, mjc;
+    orc_hybrid_phi(qi, coi, kappa, r, &pi, &mi);
+    orc_hybrid_phi(qj, coj, kappa, r, &pj, &mj);
+    orc_hybrid_phi(qi, coi, kappa, rc, &pic, &mic);
+    orc_hybrid_phi(qj, coj, kappa, rc, &pjc, &mjc);
+    double h = 0.5 * coulomb_f;
+    *fr = flj + h * (qj * mi + qi * mj) / r;
+    *u = (ulj - ulj_c) + h * ((qj * pi + qi * pj) - (qj * pic + qi * pjc));
+}
+
+/* ------------------------------------------------------------------------ */
 /* All-pairs forces.  x: [3n] AoS; ts: type-state row; q: charge; frag:       */
 /* fragment id (LJ excluded within one fragment, Sec. II.B); rep_off: [R+1]; */
-/* box: [3R] (zeros = vacuum, else minimum image); kappa: [R] 1/lambda_D.    */
+/* box: [3R] (zeros = vacuum, else minimum image); kappa: [R] 1/lambda_D;   */
+/* ne: [R] free-electron density (nm^-3) for the hybrid electrostatics, or   */
+/* NULL for the Debye-screened Coulomb term.                                  */
 /* Output: f [3n], u_atom [n] (half of every pair energy), n_pairs (i<j).    */
 /* ------------------------------------------------------------------------ */
 void orc_forces(int n, const double* x, const int* ts, const double* q, const int* frag,
                 int n_rep, const int* rep_off, const double* box, const double* kappa,
-                double rc, double coulomb_f, int nts, const double* c6, const double* c12,
-                double* f, double* u_atom, int64_t* n_pairs)
+                const double* ne, double rc, double coulomb_f, int nts, const double* c6,
+                const double* c12, double* f, double* u_atom, int64_t* n_pairs)
 {
     int64_t pairs = 0;
     for (int r = 0; r < n_rep; ++r) {
@@ -195,8 +275,12 @@ void orc_forces(int n, const double* x, const int* ts, const double* q, const in
                 double rr = sqrt(r2);
                 int lj_on = (frag[i] != frag[j]);
                 double fr, u;
-                orc_pair(rr, q[i], q[j], c6[ts[i] * nts + ts[j]], c12[ts[i] * nts + ts[j]],
-                         kap, coulomb_f, rc, lj_on, &fr, &u);
+                if (ne)
+                    orc_pair_hybrid(rr, q[i], q[j], c6[ts[i] * nts + ts[j]], c12[ts[i] * nts + ts[j]],
+                                    kap, ne[r], coulomb_f, rc, lj_on, &fr, &u);
+                else
+                    orc_pair(rr, q[i], q[j], c6[ts[i] * nts + ts[j]], c12[ts[i] * nts + ts[j]],
+                             kap, coulomb_f, rc, lj_on, &fr, &u);
                 fx += fr * d[0];
                 fy += fr * d[1];
                 fz += fr * d[2];
@@ -214,7 +298,7 @@ void orc_forces(int n, const double* x, const int* ts, const double* q, const in
 /* Forces on a subset of atoms (sampled checks of large systems). */
 void orc_forces_subset(int n, const double* x, const int* ts, const double* q, const int* frag,
                        const int* rep_of, const int* rep_off, const double* box,
-                       const double* kappa, double rc, double coulomb_f, int nts,
+                       const double* kappa, const double* ne, double rc, double coulomb_f, int nts,
                        const double* c6, const double* c12, int n_sel, const int* sel,
                        double* f_sel)
 {
@@ -236,8 +320,12 @@ void orc_forces_subset(int n, const double* x, const int* ts, const double* q, c
             double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
             if (!(r2 < rc * rc)) continue;
             double fr, u;
-            orc_pair(sqrt(r2), q[i], q[j], c6[ts[i] * nts + ts[j]], c12[ts[i] * nts + ts[j]],
-                     kappa[r], coulomb_f, rc, frag[i] != frag[j], &fr, &u);
+            if (ne)
+                orc_pair_hybrid(sqrt(r2), q[i], q[j], c6[ts[i] * nts + ts[j]], c12[ts[i] * nts + ts[j]],
+                                kappa[r], ne[r], coulomb_f, rc, frag[i] != frag[j], &fr, &u);
+            else
+                orc_pair(sqrt(r2), q[i], q[j], c6[ts[i] * nts + ts[j]], c12[ts[i] * nts + ts[j]],
+                         kappa[r], coulomb_f, rc, frag[i] != frag[j], &fr, &u);
             fx += fr * d[0];
             fy += fr * d[1];
             fz += fr * d[2];

@@ -12,6 +12,10 @@ What it computes, in the paper's order (arXiv 2401.03180):
 * Sec. II.A, Eq. 2: Debye-screened Coulomb between integer ion charges.
 * Sec. II.A, Eq. 3: Debye length from the free-electron density and
   temperature, kappa = 1/lambda_D.
+* Sec. II.A, Eqs. 4-7 (optional, ``screening="hybrid"``): ion-sphere inside
+  the transition radius r' of Eq. 7 and Debye form outside, matched in value
+  and first two derivatives (reading; see ``md_oracle.c``), the pair energy
+  being the mean of the two ions' views.
 * Sec. II.B, Eq. 8: screened LJ, with LJ parameters scaled per charge state
   (Eq. 11) and LJ excluded inside a native fragment.
 * Sec. II.B, Eq. 12: Newton's equation, integrated with velocity Verlet.
@@ -37,6 +41,10 @@ Parity pins (``tests/test_oracle_*.py``, all ``-m "not gpu"``):
   periodic images, pair counts against a KD-tree.
 * ``pulse_table``: total fluence, symmetry, flat-top closed form, FWHM.
 * ``plasma_scalars``: the NRL-formulary Debye length.
+* ``hybrid_coeffs`` / ``pair_hybrid``: continuity of phi, phi' and phi'' at
+  r' (finite differences on both sides); the identity (r' + lambda)^3 =
+  R^3 + lambda^3 of Eq. 7; the uniform-electron-gas ion sphere of Eq. 5 as
+  lambda -> 0; Coulomb as kappa -> 0; Debye as R -> 0; force = -dU/dr.
 * ``cr_step``: closed forms (PI-only survival e^{-sigma F}; Auger-only
   decay), master-equation chi-squared on histograms, exact charge
   conservation.
@@ -104,8 +112,11 @@ def _declare(L):
     L.orc_one_minus_exp_neg_many.argtypes = [i64, _P, _P, _P, i32, _P]
     L.orc_lj_table.argtypes = [i32, _P, _P, _P, _P, _P]
     L.orc_pair.argtypes = [f64] * 8 + [i32, _P, _P]
-    L.orc_forces.argtypes = [i32, _P, _P, _P, _P, i32, _P, _P, _P, f64, f64, i32, _P, _P, _P, _P, _P]
-    L.orc_forces_subset.argtypes = [i32, _P, _P, _P, _P, _P, _P, _P, _P, f64, f64, i32, _P, _P, i32, _P, _P]
+    L.orc_forces.argtypes = [i32, _P, _P, _P, _P, i32, _P, _P, _P, _P, f64, f64, i32, _P, _P, _P, _P, _P]
+    L.orc_forces_subset.argtypes = [i32, _P, _P, _P, _P, _P, _P, _P, _P, _P, f64, f64, i32, _P, _P, i32, _P, _P]
+    L.orc_hybrid_coeffs.argtypes = [f64, f64, f64, _P]
+    L.orc_hybrid_phi.argtypes = [f64, _P, f64, f64, _P, _P]
+    L.orc_pair_hybrid.argtypes = [f64] * 9 + [i32, _P, _P]
     L.orc_pulse_table.argtypes = [i32, _P, f64, f64, i32, _P]
     L.orc_cr_step.argtypes = ([i32, _P, _P, _P, _P, _P, i64, _P, _P, _P, _P, _P, i32, _P, _P, _P,
                                _P, _P, i32, _P, _P, _P, _P, i32, _P, _P, _P, _P])
@@ -167,6 +178,30 @@ def pair(r, qi, qj, c6, c12, kappa, rc, lj_on=True, coulomb_f=COULOMB_F):
     return fr.value, u.value
 
 
+def hybrid_coeffs(Q, ne, kappa):
+    """(r', c1, c2, a) of the hybrid potential of an ion of charge Q (Eqs. 4-7);
+    a = 3Q/(3 + 3x + x^2) is the Debye amplitude at r' (phi = a e^{-kappa (r - r')}/r)."""
+    co = np.zeros(4)
+    lib().orc_hybrid_coeffs(float(Q), float(ne), float(kappa), _ptr(co))
+    return tuple(float(v) for v in co)
+
+
+def hybrid_phi(Q, ne, kappa, r):
+    """(phi(r), -dphi/dr) of one ion, in e/nm and e/nm^2 (multiply by f)."""
+    co = np.ascontiguousarray(hybrid_coeffs(Q, ne, kappa))
+    phi = ctypes.c_double(); m = ctypes.c_double()
+    lib().orc_hybrid_phi(float(Q), _ptr(co), float(kappa), float(r), ctypes.byref(phi), ctypes.byref(m))
+    return phi.value, m.value
+
+
+def pair_hybrid(r, qi, qj, c6, c12, kappa, ne, rc, lj_on=True, coulomb_f=COULOMB_F):
+    """(F(r)/r, U(r) - U(rc)) for one pair with the hybrid electrostatics."""
+    fr = ctypes.c_double(); u = ctypes.c_double()
+    lib().orc_pair_hybrid(r, qi, qj, c6, c12, kappa, ne, coulomb_f, rc, int(bool(lj_on)),
+                          ctypes.byref(fr), ctypes.byref(u))
+    return fr.value, u.value
+
+
 def pulse_table(pulses, t_start_fs: float, dt_fs: float, n_steps: int) -> np.ndarray:
     """Photons/nm^2 per step for a list of pulses (photon keV, FWHM fs,
     fluence ph/um^2, centre fs, shape)."""
@@ -218,11 +253,13 @@ def plasma_scalars(n_e_count: int, e_gas_mev: int, volume: float, *, dt_ps: floa
 # ---------------------------------------------------------------------------
 # Whole-system oracle
 # ---------------------------------------------------------------------------
-def forces_of_atoms(sample, atomic, idx, *, r_cut, kappa, coulomb_f=COULOMB_F, sigma0=None, eps0=None):
+def forces_of_atoms(sample, atomic, idx, *, r_cut, kappa, coulomb_f=COULOMB_F, sigma0=None, eps0=None,
+                    ne=None):
     """Forces on the atoms `idx` of `sample` (at its positions and charges q0),
     each summed over every other atom of its replica (all pairs, FP64), with a
-    fixed screening kappa per replica.  Costs len(idx) * n_atoms pair terms,
-    so it checks or times a sample of a system too large for all pairs."""
+    fixed screening kappa per replica (and, with ``ne``, the hybrid
+    electrostatics at that electron density).  Costs len(idx) * n_atoms pair
+    terms, so it checks or times a sample of a system too large for all pairs."""
     from paper_2401_03180_gb300 import workloads as W
     md = OracleMD.__new__(OracleMD)
     md.n, md.R = sample.n_atoms, sample.n_replicas
@@ -240,7 +277,9 @@ def forces_of_atoms(sample, atomic, idx, *, r_cut, kappa, coulomb_f=COULOMB_F, s
     md.rep_of = np.repeat(np.arange(md.R, dtype=np.int32), np.diff(md.rep_off))
     md.box = np.ascontiguousarray(sample.box, np.float64).reshape(md.R, 3)
     kap = np.broadcast_to(np.asarray(kappa, np.float64), (md.R,))
-    return md.forces_subset(np.asarray(idx), kappa=np.ascontiguousarray(kap))
+    md.hybrid = ne is not None
+    nev = None if ne is None else np.ascontiguousarray(np.broadcast_to(np.asarray(ne, np.float64), (md.R,)))
+    return md.forces_subset(np.asarray(idx), kappa=np.ascontiguousarray(kap), ne=nev)
 
 
 class OracleMD:
@@ -256,7 +295,7 @@ class OracleMD:
     def __init__(self, sample, atomic, *, dt_ps=5e-5, r_cut=1.2, cr_enabled=True,
                  kappa_fixed=-1.0, te_floor_ev=1.0, t_start_fs=0.0, pulses=None,
                  dF_table=None, prescribed=None, n_steps_max=0, coulomb_f=COULOMB_F,
-                 sigma0=None, eps0=None, mass=None, threads=None):
+                 sigma0=None, eps0=None, mass=None, threads=None, screening="debye"):
         from paper_2401_03180_gb300 import workloads as W
         self.s = sample
         self.a = atomic
@@ -264,6 +303,9 @@ class OracleMD:
         self.rc = float(r_cut)
         self.cr_enabled = bool(cr_enabled)
         self.kappa_fixed = float(kappa_fixed)
+        if screening not in ("debye", "hybrid"):
+            raise ValueError("screening must be 'debye' or 'hybrid'")
+        self.hybrid = screening == "hybrid"
         self.te_floor = float(te_floor_ev)
         self.f = float(coulomb_f)
         self.n = sample.n_atoms
@@ -327,31 +369,42 @@ class OracleMD:
     def type_state(self):
         return (self.off[self.sp.astype(np.int64)] + self.q).astype(np.int32)
 
-    def forces(self, x=None, q=None, kappa=None):
+    def electron_density(self):
+        """n_e (nm^-3) per replica at the current plasma state."""
+        return np.ascontiguousarray([s["n_e"] for s in self.scal], dtype=np.float64)
+
+    def forces(self, x=None, q=None, kappa=None, ne=None):
         x = self.x if x is None else x
         q = self.q if q is None else q
         kap = self.kappa() if kappa is None else np.asarray(kappa, np.float64)
+        if self.hybrid and ne is None:
+            ne = self.electron_density()
         ts = (self.off[self.sp.astype(np.int64)] + q).astype(np.int32)
         xf = np.ascontiguousarray(x, dtype=np.float64)
         qd = np.ascontiguousarray(q, dtype=np.float64)
         F = np.zeros((self.n, 3)); U = np.zeros(self.n); npairs = ctypes.c_int64(0)
+        nep = None if ne is None else _ptr(np.ascontiguousarray(ne, dtype=np.float64))
         lib().orc_forces(self.n, _ptr(xf), _ptr(ts), _ptr(qd), _ptr(self.frag), self.R,
-                         _ptr(self.rep_off), _ptr(self.box), _ptr(np.ascontiguousarray(kap)),
+                         _ptr(self.rep_off), _ptr(self.box), _ptr(np.ascontiguousarray(kap)), nep,
                          self.rc, self.f, self.nts, _ptr(self.c6), _ptr(self.c12), _ptr(F),
                          _ptr(U), ctypes.byref(npairs))
         return F, U, int(npairs.value)
 
-    def forces_subset(self, sel, x=None, q=None, kappa=None):
+    def forces_subset(self, sel, x=None, q=None, kappa=None, ne=None):
         x = self.x if x is None else x
         q = self.q if q is None else q
         kap = self.kappa() if kappa is None else np.asarray(kappa, np.float64)
+        if getattr(self, "hybrid", False) and ne is None:
+            ne = self.electron_density()
         ts = (self.off[self.sp.astype(np.int64)] + q).astype(np.int32)
         sel = np.ascontiguousarray(sel, dtype=np.int32)
         out = np.zeros((len(sel), 3))
         lib().orc_forces_subset(self.n, _ptr(np.ascontiguousarray(x)), _ptr(ts),
                                 _ptr(np.ascontiguousarray(q, np.float64)), _ptr(self.frag),
                                 _ptr(self.rep_of), _ptr(self.rep_off), _ptr(self.box),
-                                _ptr(np.ascontiguousarray(kap)), self.rc, self.f, self.nts,
+                                _ptr(np.ascontiguousarray(kap)),
+                                None if ne is None else _ptr(np.ascontiguousarray(ne, dtype=np.float64)),
+                                self.rc, self.f, self.nts,
                                 _ptr(self.c6), _ptr(self.c12), len(sel), _ptr(sel), _ptr(out))
         return out
 
