@@ -59,6 +59,8 @@ def parse():
                     help="with --profile-case and --skin > 0: end with a checkpoint round trip, whose "
                          "last force launch runs outside the step graph over the trimmed list")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--screening", default="debye", choices=["debye", "hybrid"],
+                    help="Coulomb screening: Debye (Eq. 2) or hybrid ion sphere / Debye (Eqs. 4-7)")
     ap.add_argument("--skin", type=float, default=SKIN_NM,
                     help="Verlet buffer of the cluster-pair list (nm); 0 rebuilds every step")
     return ap.parse_args()
@@ -208,7 +210,7 @@ def run_gpu(args, rank, world, local):
     def make(prec, profile):
         g = M.IonisingMD(s, atom, precision=prec, r_cut=1.2, dt_ps=5e-5, max_steps=max_steps,
                          t_start_fs=wl.t_start_fs, autotune=(prec == "mixed"), profile=profile,
-                         list_skin_nm=args.skin)
+                         list_skin_nm=args.skin, screening=args.screening)
         for r in range(s.n_replicas):
             g.set_pulse(wl.pulses[r], replica=r)
         return g
@@ -301,7 +303,7 @@ def run_gpu(args, rank, world, local):
                    "pulse": [vars(p) for p in wl.pulses[0]], "t_start_fs": wl.t_start_fs,
                    "l2": "flushed between steps (256 MB write, untimed)",
                    "pair_tile": {"warps": tim.tile_warps, "blocks_per_sm": tim.tile_blocks_per_sm},
-                   "list_skin_nm": args.skin,
+                   "list_skin_nm": args.skin, "screening": args.screening,
                    "parallelism": f"replicas{world}"},
         "pair_interactions_per_s": world * pairs * K / (ms / 1e3),
         "pairs_per_step": pairs,
@@ -333,14 +335,14 @@ def run_gpu(args, rank, world, local):
 # ---------------------------------------------------------------------------
 # CPU oracle: baseline leg and reference arm
 # ---------------------------------------------------------------------------
-def _oracle_run(wl, atom, seconds, max_steps_cap=50):
+def _oracle_run(wl, atom, seconds, max_steps_cap=50, screening="debye"):
     from oracle import oracle as O
     threads = os.cpu_count() or 1
     os.environ.setdefault("OMP_NUM_THREADS", str(threads))
     s = wl.sample
     t0 = time.perf_counter()
     md = O.OracleMD(s, atom, r_cut=1.2, t_start_fs=wl.t_start_fs, pulses=wl.pulses,
-                    n_steps_max=max(wl.n_steps, max_steps_cap + 1))
+                    n_steps_max=max(wl.n_steps, max_steps_cap + 1), screening=screening)
     t_init = time.perf_counter() - t0
     md.F0 = md.F.copy()
     steps = 0
@@ -379,7 +381,8 @@ def cpu_baseline_sampled(args, wl, atom, compare_gpu=True):
     err = {}
     try:
         for prec in ("mixed", "fp64"):
-            g = M.IonisingMD(s, atom, precision=prec, r_cut=1.2, max_steps=wl.n_steps, t_start_fs=wl.t_start_fs)
+            g = M.IonisingMD(s, atom, precision=prec, r_cut=1.2, max_steps=wl.n_steps, t_start_fs=wl.t_start_fs,
+                             screening=args.screening)
             F = g.get_state(M.MD_FIELD_F)["f"][idx]
             g.close()
             d = F - F_ref
@@ -395,7 +398,7 @@ def cpu_baseline_sampled(args, wl, atom, compare_gpu=True):
 def cpu_baseline(args, wl, atom):
     if wl.sample.n_atoms > SAMPLED_ABOVE:
         return cpu_baseline_sampled(args, wl, atom)
-    md, steps, dt, t_init, cores = _oracle_run(wl, atom, args.cpu_seconds)
+    md, steps, dt, t_init, cores = _oracle_run(wl, atom, args.cpu_seconds, screening=args.screening)
     s = wl.sample
     val = s.n_atoms * steps / dt
     base = {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -408,7 +411,8 @@ def cpu_baseline(args, wl, atom):
         F_ref = md.F0
         err = {}
         for prec in ("mixed", "fp64"):
-            g = M.IonisingMD(s, atom, precision=prec, r_cut=1.2, max_steps=wl.n_steps, t_start_fs=wl.t_start_fs)
+            g = M.IonisingMD(s, atom, precision=prec, r_cut=1.2, max_steps=wl.n_steps, t_start_fs=wl.t_start_fs,
+                             screening=args.screening)
             F = g.get_state(M.MD_FIELD_F)["f"]
             g.close()
             d = F - F_ref
@@ -434,7 +438,7 @@ def run_reference(args, rank, world):
         val, cores, sample = base["value"], base["cores"], base["sample"]
         dt, k, w = s.n_atoms / val, 1, 0
     else:
-        md, steps, dt, t_init, cores = _oracle_run(wl, atom, seconds=1e9, max_steps_cap=w)
+        md, steps, dt, t_init, cores = _oracle_run(wl, atom, seconds=1e9, max_steps_cap=w, screening=args.screening)
         t0 = time.perf_counter()
         for _ in range(k):
             md.step()
@@ -461,7 +465,7 @@ def run_profile_case(args):
     wl, atom = make_workload(args.workload, args.scale, 0)
     s = wl.sample
     g = M.IonisingMD(s, atom, precision=args.precision, r_cut=1.2, max_steps=max(wl.n_steps, args.warmup + args.steps + 1),
-                     t_start_fs=wl.t_start_fs, autotune=False, list_skin_nm=args.skin)
+                     t_start_fs=wl.t_start_fs, autotune=False, list_skin_nm=args.skin, screening=args.screening)
     g.set_pulse(wl.pulses[0])
     g.step(args.warmup)
     g.step(args.steps)

@@ -61,6 +61,7 @@ enum {
 
 enum { MD_PREC_MIXED = 0, MD_PREC_FP64 = 1 };
 enum { MD_PLASMA_BOOKKEEPING = 0, MD_PLASMA_PRESCRIBED = 1 };
+enum { MD_SCREEN_DEBYE = 0, MD_SCREEN_HYBRID = 1 };
 enum { MD_PULSE_GAUSSIAN = 0, MD_PULSE_FLAT_TOP = 1 };
 
 /*
@@ -132,6 +133,19 @@ typedef struct md_config {
                                 grouping of the FP32 partial sums follows the
                                 build (one schedule for all replicas).  Periodic
                                 edges need >= 3 (r_cut + skin).                 */
+    int screening;           /* MD_SCREEN_DEBYE: the Coulomb term is Debye-
+                                screened (Sec. II.A, Eq. 2).  MD_SCREEN_HYBRID:
+                                hybrid ion-sphere / Debye electrostatics (Sec.
+                                II.A, Eqs. 4-7), read as follows.  An ion of
+                                charge Q has R = (3Q/(4 pi n_e))^{1/3} and r'
+                                from Eq. 7; its potential is Q/r + c1 - c2 r^2
+                                for r < r' and G e^{-kappa r}/r outside, with
+                                c1, c2 and G from the continuity of the
+                                potential and its first two derivatives at r'.
+                                A pair's Coulomb energy is f (q_j phi_i +
+                                q_i phi_j) / 2, shifted to zero at r_cut.  The
+                                mixed path keeps G in FP32 and saturates it at
+                                1e30 (kappa r' > ~69).  0 (Debye) by default.  */
 } md_config;
 
 /*

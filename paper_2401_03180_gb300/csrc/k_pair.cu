@@ -89,13 +89,33 @@ struct Prec<true> {
 // per-warp shared-memory layout; rows kSCAtoms + tx are far-away, uncharged
 // stand-ins for lane column tx once its queue of i-clusters is used up
 constexpr int kFiRow = kSCAtoms + kClusterSize;   // rows per lane row of the i-force partials
+template <bool FP64, bool HYB>
+struct HybSmem {};
 template <bool FP64>
+struct HybSmem<FP64, true> {                   // hybrid electrostatics (Eqs. 4-7)
+    typename Prec<FP64>::S4 ih[kFiRow];        // (f/2) G_i, (f/2) q_i, q_i of the SC atoms
+    typename Prec<FP64>::T jG[kChunk * kClusterSize];    // G_j of the chunk's j-atoms
+};
+template <bool FP64, bool HYB>
 struct WarpSmem {
     typename Prec<FP64>::S4 ix[kFiRow];        // x, y, z, f*q of the SC atoms
     int2 it[kFiRow];                           // LJ row byte offset, fragment
     typename Prec<FP64>::S4 fi[4 * kFiRow];    // [ty][atom] force (+energy)
     typename Prec<FP64>::S4 jx[kChunk * kClusterSize];   // the chunk's j-atoms, shifted: x, y, z, q
     int2 jt[kChunk * kClusterSize];                      // their LJ column byte offset, fragment
+    HybSmem<FP64, HYB> hy;
+};
+
+// Hybrid electrostatics of one pair (Sec. II.A, Eqs. 4-7; the reading is in
+// include/md.h): an ion's potential is q/r + c1 - c2 r^2 inside its
+// transition radius r' and G e^{-kappa r}/r outside, and the pair's Coulomb
+// energy f (q_j phi_i + q_i phi_j) / 2.
+template <typename T>
+struct HybArg {
+    T hGi, hqi, qi;          // (f/2) G_i, (f/2) q_i, q_i
+    T Gj, Gjk;               // G_j, G_j kappa
+    T kap, c2, rpm2, hf;     // kappa, c2, (largest r')^2 of the replica, f/2
+    const HybQ* rows;        // the replica's charge states
 };
 
 template <bool FP64>
@@ -117,7 +137,7 @@ __device__ __forceinline__ void red_fix(long long* dst, typename Prec<FP64>::T v
 // force on j into (fjx, fjy, fjz); with ENERGY the cutoff-shifted pair
 // energy into u.  r2o returns |d|^2.  Multiply-adds are written out so that
 // each accumulation is one fused operation.
-template <bool FP64, bool ENERGY, bool EXCL>
+template <bool FP64, bool ENERGY, bool EXCL, bool HYB>
 __device__ __forceinline__ void pair(const typename Prec<FP64>::S4& xi, int row_off, int fri,
                                      typename Prec<FP64>::T xj, typename Prec<FP64>::T yj,
                                      typename Prec<FP64>::T zj, typename Prec<FP64>::T qj,
@@ -128,7 +148,8 @@ __device__ __forceinline__ void pair(const typename Prec<FP64>::S4& xi, int row_
                                      typename Prec<FP64>::T& fz, typename Prec<FP64>::T& fjx,
                                      typename Prec<FP64>::T& fjy, typename Prec<FP64>::T& fjz,
                                      typename Prec<FP64>::T& u, int& npair, typename Prec<FP64>::T erc,
-                                     typename Prec<FP64>::T irc, typename Prec<FP64>::T& r2o)
+                                     typename Prec<FP64>::T irc, typename Prec<FP64>::T& r2o,
+                                     const HybArg<typename Prec<FP64>::T>& ha)
 {
     using P = Prec<FP64>;
     using T = typename P::T;
@@ -149,19 +170,47 @@ __device__ __forceinline__ void pair(const typename Prec<FP64>::S4& xi, int row_
     const T Bn = P::fma(c.x, T(-kLn2 / 6), An); // -ln2 (c12/r^6 - c6)
     const T D6 = P::fma(An, T(-12 / kLn2), c.x);  // 12 c12/r^6 - 6 c6
     const T E1 = P::fma(t, Bn, D6);             // D6 + kappa r (c12/r^6 - c6)
-    const T Cc = xi.w * P::fma(qj, rinv, qjk);  // f q_i q_j (1/r + kappa)
+    // f q_i q_j (1/r + kappa); hybrid, outside both transition radii:
+    // (f/2)(G_i q_j + q_i G_j)(1/r + kappa)
+    const T Cc = HYB ? P::fma(ha.hGi, P::fma(qj, rinv, qjk), ha.hqi * P::fma(ha.Gj, rinv, ha.Gjk))
+                     : xi.w * P::fma(qj, rinv, qjk);
     const T S = P::fma(lj6, E1, Cc);
-    const T fs = S * (rinv2 * e);               // F(r)/r
+    T fs = S * (rinv2 * e);                     // F(r)/r
+    if (HYB && in && r2 < ha.rpm2) {
+        // inside some ion's transition radius: each ion's -phi' from its own form
+        const HybQ& Ri = ha.rows[(int)ha.qi];
+        const HybQ& Rj = ha.rows[(int)qj];
+        const T rpi = FP64 ? T(Ri.rp) : T(Ri.rpf), rpj = FP64 ? T(Rj.rp) : T(Rj.rpf);
+        const T Gj = ha.Gj;
+        const T outf = e * P::fma(ha.kap, r, T(1)) * rinv2;   // e^{-kappa r} (1 + kappa r) / r^2
+        const T fc2r = T(2) * ha.hf * ha.c2 * r;                // (f/2) 2 c2 r
+        const T hmi = r < rpi ? P::fma(ha.hqi, rinv2, fc2r) : ha.hGi * outf;            // (f/2)(-phi_i')
+        const T hmj = r < rpj ? P::fma(ha.hf * qj, rinv2, fc2r) : (ha.hf * Gj) * outf;  // (f/2)(-phi_j')
+        fs = P::fma(lj6 * E1, rinv2 * e, P::fma(qj, hmi, ha.qi * hmj) * rinv);
+    }
     const T nfs = -fs;
     fx = P::fma(fs, dx, fx); fy = P::fma(fs, dy, fy); fz = P::fma(fs, dz, fz);
     fjx = P::fma(nfs, dx, fjx); fjy = P::fma(nfs, dy, fjy); fjz = P::fma(nfs, dz, fjz);
     if (ENERGY) {
         if (in) {
-            const T qq = xi.w * qj;
             const T irc6 = irc * irc * irc * irc * irc * irc;
             const T lj_on = (EXCL && fri == frj) ? T(0) : T(1);
-            const T ush = erc * (qq * irc + lj_on * (c.y * T(-1 / kLn2) * irc6 + c.x * T(1.0 / 6.0)) * irc6);
-            u += e * (qq * rinv + lj6 * (Bn * T(-1 / kLn2))) - ush;
+            const T ulj = e * (lj6 * (Bn * T(-1 / kLn2))) - erc * lj_on * (c.y * T(-1 / kLn2) * irc6 + c.x * T(1.0 / 6.0)) * irc6;
+            if (HYB) {
+                const HybQ& Ri = ha.rows[(int)ha.qi];
+                const HybQ& Rj = ha.rows[(int)qj];
+                const T rpi = FP64 ? T(Ri.rp) : T(Ri.rpf), rpj = FP64 ? T(Rj.rp) : T(Rj.rpf);
+                const T c1i = FP64 ? T(Ri.c1) : T(Ri.c1f), c1j = FP64 ? T(Rj.c1) : T(Rj.c1f);
+                const T Gi = FP64 ? T(Ri.G) : T(Ri.Gf);
+                const T pci = FP64 ? T(Ri.phirc) : T(Ri.phircf), pcj = FP64 ? T(Rj.phirc) : T(Rj.phircf);
+                const T cr2 = ha.c2 * r2;
+                const T phi_i = r < rpi ? ha.qi * rinv + c1i - cr2 : Gi * e * rinv;
+                const T phi_j = r < rpj ? qj * rinv + c1j - cr2 : ha.Gj * e * rinv;
+                u += ulj + ha.hf * (qj * (phi_i - pci) + ha.qi * (phi_j - pcj));
+            } else {
+                const T qq = xi.w * qj;
+                u += ulj + e * qq * rinv - erc * qq * irc;
+            }
             npair += 1;
         }
     }
@@ -365,7 +414,7 @@ __global__ void __launch_bounds__(kHalfShell * 32) k_pair_list(Params p)
 
 // Forces over the cluster-pair list.  A warp takes one chunk (up to kChunk
 // entries of one SC) at a time from an atomic counter.
-template <bool FP64, bool ENERGY>
+template <bool FP64, bool ENERGY, bool HYB>
 __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
 {
     using P = Prec<FP64>;
@@ -373,7 +422,7 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
     using T4 = typename P::T4;
     using S4 = typename P::S4;
     using C2 = typename P::C2;
-    using WS = WarpSmem<FP64>;
+    using WS = WarpSmem<FP64, HYB>;
     constexpr unsigned kFull = 0xffffffffu;
     extern __shared__ __align__(16) unsigned char smem[];
     const int nts = p.n_ts_lj;
@@ -400,6 +449,7 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
     if (lane < kClusterSize) {
         w.ix[kSCAtoms + lane] = P::mk(T(-1.0e6), T(-1.0e6), T(-1.0e6), T(0));
         w.it[kSCAtoms + lane] = make_int2(0, (int)0x80000000);
+        if constexpr (HYB) w.hy.ih[kSCAtoms + lane] = P::mk(T(0), T(0), T(0), T(0));
     }
     __syncthreads();
     if (*p.err & (ERR_CELL | ERR_LIST)) return;
@@ -436,6 +486,17 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
         const T kap = FP64 ? T(p.rs[rr].kappa_force) : T(p.rs[rr].kappa_f);
         const T kl = kap * T(-1.4426950408889634);   // -kappa log2(e)
         const T erc = ENERGY ? P::expneg(kap * T(p.r_cut)) : T(0);
+        HybArg<T> ha{};
+        const HybQ* hrows = nullptr;
+        if constexpr (HYB) {
+            hrows = p.hq + (size_t)rr * kHybQ;
+            const HybRep hr = p.hrep[rr];
+            ha.kap = kap;
+            ha.c2 = FP64 ? T(hr.c2) : T(hr.c2f);
+            ha.rpm2 = FP64 ? T(hr.rpm2) : T(hr.rpm2f);
+            ha.hf = T(0.5) * coulf;
+            ha.rows = hrows;
+        }
 
         // the super-cluster's atoms and the chunk's j-atoms (shifted into the
         // SC's cell frame) into shared memory, partial forces cleared: one load
@@ -448,6 +509,11 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
                 const int2 t = p.tf[slot];
                 w.ix[a] = P::mk(v.x, v.y, v.z, coulf * v.w);
                 w.it[a] = make_int2(t.x * nts * (int)sizeof(C2), t.y);   // byte offset of the LJ row
+                if constexpr (HYB) {
+                    const HybQ& hq = hrows[(int)v.w];
+                    const T G = FP64 ? T(hq.G) : T(hq.Gf);
+                    w.hy.ih[a] = P::mk(T(0.5) * coulf * G, T(0.5) * coulf * v.w, v.w, T(0));
+                }
             }
         }
         for (int a0 = 0; a0 < kChunk * kClusterSize; a0 += 32) {
@@ -464,6 +530,10 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
                 else w.jx[a] = P::mk(v.x + T((float)dx * g.edge_f[0]), v.y + T((float)dy * g.edge_f[1]),
                                      v.z + T((float)dz * g.edge_f[2]), v.w);
                 w.jt[a] = make_int2(t.x * (int)sizeof(C2), t.y);   // byte offset of the LJ column
+                if constexpr (HYB) {
+                    const HybQ& hq = hrows[(int)v.w];
+                    w.hy.jG[a] = FP64 ? T(hq.G) : T(hq.Gf);
+                }
             }
         }
         for (int k = lane; k < 4 * kFiRow; k += 32) w.fi[k] = P::mk(T(0), T(0), T(0), T(0));
@@ -484,6 +554,13 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
             const T x1 = a1.x, y1 = a1.y, z1 = a1.z;
             const T q0k = a0.w * kap, q1k = a1.w * kap;
             const int j0off = t0.x, j1off = t1.x;
+            HybArg<T> h0 = ha, h1 = ha;   // the j-atom halves of the hybrid arguments
+            if constexpr (HYB) {
+                h0.Gj = w.hy.jG[v * kClusterSize + ty];
+                h1.Gj = w.hy.jG[v * kClusterSize + ty + 4];
+                h0.Gjk = h0.Gj * kap;
+                h1.Gjk = h1.Gj * kap;
+            }
             const int kdiag = nb == 0 ? jcl - fc : -1;   // i-cluster equal to this j-cluster
 
             // this lane column's i-clusters (byte tx of the column-major mask: bit k
@@ -515,10 +592,18 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
                         ok1 = !dg || tx < ty + 4;
                     }
                     T r20, r21;
-                    pair<FP64, ENERGY, EXCL>(xi, ti.x, ti.y, x0, y0, z0, a0.w, q0k, j0off, t0.y, ok0, lj_bytes, kl,
-                                             rc2, acc.x, acc.y, acc.z, fj0x, fj0y, fj0z, acc.w, npair, erc, irc, r20);
-                    pair<FP64, ENERGY, EXCL>(xi, ti.x, ti.y, x1, y1, z1, a1.w, q1k, j1off, t1.y, ok1, lj_bytes, kl,
-                                             rc2, acc.x, acc.y, acc.z, fj1x, fj1y, fj1z, acc.w, npair, erc, irc, r21);
+                    if constexpr (HYB) {
+                        const S4 hi = w.hy.ih[ia];
+                        h0.hGi = h1.hGi = hi.x;
+                        h0.hqi = h1.hqi = hi.y;
+                        h0.qi = h1.qi = hi.z;
+                    }
+                    pair<FP64, ENERGY, EXCL, HYB>(xi, ti.x, ti.y, x0, y0, z0, a0.w, q0k, j0off, t0.y, ok0, lj_bytes, kl,
+                                                  rc2, acc.x, acc.y, acc.z, fj0x, fj0y, fj0z, acc.w, npair, erc, irc,
+                                                  r20, h0);
+                    pair<FP64, ENERGY, EXCL, HYB>(xi, ti.x, ti.y, x1, y1, z1, a1.w, q1k, j1off, t1.y, ok1, lj_bytes, kl,
+                                                  rc2, acc.x, acc.y, acc.z, fj1x, fj1y, fj1z, acc.w, npair, erc, irc,
+                                                  r21, h1);
                     w.fi[ty * kFiRow + ia] = acc;
                     if (PRUNE) {
                         const bool n0 = ok0 && r20 < rl2, n1 = ok1 && r21 < rl2;
@@ -591,30 +676,40 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
     }
 }
 
-template <bool FP64>
+template <bool FP64, bool HYB>
 static size_t pair_smem(int n_ts, int warps)
 {
     const size_t tab = ((size_t)n_ts * n_ts * sizeof(typename Prec<FP64>::C2) + 127) / 128 * 128;
-    return tab + 256 * sizeof(unsigned) + (size_t)warps * sizeof(WarpSmem<FP64>);
+    return tab + 256 * sizeof(unsigned) + (size_t)warps * sizeof(WarpSmem<FP64, HYB>);
 }
 
-template <bool FP64, bool ENERGY>
+template <bool FP64, bool ENERGY, bool HYB>
 static void set_smem_attr()
 {
     static bool done = false;   // one per instantiation
     if (!done) {
-        cudaFuncSetAttribute(k_pair<FP64, ENERGY>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(k_pair<FP64, ENERGY>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        cudaFuncSetAttribute(k_pair<FP64, ENERGY, HYB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_pair<FP64, ENERGY, HYB>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
         done = true;
     }
 }
 
-template <bool FP64, bool ENERGY>
+template <bool FP64, bool ENERGY, bool HYB>
 static void launch_one(const Params& p, cudaStream_t s, int blocks, int warps)
 {
-    set_smem_attr<FP64, ENERGY>();
-    k_pair<FP64, ENERGY><<<blocks, warps * 32, pair_smem<FP64>(p.n_ts_lj, warps), s>>>(p);
+    set_smem_attr<FP64, ENERGY, HYB>();
+    k_pair<FP64, ENERGY, HYB><<<blocks, warps * 32, pair_smem<FP64, HYB>(p.n_ts_lj, warps), s>>>(p);
+}
+
+template <bool FP64, bool ENERGY, bool HYB>
+static int max_blocks(int warps, int n_ts)
+{
+    set_smem_attr<FP64, ENERGY, HYB>();
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pair<FP64, ENERGY, HYB>, warps * 32,
+                                                  pair_smem<FP64, HYB>(n_ts, warps));
+    return n;
 }
 
 void launch_pair_list(const Params& p, cudaStream_t s, int blocks)
@@ -624,30 +719,35 @@ void launch_pair_list(const Params& p, cudaStream_t s, int blocks)
 
 void launch_pair_forces(const Params& p, cudaStream_t s, bool energy, int blocks, int warps)
 {
+    const bool hyb = p.screening != 0;
     if (p.precision == 0) {
-        if (energy) launch_one<false, true>(p, s, blocks, warps);
-        else launch_one<false, false>(p, s, blocks, warps);
+        if (hyb) {
+            if (energy) launch_one<false, true, true>(p, s, blocks, warps);
+            else launch_one<false, false, true>(p, s, blocks, warps);
+        } else {
+            if (energy) launch_one<false, true, false>(p, s, blocks, warps);
+            else launch_one<false, false, false>(p, s, blocks, warps);
+        }
     } else {
-        if (energy) launch_one<true, true>(p, s, blocks, warps);
-        else launch_one<true, false>(p, s, blocks, warps);
+        if (hyb) {
+            if (energy) launch_one<true, true, true>(p, s, blocks, warps);
+            else launch_one<true, false, true>(p, s, blocks, warps);
+        } else {
+            if (energy) launch_one<true, true, false>(p, s, blocks, warps);
+            else launch_one<true, false, false>(p, s, blocks, warps);
+        }
     }
 }
 
-int pair_max_blocks_per_sm(bool fp64, bool energy, int warps, int n_ts)
+int pair_max_blocks_per_sm(bool fp64, bool energy, bool hyb, int warps, int n_ts)
 {
-    int n = 0;
+    int n;
     if (!fp64) {
-        set_smem_attr<false, false>();
-        set_smem_attr<false, true>();
-        const size_t smem = pair_smem<false>(n_ts, warps);
-        if (energy) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pair<false, true>, warps * 32, smem);
-        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pair<false, false>, warps * 32, smem);
+        if (hyb) n = energy ? max_blocks<false, true, true>(warps, n_ts) : max_blocks<false, false, true>(warps, n_ts);
+        else n = energy ? max_blocks<false, true, false>(warps, n_ts) : max_blocks<false, false, false>(warps, n_ts);
     } else {
-        set_smem_attr<true, false>();
-        set_smem_attr<true, true>();
-        const size_t smem = pair_smem<true>(n_ts, warps);
-        if (energy) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pair<true, true>, warps * 32, smem);
-        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pair<true, false>, warps * 32, smem);
+        if (hyb) n = energy ? max_blocks<true, true, true>(warps, n_ts) : max_blocks<true, false, true>(warps, n_ts);
+        else n = energy ? max_blocks<true, true, false>(warps, n_ts) : max_blocks<true, false, false>(warps, n_ts);
     }
     return n > 0 ? n : 1;
 }

@@ -162,6 +162,50 @@ __device__ __forceinline__ void half_kick(const Params& p, int s, int slot, doub
 // ---------------------------------------------------------------------------
 constexpr int kInlineReps = 4;   // up to this many replicas the step kernel's last block reduces them
 
+// Hybrid ion-sphere / Debye electrostatics of every charge state at the
+// plasma state just computed (Sec. II.A, Eqs. 4-7), by the warp that reduced
+// replica rr.  An ion of charge Q has R = (3Q / (4 pi n_e))^{1/3} (Eq. 4) and
+// the transition radius r' of Eq. 7, evaluated as s^3 / (kappa (t^2 + t + 1))
+// with s = kappa R and t = (1 + s^3)^{1/3} (no cancellation).  Its potential
+// is Q/r + c1 - c2 r^2 inside r' and G e^{-kappa r}/r outside; the continuity
+// of the potential and its first two derivatives at r' gives, with
+// x = kappa r' and D = 3 + 3x + x^2, G = 3 Q e^x / D,
+// c1 = -Q kappa (3 + 3x/2) / D and c2 = -2 pi n_e / 3 for every Q.
+// Without an ion sphere (Q = 0, n_e = 0 or kappa = 0): r' = 0, G = Q.
+__device__ void hyb_table(const Params& p, int rr, int lane, double kap, double ne)
+{
+    HybQ* rows = p.hq + (size_t)rr * kHybQ;
+    const double c2 = -2.0 * kPi * ne / 3.0;
+    const double rc = p.r_cut;
+    double rpm = 0.0;
+    for (int q = lane; q < kHybQ; q += 32) {
+        const double Q = (double)q;
+        double G = Q, rp = 0.0, c1 = 0.0;
+        if (q > 0 && ne > 0.0 && kap > 0.0) {
+            const double R = cbrt(3.0 * Q / (4.0 * kPi * ne));
+            const double s = R * kap, s3 = s * s * s;
+            const double t = cbrt(1.0 + s3);
+            rp = s3 / (kap * (t * t + t + 1.0));
+            const double x = kap * rp;
+            const double D = 3.0 + 3.0 * x + x * x;
+            c1 = -Q * kap * (3.0 + 1.5 * x) / D;
+            G = 3.0 * Q * exp(x) / D;
+        }
+        const double phirc = rc < rp ? Q / rc + c1 - c2 * rc * rc : G * exp(-kap * rc) / rc;
+        HybQ h;
+        h.G = G; h.rp = rp; h.c1 = c1; h.phirc = phirc;
+        h.Gf = (float)fmin(G, 1.0e30); h.rpf = (float)rp; h.c1f = (float)c1; h.phircf = (float)phirc;
+        rows[q] = h;
+        if (q <= p.z_max) rpm = fmax(rpm, rp);
+    }
+    for (int o = 16; o; o >>= 1) rpm = fmax(rpm, __shfl_xor_sync(0xffffffffu, rpm, o));
+    if (lane == 0) {
+        HybRep r;
+        r.c2 = c2; r.rpm2 = rpm * rpm; r.c2f = (float)c2; r.rpm2f = (float)(rpm * rpm);
+        p.hrep[rr] = r;
+    }
+}
+
 // Replica rr's per-step reduction by one warp: lane c reads accumulator copy
 // c and clears it, the warp reduces, lane 0 updates the plasma scalars (Eq. 3)
 // and the next grid.
@@ -205,6 +249,11 @@ __device__ void finalize_replica(const Params& p, int rr, int lane, long long ne
         plasma_scalars(p, rr, next, st);
         p.rs[rr] = st;
         make_grid(p, rr, mn, mx);
+    }
+    if (p.screening) {
+        const double kap = __shfl_sync(0xffffffffu, st.kappa_force, 0);
+        const double ne = __shfl_sync(0xffffffffu, st.n_dens, 0);
+        hyb_table(p, rr, lane, kap, ne);
     }
 }
 

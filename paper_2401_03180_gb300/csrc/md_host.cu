@@ -367,7 +367,7 @@ md_status autotune(md_handle* h)
     int bw = h->pair_warps, bb = h->pair_blocks;
     const int warps_c[] = {4, 8};
     for (int w : warps_c) {
-        int maxb = pair_max_blocks_per_sm(fp64, false, w, h->NTS_LJ);
+        int maxb = pair_max_blocks_per_sm(fp64, false, h->P.screening != 0, w, h->NTS_LJ);
         for (int bps = 1; bps <= maxb; ++bps) {
             int blocks = bps * h->n_sm;
             float tot = 0.0f;
@@ -407,6 +407,8 @@ md_status validate(const md_config* c, const md_system* s)
         return fail(h, MD_ERR_INVALID_ARG, "precision must be MD_PREC_MIXED or MD_PREC_FP64");
     if (c->plasma_mode != MD_PLASMA_BOOKKEEPING && c->plasma_mode != MD_PLASMA_PRESCRIBED)
         return fail(h, MD_ERR_INVALID_ARG, "bad plasma_mode");
+    if (c->screening != MD_SCREEN_DEBYE && c->screening != MD_SCREEN_HYBRID)
+        return fail(h, MD_ERR_INVALID_ARG, "screening must be MD_SCREEN_DEBYE or MD_SCREEN_HYBRID");
     if (c->max_steps < 1) return fail(h, MD_ERR_INVALID_ARG, "max_steps must be >= 1");
     if (!(c->te_floor_ev > 0)) return fail(h, MD_ERR_INVALID_ARG, "te_floor_ev must be > 0");
     if (!(c->coulomb_f > 0)) return fail(h, MD_ERR_INVALID_ARG, "coulomb_f must be > 0");
@@ -642,6 +644,9 @@ static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* 
     P.precision = c.precision; P.cr_enabled = c.cr_enabled; P.plasma_mode = c.plasma_mode;
     P.dt = c.dt_ps; P.r_cut = c.r_cut; P.rc2 = c.r_cut * c.r_cut; P.kappa_fixed = c.kappa_fixed;
     P.te_floor = c.te_floor_ev; P.coulomb_f = c.coulomb_f;
+    P.screening = c.screening;
+    P.z_max = 0;
+    for (int k = 0; k < c.n_species; ++k) P.z_max = std::max(P.z_max, c.z[k]);
     P.four_pi_f = 4.0 * M_PI * c.coulomb_f;
     P.inv_dte = 1.0 / c.dte_ev;
     P.rc_f = (float)c.r_cut;
@@ -672,6 +677,10 @@ static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* 
     double *d_dF, *d_pne, *d_pte, *d_vol;
     int* d_repoff;
     DALLOC(P.grid, R); DALLOC(P.rs, R); DALLOC(P.acc, (size_t)R * 16);
+    if (c.screening == MD_SCREEN_HYBRID) {
+        DALLOC(P.hq, (size_t)R * kHybQ);
+        DALLOC(P.hrep, R);
+    }
     DALLOC(d_seed, R); DALLOC(d_dF, (size_t)R * c.max_steps);
     DALLOC(d_pne, (size_t)R * (c.max_steps + 1)); DALLOC(d_pte, (size_t)R * (c.max_steps + 1));
     DALLOC(d_vol, R); DALLOC(d_repoff, R + 1);
@@ -790,7 +799,7 @@ static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* 
     h->grid_atoms = (N + 255) / 256;
     h->grid_cells = std::max(1, std::min(C, h->n_sm * 8));
     h->pair_warps = 8;
-    h->pair_blocks = h->n_sm * pair_max_blocks_per_sm(c.precision == MD_PREC_FP64, false, 8, h->NTS_LJ);
+    h->pair_blocks = h->n_sm * pair_max_blocks_per_sm(c.precision == MD_PREC_FP64, false, c.screening != 0, 8, h->NTS_LJ);
     h->list_blocks = std::max(1, std::min(P.sc_cap, 4 * h->n_sm));
     CU(cudaDeviceSynchronize());
 

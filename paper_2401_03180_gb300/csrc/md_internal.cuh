@@ -27,6 +27,7 @@ constexpr double kFixInv = 1.0 / 4294967296.0;
 constexpr double kFixLimit = 4.611686018427388e18;  // 2^62 (overflow guard)
 constexpr double kEvKJmol = 96.48533212;          // kJ/mol per eV
 constexpr double kLn2 = 0.69314718055994530942;   // ln 2 (scales the LJ table's c12 column)
+constexpr double kPi = 3.14159265358979323846;
 constexpr float kBBoxMargin = 1e-4f;               // nm, slack of the cluster prefilter
 
 // device error bits (mirrored to md_status by the host)
@@ -58,6 +59,23 @@ struct Grid {                // cell grid of one replica (rebuilt every step)
     int periodic;
 };
 
+// Hybrid ion-sphere / Debye electrostatics of one charge state q at the
+// plasma state of a step (Sec. II.A, Eqs. 4-7; reading in include/md.h):
+// phi(r) = q/r + c1 - c2 r^2 for r < rp, G e^{-kappa r}/r for r >= rp.
+constexpr int kHybQ = 33;    // charge states 0 .. MD_MAX_Z
+struct HybQ {
+    double G;                // Debye-form amplitude (q g(q)); q when there is no ion sphere
+    double rp;               // transition radius r' (nm); 0: no ion sphere
+    double c1;               // constant of the ion-sphere form
+    double phirc;            // phi(r_cut), the energy shift
+    float Gf, rpf, c1f, phircf;
+};
+struct HybRep {              // per replica
+    double c2;               // -2 pi n_e / 3 (the same for every q)
+    double rpm2;             // (max r' over the charge states present)^2
+    float c2f, rpm2f;
+};
+
 struct RepState {            // plasma and bookkeeping of one replica
     long long n_e;           // free electrons
     long long e_gas;         // gas energy, meV
@@ -86,6 +104,8 @@ struct Params {
     int n_ts_lj;             // type states of the species present (LJ table side)
     int cell_cap_total, slot_cap, cluster_cap, sc_cap;
     int precision, cr_enabled, plasma_mode;
+    int screening;           // MD_SCREEN_*
+    int z_max;               // largest nuclear charge of the species present
     double dt, r_cut, rc2, kappa_fixed, te_floor, four_pi_f, coulomb_f, inv_dte;
     float rc2_f, rc_f;
     double r_list;           // r_cut + Verlet skin: cell edge and list cutoff
@@ -120,6 +140,8 @@ struct Params {
     Grid* grid_b;            // grid of the last build (list, forces, refresh); may alias grid
     RepState* rs;
     RepAccum* acc;
+    HybQ* hq;                // [n_rep][kHybQ] (hybrid screening only, else null)
+    HybRep* hrep;            // [n_rep]
     const unsigned long long* seed;
     const double* dF;        // [n_rep][max_steps]
     const double* pres_ne;   // [n_rep][max_steps + 1]
@@ -256,7 +278,7 @@ void launch_philox(unsigned long long seed, const uint32_t* ctr, long long n, ui
                    cudaStream_t s);
 void launch_force_out(const Params& p, double* d_f_out, cudaStream_t s);
 void launch_refresh(const Params& p, cudaStream_t s);
-int pair_max_blocks_per_sm(bool fp64, bool energy, int warps, int n_ts);
+int pair_max_blocks_per_sm(bool fp64, bool energy, bool hyb, int warps, int n_ts);
 // message returned by md_last_error(NULL) (host side)
 void set_global_error(const std::string& msg);
 

@@ -21,6 +21,7 @@ MD_OK, MD_ERR_INVALID_ARG, MD_ERR_BAD_STATE, MD_ERR_OOM, MD_ERR_CUDA = 0, 1, 2, 
 MD_ERR_FIXED_OVERFLOW, MD_ERR_TIMEOUT, MD_ERR_NONFINITE, MD_ERR_CELL_OVERFLOW, MD_ERR_TABLE_END = 5, 6, 7, 8, 9
 MD_PREC_MIXED, MD_PREC_FP64 = 0, 1
 MD_PLASMA_BOOKKEEPING, MD_PLASMA_PRESCRIBED = 0, 1
+MD_SCREEN_DEBYE, MD_SCREEN_HYBRID = 0, 1
 MD_FIELD_X, MD_FIELD_V, MD_FIELD_F, MD_FIELD_Q, MD_FIELD_H = 1, 2, 4, 8, 16
 MD_FIELD_PLASMA, MD_FIELD_COUNTS, MD_FIELD_STEP, MD_FIELD_XLIST, MD_FIELD_ALL = 32, 64, 128, 256, 511
 MD_MAX_SPECIES = 8
@@ -44,7 +45,8 @@ class MDConfig(C.Structure):
                 ("ip_mev", C.c_void_p), ("e_pi_mev", C.c_void_p), ("e_auger_mev", C.c_void_p),
                 ("n_te", C.c_int), ("dte_ev", C.c_double), ("dev_alloc", ALLOC_FN),
                 ("dev_free", FREE_FN), ("alloc_ctx", C.c_void_p), ("autotune", C.c_int),
-                ("profile", C.c_int), ("list_reserve", C.c_int), ("list_skin_nm", C.c_double)]
+                ("profile", C.c_int), ("list_reserve", C.c_int), ("list_skin_nm", C.c_double),
+                ("screening", C.c_int)]
 
 
 class MDSystem(C.Structure):
@@ -288,7 +290,7 @@ class IonisingMD:
     def __init__(self, sample, atomic, *, dt_ps=5e-5, r_cut=1.2, precision="mixed", cr_enabled=True,
                  plasma_mode=MD_PLASMA_BOOKKEEPING, max_steps=1000, kappa_fixed=-1.0, t_start_fs=0.0,
                  te_floor_ev=1.0, coulomb_f=COULOMB_F, autotune=False, profile=False, list_reserve=0,
-                 list_skin_nm=0.0,
+                 list_skin_nm=0.0, screening="debye",
                  torch_allocator=True, sigma0=None, eps0=None, mass=None):
         import torch
         from . import workloads as W
@@ -321,6 +323,9 @@ class IonisingMD:
         cfg.autotune, cfg.profile = int(bool(autotune)), int(bool(profile))
         cfg.list_reserve = int(list_reserve)
         cfg.list_skin_nm = float(list_skin_nm)
+        if screening not in ("debye", "hybrid"):
+            raise ValueError("screening must be 'debye' or 'hybrid'")
+        cfg.screening = MD_SCREEN_HYBRID if screening == "hybrid" else MD_SCREEN_DEBYE
         s = sample
         arrs = [_c(s.x, np.float64), _c(s.v, np.float64), _c(s.species, np.uint8), _c(s.fragment, np.int32),
                 _c(s.q0, np.uint8), _c(s.replica_offset, np.int32), _c(s.seed, np.uint64),
