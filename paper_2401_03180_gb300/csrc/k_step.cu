@@ -178,7 +178,7 @@ __device__ void hyb_table(const Params& p, int rr, int lane, double kap, double 
     const double c2 = -2.0 * kPi * ne / 3.0;
     const double rc = p.r_cut;
     double rpm = 0.0;
-    for (int q = lane; q < kHybQ; q += 32) {
+    for (int q = lane; q <= p.z_max; q += 32) {   // the charge states the species can reach
         const double Q = (double)q;
         double G = Q, rp = 0.0, c1 = 0.0;
         if (q > 0 && ne > 0.0 && kap > 0.0) {
@@ -196,7 +196,7 @@ __device__ void hyb_table(const Params& p, int rr, int lane, double kap, double 
         h.G = G; h.rp = rp; h.c1 = c1; h.phirc = phirc;
         h.Gf = (float)fmin(G, 1.0e30); h.rpf = (float)rp; h.c1f = (float)c1; h.phircf = (float)phirc;
         rows[q] = h;
-        if (q <= p.z_max) rpm = fmax(rpm, rp);
+        rpm = fmax(rpm, rp);
     }
     for (int o = 16; o; o >>= 1) rpm = fmax(rpm, __shfl_xor_sync(0xffffffffu, rpm, o));
     if (lane == 0) {
