@@ -19,6 +19,11 @@ What it computes, in the paper's order (arXiv 2401.03180):
 * Sec. II.B, Eq. 8: screened LJ, with LJ parameters scaled per charge state
   (Eq. 11) and LJ excluded inside a native fragment.
 * Sec. II.B, Eq. 12: Newton's equation, integrated with velocity Verlet.
+* Sec. II.B, Eqs. 13-14 (optional, ``langevin_g``): electron-ion coupling as
+  Langevin friction gamma = n_e g_s and a Gaussian force with
+  <f f> = 2 m gamma k_B T_e, integrated as an exact Ornstein-Uhlenbeck
+  velocity update after the first half kick (reading), with Gaussians from
+  Philox stream 1 keyed by (seed, atom, step) through Box-Muller.
 * Sec. II.A (stochastic integer charges, processes named there): the
   reading "RCM-1" -- at most one photo-ionisation, Auger, collisional
   ionisation or recombination event per atom per step, drawn with
@@ -50,6 +55,9 @@ Parity pins (``tests/test_oracle_*.py``, all ``-m "not gpu"``):
   conservation.
 * ``OracleMD`` (velocity Verlet): NVE energy conservation and second-order
   convergence in dt.
+* ``gaussians`` / ``langevin_update``: normal moments and a KS test; the
+  friction-only decay c^n exactly; equipartition <m v^2> -> k_B T_e; the
+  Ornstein-Uhlenbeck autocorrelation e^{-gamma t}; charges unaffected.
 Trajectory agreement with the GPU beyond short horizons is *parity
 unpinned*: MD is chaotic, so only the first steps are compared.
 """
@@ -202,6 +210,32 @@ def pair_hybrid(r, qi, qj, c6, c12, kappa, ne, rc, lj_on=True, coulomb_f=COULOMB
     return fr.value, u.value
 
 
+def gaussians(seed: int, ids, step: int) -> np.ndarray:
+    """Three standard normal numbers per atom for the Langevin force of one
+    step (Sec. II.B, Eq. 14): Philox4x32-10 with key = seed and counter =
+    (atom id, step, 1, 0) (stream 1; the charge update uses stream 0) gives
+    four words w0..w3; Box-Muller on u = (w + 1/2) 2^-32 turns (w0, w1) and
+    (w2, w3) into two pairs, of which the first three numbers are used:
+    sqrt(-2 ln u_a) (cos 2 pi u_b, sin 2 pi u_b)."""
+    ids = np.ascontiguousarray(ids, dtype=np.uint32)
+    w = philox(seed, ids, np.full(len(ids), step, np.uint32), 1, 0).astype(np.float64)
+    u = (w + 0.5) * 2.0 ** -32
+    ra = np.sqrt(-2.0 * np.log(u[:, 0]))
+    rb = np.sqrt(-2.0 * np.log(u[:, 2]))
+    return np.stack([ra * np.cos(2.0 * np.pi * u[:, 1]), ra * np.sin(2.0 * np.pi * u[:, 1]),
+                     rb * np.cos(2.0 * np.pi * u[:, 3])], axis=1)
+
+
+def langevin_update(v, mass, gamma, kT, dt, xi):
+    """Exact Ornstein-Uhlenbeck update of the velocities over dt for
+    m dv/dt = -m gamma v + f(t), <f(t) f(t')> = 2 m gamma kT delta(t - t')
+    (Eqs. 13-14 without the potential force): v <- c v + sqrt((1 - c^2) kT / m) xi,
+    c = exp(-gamma dt).  kT in kJ/mol, mass in amu, v in nm/ps."""
+    c = np.exp(-np.asarray(gamma, np.float64) * dt)
+    sig = np.sqrt((1.0 - c * c) * kT / np.asarray(mass, np.float64))
+    return np.asarray(c)[..., None] * v + np.asarray(sig)[..., None] * xi
+
+
 def pulse_table(pulses, t_start_fs: float, dt_fs: float, n_steps: int) -> np.ndarray:
     """Photons/nm^2 per step for a list of pulses (photon keV, FWHM fs,
     fluence ph/um^2, centre fs, shape)."""
@@ -295,7 +329,7 @@ class OracleMD:
     def __init__(self, sample, atomic, *, dt_ps=5e-5, r_cut=1.2, cr_enabled=True,
                  kappa_fixed=-1.0, te_floor_ev=1.0, t_start_fs=0.0, pulses=None,
                  dF_table=None, prescribed=None, n_steps_max=0, coulomb_f=COULOMB_F,
-                 sigma0=None, eps0=None, mass=None, threads=None, screening="debye"):
+                 sigma0=None, eps0=None, mass=None, threads=None, screening="debye", langevin_g=None):
         from paper_2401_03180_gb300 import workloads as W
         self.s = sample
         self.a = atomic
@@ -306,6 +340,8 @@ class OracleMD:
         if screening not in ("debye", "hybrid"):
             raise ValueError("screening must be 'debye' or 'hybrid'")
         self.hybrid = screening == "hybrid"
+        # electron-ion coupling coefficient per species (nm^3/ps): gamma = n_e g_s
+        self.langevin_g = None if langevin_g is None else np.asarray(langevin_g, dtype=np.float64)
         self.te_floor = float(te_floor_ev)
         self.f = float(coulomb_f)
         self.n = sample.n_atoms
@@ -438,10 +474,23 @@ class OracleMD:
                 self.x[sl] -= L * np.floor(self.x[sl] / L)
 
     # -- the step ----------------------------------------------------------
+    def langevin(self, n):
+        """The O step of step n (reading of Eqs. 13-14): each replica's atoms
+        relax towards T_e with gamma = n_e g_s, n_e and T_e being the plasma
+        scalars the charge update of step n reads."""
+        for r in range(self.R):
+            sl = slice(self.rep_off[r], self.rep_off[r + 1])
+            sc = self.scal[r]
+            gam = sc["n_e"] * self.langevin_g[self.sp[sl]]
+            xi = gaussians(int(self.seed[r]), self.local[sl], n)
+            self.v[sl] = langevin_update(self.v[sl], self.mass[self.sp[sl]], gam, sc["te_ev"] * EV_KJMOL, self.dt, xi)
+
     def step(self):
         n = self.step_index
         hd = self.hdtm[self.sp][:, None]
         self.v += hd * self.F
+        if self.langevin_g is not None:
+            self.langevin(n)
         self.x += self.dt * self.v
         self._wrap()
         if self.cr_enabled:
