@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--screening", default="debye", choices=["debye", "hybrid"],
                     help="Coulomb screening: Debye (Eq. 2) or hybrid ion sphere / Debye (Eqs. 4-7)")
+    ap.add_argument("--langevin", type=float, default=0.0,
+                    help="electron-ion coupling g (nm^3/ps) of every species, Eqs. 13-14; 0: off")
     ap.add_argument("--skin", type=float, default=SKIN_NM,
                     help="Verlet buffer of the cluster-pair list (nm); 0 rebuilds every step")
     return ap.parse_args()
@@ -210,7 +212,8 @@ def run_gpu(args, rank, world, local):
     def make(prec, profile):
         g = M.IonisingMD(s, atom, precision=prec, r_cut=1.2, dt_ps=5e-5, max_steps=max_steps,
                          t_start_fs=wl.t_start_fs, autotune=(prec == "mixed"), profile=profile,
-                         list_skin_nm=args.skin, screening=args.screening)
+                         list_skin_nm=args.skin, screening=args.screening,
+                         langevin_g=args.langevin if args.langevin > 0 else None)
         for r in range(s.n_replicas):
             g.set_pulse(wl.pulses[r], replica=r)
         return g
@@ -303,7 +306,7 @@ def run_gpu(args, rank, world, local):
                    "pulse": [vars(p) for p in wl.pulses[0]], "t_start_fs": wl.t_start_fs,
                    "l2": "flushed between steps (256 MB write, untimed)",
                    "pair_tile": {"warps": tim.tile_warps, "blocks_per_sm": tim.tile_blocks_per_sm},
-                   "list_skin_nm": args.skin, "screening": args.screening,
+                   "list_skin_nm": args.skin, "screening": args.screening, "langevin_g": args.langevin,
                    "parallelism": f"replicas{world}"},
         "pair_interactions_per_s": world * pairs * K / (ms / 1e3),
         "pairs_per_step": pairs,

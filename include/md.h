@@ -146,6 +146,20 @@ typedef struct md_config {
                                 q_i phi_j) / 2, shifted to zero at r_cut.  The
                                 mixed path keeps G in FP32 and saturates it at
                                 1e30 (kappa r' > ~69).  0 (Debye) by default.  */
+    double langevin_g[MD_MAX_SPECIES];
+                             /* electron-ion coupling per species (nm^3/ps),
+                                Sec. II.B, Eqs. 13-14, read as follows: each
+                                atom of species s feels the friction
+                                -m gamma v with gamma = n_e langevin_g[s] and a
+                                Gaussian force with <f f> = 2 m gamma k_B T_e
+                                (n_e and T_e: the plasma scalars the step's
+                                charge update reads), integrated as the exact
+                                Ornstein-Uhlenbeck update v <- c v +
+                                sqrt((1 - c^2) k_B T_e / m) xi, c = e^{-gamma
+                                dt}, after the first half kick.  xi: Philox4x32-
+                                10 stream 1 (key = seed, counter = (atom index
+                                in the replica, step, 1, 0)) through Box-Muller.
+                                All zero (the default): no coupling.           */
 } md_config;
 
 /*

@@ -162,6 +162,36 @@ __device__ __forceinline__ void half_kick(const Params& p, int s, int slot, doub
 // ---------------------------------------------------------------------------
 constexpr int kInlineReps = 4;   // up to this many replicas the step kernel's last block reduces them
 
+// Three standard normal numbers for the Langevin force (Sec. II.B, Eq. 14)
+// from four Philox words: Box-Muller on u = (w + 1/2) 2^-32 for the pairs
+// (w0, w1) and (w2, w3), of which the first three results are used.  The
+// mixed path works in FP32 (u from the top 24 bits), the FP64 path in FP64.
+__device__ __forceinline__ void gauss3(uint4 w, bool fp32, double& g0, double& g1, double& g2)
+{
+    if (fp32) {
+        const float ua = __fmaf_rn((float)(w.x >> 8), 5.9604645e-08f, 2.9802322e-08f);
+        const float ub = __fmaf_rn((float)(w.y >> 8), 5.9604645e-08f, 2.9802322e-08f);
+        const float uc = __fmaf_rn((float)(w.z >> 8), 5.9604645e-08f, 2.9802322e-08f);
+        const float ud = __fmaf_rn((float)(w.w >> 8), 5.9604645e-08f, 2.9802322e-08f);
+        const float ra = sqrtf(-2.0f * logf(ua)), rb = sqrtf(-2.0f * logf(uc));
+        float sb, cb;
+        sincospif(2.0f * ub, &sb, &cb);
+        g0 = (double)(ra * cb);
+        g1 = (double)(ra * sb);
+        g2 = (double)(rb * cospif(2.0f * ud));
+    } else {
+        const double s = 2.3283064365386963e-10;   // 2^-32
+        const double ua = ((double)w.x + 0.5) * s, ub = ((double)w.y + 0.5) * s;
+        const double uc = ((double)w.z + 0.5) * s, ud = ((double)w.w + 0.5) * s;
+        const double ra = sqrt(-2.0 * log(ua)), rb = sqrt(-2.0 * log(uc));
+        double sb, cb;
+        sincospi(2.0 * ub, &sb, &cb);
+        g0 = ra * cb;
+        g1 = ra * sb;
+        g2 = rb * cospi(2.0 * ud);
+    }
+}
+
 // Hybrid ion-sphere / Debye electrostatics of every charge state at the
 // plasma state just computed (Sec. II.A, Eqs. 4-7), by the warp that reduced
 // replica rr.  An ion of charge Q has R = (3Q / (4 pi n_e))^{1/3} (Eq. 4) and
@@ -255,6 +285,18 @@ __device__ void finalize_replica(const Params& p, int rr, int lane, long long ne
         const double ne = __shfl_sync(0xffffffffu, st.n_dens, 0);
         hyb_table(p, rr, lane, kap, ne);
     }
+    if (p.langevin) {
+        // Langevin update of the next step per species (Eqs. 13-14): gamma =
+        // n_e g_s, c = e^{-gamma dt}, sigma = sqrt((1 - c^2) k_B T_e / m_s)
+        const double ne = __shfl_sync(0xffffffffu, st.n_dens, 0);
+        const double te = __shfl_sync(0xffffffffu, st.te_ev, 0);
+        if (lane < p.n_species) {
+            const double gam = ne * p.lgv_g[lane];
+            const double c = exp(-gam * p.dt);
+            const double kT = te * kEvKJmol;
+            p.lgv[(size_t)rr * kMaxSpecies + lane] = make_double2(c, sqrt((1.0 - c * c) * kT / p.mass[lane]));
+        }
+    }
 }
 
 // Once per step, after every replica: counters, step number and, with the
@@ -342,6 +384,19 @@ __global__ void __launch_bounds__(kStepThreads) k_step_a(Params p, int mode)
             double vx = p.vx[i], vy = p.vy[i], vz = p.vz[i];
             if (kick_full) { vx = vx + ax; vy = vy + ay; vz = vz + az; }
             vx = vx + ax; vy = vy + ay; vz = vz + az;
+            if (p.langevin) {
+                // electron-ion coupling (Eqs. 13-14): exact Ornstein-Uhlenbeck
+                // update with Philox stream 1 of (seed, atom, step)
+                const double2 cs = p.lgv[(size_t)r * kMaxSpecies + s];
+                const unsigned long long sd = p.seed[r];
+                const uint4 w4 = philox4x32_10(make_uint4((unsigned)p.local_id[i], (unsigned)step, 1u, 0u),
+                                               make_uint2((unsigned)sd, (unsigned)(sd >> 32)));
+                double gx, gy, gz;
+                gauss3(w4, p.precision == 0, gx, gy, gz);
+                vx = cs.x * vx + cs.y * gx;
+                vy = cs.x * vy + cs.y * gy;
+                vz = cs.x * vz + cs.y * gz;
+            }
             x += p.dt * vx;
             y += p.dt * vy;
             z += p.dt * vz;

@@ -409,6 +409,9 @@ md_status validate(const md_config* c, const md_system* s)
         return fail(h, MD_ERR_INVALID_ARG, "bad plasma_mode");
     if (c->screening != MD_SCREEN_DEBYE && c->screening != MD_SCREEN_HYBRID)
         return fail(h, MD_ERR_INVALID_ARG, "screening must be MD_SCREEN_DEBYE or MD_SCREEN_HYBRID");
+    for (int k = 0; k < MD_MAX_SPECIES; ++k)
+        if (!(c->langevin_g[k] >= 0.0) || !(c->langevin_g[k] < 1e30))
+            return fail(h, MD_ERR_INVALID_ARG, "langevin_g must be finite and >= 0");
     if (c->max_steps < 1) return fail(h, MD_ERR_INVALID_ARG, "max_steps must be >= 1");
     if (!(c->te_floor_ev > 0)) return fail(h, MD_ERR_INVALID_ARG, "te_floor_ev must be > 0");
     if (!(c->coulomb_f > 0)) return fail(h, MD_ERR_INVALID_ARG, "coulomb_f must be > 0");
@@ -680,6 +683,16 @@ static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* 
     if (c.screening == MD_SCREEN_HYBRID) {
         DALLOC(P.hq, (size_t)R * kHybQ);
         DALLOC(P.hrep, R);
+    }
+    P.langevin = 0;
+    for (int k = 0; k < c.n_species; ++k)
+        if (c.langevin_g[k] > 0.0) P.langevin = 1;
+    if (P.langevin) {
+        double* d_g;
+        DALLOC(d_g, kMaxSpecies);
+        DALLOC(P.lgv, (size_t)R * kMaxSpecies);
+        CU(cudaMemcpy(d_g, c.langevin_g, sizeof(double) * std::min(kMaxSpecies, MD_MAX_SPECIES), cudaMemcpyHostToDevice));
+        P.lgv_g = d_g;
     }
     DALLOC(d_seed, R); DALLOC(d_dF, (size_t)R * c.max_steps);
     DALLOC(d_pne, (size_t)R * (c.max_steps + 1)); DALLOC(d_pte, (size_t)R * (c.max_steps + 1));

@@ -105,6 +105,7 @@ struct Params {
     int cell_cap_total, slot_cap, cluster_cap, sc_cap;
     int precision, cr_enabled, plasma_mode;
     int screening;           // MD_SCREEN_*
+    int langevin;            // 1: electron-ion coupling (some langevin_g > 0)
     int z_max;               // largest nuclear charge of the species present
     double dt, r_cut, rc2, kappa_fixed, te_floor, four_pi_f, coulomb_f, inv_dte;
     float rc2_f, rc_f;
@@ -142,6 +143,8 @@ struct Params {
     RepAccum* acc;
     HybQ* hq;                // [n_rep][kHybQ] (hybrid screening only, else null)
     HybRep* hrep;            // [n_rep]
+    const double* lgv_g;     // [n_species] electron-ion coupling (nm^3/ps)
+    double2* lgv;            // [n_rep][kMaxSpecies] (c, sigma) of the Langevin update of the next step
     const unsigned long long* seed;
     const double* dF;        // [n_rep][max_steps]
     const double* pres_ne;   // [n_rep][max_steps + 1]

@@ -46,7 +46,7 @@ class MDConfig(C.Structure):
                 ("n_te", C.c_int), ("dte_ev", C.c_double), ("dev_alloc", ALLOC_FN),
                 ("dev_free", FREE_FN), ("alloc_ctx", C.c_void_p), ("autotune", C.c_int),
                 ("profile", C.c_int), ("list_reserve", C.c_int), ("list_skin_nm", C.c_double),
-                ("screening", C.c_int)]
+                ("screening", C.c_int), ("langevin_g", C.c_double * MD_MAX_SPECIES)]
 
 
 class MDSystem(C.Structure):
@@ -290,7 +290,7 @@ class IonisingMD:
     def __init__(self, sample, atomic, *, dt_ps=5e-5, r_cut=1.2, precision="mixed", cr_enabled=True,
                  plasma_mode=MD_PLASMA_BOOKKEEPING, max_steps=1000, kappa_fixed=-1.0, t_start_fs=0.0,
                  te_floor_ev=1.0, coulomb_f=COULOMB_F, autotune=False, profile=False, list_reserve=0,
-                 list_skin_nm=0.0, screening="debye",
+                 list_skin_nm=0.0, screening="debye", langevin_g=None,
                  torch_allocator=True, sigma0=None, eps0=None, mass=None):
         import torch
         from . import workloads as W
@@ -326,6 +326,10 @@ class IonisingMD:
         if screening not in ("debye", "hybrid"):
             raise ValueError("screening must be 'debye' or 'hybrid'")
         cfg.screening = MD_SCREEN_HYBRID if screening == "hybrid" else MD_SCREEN_DEBYE
+        if langevin_g is not None:
+            g = np.broadcast_to(np.asarray(langevin_g, np.float64), (len(atomic.z),))
+            for k in range(len(g)):
+                cfg.langevin_g[k] = float(g[k])
         s = sample
         arrs = [_c(s.x, np.float64), _c(s.v, np.float64), _c(s.species, np.uint8), _c(s.fragment, np.int32),
                 _c(s.q0, np.uint8), _c(s.replica_offset, np.int32), _c(s.seed, np.uint64),

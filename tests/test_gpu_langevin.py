@@ -1,0 +1,71 @@
+"""Langevin electron-ion coupling (Sec. II.B, Eqs. 13-14) on the GPU, through
+the C ABI (-m gpu): an ionising trajectory against the FP64 oracle (charges
+bit-exact, positions within the Debye path's tolerances), and free atoms
+coupled to a prescribed electron gas reaching equipartition at T_e."""
+import numpy as np
+import pytest
+
+from paper_2401_03180_gb300 import md as M
+from paper_2401_03180_gb300 import workloads as W
+
+from gpu_common import force_errors, methane, water
+
+pytestmark = pytest.mark.gpu
+
+TOL_X = {"mixed": 1e-6, "fp64": 1e-9}
+TOL_V = {"mixed": 5e-4, "fp64": 5e-11}   # 98th percentile of |dv| (nm/ps), as the Debye path plus the noise rounding
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+    from paper_2401_03180_gb300 import build
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need a GPU"
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_langevin_trajectory_matches_oracle(oracle_mod, prec):
+    s, rc = water(400)
+    atom = W.atomic_data(6.0, pi_scale=3000.0)
+    pulses = [W.Pulse(6.0, 5.0, 1e12, 0.0)]
+    g_e = np.full(len(atom.z), 1.0)        # nm^3/ps: gamma = n_e g ~ 50/ps here
+    kw = dict(r_cut=rc, max_steps=40, t_start_fs=-2.0)
+    gpu = M.IonisingMD(s, atom, precision=prec, langevin_g=g_e, **kw)
+    gpu.set_pulse(pulses)
+    ora = oracle_mod.OracleMD(s, atom, r_cut=rc, t_start_fs=-2.0, pulses=[pulses], n_steps_max=40, langevin_g=g_e)
+    plain = oracle_mod.OracleMD(s, atom, r_cut=rc, t_start_fs=-2.0, pulses=[pulses], n_steps_max=40)
+    for _ in range(30):
+        gpu.step(1)
+        ora.step()
+        plain.step()
+    st = gpu.get_state(M.MD_FIELD_X | M.MD_FIELD_V | M.MD_FIELD_Q)
+    gpu.close()
+    assert np.array_equal(st["q"], ora.q)
+    assert ora.e_gas[0] > 0                          # T_e > 0: the noise is on
+    L = s.box[0]
+    d = st["x"] - ora.x
+    d -= L * np.round(d / L)
+    assert float(np.sqrt((d ** 2).sum(1).mean())) <= TOL_X[prec]
+    dv = np.abs(st["v"] - ora.v).max(1)
+    assert np.percentile(dv, 98) <= TOL_V[prec], np.percentile(dv, 98)
+    # the coupling changes the velocities far beyond these tolerances
+    assert np.percentile(np.abs(plain.v - ora.v).max(1), 50) > 100 * TOL_V[prec]
+
+
+def test_free_atoms_reach_equipartition_at_te():
+    s = methane(300, charge_frac=0.0)
+    atom = W.atomic_data(8.0)
+    n_steps = 1500
+    te_ev, ne = 5.0, 100.0
+    gpu = M.IonisingMD(s, atom, r_cut=1.2, cr_enabled=False, max_steps=n_steps + 1,
+                       plasma_mode=M.MD_PLASMA_PRESCRIBED, eps0=np.zeros(5),
+                       langevin_g=np.full(len(atom.z), 2.0))   # gamma = 200/ps: 100-step relaxation
+    gpu.set_plasma_table(np.full(n_steps + 2, ne), np.full(n_steps + 2, te_ev))
+    gpu.step(n_steps)
+    st = gpu.get_state(M.MD_FIELD_V | M.MD_FIELD_F)
+    gpu.close()
+    assert np.abs(st["f"]).max() == 0.0              # neutral atoms, LJ off: free particles
+    m = W.MASS[s.species][:, None]
+    kT = te_ev * 96.48533212
+    assert float((m * st["v"] ** 2).mean()) == pytest.approx(kT, rel=0.03)
