@@ -165,14 +165,15 @@ constexpr int kInlineReps = 4;   // up to this many replicas the step kernel's l
 // Three standard normal numbers for the Langevin force (Sec. II.B, Eq. 14)
 // from four Philox words: Box-Muller on u = (w + 1/2) 2^-32 for the pairs
 // (w0, w1) and (w2, w3), of which the first three results are used.  The
-// mixed path works in FP32 (u from the top 24 bits), the FP64 path in FP64.
+// mixed path works in FP32 (u rounded to 24 bits, relative error 6e-8 down to
+// the smallest u, which rounds up to 1 at most), the FP64 path in FP64.
 __device__ __forceinline__ void gauss3(uint4 w, bool fp32, double& g0, double& g1, double& g2)
 {
     if (fp32) {
-        const float ua = __fmaf_rn((float)(w.x >> 8), 5.9604645e-08f, 2.9802322e-08f);
-        const float ub = __fmaf_rn((float)(w.y >> 8), 5.9604645e-08f, 2.9802322e-08f);
-        const float uc = __fmaf_rn((float)(w.z >> 8), 5.9604645e-08f, 2.9802322e-08f);
-        const float ud = __fmaf_rn((float)(w.w >> 8), 5.9604645e-08f, 2.9802322e-08f);
+        const float ua = __fmul_rn(__fadd_rn((float)w.x, 0.5f), 2.3283064e-10f);
+        const float ub = __fmul_rn(__fadd_rn((float)w.y, 0.5f), 2.3283064e-10f);
+        const float uc = __fmul_rn(__fadd_rn((float)w.z, 0.5f), 2.3283064e-10f);
+        const float ud = __fmul_rn(__fadd_rn((float)w.w, 0.5f), 2.3283064e-10f);
         const float ra = sqrtf(-2.0f * logf(ua)), rb = sqrtf(-2.0f * logf(uc));
         float sb, cb;
         sincospif(2.0f * ub, &sb, &cb);

@@ -13,7 +13,10 @@ from gpu_common import force_errors, methane, water
 pytestmark = pytest.mark.gpu
 
 TOL_X = {"mixed": 1e-6, "fp64": 1e-9}
-TOL_V = {"mixed": 5e-4, "fp64": 5e-11}   # 98th percentile of |dv| (nm/ps), as the Debye path plus the noise rounding
+# velocities relative to their scale: the coupling heats the ions to T_e (tens of
+# eV here, ~30x the thermal speed of the Debye test), and the FP32 force error
+# (1e-5 RMS) kicks them in proportion; 98th percentile of |dv| / (|v| + 1 nm/ps)
+TOL_V = {"mixed": 1e-4, "fp64": 1e-10}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -47,10 +50,11 @@ def test_langevin_trajectory_matches_oracle(oracle_mod, prec):
     d = st["x"] - ora.x
     d -= L * np.round(d / L)
     assert float(np.sqrt((d ** 2).sum(1).mean())) <= TOL_X[prec]
-    dv = np.abs(st["v"] - ora.v).max(1)
+    scale = np.linalg.norm(ora.v, axis=1) + 1.0
+    dv = np.abs(st["v"] - ora.v).max(1) / scale
     assert np.percentile(dv, 98) <= TOL_V[prec], np.percentile(dv, 98)
     # the coupling changes the velocities far beyond these tolerances
-    assert np.percentile(np.abs(plain.v - ora.v).max(1), 50) > 100 * TOL_V[prec]
+    assert np.percentile(np.abs(plain.v - ora.v).max(1) / scale, 50) > 100 * TOL_V[prec]
 
 
 def test_free_atoms_reach_equipartition_at_te():
@@ -62,10 +66,15 @@ def test_free_atoms_reach_equipartition_at_te():
                        plasma_mode=M.MD_PLASMA_PRESCRIBED, eps0=np.zeros(5),
                        langevin_g=np.full(len(atom.z), 2.0))   # gamma = 200/ps: 100-step relaxation
     gpu.set_plasma_table(np.full(n_steps + 2, ne), np.full(n_steps + 2, te_ev))
-    gpu.step(n_steps)
-    st = gpu.get_state(M.MD_FIELD_V | M.MD_FIELD_F)
-    gpu.close()
-    assert np.abs(st["f"]).max() == 0.0              # neutral atoms, LJ off: free particles
     m = W.MASS[s.species][:, None]
+    gpu.step(500)                                    # 5 relaxation times
+    temps = []
+    for _ in range(10):                              # snapshots one relaxation time apart
+        gpu.step(100)
+        st = gpu.get_state(M.MD_FIELD_V | M.MD_FIELD_F)
+        assert np.abs(st["f"]).max() == 0.0          # neutral atoms, LJ off: free particles
+        temps.append(float((m * st["v"] ** 2).mean()))
+    gpu.close()
     kT = te_ev * 96.48533212
-    assert float((m * st["v"] ** 2).mean()) == pytest.approx(kT, rel=0.03)
+    # 10 snapshots x 4,500 degrees of freedom: relative standard error ~0.7 %
+    assert float(np.mean(temps)) == pytest.approx(kT, rel=0.03)
