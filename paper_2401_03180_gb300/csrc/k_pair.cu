@@ -415,7 +415,7 @@ __global__ void __launch_bounds__(kHalfShell * 32) k_pair_list(Params p)
 // Forces over the cluster-pair list.  A warp takes one chunk (up to kChunk
 // entries of one SC) at a time from an atomic counter.
 template <bool FP64, bool ENERGY, bool HYB>
-__global__ void __launch_bounds__(256, (FP64 || HYB) ? 2 : 3) k_pair(Params p)
+__global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
 {
     using P = Prec<FP64>;
     using T = typename P::T;
