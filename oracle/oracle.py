@@ -19,6 +19,11 @@ What it computes, in the paper's order (arXiv 2401.03180):
 * Sec. II.B, Eq. 8: screened LJ, with LJ parameters scaled per charge state
   (Eq. 11) and LJ excluded inside a native fragment.
 * Sec. II.B, Eq. 12: Newton's equation, integrated with velocity Verlet.
+* Sec. II.A (optional, ``charge_table``): charges assigned from per-step
+  charge-state fractions of a CR calculation, "stochastically, so that they
+  match on average" -- read as quantile coupling: each atom keeps one uniform
+  quantile u (Philox stream 2, counter (atom, 0, 2, 0), res53) and takes the
+  smallest charge whose cumulative fraction of its species exceeds u.
 * Sec. II.B, Eqs. 13-14 (optional, ``langevin_g``): electron-ion coupling as
   Langevin friction gamma = n_e g_s and a Gaussian force with
   <f f> = 2 m gamma k_B T_e, integrated as an exact Ornstein-Uhlenbeck
@@ -55,6 +60,10 @@ Parity pins (``tests/test_oracle_*.py``, all ``-m "not gpu"``):
   conservation.
 * ``OracleMD`` (velocity Verlet): NVE energy conservation and second-order
   convergence in dt.
+* ``table_charges``: populations match the fractions (chi-squared); a
+  one-state table puts every atom in that state; monotone fractions give
+  monotone charges (no atom recombines while the distribution ionises);
+  charge conservation N_e = sum q.
 * ``gaussians`` / ``langevin_update``: normal moments and a KS test; the
   friction-only decay c^n exactly; equipartition <m v^2> -> k_B T_e; the
   Ornstein-Uhlenbeck autocorrelation e^{-gamma t}; charges unaffected.
@@ -210,6 +219,40 @@ def pair_hybrid(r, qi, qj, c6, c12, kappa, ne, rc, lj_on=True, coulomb_f=COULOMB
     return fr.value, u.value
 
 
+def charge_quantiles(seed: int, ids) -> np.ndarray:
+    """Each atom's fixed quantile for the table-driven charges: res53 of the
+    first two words of Philox4x32-10 with key = seed, counter = (atom id, 0, 2, 0)."""
+    ids = np.ascontiguousarray(ids, dtype=np.uint32)
+    w = philox(seed, ids, np.zeros(len(ids), np.uint32), 2, 0)
+    return ((w[:, 0] >> 5).astype(np.float64) * 67108864.0 + (w[:, 1] >> 6).astype(np.float64)) \
+        * 1.1102230246251565e-16
+
+
+def cumulative_fractions(frac_row, ts_off):
+    """Per species, the running sums of the charge-state fractions of one table
+    row (FP64, in charge order): cum[ts_off[s] + q] = sum_{q' <= q} f_{s,q'}."""
+    frac = np.asarray(frac_row, dtype=np.float64)
+    cum = np.empty_like(frac)
+    for s in range(len(ts_off) - 1):
+        acc = 0.0
+        for k in range(ts_off[s], ts_off[s + 1]):
+            acc = acc + float(frac[k])
+            cum[k] = acc
+    return cum
+
+
+def table_charges(u, species, z, ts_off, cum_row):
+    """Charges from one row of cumulative fractions: the smallest q with
+    u < cum[ts_off[s] + q]; Z if rounding leaves none."""
+    q = np.empty(len(u), dtype=np.uint8)
+    for i in range(len(u)):
+        s = int(species[i])
+        c = cum_row[ts_off[s]:ts_off[s + 1]]
+        k = int(np.searchsorted(c, u[i], side="right"))   # first c > u
+        q[i] = min(k, int(z[s]))
+    return q
+
+
 def gaussians(seed: int, ids, step: int) -> np.ndarray:
     """Three standard normal numbers per atom for the Langevin force of one
     step (Sec. II.B, Eq. 14): Philox4x32-10 with key = seed and counter =
@@ -329,7 +372,8 @@ class OracleMD:
     def __init__(self, sample, atomic, *, dt_ps=5e-5, r_cut=1.2, cr_enabled=True,
                  kappa_fixed=-1.0, te_floor_ev=1.0, t_start_fs=0.0, pulses=None,
                  dF_table=None, prescribed=None, n_steps_max=0, coulomb_f=COULOMB_F,
-                 sigma0=None, eps0=None, mass=None, threads=None, screening="debye", langevin_g=None):
+                 sigma0=None, eps0=None, mass=None, threads=None, screening="debye", langevin_g=None,
+                 charge_table=None):
         from paper_2401_03180_gb300 import workloads as W
         self.s = sample
         self.a = atomic
@@ -340,6 +384,8 @@ class OracleMD:
         if screening not in ("debye", "hybrid"):
             raise ValueError("screening must be 'debye' or 'hybrid'")
         self.hybrid = screening == "hybrid"
+        # charge-state fractions per replica and step, [R][rows][n_ts] (None: RCM-1 rates)
+        self.charge_table = None if charge_table is None else np.asarray(charge_table, np.float64)
         # electron-ion coupling coefficient per species (nm^3/ps): gamma = n_e g_s
         self.langevin_g = None if langevin_g is None else np.asarray(langevin_g, dtype=np.float64)
         self.te_floor = float(te_floor_ev)
@@ -485,6 +531,24 @@ class OracleMD:
             xi = gaussians(int(self.seed[r]), self.local[sl], n)
             self.v[sl] = langevin_update(self.v[sl], self.mass[self.sp[sl]], gam, sc["te_ev"] * EV_KJMOL, self.dt, xi)
 
+    def table_step(self, step):
+        """Charges of the state after step n from row n + 1 of the fractions
+        table (reading of Sec. II.A); K holes are not tracked (h = 0)."""
+        R = self.R
+        dNe = np.zeros(R, dtype=np.int64); cnt = np.zeros((R, 4), dtype=np.int64)
+        for r in range(R):
+            sl = slice(self.rep_off[r], self.rep_off[r + 1])
+            cum = cumulative_fractions(self.charge_table[r][step + 1], self.off)
+            u = charge_quantiles(int(self.seed[r]), self.local[sl])
+            qn = table_charges(u, self.sp[sl], self.z, self.off, cum)
+            dq = qn.astype(np.int64) - self.q[sl].astype(np.int64)
+            dNe[r] = int(dq.sum())
+            cnt[r, 0] = int(dq[dq > 0].sum())
+            cnt[r, 3] = int(-dq[dq < 0].sum())
+            self.q[sl] = qn
+            self.h[sl] = 0
+        return dNe, np.zeros(R, dtype=np.int64), cnt
+
     def step(self):
         n = self.step_index
         hd = self.hdtm[self.sp][:, None]
@@ -494,7 +558,7 @@ class OracleMD:
         self.x += self.dt * self.v
         self._wrap()
         if self.cr_enabled:
-            dNe, dE, cnt = self.cr_step(n)
+            dNe, dE, cnt = self.table_step(n) if self.charge_table is not None else self.cr_step(n)
             self.n_e += dNe
             self.e_gas = np.maximum(self.e_gas + dE, 0)
             self.counts += cnt
