@@ -63,6 +63,8 @@ def parse():
                     help="Coulomb screening: Debye (Eq. 2) or hybrid ion sphere / Debye (Eqs. 4-7)")
     ap.add_argument("--langevin", type=float, default=0.0,
                     help="electron-ion coupling g (nm^3/ps) of every species, Eqs. 13-14; 0: off")
+    ap.add_argument("--charge-table", action="store_true",
+                    help="charges from per-step CR charge-state fractions (a synthetic table) instead of the rates")
     ap.add_argument("--skin", type=float, default=SKIN_NM,
                     help="Verlet buffer of the cluster-pair list (nm); 0 rebuilds every step")
     return ap.parse_args()
@@ -194,6 +196,7 @@ def run_gpu(args, rank, world, local):
     import torch
     from paper_2401_03180_gb300 import build as B
     from paper_2401_03180_gb300 import md as M
+    from paper_2401_03180_gb300 import workloads as W
 
     B.build()
     torch.cuda.set_device(local)
@@ -213,9 +216,13 @@ def run_gpu(args, rank, world, local):
         g = M.IonisingMD(s, atom, precision=prec, r_cut=1.2, dt_ps=5e-5, max_steps=max_steps,
                          t_start_fs=wl.t_start_fs, autotune=(prec == "mixed"), profile=profile,
                          list_skin_nm=args.skin, screening=args.screening,
-                         langevin_g=args.langevin if args.langevin > 0 else None)
+                         langevin_g=args.langevin if args.langevin > 0 else None,
+                         charge_mode="table" if args.charge_table else "rates")
         for r in range(s.n_replicas):
             g.set_pulse(wl.pulses[r], replica=r)
+            if args.charge_table:
+                g.set_charge_table(W.charge_fraction_table(wl.pulses[r], wl.t_start_fs, 5e-5 * 1000.0, max_steps + 1),
+                                   replica=r)
         return g
 
     def timed_steps(g, k_steps):
@@ -316,6 +323,7 @@ def run_gpu(args, rank, world, local):
                    "l2": "flushed between steps (256 MB write, untimed)",
                    "pair_tile": {"warps": tim.tile_warps, "blocks_per_sm": tim.tile_blocks_per_sm},
                    "list_skin_nm": args.skin, "screening": args.screening, "langevin_g": args.langevin,
+                   "charges": "table" if args.charge_table else "rates",
                    "parallelism": f"replicas{world}"},
         "pair_interactions_per_s": world * pairs * K / (ms / 1e3),
         "pairs_per_step": pairs,

@@ -62,6 +62,7 @@ enum {
 enum { MD_PREC_MIXED = 0, MD_PREC_FP64 = 1 };
 enum { MD_PLASMA_BOOKKEEPING = 0, MD_PLASMA_PRESCRIBED = 1 };
 enum { MD_SCREEN_DEBYE = 0, MD_SCREEN_HYBRID = 1 };
+enum { MD_CHARGE_RATES = 0, MD_CHARGE_TABLE = 1 };
 enum { MD_PULSE_GAUSSIAN = 0, MD_PULSE_FLAT_TOP = 1 };
 
 /*
@@ -160,6 +161,22 @@ typedef struct md_config {
                                 10 stream 1 (key = seed, counter = (atom index
                                 in the replica, step, 1, 0)) through Box-Muller.
                                 All zero (the default): no coupling.           */
+    int charge_mode;         /* MD_CHARGE_RATES (default): the charge update
+                                draws events from the rates (RCM-1).
+                                MD_CHARGE_TABLE: charges follow per-step
+                                charge-state fractions of a CR calculation
+                                (md_set_charge_table), the paper's mode (Sec.
+                                II.A: integer charges assigned stochastically
+                                so that, averaged, they match the CR charge
+                                states).  Read as quantile coupling: each atom
+                                keeps one uniform quantile u (Philox4x32-10
+                                stream 2, key = seed, counter = (atom index in
+                                the replica, 0, 2, 0), 53-bit) and takes the
+                                smallest q whose cumulative fraction of its
+                                species exceeds u (Z if rounding leaves none).
+                                K holes stay 0; N_e follows sum q; the gas
+                                energy is not changed (use plasma_mode =
+                                MD_PLASMA_PRESCRIBED for T_e).                 */
 } md_config;
 
 /*
@@ -273,6 +290,20 @@ md_status md_set_pulse_table_at(md_handle* h, int replica, int first_step, const
  * has passed the copy; pageable memory is staged by the driver).  Errors:
  * INVALID_ARG (step outside [0, max_steps), null or bad values), CUDA. */
 md_status md_set_fluence_at(md_handle* h, int step, const double* dF);
+
+/* Charge-state fractions per step for charge_mode = MD_CHARGE_TABLE (Sec.
+ * II.A: the CR calculation's time-resolved fraction of each charge state of
+ * every species).  frac: host array [n_rows][n_ts] (copied), n_ts = the sum
+ * over species of Z_s + 1, type state (s, q) in column off_s + q with off_s
+ * = sum_{s' < s} (Z_s' + 1).  Row n holds the fractions at t_n = t_start +
+ * n dt; the charge update of step n reads row n + 1.  Rows n_rows ..
+ * max_steps keep their previous contents (at init: every atom neutral).
+ * Each species' fractions must be >= 0 and sum to 1 within 1e-9.  The
+ * library stores their running sums (FP64, in charge order).  replica = -1:
+ * all replicas.  Errors: INVALID_ARG (bad replica, n_rows outside
+ * [1, max_steps + 1], bad fractions), BAD_STATE (charge_mode is not
+ * MD_CHARGE_TABLE), CUDA. */
+md_status md_set_charge_table(md_handle* h, int replica, const double* frac, int n_rows);
 
 /* Prescribed plasma (plasma_mode = MD_PLASMA_PRESCRIBED): n_e (nm^-3) and
  * T_e (eV) for steps 0 .. n_steps-1 (n_steps <= max_steps + 1). */

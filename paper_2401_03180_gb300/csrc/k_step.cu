@@ -485,7 +485,46 @@ __global__ void __launch_bounds__(kStepThreads) k_step_a(Params p, int mode)
     }
 
     // ---- collisional-radiative update (reading of Sec. II.A) ----
-    if (live && cr_role && (mode & STEP_CR)) {
+    if (live && cr_role && (mode & STEP_CR) && p.charge_mode == kChargeTable) {
+        // charges from the CR charge-state fractions (reading of Sec. II.A): the
+        // atom's fixed quantile u (Philox stream 2) against the running sums of
+        // its species at the end of this step (table row step + 1)
+        const int s = p.species[i];
+        const int Z = p.zs[s];
+        const int qi = p.q[i];
+        int qn = qi;
+        if (step < p.max_steps) {
+            const double* cum = p.qcum + ((size_t)r * (p.max_steps + 1) + (size_t)(step + 1)) * p.n_ts + p.ts_off[s];
+            const unsigned long long sd = p.seed[r];
+            const uint4 w4 = philox4x32_10(make_uint4((unsigned)p.local_id[i], 0u, 2u, 0u),
+                                           make_uint2((unsigned)sd, (unsigned)(sd >> 32)));
+            const double u = u53(w4.x, w4.y);
+            qn = Z;
+            for (int k = 0; k <= Z; ++k)
+                if (u < cum[k]) { qn = k; break; }
+        } else {
+            atomicOr(p.err, ERR_TABLE_END);
+        }
+        s_q[i - first] = (uint8_t)qn;
+        if (qn != qi || p.h[i]) {
+            p.q[i] = (uint8_t)qn;
+            p.h[i] = 0;
+        }
+        const int dq = qn - qi;
+        if (dq != 0) {
+            const int w = r - r0;
+            const unsigned long long up = (unsigned long long)(dq > 0 ? dq : -dq);
+            if (w < kRepWindow) {
+                atomicAdd((unsigned long long*)&s_acc[w][0], (unsigned long long)(long long)dq);
+                atomicAdd((unsigned long long*)&s_acc[w][dq > 0 ? 2 : 5], up);
+            } else {
+                RepAccum* a = p.acc + (size_t)r * kAccCopies + (blockIdx.x & (kAccCopies - 1));
+                atomicAdd((unsigned long long*)&a->dNe, (unsigned long long)(long long)dq);
+                atomicAdd((unsigned long long*)&a->counts[dq > 0 ? 0 : 3], up);
+            }
+        }
+    }
+    if (live && cr_role && (mode & STEP_CR) && p.charge_mode != kChargeTable) {
         const int s = p.species[i];
         const int Z = p.zs[s];
         const int qi = p.q[i], hi = p.h[i];

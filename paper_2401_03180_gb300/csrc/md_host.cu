@@ -412,6 +412,8 @@ md_status validate(const md_config* c, const md_system* s)
     for (int k = 0; k < MD_MAX_SPECIES; ++k)
         if (!(c->langevin_g[k] >= 0.0) || !(c->langevin_g[k] < 1e30))
             return fail(h, MD_ERR_INVALID_ARG, "langevin_g must be finite and >= 0");
+    if (c->charge_mode != MD_CHARGE_RATES && c->charge_mode != MD_CHARGE_TABLE)
+        return fail(h, MD_ERR_INVALID_ARG, "charge_mode must be MD_CHARGE_RATES or MD_CHARGE_TABLE");
     if (c->max_steps < 1) return fail(h, MD_ERR_INVALID_ARG, "max_steps must be >= 1");
     if (!(c->te_floor_ev > 0)) return fail(h, MD_ERR_INVALID_ARG, "te_floor_ev must be > 0");
     if (!(c->coulomb_f > 0)) return fail(h, MD_ERR_INVALID_ARG, "coulomb_f must be > 0");
@@ -684,6 +686,14 @@ static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* 
         DALLOC(P.hq, (size_t)R * kHybQ);
         DALLOC(P.hrep, R);
     }
+    P.charge_mode = c.charge_mode;
+    if (c.charge_mode == MD_CHARGE_TABLE) {
+        // every atom neutral until a table is set: running sums of 1 everywhere
+        const size_t n = (size_t)R * (c.max_steps + 1) * nts;
+        DALLOC(P.qcum, n);
+        std::vector<double> ones(n, 1.0);
+        CU(cudaMemcpy(P.qcum, ones.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+    }
     P.langevin = 0;
     for (int k = 0; k < c.n_species; ++k)
         if (c.langevin_g[k] > 0.0) P.langevin = 1;
@@ -936,6 +946,36 @@ md_status md_set_fluence_at(md_handle* h, int step, const double* dF)
     double* dst = const_cast<double*>(h->P.dF) + step;
     CU(cudaMemcpy2DAsync(dst, (size_t)h->cfg.max_steps * sizeof(double), dF, sizeof(double), sizeof(double),
                          (size_t)h->R, cudaMemcpyHostToDevice, h->stream));
+    return MD_OK;
+}
+
+md_status md_set_charge_table(md_handle* h, int replica, const double* frac, int n_rows)
+{
+    md_status st = check_replica(h, replica);
+    if (st != MD_OK) return st;
+    if (h->cfg.charge_mode != MD_CHARGE_TABLE) return fail(h, MD_ERR_BAD_STATE, "charge_mode is not MD_CHARGE_TABLE");
+    if (!frac || n_rows < 1 || n_rows > h->cfg.max_steps + 1)
+        return fail(h, MD_ERR_INVALID_ARG, "n_rows must be in [1, max_steps + 1]");
+    const int nts = h->NTS;
+    std::vector<double> cum((size_t)n_rows * nts);
+    for (int n = 0; n < n_rows; ++n)
+        for (int s = 0; s < h->NS; ++s) {
+            double acc = 0.0;
+            for (int k = h->ts_off[s]; k < h->ts_off[s + 1]; ++k) {
+                const double f = frac[(size_t)n * nts + k];
+                if (!(f >= 0.0) || !(f <= 1.0)) return fail(h, MD_ERR_INVALID_ARG, "fractions must be in [0, 1]");
+                acc = acc + f;
+                cum[(size_t)n * nts + k] = acc;
+            }
+            if (!(std::fabs(acc - 1.0) <= 1e-9))
+                return fail(h, MD_ERR_INVALID_ARG, "the fractions of a species must sum to 1 (row " + std::to_string(n) + ")");
+        }
+    const int r0 = replica < 0 ? 0 : replica, r1 = replica < 0 ? h->R : replica + 1;
+    const size_t stride = (size_t)(h->cfg.max_steps + 1) * nts;
+    for (int r = r0; r < r1; ++r)
+        CU(cudaMemcpyAsync(h->P.qcum + r * stride, cum.data(), cum.size() * sizeof(double), cudaMemcpyHostToDevice,
+                           h->stream));
+    CU(cudaStreamSynchronize(h->stream));
     return MD_OK;
 }
 

@@ -28,6 +28,7 @@ constexpr double kFixLimit = 4.611686018427388e18;  // 2^62 (overflow guard)
 constexpr double kEvKJmol = 96.48533212;          // kJ/mol per eV
 constexpr double kLn2 = 0.69314718055994530942;   // ln 2 (scales the LJ table's c12 column)
 constexpr double kPi = 3.14159265358979323846;
+constexpr int kChargeTable = 1;                  // MD_CHARGE_TABLE
 constexpr float kBBoxMargin = 1e-4f;               // nm, slack of the cluster prefilter
 
 // device error bits (mirrored to md_status by the host)
@@ -106,6 +107,7 @@ struct Params {
     int precision, cr_enabled, plasma_mode;
     int screening;           // MD_SCREEN_*
     int langevin;            // 1: electron-ion coupling (some langevin_g > 0)
+    int charge_mode;         // MD_CHARGE_*
     int z_max;               // largest nuclear charge of the species present
     double dt, r_cut, rc2, kappa_fixed, te_floor, four_pi_f, coulomb_f, inv_dte;
     float rc2_f, rc_f;
@@ -145,6 +147,7 @@ struct Params {
     HybRep* hrep;            // [n_rep]
     const double* lgv_g;     // [n_species] electron-ion coupling (nm^3/ps)
     double2* lgv;            // [n_rep][kMaxSpecies] (c, sigma) of the Langevin update of the next step
+    double* qcum;            // [n_rep][max_steps + 1][n_ts] running sums of the charge-state fractions
     const unsigned long long* seed;
     const double* dF;        // [n_rep][max_steps]
     const double* pres_ne;   // [n_rep][max_steps + 1]

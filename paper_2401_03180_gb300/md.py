@@ -22,6 +22,7 @@ MD_ERR_FIXED_OVERFLOW, MD_ERR_TIMEOUT, MD_ERR_NONFINITE, MD_ERR_CELL_OVERFLOW, M
 MD_PREC_MIXED, MD_PREC_FP64 = 0, 1
 MD_PLASMA_BOOKKEEPING, MD_PLASMA_PRESCRIBED = 0, 1
 MD_SCREEN_DEBYE, MD_SCREEN_HYBRID = 0, 1
+MD_CHARGE_RATES, MD_CHARGE_TABLE = 0, 1
 MD_FIELD_X, MD_FIELD_V, MD_FIELD_F, MD_FIELD_Q, MD_FIELD_H = 1, 2, 4, 8, 16
 MD_FIELD_PLASMA, MD_FIELD_COUNTS, MD_FIELD_STEP, MD_FIELD_XLIST, MD_FIELD_ALL = 32, 64, 128, 256, 511
 MD_MAX_SPECIES = 8
@@ -46,7 +47,8 @@ class MDConfig(C.Structure):
                 ("n_te", C.c_int), ("dte_ev", C.c_double), ("dev_alloc", ALLOC_FN),
                 ("dev_free", FREE_FN), ("alloc_ctx", C.c_void_p), ("autotune", C.c_int),
                 ("profile", C.c_int), ("list_reserve", C.c_int), ("list_skin_nm", C.c_double),
-                ("screening", C.c_int), ("langevin_g", C.c_double * MD_MAX_SPECIES)]
+                ("screening", C.c_int), ("langevin_g", C.c_double * MD_MAX_SPECIES),
+                ("charge_mode", C.c_int)]
 
 
 class MDSystem(C.Structure):
@@ -114,6 +116,7 @@ def lib():
             L.md_set_pulse_table.argtypes = [P, C.c_int, P, C.c_int]
             L.md_set_pulse_table_at.argtypes = [P, C.c_int, C.c_int, P, C.c_int]
             L.md_set_plasma_table.argtypes = [P, C.c_int, P, P, C.c_int]
+            L.md_set_charge_table.argtypes = [P, C.c_int, P, C.c_int]
             L.md_set_fluence_at.argtypes = [P, C.c_int, P]
             L.md_step.argtypes = [P, C.c_int]
             L.md_step_async.argtypes = [P, C.c_int]
@@ -187,6 +190,11 @@ def md_set_pulse_table_at(h, replica: int, first_step: int, dF):
 def md_set_fluence_at(h, step: int, dF):
     """dF[r]: fluence of `step` for each replica r (float64 array, pinned for overlap)."""
     _check(lib().md_set_fluence_at(h, int(step), _p(dF)), h)
+
+
+def md_set_charge_table(h, replica: int, frac):
+    f = np.ascontiguousarray(frac, dtype=np.float64)
+    _check(lib().md_set_charge_table(h, int(replica), _p(f), int(f.shape[0])), h)
 
 
 def md_set_plasma_table(h, replica: int, ne, te_ev):
@@ -290,7 +298,7 @@ class IonisingMD:
     def __init__(self, sample, atomic, *, dt_ps=5e-5, r_cut=1.2, precision="mixed", cr_enabled=True,
                  plasma_mode=MD_PLASMA_BOOKKEEPING, max_steps=1000, kappa_fixed=-1.0, t_start_fs=0.0,
                  te_floor_ev=1.0, coulomb_f=COULOMB_F, autotune=False, profile=False, list_reserve=0,
-                 list_skin_nm=0.0, screening="debye", langevin_g=None,
+                 list_skin_nm=0.0, screening="debye", langevin_g=None, charge_mode="rates",
                  torch_allocator=True, sigma0=None, eps0=None, mass=None):
         import torch
         from . import workloads as W
@@ -326,6 +334,9 @@ class IonisingMD:
         if screening not in ("debye", "hybrid"):
             raise ValueError("screening must be 'debye' or 'hybrid'")
         cfg.screening = MD_SCREEN_HYBRID if screening == "hybrid" else MD_SCREEN_DEBYE
+        if charge_mode not in ("rates", "table"):
+            raise ValueError("charge_mode must be 'rates' or 'table'")
+        cfg.charge_mode = MD_CHARGE_TABLE if charge_mode == "table" else MD_CHARGE_RATES
         if langevin_g is not None:
             g = np.broadcast_to(np.asarray(langevin_g, np.float64), (len(atomic.z),))
             for k in range(len(g)):
@@ -346,6 +357,10 @@ class IonisingMD:
 
     def set_pulse_table(self, dF, replica=-1):
         md_set_pulse_table(self.h, replica, dF)
+
+    def set_charge_table(self, frac, replica=-1):
+        """Charge-state fractions [rows][n_ts] for charge_mode="table"."""
+        md_set_charge_table(self.h, replica, frac)
 
     def set_plasma_table(self, ne, te_ev, replica=-1):
         md_set_plasma_table(self.h, replica, ne, te_ev)

@@ -55,6 +55,35 @@ def ts_offsets(z: np.ndarray = Z) -> np.ndarray:
     return np.concatenate([[0], np.cumsum(np.asarray(z) + 1)]).astype(np.int32)
 
 
+def charge_fraction_table(pulses, t_start_fs: float, dt_fs: float, n_rows: int, z=Z,
+                          mean_final: float = 2.0) -> np.ndarray:
+    """A synthetic stand-in for a CR code's time-resolved charge-state
+    fractions (the paper reads them from Cretin, which is not available):
+    per species a Poisson distribution truncated at Z, whose mean rises with
+    the pulses' cumulative fluence to ``mean_final`` * Z_s / 6 at the end.
+    Row n holds the fractions at t_n = t_start + n dt; columns follow the
+    type-state layout (species s, charge q) -> off[s] + q.  Input data only."""
+    from math import erf, exp, factorial, log, sqrt
+    z = np.asarray(z)
+    off = ts_offsets(z)
+    t = t_start_fs + dt_fs * np.arange(n_rows)
+    cum = np.zeros(n_rows)
+    tot = 0.0
+    for p in pulses:
+        sig = p.fwhm_fs / (2.0 * sqrt(2.0 * log(2.0)))
+        cum += p.fluence_ph_um2 * np.array([0.5 * (1.0 + erf((tt - p.t_center_fs) / (sig * sqrt(2.0)))) for tt in t])
+        tot += p.fluence_ph_um2
+    frac_t = cum / tot if tot > 0 else np.zeros(n_rows)
+    out = np.zeros((n_rows, int(off[-1])))
+    for s, zs in enumerate(z):
+        for n in range(n_rows):
+            lam = mean_final * zs / 6.0 * frac_t[n]
+            f = np.array([exp(-lam) * lam ** k / factorial(k) for k in range(zs + 1)])
+            f[-1] = max(0.0, 1.0 - f[:-1].sum())
+            out[n, off[s]:off[s + 1]] = f / f.sum()
+    return out
+
+
 # ----------------------------------------------------------------------------
 # Synthetic atomic data
 # ----------------------------------------------------------------------------
