@@ -24,6 +24,9 @@ What it computes, in the paper's order (arXiv 2401.03180):
   match on average" -- read as quantile coupling: each atom keeps one uniform
   quantile u (Philox stream 2, counter (atom, 0, 2, 0), res53) and takes the
   smallest charge whose cumulative fraction of its species exceeds u.
+* Sec. II.C, Eq. 18 (analysis): radial distribution functions g_ab(r) from
+  all-pairs distance histograms, and the partial structure factors
+  S_ab(q) = 1 + (4 pi rho0 / q) int r (g_ab(r) - 1) sin(q r) dr.
 * Sec. II.B, Eqs. 13-14 (optional, ``langevin_g``): electron-ion coupling as
   Langevin friction gamma = n_e g_s and a Gaussian force with
   <f f> = 2 m gamma k_B T_e, integrated as an exact Ornstein-Uhlenbeck
@@ -64,6 +67,10 @@ Parity pins (``tests/test_oracle_*.py``, all ``-m "not gpu"``):
   one-state table puts every atom in that state; monotone fractions give
   monotone charges (no atom recombines while the distribution ionises);
   charge conservation N_e = sum q.
+* ``rdf_counts`` / ``rdf`` / ``structure_factor``: histogram total = pairs
+  within r_max (KD-tree); g -> 1 for an ideal gas (one and two species);
+  S(q) of a step-function g(r) against its closed form
+  1 - 4 pi rho0 (sin q s - q s cos q s) / q^3; S(q) -> 1 for an ideal gas.
 * ``gaussians`` / ``langevin_update``: normal moments and a KS test; the
   friction-only decay c^n exactly; equipartition <m v^2> -> k_B T_e; the
   Ornstein-Uhlenbeck autocorrelation e^{-gamma t}; charges unaffected.
@@ -217,6 +224,55 @@ def pair_hybrid(r, qi, qj, c6, c12, kappa, ne, rc, lj_on=True, coulomb_f=COULOMB
     lib().orc_pair_hybrid(r, qi, qj, c6, c12, kappa, ne, coulomb_f, rc, int(bool(lj_on)),
                           ctypes.byref(fr), ctypes.byref(u))
     return fr.value, u.value
+
+
+def rdf_counts(x, species, n_species, box, rep_off, r_max, n_bins):
+    """Unordered atom pairs per species pair (a <= b, mirrored) and distance
+    bin k = floor(r / dr), dr = r_max / n_bins, for r < r_max (minimum image
+    in periodic boxes), summed over replicas; all pairs, FP64."""
+    x = np.asarray(x, np.float64)
+    species = np.asarray(species, np.int64)
+    box = np.asarray(box, np.float64).reshape(-1, 3)
+    dr = r_max / n_bins
+    out = np.zeros((n_species, n_species, n_bins), dtype=np.int64)
+    for r in range(len(rep_off) - 1):
+        a0, a1 = int(rep_off[r]), int(rep_off[r + 1])
+        L = box[r]
+        periodic = bool(np.all(L > 0))
+        for i in range(a0, a1 - 1):
+            d = x[i + 1:a1] - x[i]
+            if periodic:
+                d -= L * np.round(d / L)
+            rr = np.sqrt((d * d).sum(1))
+            sel = rr < r_max
+            k = np.minimum((rr[sel] / dr).astype(np.int64), n_bins - 1)
+            sa = species[i]
+            sb = species[i + 1:a1][sel]
+            lo, hi = np.minimum(sa, sb), np.maximum(sa, sb)
+            np.add.at(out, (lo, hi, k), 1)
+    for a in range(n_species):
+        for b in range(a):
+            out[a, b] = out[b, a]
+    return out
+
+
+def rdf(counts_ab, n_a, n_b, same, volume, r_max):
+    """g_ab at the bin centres from a pair histogram: counts over the pairs
+    an ideal gas of the same density puts in each spherical shell
+    (N_a N_b / V, or N_a (N_a - 1) / (2V) for a = b, times the shell volume)."""
+    n_bins = len(counts_ab)
+    edges = np.linspace(0.0, r_max, n_bins + 1)
+    shell = 4.0 * math.pi / 3.0 * (edges[1:] ** 3 - edges[:-1] ** 3)
+    pairs = n_a * (n_a - 1) / 2.0 if same else float(n_a) * n_b
+    return 0.5 * (edges[1:] + edges[:-1]), np.asarray(counts_ab, np.float64) / (pairs / volume * shell)
+
+
+def structure_factor(r, g, rho0, q, dr):
+    """S(q) = 1 + (4 pi rho0 / q) int_0^r_max r (g(r) - 1) sin(q r) dr (Eq. 18),
+    midpoint rule over the histogram bins."""
+    q = np.asarray(q, np.float64)
+    integ = (np.asarray(r)[None, :] * (np.asarray(g)[None, :] - 1.0) * np.sin(q[:, None] * np.asarray(r)[None, :])).sum(1) * dr
+    return 1.0 + 4.0 * math.pi * rho0 / q * integ
 
 
 def charge_quantiles(seed: int, ids) -> np.ndarray:
