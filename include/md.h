@@ -343,6 +343,29 @@ md_status md_set_state(md_handle* h, const md_state* in, unsigned fields);
  * each) and the number of in-cutoff pairs at the current state. */
 md_status md_get_energies(md_handle* h, double* e_kin, double* e_pot, int64_t* n_pairs);
 
+/* Radial distribution data for the partial structure factors of Sec. II.C
+ * (Eq. 18): the number of unordered atom pairs of each species pair (a, b)
+ * whose distance r (minimum image in periodic boxes) lies in bin
+ * k = floor(r / dr), dr = r_max / n_bins, for r < r_max, at the current
+ * positions, summed over replicas.  Each pair is counted once.  The distances
+ * are those of the force evaluation: FP32 coordinates relative to the cell
+ * centre on the mixed path, FP64 on the FP64 path.  A pair within rounding of
+ * a bin edge may fall on either side.  counts: host array
+ * [n_species][n_species][n_bins] (caller-owned), filled for a <= b and
+ * mirrored.  Errors: INVALID_ARG (r_max not in (0, r_cut], n_bins not in
+ * [1, 65536], null counts), BAD_STATE, CUDA. */
+md_status md_rdf(md_handle* h, double r_max, int n_bins, int64_t* counts);
+
+/* Partial structure factor of Sec. II.C, Eq. 18, from one species pair's
+ * histogram (md_rdf): g_ab at the bin centres r_k is counts_k over the pairs
+ * an ideal gas of the same density puts in the shell, n_a n_b / V (or
+ * n_a (n_a - 1) / (2V) when same != 0) times (4 pi / 3)(r_{k+1}^3 - r_k^3).
+ * Then S_ab(q) = 1 + (4 pi rho0 / q) sum_k dr r_k (g_ab(r_k) - 1) sin(q r_k),
+ * with rho0 the total number density.  Host-only; q[n_q] > 0 (nm^-1), out
+ * s[n_q].  Errors: INVALID_ARG (bad sizes, null pointers, q <= 0, V <= 0). */
+md_status md_structure_factor(const int64_t* counts, int n_bins, double r_max, double n_a, double n_b,
+                              int same, double volume, double rho0, const double* q, int n_q, double* s);
+
 md_status md_get_timing(md_handle* h, md_timing* out);
 md_status md_reset_timing(md_handle* h);
 

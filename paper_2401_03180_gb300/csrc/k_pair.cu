@@ -676,6 +676,145 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
     }
 }
 
+// Pair-distance histogram over the cluster-pair list (analysis for the
+// radial distribution functions of Sec. II.C, Eq. 18): every unordered pair
+// within r_max <= r_cut once, by species pair (a <= b) and bin
+// k = floor(r / dr).  The traversal is the force kernel's (chunks, staged
+// atoms, column queues), so the distances are the force evaluation's.  Counts
+// go to a block histogram in shared memory (when it fits, else straight to
+// global memory) and are added to the global one as 64-bit integers.
+template <bool FP64>
+struct RdfWarp {
+    typename Prec<FP64>::S4 ix[kFiRow];                  // x, y, z, species of the SC atoms (-1: none)
+    typename Prec<FP64>::S4 jx[kChunk * kClusterSize];   // the chunk's j-atoms, shifted
+};
+
+template <bool FP64>
+__global__ void __launch_bounds__(256) k_rdf(Params p, int n_bins, double r_max, int smem_hist,
+                                             unsigned long long* hist)
+{
+    using P = Prec<FP64>;
+    using T = typename P::T;
+    using T4 = typename P::T4;
+    using S4 = typename P::S4;
+    constexpr unsigned kFull = 0xffffffffu;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int nsp = p.n_species;
+    const int nh = nsp * nsp * n_bins;
+    unsigned* s_h = reinterpret_cast<unsigned*>(smem);
+    const size_t hb = smem_hist ? ((size_t)nh * sizeof(unsigned) + 15) / 16 * 16 : 0;
+    unsigned* s_kq = reinterpret_cast<unsigned*>(smem + hb);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    RdfWarp<FP64>& w = reinterpret_cast<RdfWarp<FP64>*>(smem + hb + 256 * sizeof(unsigned))[warp];
+    if (smem_hist)
+        for (int k = threadIdx.x; k < nh; k += blockDim.x) s_h[k] = 0u;
+    for (int c = threadIdx.x; c < 256; c += blockDim.x) {
+        unsigned q = 0x88888888u;
+        int n = 0;
+        for (int k = 0; k < 8; ++k)
+            if ((c >> k) & 1) {
+                q = (q & ~(0xfu << (4 * n))) | ((unsigned)k << (4 * n));
+                ++n;
+            }
+        s_kq[c] = q;
+    }
+    if (lane < kClusterSize) w.ix[kSCAtoms + lane] = P::mk(T(-1.0e6), T(-1.0e6), T(-1.0e6), T(-1));
+    __syncthreads();
+    const int tx = lane & 7, ty = lane >> 3;
+    const int n_chunks = min(p.counters[7], p.chunk_cap);
+    const T rmax2 = T(r_max * r_max), inv_dr = T((double)n_bins / r_max);
+    auto count = [&](const S4& a, const S4& b, bool ok) {
+        const T dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+        const T r2 = P::fma(dz, dz, P::fma(dy, dy, dx * dx));
+        if (ok && r2 < rmax2 && a.w >= T(0) && b.w >= T(0)) {
+            const int k = min((int)(sqrt(r2) * inv_dr), n_bins - 1);
+            const int sa = (int)a.w, sb = (int)b.w;
+            const int idx = (min(sa, sb) * nsp + max(sa, sb)) * n_bins + k;
+            if (smem_hist) atomicAdd(&s_h[idx], 1u);
+            else atomicAdd(&hist[idx], 1ull);
+        }
+    };
+    while (true) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(&p.counters[2], 1);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= n_chunks) break;
+        const int4 ch = p.pl_chunk[item];
+        const int sc = ch.x, n_ent = ch.z, rr = ch.w;
+        const PairEntry ent = lane < n_ent ? p.pl[ch.y + lane] : make_uint4(0u, 0u, 0u, 0u);
+        const int fc = p.sc_first[sc], ncl = p.sc_ncl[sc];
+        const Grid& g = p.grid_b[rr];
+        __syncwarp();
+        for (int a = lane; a < kSCAtoms; a += 32) {
+            if ((a >> 3) < ncl) {
+                const int slot = fc * kClusterSize + a;
+                const T4 v = P::pos(p, slot);
+                const int at = p.atom_of[slot];
+                w.ix[a] = P::mk(v.x, v.y, v.z, at >= 0 ? T(p.species[at]) : T(-1));
+            }
+        }
+        for (int a0 = 0; a0 < kChunk * kClusterSize; a0 += 32) {
+            const int a = a0 + lane, e = a >> 3;
+            const unsigned jc = __shfl_sync(kFull, ent.x, e);
+            const unsigned cd = __shfl_sync(kFull, ent.y, e);
+            if (e < n_ent) {
+                int dx, dy, dz;
+                half_shell((int)(cd & 0xffu), dx, dy, dz);
+                const int slot = (int)jc * kClusterSize + (a & 7);
+                const T4 v = P::pos(p, slot);
+                const int at = p.atom_of[slot];
+                const T sp = at >= 0 ? T(p.species[at]) : T(-1);
+                if (FP64) w.jx[a] = P::mk(v.x + T(dx * g.edge[0]), v.y + T(dy * g.edge[1]), v.z + T(dz * g.edge[2]), sp);
+                else w.jx[a] = P::mk(v.x + T((float)dx * g.edge_f[0]), v.y + T((float)dy * g.edge_f[1]),
+                                     v.z + T((float)dz * g.edge_f[2]), sp);
+            }
+        }
+        __syncwarp();
+        for (int v = 0; v < n_ent; ++v) {
+            const int jcl = (int)__shfl_sync(kFull, ent.x, v);
+            const unsigned code = __shfl_sync(kFull, ent.y, v);
+            const unsigned mlo = __shfl_sync(kFull, ent.z, v), mhi = __shfl_sync(kFull, ent.w, v);
+            if ((mlo | mhi) == 0u) continue;
+            const int kdiag = (code & 0xffu) == 0u ? jcl - fc : -1;
+            const S4 a0 = w.jx[v * kClusterSize + ty], a1 = w.jx[v * kClusterSize + ty + 4];
+            const unsigned col0 = ((tx < 4 ? mlo : mhi) >> ((tx & 3) * 8)) & 0xffu;
+            const int n_t = (int)__reduce_max_sync(kFull, (unsigned)__popc(col0));
+            unsigned kq = s_kq[col0];
+            for (int t = 0; t < n_t; ++t) {
+                const int k = (int)(kq & 0xfu);
+                kq >>= 4;
+                const S4 xi = w.ix[k * kClusterSize + tx];
+                const bool dg = k == kdiag;
+                count(xi, a0, !dg || tx < ty);
+                count(xi, a1, !dg || tx < ty + 4);
+            }
+        }
+    }
+    if (smem_hist) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < nh; k += blockDim.x)
+            if (s_h[k]) atomicAdd(&hist[k], (unsigned long long)s_h[k]);
+    }
+}
+
+void launch_rdf(const Params& p, cudaStream_t s, int blocks, int n_bins, double r_max, unsigned long long* hist)
+{
+    const size_t nh = (size_t)p.n_species * p.n_species * n_bins;
+    const bool fp64 = p.precision != 0;
+    const size_t warp_b = fp64 ? sizeof(RdfWarp<true>) : sizeof(RdfWarp<false>);
+    const size_t base = 256 * sizeof(unsigned) + 8 * warp_b;
+    const size_t hb = (nh * sizeof(unsigned) + 15) / 16 * 16;
+    const int smem_hist = base + hb <= 160 * 1024 ? 1 : 0;
+    const size_t smem = base + (smem_hist ? hb : 0);
+    if (fp64) {
+        cudaFuncSetAttribute(k_rdf<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        k_rdf<true><<<blocks, 256, smem, s>>>(p, n_bins, r_max, smem_hist, hist);
+    } else {
+        cudaFuncSetAttribute(k_rdf<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        k_rdf<false><<<blocks, 256, smem, s>>>(p, n_bins, r_max, smem_hist, hist);
+    }
+}
+
 template <bool FP64, bool HYB>
 static size_t pair_smem(int n_ts, int warps)
 {

@@ -1244,6 +1244,66 @@ md_status md_set_state(md_handle* h, const md_state* in, unsigned fields)
     return grown ? capture_graph(h) : MD_OK;
 }
 
+md_status md_rdf(md_handle* h, double r_max, int n_bins, int64_t* counts)
+{
+    if (!h) return fail(nullptr, MD_ERR_INVALID_ARG, "null handle");
+    if (!counts) return fail(h, MD_ERR_INVALID_ARG, "null counts");
+    if (!(r_max > 0.0) || r_max > h->cfg.r_cut) return fail(h, MD_ERR_INVALID_ARG, "r_max must be in (0, r_cut]");
+    if (n_bins < 1 || n_bins > 65536) return fail(h, MD_ERR_INVALID_ARG, "n_bins must be in [1, 65536]");
+    if (h->pending && !h->poisoned) {
+        md_status st_ = md_sync(h);
+        if (st_ != MD_OK) return st_;
+    }
+    if (h->poisoned) return fail(h, MD_ERR_BAD_STATE, "handle is in an error state: " + h->err);
+    const int ns = h->NS;
+    const size_t nh = (size_t)ns * ns * n_bins;
+    unsigned long long* d_hist = nullptr;
+    md_status st = dalloc(h, &d_hist, nh);
+    if (st != MD_OK) return st;
+    // the list of the last build covers every pair within r_cut at the current
+    // positions, and the packed records hold the current positions
+    CU(cudaMemsetAsync(d_hist, 0, nh * sizeof(unsigned long long), h->stream));
+    CU(cudaMemsetAsync(h->P.counters + 2, 0, sizeof(int), h->stream));
+    launch_rdf(h->P, h->stream, h->n_sm * 4, n_bins, r_max, d_hist);
+    CU(cudaMemsetAsync(h->P.counters + 2, 0, sizeof(int), h->stream));
+    CU(cudaGetLastError());
+    std::vector<unsigned long long> tmp(nh);
+    CU(cudaMemcpyAsync(tmp.data(), d_hist, nh * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    dfree(h, d_hist);
+    for (int a = 0; a < ns; ++a)
+        for (int b = 0; b < ns; ++b)
+            for (int k = 0; k < n_bins; ++k) {
+                const int lo = std::min(a, b), hi = std::max(a, b);
+                counts[((size_t)a * ns + b) * n_bins + k] = (int64_t)tmp[((size_t)lo * ns + hi) * n_bins + k];
+            }
+    return MD_OK;
+}
+
+md_status md_structure_factor(const int64_t* counts, int n_bins, double r_max, double n_a, double n_b, int same,
+                              double volume, double rho0, const double* q, int n_q, double* s)
+{
+    if (!counts || !q || !s || n_bins < 1 || n_q < 1 || !(r_max > 0.0) || !(volume > 0.0) || !(rho0 >= 0.0))
+        return fail(nullptr, MD_ERR_INVALID_ARG, "bad arguments to md_structure_factor");
+    const double dr = r_max / n_bins;
+    const double pairs = same ? 0.5 * n_a * (n_a - 1.0) : n_a * n_b;
+    if (!(pairs > 0.0)) return fail(nullptr, MD_ERR_INVALID_ARG, "no pairs for this species pair");
+    std::vector<double> rk(n_bins), gk(n_bins);
+    for (int k = 0; k < n_bins; ++k) {
+        const double r0 = k * dr, r1 = (k + 1) * dr;
+        const double shell = 4.0 * kPi / 3.0 * (r1 * r1 * r1 - r0 * r0 * r0);
+        rk[k] = 0.5 * (r0 + r1);
+        gk[k] = (double)counts[k] / (pairs / volume * shell);
+    }
+    for (int j = 0; j < n_q; ++j) {
+        if (!(q[j] > 0.0)) return fail(nullptr, MD_ERR_INVALID_ARG, "q must be > 0");
+        double acc = 0.0;
+        for (int k = 0; k < n_bins; ++k) acc += rk[k] * (gk[k] - 1.0) * std::sin(q[j] * rk[k]);
+        s[j] = 1.0 + 4.0 * kPi * rho0 / q[j] * acc * dr;
+    }
+    return MD_OK;
+}
+
 md_status md_get_energies(md_handle* h, double* e_kin, double* e_pot, int64_t* n_pairs)
 {
     if (!h) return fail(nullptr, MD_ERR_INVALID_ARG, "null handle");

@@ -284,6 +284,7 @@ void launch_philox(unsigned long long seed, const uint32_t* ctr, long long n, ui
                    cudaStream_t s);
 void launch_force_out(const Params& p, double* d_f_out, cudaStream_t s);
 void launch_refresh(const Params& p, cudaStream_t s);
+void launch_rdf(const Params& p, cudaStream_t s, int blocks, int n_bins, double r_max, unsigned long long* hist);
 int pair_max_blocks_per_sm(bool fp64, bool energy, bool hyb, int warps, int n_ts);
 // message returned by md_last_error(NULL) (host side)
 void set_global_error(const std::string& msg);

@@ -117,6 +117,9 @@ def lib():
             L.md_set_pulse_table_at.argtypes = [P, C.c_int, C.c_int, P, C.c_int]
             L.md_set_plasma_table.argtypes = [P, C.c_int, P, P, C.c_int]
             L.md_set_charge_table.argtypes = [P, C.c_int, P, C.c_int]
+            L.md_rdf.argtypes = [P, C.c_double, C.c_int, P]
+            L.md_structure_factor.argtypes = [P, C.c_int, C.c_double, C.c_double, C.c_double, C.c_int, C.c_double,
+                                              C.c_double, P, C.c_int, P]
             L.md_set_fluence_at.argtypes = [P, C.c_int, P]
             L.md_step.argtypes = [P, C.c_int]
             L.md_step_async.argtypes = [P, C.c_int]
@@ -190,6 +193,21 @@ def md_set_pulse_table_at(h, replica: int, first_step: int, dF):
 def md_set_fluence_at(h, step: int, dF):
     """dF[r]: fluence of `step` for each replica r (float64 array, pinned for overlap)."""
     _check(lib().md_set_fluence_at(h, int(step), _p(dF)), h)
+
+
+def md_rdf(h, n_species: int, r_max: float, n_bins: int):
+    out = np.zeros((n_species, n_species, n_bins), dtype=np.int64)
+    _check(lib().md_rdf(h, float(r_max), int(n_bins), _p(out)), h)
+    return out
+
+
+def md_structure_factor(counts_ab, r_max, n_a, n_b, same, volume, rho0, q):
+    c = np.ascontiguousarray(counts_ab, dtype=np.int64)
+    qq = np.ascontiguousarray(q, dtype=np.float64)
+    out = np.zeros(len(qq))
+    _check(lib().md_structure_factor(_p(c), len(c), float(r_max), float(n_a), float(n_b), int(bool(same)),
+                                     float(volume), float(rho0), _p(qq), len(qq), _p(out)), None)
+    return out
 
 
 def md_set_charge_table(h, replica: int, frac):
@@ -307,6 +325,7 @@ class IonisingMD:
         self.n = sample.n_atoms
         self.R = sample.n_replicas
         ns = len(atomic.z)
+        self.ns = ns
         cfg = MDConfig()
         cfg.dt_ps, cfg.r_cut = float(dt_ps), float(r_cut)
         cfg.precision = MD_PREC_FP64 if precision == "fp64" else MD_PREC_MIXED
@@ -357,6 +376,10 @@ class IonisingMD:
 
     def set_pulse_table(self, dF, replica=-1):
         md_set_pulse_table(self.h, replica, dF)
+
+    def rdf(self, r_max, n_bins):
+        """Pair counts [n_species][n_species][n_bins] by distance bin (md_rdf)."""
+        return md_rdf(self.h, self.ns, r_max, n_bins)
 
     def set_charge_table(self, frac, replica=-1):
         """Charge-state fractions [rows][n_ts] for charge_mode="table"."""
