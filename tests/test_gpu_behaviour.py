@@ -73,6 +73,46 @@ def test_batched_replicas_equal_solo_runs():
         assert sb["n_e"][k] == so["n_e"][0] and sb["e_gas_mev"][k] == so["e_gas_mev"][0]
 
 
+@pytest.mark.parametrize("mode", ["hybrid_langevin", "table"])
+def test_batched_replicas_equal_solo_runs_in_the_widened_modes(mode):
+    """The per-replica tables of the hybrid electrostatics, the Langevin
+    coupling and the charge-state fractions: each replica of a batch of six
+    equals its solo run, bit for bit."""
+    reps = [methane(n, seed=k + 11) for k, n in enumerate((40, 75, 23, 31, 52, 18))]
+    for k, r in enumerate(reps):
+        r.seed[:] = 900 + k
+    atom = W.atomic_data(8.0, pi_scale=1500.0, ci_scale=10.0)
+    pulses = [[W.Pulse(8.0, 10.0, f, 0.0)] for f in (1e12, 3e11, 2e12, 5e11, 1.5e12, 8e11)]
+    if mode == "table":
+        kw = dict(max_steps=80, t_start_fs=-5.0, charge_mode="table")
+        tabs = [W.charge_fraction_table(p, -5.0, 0.05, 81, mean_final=1.0 + 0.3 * k) for k, p in enumerate(pulses)]
+    else:
+        kw = dict(max_steps=80, t_start_fs=-5.0, screening="hybrid", langevin_g=np.full(len(atom.z), 0.5))
+    batch = W.concat(reps)
+    g = M.IonisingMD(batch, atom, **kw)
+    for k, p in enumerate(pulses):
+        g.set_pulse(p, replica=k)
+        if mode == "table":
+            g.set_charge_table(tabs[k], replica=k)
+    g.step(60)
+    sb = g.get_state(ALL)
+    g.close()
+    off = batch.replica_offset
+    for k, r in enumerate(reps):
+        h = M.IonisingMD(r, atom, **kw)
+        h.set_pulse(pulses[k])
+        if mode == "table":
+            h.set_charge_table(tabs[k])
+        h.step(60)
+        so = h.get_state(ALL)
+        h.close()
+        sl = slice(off[k], off[k + 1])
+        for key in ("x", "v", "f", "q", "h"):
+            assert np.array_equal(sb[key][sl], so[key]), (k, key)
+        assert sb["n_e"][k] == so["n_e"][0] and sb["kappa"][k] == so["kappa"][0]
+    assert sb["q"].any()
+
+
 def test_checkpoint_resume_bit_exact():
     s, rc = water(500)
     atom = W.atomic_data(6.0, pi_scale=800.0, ci_scale=20.0)
