@@ -24,6 +24,11 @@ What it computes, in the paper's order (arXiv 2401.03180):
   match on average" -- read as quantile coupling: each atom keeps one uniform
   quantile u (Philox stream 2, counter (atom, 0, 2, 0), res53) and takes the
   smallest charge whose cumulative fraction of its species exceeds u.
+* Sec. II.B, Eqs. 9-10 (optional, a sample with a ``topology``): Morse bonds
+  D_e (1 - e^{-beta (r - b_e)})^2 (reading of the garbled Eq. 10) and
+  harmonic angles (k/2)(theta - theta_0)^2 (Sec. III), each scaled by
+  c = 1 - zbar/N clamped to [0, 1], zbar the summed charge of its N atoms
+  (reading of Eq. 9).
 * Sec. II.C, Eq. 18 (analysis): radial distribution functions g_ab(r) from
   all-pairs distance histograms, and the partial structure factors
   S_ab(q) = 1 + (4 pi rho0 / q) int r (g_ab(r) - 1) sin(q r) dr.
@@ -71,6 +76,13 @@ Parity pins (``tests/test_oracle_*.py``, all ``-m "not gpu"``):
   within r_max (KD-tree); g -> 1 for an ideal gas (one and two species);
   S(q) of a step-function g(r) against its closed form
   1 - 4 pi rho0 (sin q s - q s cos q s) / q^3; S(q) -> 1 for an ideal gas.
+* ``morse`` / ``harmonic_angle`` / ``bond_scale`` / ``bonded_forces``: the
+  Morse zero at b_e, its dissociation limit D_e and curvature 2 D_e beta^2;
+  dV/dr and F = -grad U by finite differences on every coordinate; zero net
+  force and torque per molecule; the angle of the tetrahedral and right-angle
+  geometries; the scaling limits; minimum image across a periodic boundary;
+  the small-amplitude vibration period 2 pi / (beta sqrt(2 D_e / mu)) of a
+  diatomic integrated with velocity Verlet.
 * ``gaussians`` / ``langevin_update``: normal moments and a KS test; the
   friction-only decay c^n exactly; equipartition <m v^2> -> k_B T_e; the
   Ornstein-Uhlenbeck autocorrelation e^{-gamma t}; charges unaffected.
@@ -386,6 +398,80 @@ def plasma_scalars(n_e_count: int, e_gas_mev: int, volume: float, *, dt_ps: floa
 # ---------------------------------------------------------------------------
 # Whole-system oracle
 # ---------------------------------------------------------------------------
+def bond_scale(q_sum, n_atoms):
+    """Scaling of a bonded term by the charges of its atoms (Sec. II.B, Eq. 9,
+    reading): c = 1 - zbar/N with zbar the summed charge of the term's N atoms,
+    clamped to [0, 1] -- 1 for neutral atoms, 0 once their mean charge is 1."""
+    return np.clip(1.0 - np.asarray(q_sum, np.float64) / float(n_atoms), 0.0, 1.0)
+
+
+def morse(r, De, be, beta):
+    """Morse bond (Sec. II.B, Eq. 10, reading): V = D_e (1 - e^{-beta (r - b_e)})^2,
+    zero at the equilibrium distance b_e and D_e at dissociation.  Returns
+    (V, dV/dr)."""
+    e = np.exp(-beta * (r - be))
+    return De * (1.0 - e) ** 2, 2.0 * De * beta * e * (1.0 - e)
+
+
+def harmonic_angle(theta, k, theta0):
+    """Harmonic angle term (Sec. III: methane clusters): V = (k/2)(theta - theta0)^2.
+    Returns (V, dV/dtheta)."""
+    return 0.5 * k * (theta - theta0) ** 2, k * (theta - theta0)
+
+
+def _min_image(d, L):
+    """d minus the nearest multiple of the box L, per row (L = 0: vacuum)."""
+    per = L > 0
+    return np.where(per, d - L * np.round(d / np.where(per, L, 1.0)), d)
+
+
+def bonded_forces(x, q, box_of_atom, topology):
+    """Forces and per-atom energies of the bonded terms (Sec. II.B, Eqs. 9-10):
+    Morse bonds and harmonic angles, each scaled by its bond_scale at the
+    current charges (a constant factor of the term: charges are integers and
+    are not differentiated).  A term's energy is shared equally among its
+    atoms.  Distances take the minimum image of the replica's box."""
+    n = len(x)
+    F = np.zeros((n, 3))
+    U = np.zeros(n)
+    q = np.asarray(q, np.float64)
+    b = np.asarray(topology.bonds)
+    if len(b):
+        i, j, t = b[:, 0], b[:, 1], b[:, 2]
+        De, be, beta = np.asarray(topology.bond_params, np.float64)[t].T
+        d = _min_image(x[i] - x[j], box_of_atom[i])
+        r = np.sqrt((d * d).sum(1))
+        V, dV = morse(r, De, be, beta)
+        c = bond_scale(q[i] + q[j], 2)
+        fi = (-c * dV / r)[:, None] * d
+        np.add.at(F, i, fi)
+        np.add.at(F, j, -fi)
+        np.add.at(U, i, 0.5 * c * V)
+        np.add.at(U, j, 0.5 * c * V)
+    a = np.asarray(topology.angles)
+    if len(a):
+        i, j, k, t = a[:, 0], a[:, 1], a[:, 2], a[:, 3]
+        kt, th0 = np.asarray(topology.angle_params, np.float64)[t].T
+        u = _min_image(x[i] - x[j], box_of_atom[j])
+        w = _min_image(x[k] - x[j], box_of_atom[j])
+        ru = np.sqrt((u * u).sum(1))
+        rw = np.sqrt((w * w).sum(1))
+        cos = (u * w).sum(1) / (ru * rw)
+        theta = np.arccos(np.clip(cos, -1.0, 1.0))
+        V, dV = harmonic_angle(theta, kt, th0)
+        c = bond_scale(q[i] + q[j] + q[k], 3)
+        # -dV/dx_i = (dV/dtheta / sin theta) d(cos theta)/dx_i, likewise for k
+        g = c * dV / np.sin(theta)
+        fi = g[:, None] * (w / (ru * rw)[:, None] - (cos / (ru * ru))[:, None] * u)
+        fk = g[:, None] * (u / (ru * rw)[:, None] - (cos / (rw * rw))[:, None] * w)
+        np.add.at(F, i, fi)
+        np.add.at(F, k, fk)
+        np.add.at(F, j, -(fi + fk))
+        for m in (i, j, k):
+            np.add.at(U, m, c * V / 3.0)
+    return F, U
+
+
 def forces_of_atoms(sample, atomic, idx, *, r_cut, kappa, coulomb_f=COULOMB_F, sigma0=None, eps0=None,
                     ne=None):
     """Forces on the atoms `idx` of `sample` (at its positions and charges q0),
@@ -412,7 +498,10 @@ def forces_of_atoms(sample, atomic, idx, *, r_cut, kappa, coulomb_f=COULOMB_F, s
     kap = np.broadcast_to(np.asarray(kappa, np.float64), (md.R,))
     md.hybrid = ne is not None
     nev = None if ne is None else np.ascontiguousarray(np.broadcast_to(np.asarray(ne, np.float64), (md.R,)))
-    return md.forces_subset(np.asarray(idx), kappa=np.ascontiguousarray(kap), ne=nev)
+    out = md.forces_subset(np.asarray(idx), kappa=np.ascontiguousarray(kap), ne=nev)
+    if getattr(sample, "topology", None) is not None:
+        out += bonded_forces(md.x, md.q, md.box[md.rep_of], sample.topology)[0][np.asarray(idx)]
+    return out
 
 
 class OracleMD:
@@ -465,6 +554,7 @@ class OracleMD:
         self.rep_of = np.repeat(np.arange(self.R, dtype=np.int32), np.diff(self.rep_off))
         self.local = (np.arange(self.n) - self.rep_off[self.rep_of]).astype(np.int32)
         self.box = np.ascontiguousarray(sample.box, dtype=np.float64).reshape(self.R, 3)
+        self.topology = getattr(sample, "topology", None)
         self.vol = np.asarray(sample.volume, dtype=np.float64)
         self.seed = np.ascontiguousarray(sample.seed, dtype=np.uint64)
         self.step_index = 0
@@ -526,6 +616,10 @@ class OracleMD:
                          _ptr(self.rep_off), _ptr(self.box), _ptr(np.ascontiguousarray(kap)), nep,
                          self.rc, self.f, self.nts, _ptr(self.c6), _ptr(self.c12), _ptr(F),
                          _ptr(U), ctypes.byref(npairs))
+        if getattr(self, "topology", None) is not None:
+            Fb, Ub = bonded_forces(xf, q, self.box[self.rep_of], self.topology)
+            F += Fb
+            U += Ub
         return F, U, int(npairs.value)
 
     def forces_subset(self, sel, x=None, q=None, kappa=None, ne=None):
@@ -544,6 +638,8 @@ class OracleMD:
                                 None if ne is None else _ptr(np.ascontiguousarray(ne, dtype=np.float64)),
                                 self.rc, self.f, self.nts,
                                 _ptr(self.c6), _ptr(self.c12), len(sel), _ptr(sel), _ptr(out))
+        if getattr(self, "topology", None) is not None:
+            out += bonded_forces(np.ascontiguousarray(x, np.float64), q, self.box[self.rep_of], self.topology)[0][sel]
         return out
 
     def cr_step(self, step):

@@ -225,6 +225,7 @@ class Sample:
     volume: np.ndarray       # [R] electron-gas volume nm^3
     name: str = ""
     meta: dict = field(default_factory=dict)
+    topology: "Topology | None" = None   # bonded terms (None: no bonds)
 
     @property
     def n_atoms(self) -> int:
@@ -233,6 +234,69 @@ class Sample:
     @property
     def n_replicas(self) -> int:
         return int(self.replica_offset.shape[0] - 1)
+
+
+@dataclass
+class Topology:
+    """Bonded terms of the native structure (Sec. II.B): Morse bonds i-j and
+    angles i-j-k with vertex j, by type.  Atom indices are global (into the
+    concatenated sample).  Input data only: the potentials are evaluated by
+    the library and by the oracle."""
+    bonds: np.ndarray          # [n_bonds, 3] int32: i, j, type
+    bond_params: np.ndarray    # [n_bond_types, 3] float64: D_e (kJ/mol), b_e (nm), beta (1/nm)
+    angles: np.ndarray         # [n_angles, 4] int32: i, j (vertex), k, type
+    angle_params: np.ndarray   # [n_angle_types, 2] float64: k_theta (kJ/mol/rad^2), theta_0 (rad)
+
+
+# Synthetic bonded parameters: round numbers of the usual magnitude, not copied
+# from any force field.  The equilibrium geometry is that of the molecule
+# templates below (O-H 0.1 nm, H-O-H 104.5 deg; C-H 0.109 nm, tetrahedral).
+BOND_PARAMS = np.array([[450.0, 0.100, 22.0],     # 0: O-H
+                        [420.0, 0.109, 18.0]])    # 1: C-H
+ANGLE_PARAMS = np.array([[380.0, math.radians(104.5)],                  # 0: H-O-H
+                         [320.0, math.acos(-1.0 / 3.0)]])               # 1: H-C-H
+
+
+def molecular_topology(sample: "Sample") -> Topology:
+    """Bonds and angles of every water (O, H, H) and methane (C, H, H, H, H)
+    molecule of a sample, found as fragments of consecutive atoms with that
+    species sequence.  Other fragments (the protein's pseudo-residues) get no
+    bonded terms."""
+    frag = np.asarray(sample.fragment)
+    sp = np.asarray(sample.species)
+    n = len(frag)
+    if n == 0:
+        return Topology(np.zeros((0, 3), np.int32), BOND_PARAMS.copy(), np.zeros((0, 4), np.int32),
+                        ANGLE_PARAMS.copy())
+    start = np.flatnonzero(np.concatenate([[True], frag[1:] != frag[:-1]]))
+    length = np.diff(np.concatenate([start, [n]]))
+    bonds, angles = [], []
+
+    def match(ln, seq):
+        ok = length == ln
+        for k, s_k in enumerate(seq):
+            ok &= sp[np.minimum(start + k, n - 1)] == s_k
+        return start[ok]
+
+    w = match(3, (O, H, H))
+    if len(w):
+        bonds += [np.stack([w, w + 1, np.zeros_like(w)], 1), np.stack([w, w + 2, np.zeros_like(w)], 1)]
+        angles += [np.stack([w + 1, w, w + 2, np.zeros_like(w)], 1)]
+    m = match(5, (C, H, H, H, H))
+    if len(m):
+        one = np.ones_like(m)
+        bonds += [np.stack([m, m + k, one], 1) for k in range(1, 5)]
+        angles += [np.stack([m + a, m, m + b, one], 1) for a in range(1, 5) for b in range(a + 1, 5)]
+    b = np.concatenate(bonds).astype(np.int32) if bonds else np.zeros((0, 3), np.int32)
+    a = np.concatenate(angles).astype(np.int32) if angles else np.zeros((0, 4), np.int32)
+    return Topology(b[np.argsort(b[:, 0], kind="stable")], BOND_PARAMS.copy(),
+                    a[np.argsort(a[:, 1], kind="stable")], ANGLE_PARAMS.copy())
+
+
+def with_topology(sample: "Sample") -> "Sample":
+    """The sample with the bonded terms of its water and methane molecules."""
+    import dataclasses
+    return dataclasses.replace(sample, topology=molecular_topology(sample))
 
 
 def _rand_rotations(rng, n):
@@ -553,7 +617,25 @@ def concat(samples: list[Sample], name: str = "batch") -> Sample:
                   seed=np.concatenate([s.seed for s in samples]),
                   box=np.concatenate([s.box for s in samples]),
                   volume=np.concatenate([s.volume for s in samples]),
-                  name=name)
+                  name=name, topology=_concat_topology(samples, offs))
+
+
+def _concat_topology(samples, offs):
+    tops = [s.topology for s in samples]
+    if all(t is None for t in tops):
+        return None
+    ref = next(t for t in tops if t is not None)
+    bonds, angles = [], []
+    for t, o in zip(tops, offs[:-1]):
+        if t is None:
+            continue
+        if not (np.array_equal(t.bond_params, ref.bond_params) and np.array_equal(t.angle_params, ref.angle_params)):
+            raise ValueError("replicas with bonded terms must share the parameter tables")
+        b = t.bonds.copy(); b[:, :2] += o
+        a = t.angles.copy(); a[:, :3] += o
+        bonds.append(b); angles.append(a)
+    return Topology(np.concatenate(bonds).astype(np.int32), ref.bond_params.copy(),
+                    np.concatenate(angles).astype(np.int32), ref.angle_params.copy())
 
 
 # ----------------------------------------------------------------------------
