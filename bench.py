@@ -65,6 +65,8 @@ def parse():
                     help="electron-ion coupling g (nm^3/ps) of every species, Eqs. 13-14; 0: off")
     ap.add_argument("--charge-table", action="store_true",
                     help="charges from per-step CR charge-state fractions (a synthetic table) instead of the rates")
+    ap.add_argument("--bonded", action="store_true",
+                    help="add the Morse bonds and harmonic angles of the water/methane molecules (Eqs. 9-10)")
     ap.add_argument("--skin", type=float, default=SKIN_NM,
                     help="Verlet buffer of the cluster-pair list (nm); 0 rebuilds every step")
     return ap.parse_args()
@@ -205,6 +207,8 @@ def run_gpu(args, rank, world, local):
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     wl, atom = make_workload(args.workload, args.scale, rank)
+    if args.bonded:
+        wl.sample = W.with_topology(wl.sample)
     s = wl.sample
     n_atoms = s.n_atoms
     W_, K = args.warmup, args.steps
@@ -324,6 +328,8 @@ def run_gpu(args, rank, world, local):
                    "pair_tile": {"warps": tim.tile_warps, "blocks_per_sm": tim.tile_blocks_per_sm},
                    "list_skin_nm": args.skin, "screening": args.screening, "langevin_g": args.langevin,
                    "charges": "table" if args.charge_table else "rates",
+                   "bonded": ({"bonds": int(len(s.topology.bonds)), "angles": int(len(s.topology.angles))}
+                              if s.topology is not None else None),
                    "parallelism": f"replicas{world}"},
         "pair_interactions_per_s": world * pairs * K / (ms / 1e3),
         "pairs_per_step": pairs,
@@ -335,9 +341,9 @@ def run_gpu(args, rank, world, local):
                      "flops_per_pair": FLOPS_PER_PAIR, "pair_kernel_ms": pair_ms,
                      "pair_kernel_share": pair_ms / (ms / K)},
         "e2e": e2e,
-        # per step: step kernel + force kernel, and 5 more (4 cell kernels + list)
-        # in the steps whose list is rebuilt
-        "gpu_launches": 2 * K + 5 * int(tim.list_builds),
+        # per step: step kernel + force kernel (+ the bonded kernel), and 5 more
+        # (4 cell kernels + list) in the steps whose list is rebuilt
+        "gpu_launches": (3 if s.topology is not None else 2) * K + 5 * int(tim.list_builds),
         "pair_list": {"skin_nm": args.skin, "builds": int(tim.list_builds), "steps": K,
                       "entries_last_build": int(tim.list_entries), "capacity": int(tim.list_capacity)},
         "clocks": clk.summary(),
@@ -449,6 +455,9 @@ def run_reference(args, rank, world):
     if rank != 0:
         return None
     wl, atom = make_workload(args.workload, args.scale, 0)
+    if args.bonded:
+        from paper_2401_03180_gb300 import workloads as W
+        wl.sample = W.with_topology(wl.sample)
     s = wl.sample
     # each timed step is one oracle step; a bounded number keeps the arm within minutes
     k = min(args.steps, 10)
@@ -483,6 +492,9 @@ def run_profile_case(args):
     from paper_2401_03180_gb300 import md as M
     B.build()
     wl, atom = make_workload(args.workload, args.scale, 0)
+    if args.bonded:
+        from paper_2401_03180_gb300 import workloads as W
+        wl.sample = W.with_topology(wl.sample)
     s = wl.sample
     g = M.IonisingMD(s, atom, precision=args.precision, r_cut=1.2, max_steps=max(wl.n_steps, args.warmup + args.steps + 1),
                      t_start_fs=wl.t_start_fs, autotune=False, list_skin_nm=args.skin, screening=args.screening)

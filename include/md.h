@@ -203,6 +203,35 @@ typedef struct md_system {
     const uint64_t* seed;             /* [n_replicas] Philox key            */
     const double* box;                /* [3*n_replicas]                     */
     const double* volume;             /* [n_replicas] > 0                   */
+    /*
+     * Bonded terms of the native structure (Sec. II.B, Eqs. 9-10; Sec. III
+     * names the harmonic angle term).  All optional: n_bonds = n_angles = 0
+     * (a zero-filled tail of the struct) gives none.  Readings:
+     *  - a bond i-j is the Morse potential V = D_e (1 - e^{-beta (r - b_e)})^2,
+     *    zero at the equilibrium distance b_e and D_e at dissociation (the
+     *    printed Eq. 10 has lost the width beta and the square of the bracket);
+     *  - an angle i-j-k with vertex j is V = (k_theta / 2)(theta - theta_0)^2;
+     *  - each term is scaled by c = 1 - zbar/N clamped to [0, 1] (Eq. 9), zbar
+     *    the summed charge of its N atoms (2 or 3) at the current charges:
+     *    c = 1 for neutral atoms and 0 once their mean charge reaches 1.  c is
+     *    a constant of the force (charges are integers);
+     *  - a term's energy is shared equally among its atoms; distances take the
+     *    minimum image of the replica's box.
+     * The atoms of a term must be distinct and belong to one replica and one
+     * fragment: LJ is omitted between bonded atoms while the screened Coulomb
+     * stays (Sec. II.B), which the fragment rule gives.  Anything else is
+     * MD_ERR_INVALID_ARG.  The library copies the arrays.
+     */
+    int n_bonds;                      /* >= 0                               */
+    const int32_t* bonds;             /* [n_bonds][3]: i, j, bond type      */
+    int n_bond_types;                 /* >= 1 when n_bonds > 0              */
+    const double* bond_params;        /* [n_bond_types][3]: D_e >= 0 (kJ/mol),
+                                         b_e >= 0 (nm), beta > 0 (1/nm)     */
+    int n_angles;                     /* >= 0                               */
+    const int32_t* angles;            /* [n_angles][4]: i, j (vertex), k, angle type */
+    int n_angle_types;                /* >= 1 when n_angles > 0             */
+    const double* angle_params;       /* [n_angle_types][2]: k_theta >= 0
+                                         (kJ/mol/rad^2), theta_0 in [0, pi] (rad) */
 } md_system;
 
 /* One X-ray pulse (Sec. II.A: pulse energy, duration, photon energy). */

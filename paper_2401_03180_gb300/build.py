@@ -26,6 +26,7 @@ SOURCES = {
     "k_cells.cu": [],
     "k_pair.cu": [],
     "md_noalloc.cu": [],
+    "k_bonded.cu": ["-fmad=false"],
 }
 
 

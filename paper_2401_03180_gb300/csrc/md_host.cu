@@ -155,6 +155,7 @@ void enqueue_rebuild(md_handle* h, cudaStream_t s, bool energy)
     launch_pair_list(h->P, s, h->list_blocks);
     set_build_step(h, s, true);   // forces at the build positions: the list may be pruned
     launch_pair_forces(h->P, s, energy, h->pair_blocks, h->pair_warps);
+    launch_bonded(h->P, s, energy);
 }
 
 // Cell + list build at the positions held in xr/yr/zr (a checkpoint's list
@@ -182,6 +183,7 @@ void enqueue_rebuild_from_ref(md_handle* h, cudaStream_t s)
     launch_refresh(P, s);
     set_build_step(h, s, false);  // forces away from the build positions: no pruning
     launch_pair_forces(P, s, false, h->pair_blocks, h->pair_warps);
+    launch_bonded(P, s, false);
 }
 
 void enqueue_step(md_handle* h, cudaStream_t s)
@@ -194,6 +196,7 @@ void enqueue_step(md_handle* h, cudaStream_t s)
     if (h->cfg.profile) cudaEventRecordWithFlags(h->ev_pair0, s, cudaEventRecordExternal);
     launch_pair_forces(h->P, s, false, h->pair_blocks, h->pair_warps);
     if (h->cfg.profile) cudaEventRecordWithFlags(h->ev_pair1, s, cudaEventRecordExternal);
+    launch_bonded(h->P, s, false);
 }
 
 // Device error flags without acting on them.
@@ -290,6 +293,7 @@ md_status capture_buffered_step(md_handle* h)
     if (h->cfg.profile) cudaEventRecordWithFlags(h->ev_pair0, s, cudaEventRecordExternal);
     launch_pair_forces(h->P, s, false, h->pair_blocks, h->pair_warps);
     if (h->cfg.profile) cudaEventRecordWithFlags(h->ev_pair1, s, cudaEventRecordExternal);
+    launch_bonded(h->P, s, false);
     return MD_OK;
 }
 
@@ -395,9 +399,60 @@ md_status autotune(md_handle* h)
     return MD_OK;
 }
 
+// The bonded terms of md_system: counts, parameter tables, and atoms that are
+// distinct, in range, and in one replica and one fragment.
+md_status validate_bonded(const md_system* s)
+{
+    md_handle* h = nullptr;
+    if (s->n_bonds < 0 || s->n_angles < 0) return fail(h, MD_ERR_INVALID_ARG, "n_bonds and n_angles must be >= 0");
+    if ((long long)s->n_bonds + s->n_angles > (1LL << 30)) return fail(h, MD_ERR_INVALID_ARG, "too many bonded terms");
+    if (s->n_bonds > 0 && (!s->bonds || !s->bond_params || s->n_bond_types < 1))
+        return fail(h, MD_ERR_INVALID_ARG, "bonds need the bonds array and n_bond_types >= 1 parameter rows");
+    if (s->n_angles > 0 && (!s->angles || !s->angle_params || s->n_angle_types < 1))
+        return fail(h, MD_ERR_INVALID_ARG, "angles need the angles array and n_angle_types >= 1 parameter rows");
+    if (s->n_bonds == 0 && s->n_angles == 0) return MD_OK;
+    for (int t = 0; t < (s->n_bonds > 0 ? s->n_bond_types : 0); ++t) {
+        const double* b = s->bond_params + 3 * t;
+        if (!(b[0] >= 0 && b[0] < 1e9) || !(b[1] >= 0 && b[1] < 1e3) || !(b[2] > 0 && b[2] < 1e6))
+            return fail(h, MD_ERR_INVALID_ARG, "bond parameters must be finite with D_e >= 0, b_e >= 0, beta > 0");
+    }
+    for (int t = 0; t < (s->n_angles > 0 ? s->n_angle_types : 0); ++t) {
+        const double* a = s->angle_params + 2 * t;
+        if (!(a[0] >= 0 && a[0] < 1e9) || !(a[1] >= 0 && a[1] <= 3.141592653589793))
+            return fail(h, MD_ERR_INVALID_ARG, "angle parameters must have 0 <= k_theta < 1e9 and theta_0 in [0, pi]");
+    }
+    const int N = s->n_atoms;
+    std::vector<int> rep(N);
+    for (int r = 0; r < s->n_replicas; ++r)
+        for (int i = s->replica_offset[r]; i < s->replica_offset[r + 1]; ++i) rep[i] = r;
+    auto same = [&](int a, int b) { return rep[a] == rep[b] && s->fragment[a] == s->fragment[b]; };
+    for (int t = 0; t < s->n_bonds; ++t) {
+        const int* b = s->bonds + 3 * t;
+        if (b[0] < 0 || b[0] >= N || b[1] < 0 || b[1] >= N || b[0] == b[1])
+            return fail(h, MD_ERR_INVALID_ARG, "bond " + std::to_string(t) + ": atoms out of range or equal");
+        if (b[2] < 0 || b[2] >= s->n_bond_types)
+            return fail(h, MD_ERR_INVALID_ARG, "bond " + std::to_string(t) + ": type out of range");
+        if (!same(b[0], b[1]))
+            return fail(h, MD_ERR_INVALID_ARG, "bond " + std::to_string(t) + ": atoms in different replicas or fragments");
+    }
+    for (int t = 0; t < s->n_angles; ++t) {
+        const int* a = s->angles + 4 * t;
+        for (int k = 0; k < 3; ++k)
+            if (a[k] < 0 || a[k] >= N) return fail(h, MD_ERR_INVALID_ARG, "angle " + std::to_string(t) + ": atom out of range");
+        if (a[0] == a[1] || a[1] == a[2] || a[0] == a[2])
+            return fail(h, MD_ERR_INVALID_ARG, "angle " + std::to_string(t) + ": atoms must be distinct");
+        if (a[3] < 0 || a[3] >= s->n_angle_types)
+            return fail(h, MD_ERR_INVALID_ARG, "angle " + std::to_string(t) + ": type out of range");
+        if (!same(a[0], a[1]) || !same(a[1], a[2]))
+            return fail(h, MD_ERR_INVALID_ARG, "angle " + std::to_string(t) + ": atoms in different replicas or fragments");
+    }
+    return MD_OK;
+}
+
 md_status validate(const md_config* c, const md_system* s)
 {
     md_handle* h = nullptr;
+    md_status st_bonded = MD_OK;
     if (!c || !s) return fail(h, MD_ERR_INVALID_ARG, "null config or system");
     if (!(c->dt_ps > 0) || !(c->r_cut > 0) || !(c->r_cut < 1e3))
         return fail(h, MD_ERR_INVALID_ARG, "dt_ps and r_cut must be positive");
@@ -455,6 +510,8 @@ md_status validate(const md_config* c, const md_system* s)
                     return fail(h, MD_ERR_INVALID_ARG, "periodic box edges must all be >= 3 (r_cut + list_skin_nm)");
         }
     }
+    st_bonded = validate_bonded(s);
+    if (st_bonded != MD_OK) return st_bonded;
     for (int i = 0; i < s->n_atoms; ++i) {
         if (s->species[i] >= c->n_species) return fail(h, MD_ERR_INVALID_ARG, "species index out of range");
         if (s->q0 && s->q0[i] > c->z[s->species[i]]) return fail(h, MD_ERR_INVALID_ARG, "q0 above Z");
@@ -703,6 +760,33 @@ static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* 
         DALLOC(P.lgv, (size_t)R * kMaxSpecies);
         CU(cudaMemcpy(d_g, c.langevin_g, sizeof(double) * std::min(kMaxSpecies, MD_MAX_SPECIES), cudaMemcpyHostToDevice));
         P.lgv_g = d_g;
+    }
+    P.n_bonds = sys->n_bonds;
+    P.n_angles = sys->n_angles;
+    P.bonds = nullptr; P.angles = nullptr;
+    P.bond_pd = nullptr; P.angle_pd = nullptr; P.bond_pf = nullptr; P.angle_pf = nullptr;
+    if (sys->n_bonds > 0) {
+        std::vector<int4> b(sys->n_bonds);
+        for (int t = 0; t < sys->n_bonds; ++t)
+            b[t] = make_int4(sys->bonds[3 * t], sys->bonds[3 * t + 1], sys->bonds[3 * t + 2], 0);
+        const int nt = 3 * sys->n_bond_types;
+        std::vector<float> pf(sys->bond_params, sys->bond_params + nt);
+        int4* d_b; double* d_pd; float* d_pf;
+        DALLOC(d_b, b.size()); DALLOC(d_pd, nt); DALLOC(d_pf, nt);
+        CU(cudaMemcpy(d_b, b.data(), b.size() * sizeof(int4), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(d_pd, sys->bond_params, nt * sizeof(double), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(d_pf, pf.data(), nt * sizeof(float), cudaMemcpyHostToDevice));
+        P.bonds = d_b; P.bond_pd = d_pd; P.bond_pf = d_pf;
+    }
+    if (sys->n_angles > 0) {
+        const int nt = 2 * sys->n_angle_types;
+        std::vector<float> pf(sys->angle_params, sys->angle_params + nt);
+        int4* d_a; double* d_pd; float* d_pf;
+        DALLOC(d_a, (size_t)sys->n_angles); DALLOC(d_pd, nt); DALLOC(d_pf, nt);
+        CU(cudaMemcpy(d_a, sys->angles, (size_t)sys->n_angles * sizeof(int4), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(d_pd, sys->angle_params, nt * sizeof(double), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(d_pf, pf.data(), nt * sizeof(float), cudaMemcpyHostToDevice));
+        P.angles = d_a; P.angle_pd = d_pd; P.angle_pf = d_pf;
     }
     DALLOC(d_seed, R); DALLOC(d_dF, (size_t)R * c.max_steps);
     DALLOC(d_pne, (size_t)R * (c.max_steps + 1)); DALLOC(d_pte, (size_t)R * (c.max_steps + 1));
@@ -1319,6 +1403,7 @@ md_status md_get_energies(md_handle* h, double* e_kin, double* e_pot, int64_t* n
     launch_refresh(h->P, h->stream);
     set_build_step(h, h->stream, false);
     launch_pair_forces(h->P, h->stream, true, h->pair_blocks, h->pair_warps);
+    launch_bonded(h->P, h->stream, true);
     launch_energy(h->P, h->d_ekin, h->d_epot, h->stream);
     CU(cudaGetLastError());
     std::vector<double> ek(R);

@@ -182,6 +182,15 @@ struct Params {
     float4* bb_hi;
     int2* bb_frag;           // min/max fragment of the cluster
     long long *fx, *fy, *fz, *epot;   // fixed-point sums per slot
+
+    // bonded terms of the native structure (Sec. II.B, Eqs. 9-10); none when both counts are 0
+    int n_bonds, n_angles;
+    const int4* bonds;       // [n_bonds] (i, j, type, 0), atoms in original order
+    const int4* angles;      // [n_angles] (i, j = vertex, k, type)
+    const double* bond_pd;   // [bond types][3] D_e, b_e, beta
+    const double* angle_pd;  // [angle types][2] k_theta, theta_0
+    const float* bond_pf;    // FP32 copies of the two tables
+    const float* angle_pf;
     long long* pair_count;   // in-cutoff pairs (energy pass)
 
     // run state
@@ -285,6 +294,7 @@ void launch_philox(unsigned long long seed, const uint32_t* ctr, long long n, ui
 void launch_force_out(const Params& p, double* d_f_out, cudaStream_t s);
 void launch_refresh(const Params& p, cudaStream_t s);
 void launch_rdf(const Params& p, cudaStream_t s, int blocks, int n_bins, double r_max, unsigned long long* hist);
+void launch_bonded(const Params& p, cudaStream_t s, bool energy);
 int pair_max_blocks_per_sm(bool fp64, bool energy, bool hyb, int warps, int n_ts);
 // message returned by md_last_error(NULL) (host side)
 void set_global_error(const std::string& msg);

@@ -55,7 +55,9 @@ class MDSystem(C.Structure):
     _fields_ = [("n_atoms", C.c_int), ("x", C.c_void_p), ("v", C.c_void_p), ("species", C.c_void_p),
                 ("fragment", C.c_void_p), ("q0", C.c_void_p), ("n_replicas", C.c_int),
                 ("replica_offset", C.c_void_p), ("seed", C.c_void_p), ("box", C.c_void_p),
-                ("volume", C.c_void_p)]
+                ("volume", C.c_void_p), ("n_bonds", C.c_int), ("bonds", C.c_void_p), ("n_bond_types", C.c_int),
+                ("bond_params", C.c_void_p), ("n_angles", C.c_int), ("angles", C.c_void_p),
+                ("n_angle_types", C.c_int), ("angle_params", C.c_void_p)]
 
 
 class MDPulse(C.Structure):
@@ -307,6 +309,69 @@ class TorchAllocator:
         self._live.pop(ptr, None)
 
 
+def make_config(atomic, *, dt_ps=5e-5, r_cut=1.2, precision="mixed", cr_enabled=True,
+                plasma_mode=MD_PLASMA_BOOKKEEPING, max_steps=1000, kappa_fixed=-1.0, t_start_fs=0.0,
+                te_floor_ev=1.0, coulomb_f=COULOMB_F, autotune=False, profile=False, list_reserve=0,
+                list_skin_nm=0.0, screening="debye", langevin_g=None, charge_mode="rates",
+                sigma0=None, eps0=None, mass=None):
+    """An md_config for the atomic data and options (argument marshalling);
+    returns it with the arrays it points into, which must outlive md_init."""
+    from . import workloads as W
+    ns = len(atomic.z)
+    cfg = MDConfig()
+    cfg.dt_ps, cfg.r_cut = float(dt_ps), float(r_cut)
+    cfg.precision = MD_PREC_FP64 if precision == "fp64" else MD_PREC_MIXED
+    cfg.cr_enabled, cfg.plasma_mode, cfg.max_steps = int(bool(cr_enabled)), int(plasma_mode), int(max_steps)
+    cfg.kappa_fixed, cfg.t_start_fs, cfg.te_floor_ev = float(kappa_fixed), float(t_start_fs), float(te_floor_ev)
+    cfg.coulomb_f, cfg.photon_kev, cfg.n_species = float(coulomb_f), float(atomic.photon_kev), ns
+    mass = W.MASS if mass is None else mass
+    sigma0 = W.LJ_SIGMA0 if sigma0 is None else sigma0
+    eps0 = W.LJ_EPS0 if eps0 is None else eps0
+    for k in range(ns):
+        cfg.z[k] = int(atomic.z[k]); cfg.mass[k] = float(mass[k])
+        cfg.lj_sigma0[k] = float(sigma0[k]); cfg.lj_eps0[k] = float(eps0[k])
+        cfg.tau_auger_ps[k] = float(atomic.tau_auger_ps[k])
+    keep = [_c(atomic.sigma_pi, np.float64), _c(atomic.k_ci, np.float64), _c(atomic.k_rec, np.float64),
+            _c(atomic.ip_mev, np.int64), _c(atomic.e_pi_mev, np.int64), _c(atomic.e_auger_mev, np.int64)]
+    (cfg.sigma_pi, cfg.k_ci, cfg.k_rec, cfg.ip_mev, cfg.e_pi_mev,
+     cfg.e_auger_mev) = [a.ctypes.data for a in keep]
+    cfg.n_te, cfg.dte_ev = int(atomic.n_te), float(atomic.dte_ev)
+    cfg.autotune, cfg.profile = int(bool(autotune)), int(bool(profile))
+    cfg.list_reserve = int(list_reserve)
+    cfg.list_skin_nm = float(list_skin_nm)
+    if screening not in ("debye", "hybrid"):
+        raise ValueError("screening must be 'debye' or 'hybrid'")
+    cfg.screening = MD_SCREEN_HYBRID if screening == "hybrid" else MD_SCREEN_DEBYE
+    if charge_mode not in ("rates", "table"):
+        raise ValueError("charge_mode must be 'rates' or 'table'")
+    cfg.charge_mode = MD_CHARGE_TABLE if charge_mode == "table" else MD_CHARGE_RATES
+    if langevin_g is not None:
+        g = np.broadcast_to(np.asarray(langevin_g, np.float64), (ns,))
+        for k in range(len(g)):
+            cfg.langevin_g[k] = float(g[k])
+    return cfg, keep
+
+
+def make_system(sample):
+    """An md_system for a Sample, with its bonded terms when it has a
+    topology; returns it with the arrays it points into."""
+    s = sample
+    arrs = [_c(s.x, np.float64), _c(s.v, np.float64), _c(s.species, np.uint8), _c(s.fragment, np.int32),
+            _c(s.q0, np.uint8), _c(s.replica_offset, np.int32), _c(s.seed, np.uint64),
+            _c(s.box, np.float64), _c(s.volume, np.float64)]
+    sysd = MDSystem(s.n_atoms, *[a.ctypes.data for a in arrs[:5]], s.n_replicas, *[a.ctypes.data for a in arrs[5:]])
+    topo = getattr(s, "topology", None)
+    if topo is not None:
+        t = [_c(topo.bonds, np.int32), _c(topo.bond_params, np.float64), _c(topo.angles, np.int32),
+             _c(topo.angle_params, np.float64)]
+        arrs += t
+        sysd.n_bonds, sysd.bonds = len(t[0]), t[0].ctypes.data
+        sysd.n_bond_types, sysd.bond_params = len(t[1]), t[1].ctypes.data
+        sysd.n_angles, sysd.angles = len(t[2]), t[2].ctypes.data
+        sysd.n_angle_types, sysd.angle_params = len(t[3]), t[3].ctypes.data
+    return sysd, arrs
+
+
 # ---------------------------------------------------------------------------
 # Convenience wrapper
 # ---------------------------------------------------------------------------
@@ -319,52 +384,22 @@ class IonisingMD:
                  list_skin_nm=0.0, screening="debye", langevin_g=None, charge_mode="rates",
                  torch_allocator=True, sigma0=None, eps0=None, mass=None):
         import torch
-        from . import workloads as W
         if not torch.cuda.is_available():
             raise RuntimeError("IonisingMD needs a CUDA GPU (no CPU fallback)")
         self.n = sample.n_atoms
         self.R = sample.n_replicas
-        ns = len(atomic.z)
-        self.ns = ns
-        cfg = MDConfig()
-        cfg.dt_ps, cfg.r_cut = float(dt_ps), float(r_cut)
-        cfg.precision = MD_PREC_FP64 if precision == "fp64" else MD_PREC_MIXED
-        cfg.cr_enabled, cfg.plasma_mode, cfg.max_steps = int(bool(cr_enabled)), int(plasma_mode), int(max_steps)
-        cfg.kappa_fixed, cfg.t_start_fs, cfg.te_floor_ev = float(kappa_fixed), float(t_start_fs), float(te_floor_ev)
-        cfg.coulomb_f, cfg.photon_kev, cfg.n_species = float(coulomb_f), float(atomic.photon_kev), ns
-        mass = W.MASS if mass is None else mass
-        sigma0 = W.LJ_SIGMA0 if sigma0 is None else sigma0
-        eps0 = W.LJ_EPS0 if eps0 is None else eps0
-        for k in range(ns):
-            cfg.z[k] = int(atomic.z[k]); cfg.mass[k] = float(mass[k])
-            cfg.lj_sigma0[k] = float(sigma0[k]); cfg.lj_eps0[k] = float(eps0[k])
-            cfg.tau_auger_ps[k] = float(atomic.tau_auger_ps[k])
-        self._keep = [_c(atomic.sigma_pi, np.float64), _c(atomic.k_ci, np.float64), _c(atomic.k_rec, np.float64),
-                      _c(atomic.ip_mev, np.int64), _c(atomic.e_pi_mev, np.int64), _c(atomic.e_auger_mev, np.int64)]
-        (cfg.sigma_pi, cfg.k_ci, cfg.k_rec, cfg.ip_mev, cfg.e_pi_mev,
-         cfg.e_auger_mev) = [a.ctypes.data for a in self._keep]
-        cfg.n_te, cfg.dte_ev = int(atomic.n_te), float(atomic.dte_ev)
+        self.ns = len(atomic.z)
+        cfg, keep_c = make_config(atomic, dt_ps=dt_ps, r_cut=r_cut, precision=precision, cr_enabled=cr_enabled,
+                                  plasma_mode=plasma_mode, max_steps=max_steps, kappa_fixed=kappa_fixed,
+                                  t_start_fs=t_start_fs, te_floor_ev=te_floor_ev, coulomb_f=coulomb_f,
+                                  autotune=autotune, profile=profile, list_reserve=list_reserve,
+                                  list_skin_nm=list_skin_nm, screening=screening, langevin_g=langevin_g,
+                                  charge_mode=charge_mode, sigma0=sigma0, eps0=eps0, mass=mass)
+        self._keep = keep_c
         self._alloc = TorchAllocator() if torch_allocator else None
         if self._alloc is not None:
             cfg.dev_alloc, cfg.dev_free = self._alloc.alloc_fn, self._alloc.free_fn
-        cfg.autotune, cfg.profile = int(bool(autotune)), int(bool(profile))
-        cfg.list_reserve = int(list_reserve)
-        cfg.list_skin_nm = float(list_skin_nm)
-        if screening not in ("debye", "hybrid"):
-            raise ValueError("screening must be 'debye' or 'hybrid'")
-        cfg.screening = MD_SCREEN_HYBRID if screening == "hybrid" else MD_SCREEN_DEBYE
-        if charge_mode not in ("rates", "table"):
-            raise ValueError("charge_mode must be 'rates' or 'table'")
-        cfg.charge_mode = MD_CHARGE_TABLE if charge_mode == "table" else MD_CHARGE_RATES
-        if langevin_g is not None:
-            g = np.broadcast_to(np.asarray(langevin_g, np.float64), (len(atomic.z),))
-            for k in range(len(g)):
-                cfg.langevin_g[k] = float(g[k])
-        s = sample
-        arrs = [_c(s.x, np.float64), _c(s.v, np.float64), _c(s.species, np.uint8), _c(s.fragment, np.int32),
-                _c(s.q0, np.uint8), _c(s.replica_offset, np.int32), _c(s.seed, np.uint64),
-                _c(s.box, np.float64), _c(s.volume, np.float64)]
-        sysd = MDSystem(self.n, *[a.ctypes.data for a in arrs[:5]], self.R, *[a.ctypes.data for a in arrs[5:]])
+        sysd, arrs = make_system(sample)
         self.config = cfg
         self.stream = torch.cuda.current_stream().cuda_stream
         self.h = md_init(cfg, sysd)

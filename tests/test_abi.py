@@ -99,3 +99,39 @@ def test_binding_fails_loudly_without_gpu(libpath):
     wl = W.workload("c1_methane_1500", scale=0.02)
     with pytest.raises(RuntimeError):
         M.IonisingMD(wl.sample, W.atomic_data(8.0))
+
+
+def _init_status(sample):
+    """md_init's status and message for a system whose bonded terms are
+    invalid: the host-side checks run before any CUDA call."""
+    cfg, keep_c = M.make_config(W.atomic_data(8.0))
+    sysd, keep_s = M.make_system(sample)
+    h = ctypes.c_void_p()
+    st = M.lib().md_init(ctypes.byref(cfg), ctypes.byref(sysd), ctypes.byref(h))
+    return st, M.lib().md_last_error(None).decode()
+
+
+def test_bonded_topology_is_validated_on_the_host(libpath):
+    import dataclasses
+    base = W.with_topology(W.concat([W.methane_cluster(3, 1), W.methane_cluster(2, 2)]))
+    t = base.topology
+    cases = []
+    b = t.bonds.copy(); b[0, 1] = b[0, 0]
+    cases.append((dataclasses.replace(t, bonds=b), "atoms out of range or equal"))
+    b = t.bonds.copy(); b[1, 1] = base.n_atoms
+    cases.append((dataclasses.replace(t, bonds=b), "atoms out of range or equal"))
+    b = t.bonds.copy(); b[2, 2] = 2
+    cases.append((dataclasses.replace(t, bonds=b), "type out of range"))
+    b = t.bonds.copy(); b[3, 1] = 7                     # another methane: another fragment
+    cases.append((dataclasses.replace(t, bonds=b), "different replicas or fragments"))
+    a = t.angles.copy(); a[0, 2] = base.replica_offset[1] + 1   # an atom of the second replica
+    cases.append((dataclasses.replace(t, angles=a), "different replicas or fragments"))
+    a = t.angles.copy(); a[1, 2] = a[1, 0]
+    cases.append((dataclasses.replace(t, angles=a), "atoms must be distinct"))
+    bp = t.bond_params.copy(); bp[0, 2] = 0.0
+    cases.append((dataclasses.replace(t, bond_params=bp), "beta > 0"))
+    ap = t.angle_params.copy(); ap[1, 1] = 4.0
+    cases.append((dataclasses.replace(t, angle_params=ap), "theta_0 in [0, pi]"))
+    for topo, msg in cases:
+        st, err = _init_status(dataclasses.replace(base, topology=topo))
+        assert st == M.MD_ERR_INVALID_ARG and msg in err, (st, err)
