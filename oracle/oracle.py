@@ -29,6 +29,10 @@ What it computes, in the paper's order (arXiv 2401.03180):
   harmonic angles (k/2)(theta - theta_0)^2 (Sec. III), each scaled by
   c = 1 - zbar/N clamped to [0, 1], zbar the summed charge of its N atoms
   (reading of Eq. 9).
+* Sec. II.C, Eq. 17 (analysis): the probe-weighted displacement -- per
+  species, the RMS displacement from the initial positions at each step,
+  weighted by the probe profile times the fraction of bound electrons
+  f = 1 - zbar/Z (reading: zbar the species' mean charge at the step).
 * Sec. II.C, Eq. 18 (analysis): radial distribution functions g_ab(r) from
   all-pairs distance histograms, and the partial structure factors
   S_ab(q) = 1 + (4 pi rho0 / q) int r (g_ab(r) - 1) sin(q r) dr.
@@ -83,6 +87,12 @@ Parity pins (``tests/test_oracle_*.py``, all ``-m "not gpu"``):
   geometries; the scaling limits; minimum image across a periodic boundary;
   the small-amplitude vibration period 2 pi / (beta sqrt(2 D_e / mu)) of a
   diatomic integrated with velocity Verlet.
+* ``probe_weights`` / ``probe_sums`` / ``probe_weighted_displacement``:
+  weights sum to 1; constant f gives the pulse-table shape; f = 0 steps get
+  no weight; a symmetric window about the pulse centre gives a weighted mean
+  time equal to the centre; a falling f moves it earlier; a constant
+  displacement is returned unchanged; a rigid translation gives its length;
+  minimum image across a periodic face.
 * ``gaussians`` / ``langevin_update``: normal moments and a KS test; the
   friction-only decay c^n exactly; equipartition <m v^2> -> k_B T_e; the
   Ornstein-Uhlenbeck autocorrelation e^{-gamma t}; charges unaffected.
@@ -357,6 +367,49 @@ def pulse_table(pulses, t_start_fs: float, dt_fs: float, n_steps: int) -> np.nda
     return out
 
 
+def probe_sums(x, x0, q, species, box_of_atom, n_species):
+    """Per species: the summed charge (int64) and the summed squared
+    displacement |x - x0|^2 from the reference positions (nm^2, minimum image
+    of the replica's box) of the given atoms."""
+    d = _min_image(np.asarray(x, np.float64) - np.asarray(x0, np.float64), box_of_atom)
+    d2 = (d * d).sum(1)
+    sp = np.asarray(species).astype(np.int64)
+    qs = np.array([int(np.asarray(q, np.int64)[sp == k].sum()) for k in range(n_species)], dtype=np.int64)
+    ms = np.array([float(d2[sp == k].sum()) for k in range(n_species)])
+    return qs, ms
+
+
+def probe_weights(pulses, t_start_fs, dt_fs, f):
+    """Probe weights of Eq. 17 (Sec. II.C): w_k = int_{t_k}^{t_k + dt} g f dt /
+    int g f dt over the recorded window, t_k = t_start + k dt.  The charges,
+    hence f = 1 - zbar/Z, change only at step ends, so each step's integral is
+    f_k times the integral of the probe profile g over the step (the pulse
+    table); the pulse's fluence cancels in the ratio."""
+    f = np.asarray(f, np.float64)
+    gf = pulse_table(pulses, t_start_fs, dt_fs, len(f)) * f
+    tot = gf.sum()
+    return gf / tot if tot > 0 else np.zeros_like(gf)
+
+
+def probe_weighted_displacement(pulses, t_start_fs, dt_fs, q_sum, d2_sum, n_of_species, z):
+    """Probe-weighted displacement per species (Eq. 17 reading): records
+    k = 0..n-1 of the summed charge and squared displacement of each species
+    give f_k = 1 - (q_sum / N_s) / Z_s and the RMS displacement
+    d_k = sqrt(d2_sum / N_s); the result is sum_k w_k d_k with the weights of
+    probe_weights.  Species without atoms give 0."""
+    q_sum = np.asarray(q_sum, np.float64)
+    d2_sum = np.asarray(d2_sum, np.float64)
+    out = np.zeros(q_sum.shape[1])
+    for s in range(q_sum.shape[1]):
+        n = float(n_of_species[s])
+        if n <= 0:
+            continue
+        f = 1.0 - (q_sum[:, s] / n) / float(z[s])
+        w = probe_weights(pulses, t_start_fs, dt_fs, f)
+        out[s] = float((w * np.sqrt(d2_sum[:, s] / n)).sum())
+    return out
+
+
 def plasma_scalars(n_e_count: int, e_gas_mev: int, volume: float, *, dt_ps: float,
                    te_floor_ev: float, dte_ev: float, n_te: int,
                    coulomb_f: float = COULOMB_F, prescribed=None):
@@ -579,6 +632,11 @@ class OracleMD:
         self.counts = np.zeros((self.R, 4), dtype=np.int64)
         self.scal = [self._scalars(r, 0) for r in range(self.R)]
         self.F, self.U, self.n_pairs = self.forces()
+        # probe records (Eq. 17): per replica, the summed charge and squared
+        # displacement from the initial positions of each species, after each step
+        self.x0 = self.x.copy()
+        self.probe = [[] for _ in range(self.R)]
+        self.probe_record()
 
     # -- pieces ------------------------------------------------------------
     def _scalars(self, r, step):
@@ -671,6 +729,18 @@ class OracleMD:
                 sl = slice(self.rep_off[r], self.rep_off[r + 1])
                 self.x[sl] -= L * np.floor(self.x[sl] / L)
 
+    def probe_record(self):
+        ns = len(self.z)
+        for r in range(self.R):
+            sl = slice(self.rep_off[r], self.rep_off[r + 1])
+            self.probe[r].append(probe_sums(self.x[sl], self.x0[sl], self.q[sl], self.sp[sl],
+                                            np.repeat(self.box[r:r + 1], sl.stop - sl.start, 0), ns))
+
+    def probe_series(self, r):
+        """Records 0..step of replica r: (q_sum [n][S] int64, d2_sum [n][S] nm^2)."""
+        return (np.array([a for a, _ in self.probe[r]], dtype=np.int64),
+                np.array([b for _, b in self.probe[r]], dtype=np.float64))
+
     # -- the step ----------------------------------------------------------
     def langevin(self, n):
         """The O step of step n (reading of Eqs. 13-14): each replica's atoms
@@ -718,6 +788,7 @@ class OracleMD:
         self.F, self.U, self.n_pairs = self.forces()
         self.v += hd * self.F
         self.step_index = n + 1
+        self.probe_record()
 
     def run(self, n_steps, record=None):
         for _ in range(n_steps):
