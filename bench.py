@@ -67,6 +67,8 @@ def parse():
                     help="charges from per-step CR charge-state fractions (a synthetic table) instead of the rates")
     ap.add_argument("--bonded", action="store_true",
                     help="add the Morse bonds and harmonic angles of the water/methane molecules (Eqs. 9-10)")
+    ap.add_argument("--probe", action="store_true",
+                    help="record the per-species charge and displacement series of Eq. 17 every step")
     ap.add_argument("--skin", type=float, default=SKIN_NM,
                     help="Verlet buffer of the cluster-pair list (nm); 0 rebuilds every step")
     return ap.parse_args()
@@ -221,7 +223,7 @@ def run_gpu(args, rank, world, local):
                          t_start_fs=wl.t_start_fs, autotune=(prec == "mixed"), profile=profile,
                          list_skin_nm=args.skin, screening=args.screening,
                          langevin_g=args.langevin if args.langevin > 0 else None,
-                         charge_mode="table" if args.charge_table else "rates")
+                         charge_mode="table" if args.charge_table else "rates", probe_record=args.probe)
         for r in range(s.n_replicas):
             g.set_pulse(wl.pulses[r], replica=r)
             if args.charge_table:
@@ -330,6 +332,7 @@ def run_gpu(args, rank, world, local):
                    "charges": "table" if args.charge_table else "rates",
                    "bonded": ({"bonds": int(len(s.topology.bonds)), "angles": int(len(s.topology.angles))}
                               if s.topology is not None else None),
+                   "probe_record": bool(args.probe),
                    "parallelism": f"replicas{world}"},
         "pair_interactions_per_s": world * pairs * K / (ms / 1e3),
         "pairs_per_step": pairs,
@@ -343,7 +346,7 @@ def run_gpu(args, rank, world, local):
         "e2e": e2e,
         # per step: step kernel + force kernel (+ the bonded kernel), and 5 more
         # (4 cell kernels + list) in the steps whose list is rebuilt
-        "gpu_launches": (3 if s.topology is not None else 2) * K + 5 * int(tim.list_builds),
+        "gpu_launches": (2 + (s.topology is not None) + bool(args.probe)) * K + 5 * int(tim.list_builds),
         "pair_list": {"skin_nm": args.skin, "builds": int(tim.list_builds), "steps": K,
                       "entries_last_build": int(tim.list_entries), "capacity": int(tim.list_capacity)},
         "clocks": clk.summary(),

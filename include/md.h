@@ -177,6 +177,13 @@ typedef struct md_config {
                                 K holes stay 0; N_e follows sum q; the gas
                                 energy is not changed (use plasma_mode =
                                 MD_PLASMA_PRESCRIBED for T_e).                 */
+    int probe_record;        /* 1: keep, after every step k (record 0: the
+                                initial state), per replica and species, the
+                                summed charge and the summed squared
+                                displacement from the initial positions, for
+                                the probe-weighted displacement of Eq. 17
+                                (md_get_probe_series, md_probe_displacement).
+                                Costs one kernel per step. 0 (default): off.  */
 } md_config;
 
 /*
@@ -394,6 +401,30 @@ md_status md_rdf(md_handle* h, double r_max, int n_bins, int64_t* counts);
  * s[n_q].  Errors: INVALID_ARG (bad sizes, null pointers, q <= 0, V <= 0). */
 md_status md_structure_factor(const int64_t* counts, int n_bins, double r_max, double n_a, double n_b,
                               int same, double volume, double rho0, const double* q, int n_q, double* s);
+
+/* Probe records (md_config.probe_record = 1; Sec. II.C, Eq. 17): records
+ * first .. first + n - 1 of one replica, record k being the state after k
+ * steps (record 0: the initial state; a restored checkpoint or a grown list
+ * rewrites the record of its step).  Per record and species (row-major
+ * [n][n_species], caller-owned, either may be NULL): q_sum = the summed
+ * charge of the replica's atoms of that species, exact; d2_sum = their summed
+ * squared displacement |x - x0|^2 (nm^2) from the positions md_init was
+ * given, minimum image of the replica's box, summed exactly in 2^-40 nm^2
+ * fixed point (each atom's value capped at 2^23 nm^2).  Errors: BAD_STATE (records off, handle poisoned),
+ * INVALID_ARG (replica, or records beyond the current step), CUDA. */
+md_status md_get_probe_series(md_handle* h, int replica, int first, int n, int64_t* q_sum, double* d2_sum);
+
+/* Probe-weighted displacement per species (Sec. II.C, Eq. 17), out[n_species]:
+ * sum_k w_k d_k over records first .. first + n - 1, with d_k =
+ * sqrt(d2_sum / N_s) the RMS displacement of the species, and
+ * w_k = int_{t_k}^{t_k + dt} g f dt / sum over the records, t_k = t_start +
+ * k dt, g the probe pulse profile (the pulses' per-step fluence; their
+ * fluence cancels), f = 1 - zbar_s / Z_s the fraction of bound electrons,
+ * zbar_s = q_sum / N_s constant over a step (charges change at step ends).
+ * A species without atoms, or with no weight left (f = 0 throughout), gives
+ * 0.  Errors: those of md_get_probe_series, and INVALID_ARG for bad pulses. */
+md_status md_probe_displacement(md_handle* h, int replica, int first, int n, const md_pulse* probe, int n_pulses,
+                                double* out);
 
 md_status md_get_timing(md_handle* h, md_timing* out);
 md_status md_reset_timing(md_handle* h);

@@ -27,6 +27,7 @@ SOURCES = {
     "k_pair.cu": [],
     "md_noalloc.cu": [],
     "k_bonded.cu": ["-fmad=false"],
+    "k_probe.cu": ["-fmad=false"],
 }
 
 

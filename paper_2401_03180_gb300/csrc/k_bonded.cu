@@ -143,6 +143,8 @@ __device__ void angle_term(const Params& p, const T* par, int t)
 template <typename T, bool ENERGY>
 __global__ void __launch_bounds__(256) k_bonded(Params p)
 {
+    // a failed cell build leaves slot_of undefined; a full list stops the step
+    if (*p.err & (ERR_CELL | ERR_LIST)) return;
     const T* bp = nullptr;
     const T* ap = nullptr;
     if constexpr (sizeof(T) == 8) { bp = p.bond_pd; ap = p.angle_pd; }

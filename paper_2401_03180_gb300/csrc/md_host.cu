@@ -45,6 +45,7 @@ struct md_handle {
     double* d_scratch = nullptr;         // [3N] doubles for state exchange
     double* d_ekin = nullptr;
     long long* d_epot = nullptr;
+    std::vector<long long> n_of_species;   // [R][NS] atoms per replica and species
 };
 
 namespace {
@@ -156,6 +157,7 @@ void enqueue_rebuild(md_handle* h, cudaStream_t s, bool energy)
     set_build_step(h, s, true);   // forces at the build positions: the list may be pruned
     launch_pair_forces(h->P, s, energy, h->pair_blocks, h->pair_warps);
     launch_bonded(h->P, s, energy);
+    launch_probe(h->P, s, true);
 }
 
 // Cell + list build at the positions held in xr/yr/zr (a checkpoint's list
@@ -184,6 +186,7 @@ void enqueue_rebuild_from_ref(md_handle* h, cudaStream_t s)
     set_build_step(h, s, false);  // forces away from the build positions: no pruning
     launch_pair_forces(P, s, false, h->pair_blocks, h->pair_warps);
     launch_bonded(P, s, false);
+    launch_probe(P, s, true);
 }
 
 void enqueue_step(md_handle* h, cudaStream_t s)
@@ -197,6 +200,7 @@ void enqueue_step(md_handle* h, cudaStream_t s)
     launch_pair_forces(h->P, s, false, h->pair_blocks, h->pair_warps);
     if (h->cfg.profile) cudaEventRecordWithFlags(h->ev_pair1, s, cudaEventRecordExternal);
     launch_bonded(h->P, s, false);
+    launch_probe(h->P, s, false);
 }
 
 // Device error flags without acting on them.
@@ -294,6 +298,7 @@ md_status capture_buffered_step(md_handle* h)
     launch_pair_forces(h->P, s, false, h->pair_blocks, h->pair_warps);
     if (h->cfg.profile) cudaEventRecordWithFlags(h->ev_pair1, s, cudaEventRecordExternal);
     launch_bonded(h->P, s, false);
+    launch_probe(h->P, s, false);
     return MD_OK;
 }
 
@@ -834,6 +839,22 @@ static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* 
             CU(cudaMemcpy(dst[k], tmp.data(), N * sizeof(double), cudaMemcpyHostToDevice));
         }
         CU(cudaMemcpy(P.species, sys->species, N, cudaMemcpyHostToDevice));
+        h->n_of_species.assign((size_t)R * NS, 0);
+        for (int r = 0; r < R; ++r)
+            for (int i = h->rep_off[r]; i < h->rep_off[r + 1]; ++i) h->n_of_species[(size_t)r * NS + sys->species[i]] += 1;
+        P.x0 = P.y0 = P.z0 = nullptr;
+        P.probe = nullptr;
+        if (c.probe_record) {
+            double *d_x0, *d_y0, *d_z0;
+            DALLOC(d_x0, N); DALLOC(d_y0, N); DALLOC(d_z0, N);
+            CU(cudaMemcpy(d_x0, P.x, N * sizeof(double), cudaMemcpyDeviceToDevice));
+            CU(cudaMemcpy(d_y0, P.y, N * sizeof(double), cudaMemcpyDeviceToDevice));
+            CU(cudaMemcpy(d_z0, P.z, N * sizeof(double), cudaMemcpyDeviceToDevice));
+            P.x0 = d_x0; P.y0 = d_y0; P.z0 = d_z0;
+            const size_t nrec = (size_t)R * (c.max_steps + 1) * NS * 3;
+            DALLOC(P.probe, nrec);
+            CU(cudaMemset(P.probe, 0, nrec * sizeof(long long)));
+        }
         std::vector<uint8_t> q0(N, 0);
         if (sys->q0) std::copy(sys->q0, sys->q0 + N, q0.begin());
         CU(cudaMemcpy(P.q, q0.data(), N, cudaMemcpyHostToDevice));
@@ -1361,6 +1382,66 @@ md_status md_rdf(md_handle* h, double r_max, int n_bins, int64_t* counts)
                 const int lo = std::min(a, b), hi = std::max(a, b);
                 counts[((size_t)a * ns + b) * n_bins + k] = (int64_t)tmp[((size_t)lo * ns + hi) * n_bins + k];
             }
+    return MD_OK;
+}
+
+md_status md_get_probe_series(md_handle* h, int replica, int first, int n, int64_t* q_sum, double* d2_sum)
+{
+    if (!h) return fail(nullptr, MD_ERR_INVALID_ARG, "null handle");
+    if (!h->P.probe) return fail(h, MD_ERR_BAD_STATE, "probe records are off (md_config.probe_record = 0)");
+    if (h->pending && !h->poisoned) {
+        md_status st_ = md_sync(h);
+        if (st_ != MD_OK) return st_;
+    }
+    if (h->poisoned) return fail(h, MD_ERR_BAD_STATE, "handle is in an error state: " + h->err);
+    if (replica < 0 || replica >= h->R) return fail(h, MD_ERR_INVALID_ARG, "replica out of range");
+    if (first < 0 || n < 1 || (long long)first + n - 1 > h->host_step || (!q_sum && !d2_sum))
+        return fail(h, MD_ERR_INVALID_ARG, "records first .. first + n - 1 must lie in 0 .. the current step");
+    const int ns = h->NS;
+    std::vector<long long> tmp((size_t)n * ns * 3);
+    const size_t off = 3 * (((size_t)replica * (h->cfg.max_steps + 1) + (size_t)first) * ns);
+    CU(cudaMemcpyAsync(tmp.data(), h->P.probe + off, tmp.size() * sizeof(long long), cudaMemcpyDeviceToHost,
+                       h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    for (size_t k = 0; k < (size_t)n * ns; ++k) {
+        if (q_sum) q_sum[k] = tmp[3 * k];
+        // high and low 32-bit parts of the 2^-40 nm^2 fixed-point sum
+        if (d2_sum) d2_sum[k] = (double)tmp[3 * k + 1] * 0.00390625 + (double)tmp[3 * k + 2] * 9.094947017729282e-13;
+    }
+    return MD_OK;
+}
+
+md_status md_probe_displacement(md_handle* h, int replica, int first, int n, const md_pulse* probe, int n_pulses,
+                                double* out)
+{
+    if (!h) return fail(nullptr, MD_ERR_INVALID_ARG, "null handle");
+    if (!out || !probe || n_pulses < 1) return fail(h, MD_ERR_INVALID_ARG, "probe pulses and out are required");
+    for (int k = 0; k < n_pulses; ++k)
+        if (!(probe[k].fwhm_fs > 0) || !(probe[k].fluence_ph_um2 >= 0) ||
+            (probe[k].shape != MD_PULSE_GAUSSIAN && probe[k].shape != MD_PULSE_FLAT_TOP))
+            return fail(h, MD_ERR_INVALID_ARG, "bad probe pulse");
+    const int ns = h->NS;
+    std::vector<int64_t> qs((size_t)n > 0 ? (size_t)n * ns : 1);
+    std::vector<double> d2((size_t)n > 0 ? (size_t)n * ns : 1);
+    md_status st = md_get_probe_series(h, replica, first, n, qs.data(), d2.data());
+    if (st != MD_OK) return st;
+    // Eq. 17: w_k = int_{t_k}^{t_k + dt} g f / int g f, f constant over a step
+    std::vector<double> G(n);
+    const double dt_fs = h->cfg.dt_ps * 1000.0;
+    pulse_table_host(probe, n_pulses, h->cfg.t_start_fs + first * dt_fs, dt_fs, n, G.data());
+    for (int s = 0; s < ns; ++s) {
+        const double na = (double)h->n_of_species[(size_t)replica * ns + s];
+        out[s] = 0.0;
+        if (!(na > 0)) continue;
+        double tot = 0.0, acc = 0.0;
+        for (int k = 0; k < n; ++k) {
+            const double f = 1.0 - ((double)qs[(size_t)k * ns + s] / na) / (double)h->z[s];
+            const double gf = G[k] * f;
+            tot += gf;
+            acc += gf * std::sqrt(d2[(size_t)k * ns + s] / na);
+        }
+        out[s] = tot > 0 ? acc / tot : 0.0;
+    }
     return MD_OK;
 }
 

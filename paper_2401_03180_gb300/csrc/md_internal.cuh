@@ -191,6 +191,10 @@ struct Params {
     const double* angle_pd;  // [angle types][2] k_theta, theta_0
     const float* bond_pf;    // FP32 copies of the two tables
     const float* angle_pf;
+
+    // probe records (Sec. II.C, Eq. 17); null when off
+    const double *x0, *y0, *z0;   // initial positions, original order
+    long long* probe;        // [n_rep][max_steps + 1][n_species][3]: sum q; sum |x - x0|^2 in 2^-40 nm^2, high and low 32 bits
     long long* pair_count;   // in-cutoff pairs (energy pass)
 
     // run state
@@ -295,6 +299,7 @@ void launch_force_out(const Params& p, double* d_f_out, cudaStream_t s);
 void launch_refresh(const Params& p, cudaStream_t s);
 void launch_rdf(const Params& p, cudaStream_t s, int blocks, int n_bins, double r_max, unsigned long long* hist);
 void launch_bonded(const Params& p, cudaStream_t s, bool energy);
+void launch_probe(const Params& p, cudaStream_t s, bool rewrite);
 int pair_max_blocks_per_sm(bool fp64, bool energy, bool hyb, int warps, int n_ts);
 // message returned by md_last_error(NULL) (host side)
 void set_global_error(const std::string& msg);

@@ -48,7 +48,7 @@ class MDConfig(C.Structure):
                 ("dev_free", FREE_FN), ("alloc_ctx", C.c_void_p), ("autotune", C.c_int),
                 ("profile", C.c_int), ("list_reserve", C.c_int), ("list_skin_nm", C.c_double),
                 ("screening", C.c_int), ("langevin_g", C.c_double * MD_MAX_SPECIES),
-                ("charge_mode", C.c_int)]
+                ("charge_mode", C.c_int), ("probe_record", C.c_int)]
 
 
 class MDSystem(C.Structure):
@@ -120,6 +120,8 @@ def lib():
             L.md_set_plasma_table.argtypes = [P, C.c_int, P, P, C.c_int]
             L.md_set_charge_table.argtypes = [P, C.c_int, P, C.c_int]
             L.md_rdf.argtypes = [P, C.c_double, C.c_int, P]
+            L.md_get_probe_series.argtypes = [P, C.c_int, C.c_int, C.c_int, P, P]
+            L.md_probe_displacement.argtypes = [P, C.c_int, C.c_int, C.c_int, C.POINTER(MDPulse), C.c_int, P]
             L.md_structure_factor.argtypes = [P, C.c_int, C.c_double, C.c_double, C.c_double, C.c_int, C.c_double,
                                               C.c_double, P, C.c_int, P]
             L.md_set_fluence_at.argtypes = [P, C.c_int, P]
@@ -200,6 +202,20 @@ def md_set_fluence_at(h, step: int, dF):
 def md_rdf(h, n_species: int, r_max: float, n_bins: int):
     out = np.zeros((n_species, n_species, n_bins), dtype=np.int64)
     _check(lib().md_rdf(h, float(r_max), int(n_bins), _p(out)), h)
+    return out
+
+
+def md_get_probe_series(h, n_species: int, replica: int, first: int, n: int):
+    q = np.zeros((n, n_species), dtype=np.int64)
+    d2 = np.zeros((n, n_species), dtype=np.float64)
+    _check(lib().md_get_probe_series(h, int(replica), int(first), int(n), _p(q), _p(d2)), h)
+    return q, d2
+
+
+def md_probe_displacement(h, n_species: int, replica: int, first: int, n: int, probe):
+    out = np.zeros(n_species)
+    arr = _pulses(probe)
+    _check(lib().md_probe_displacement(h, int(replica), int(first), int(n), arr, len(probe), _p(out)), h)
     return out
 
 
@@ -382,7 +398,7 @@ class IonisingMD:
                  plasma_mode=MD_PLASMA_BOOKKEEPING, max_steps=1000, kappa_fixed=-1.0, t_start_fs=0.0,
                  te_floor_ev=1.0, coulomb_f=COULOMB_F, autotune=False, profile=False, list_reserve=0,
                  list_skin_nm=0.0, screening="debye", langevin_g=None, charge_mode="rates",
-                 torch_allocator=True, sigma0=None, eps0=None, mass=None):
+                 probe_record=False, torch_allocator=True, sigma0=None, eps0=None, mass=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("IonisingMD needs a CUDA GPU (no CPU fallback)")
@@ -395,6 +411,7 @@ class IonisingMD:
                                   autotune=autotune, profile=profile, list_reserve=list_reserve,
                                   list_skin_nm=list_skin_nm, screening=screening, langevin_g=langevin_g,
                                   charge_mode=charge_mode, sigma0=sigma0, eps0=eps0, mass=mass)
+        cfg.probe_record = int(bool(probe_record))
         self._keep = keep_c
         self._alloc = TorchAllocator() if torch_allocator else None
         if self._alloc is not None:
@@ -415,6 +432,17 @@ class IonisingMD:
     def rdf(self, r_max, n_bins):
         """Pair counts [n_species][n_species][n_bins] by distance bin (md_rdf)."""
         return md_rdf(self.h, self.ns, r_max, n_bins)
+
+    def probe_series(self, replica=0, first=0, n=None):
+        """Probe records (q_sum, d2_sum), [n][n_species], of the states after
+        steps first .. first + n - 1 (md_get_probe_series)."""
+        if n is None:
+            n = self.get_state(MD_FIELD_STEP)["step"] + 1 - first
+        return md_get_probe_series(self.h, self.ns, replica, first, n)
+
+    def probe_displacement(self, probe, replica=0, first=0, n=1):
+        """Probe-weighted RMS displacement per species (Eq. 17, md_probe_displacement)."""
+        return md_probe_displacement(self.h, self.ns, replica, first, n, probe)
 
     def set_charge_table(self, frac, replica=-1):
         """Charge-state fractions [rows][n_ts] for charge_mode="table"."""
