@@ -33,6 +33,9 @@ What it computes, in the paper's order (arXiv 2401.03180):
   species, the RMS displacement from the initial positions at each step,
   weighted by the probe profile times the fraction of bound electrons
   f = 1 - zbar/Z (reading: zbar the species' mean charge at the step).
+* Sec. III (analysis): fractional ion yields -- fragments are the connected
+  components of atoms closer than r_frag (reading), counted by mass number
+  and net charge.
 * Sec. II.C, Eq. 18 (analysis): radial distribution functions g_ab(r) from
   all-pairs distance histograms, and the partial structure factors
   S_ab(q) = 1 + (4 pi rho0 / q) int r (g_ab(r) - 1) sin(q r) dr.
@@ -93,6 +96,11 @@ Parity pins (``tests/test_oracle_*.py``, all ``-m "not gpu"``):
   time equal to the centre; a falling f moves it earlier; a constant
   displacement is returned unchanged; a rigid translation gives its length;
   minimum image across a periodic face.
+* ``fragments`` / ``ion_yield_counts``: intact molecules are one fragment
+  each (CH4: 16, H2O: 18); an atom pulled beyond r_frag splits off (CH3 +
+  H); a molecule across a periodic face stays whole; labels equal those of a
+  brute-force all-pairs union-find on small random gases; mass and charge
+  are conserved over the fragments.
 * ``gaussians`` / ``langevin_update``: normal moments and a KS test; the
   friction-only decay c^n exactly; equipartition <m v^2> -> k_B T_e; the
   Ornstein-Uhlenbeck autocorrelation e^{-gamma t}; charges unaffected.
@@ -364,6 +372,58 @@ def pulse_table(pulses, t_start_fs: float, dt_fs: float, n_steps: int) -> np.nda
                               for p in pulses], dtype=np.float64).reshape(-1, 5)
     out = np.empty(n_steps)
     lib().orc_pulse_table(len(P), _ptr(P), float(t_start_fs), float(dt_fs), int(n_steps), _ptr(out))
+    return out
+
+
+def fragments(x, box, rep_off, r_frag):
+    """Fragments of a state (the ion yields of Sec. III, reading): the
+    connected components of the graph joining atoms of one replica closer
+    than r_frag (minimum image), found by breadth-first search over the
+    KD-tree's pair set.  Returns each atom's label, the smallest atom index
+    of its fragment."""
+    from scipy.spatial import cKDTree
+    n = len(x)
+    label = np.full(n, -1, dtype=np.int64)
+    for r in range(len(rep_off) - 1):
+        a0, a1 = int(rep_off[r]), int(rep_off[r + 1])
+        L = np.asarray(box[r], np.float64)
+        per = bool((L > 0).all())
+        xr = np.mod(x[a0:a1], L) if per else x[a0:a1]
+        tree = cKDTree(xr, boxsize=L if per else None)
+        pairs = tree.query_pairs(r_frag, output_type="ndarray")
+        adj = [[] for _ in range(a1 - a0)]
+        for i, j in pairs:
+            adj[i].append(j)
+            adj[j].append(i)
+        for s in range(a1 - a0):                    # ascending: s is its fragment's smallest index
+            if label[a0 + s] >= 0:
+                continue
+            label[a0 + s] = a0 + s
+            todo = [s]
+            while todo:
+                u = todo.pop()
+                for v in adj[u]:
+                    if label[a0 + v] < 0:
+                        label[a0 + v] = a0 + s
+                        todo.append(v)
+    return label
+
+
+def ion_yield_counts(label, q, mass_number, rep_off, mass_max, charge_max):
+    """Fragments per replica by mass number (the sum of the atoms' mass
+    numbers) and net charge (the sum of their charges), [R][mass_max + 1]
+    [charge_max + 1]; larger values go to the last bin."""
+    label = np.asarray(label)
+    R = len(rep_off) - 1
+    out = np.zeros((R, mass_max + 1, charge_max + 1), dtype=np.int64)
+    m = np.zeros(len(label), dtype=np.int64)
+    z = np.zeros(len(label), dtype=np.int64)
+    np.add.at(m, label, np.asarray(mass_number, np.int64))
+    np.add.at(z, label, np.asarray(q, np.int64))
+    for r in range(R):
+        for i in range(int(rep_off[r]), int(rep_off[r + 1])):
+            if label[i] == i:
+                out[r, min(m[i], mass_max), min(z[i], charge_max)] += 1
     return out
 
 
