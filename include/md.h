@@ -402,6 +402,21 @@ md_status md_rdf(md_handle* h, double r_max, int n_bins, int64_t* counts);
 md_status md_structure_factor(const int64_t* counts, int n_bins, double r_max, double n_a, double n_b,
                               int same, double volume, double rho0, const double* q, int n_q, double* s);
 
+/* Fragments of the current state and their ion yields (Sec. III: the
+ * fractional ion yields by mass and charge).  Reading: a fragment is a
+ * connected component of the graph that joins atoms of one replica closer
+ * than r_frag (0 < r_frag <= r_cut; distances as in the force evaluation,
+ * FP32 on the mixed path, so a pair within rounding of r_frag may go either
+ * way).  label[n_atoms] (original order, caller-owned, may be NULL): the
+ * smallest atom index of the atom's fragment.  counts[n_replicas]
+ * [mass_max + 1][charge_max + 1] (may be NULL): fragments per replica by mass
+ * number (the sum of the atoms' mass numbers, round(md_config.mass)) and net
+ * charge (the sum of their charges); larger values go to the last bin.  The
+ * fractional yield of a (mass, charge) is its count over the fragments
+ * counted.  Errors: INVALID_ARG (r_frag, bin counts, both outputs NULL),
+ * BAD_STATE, OOM, CUDA. */
+md_status md_fragments(md_handle* h, double r_frag, int mass_max, int charge_max, int32_t* label, int64_t* counts);
+
 /* Probe records (md_config.probe_record = 1; Sec. II.C, Eq. 17): records
  * first .. first + n - 1 of one replica, record k being the state after k
  * steps (record 0: the initial state; a restored checkpoint or a grown list

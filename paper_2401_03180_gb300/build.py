@@ -28,6 +28,7 @@ SOURCES = {
     "md_noalloc.cu": [],
     "k_bonded.cu": ["-fmad=false"],
     "k_probe.cu": ["-fmad=false"],
+    "k_frag.cu": [],
 }
 
 

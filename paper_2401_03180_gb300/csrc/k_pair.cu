@@ -676,22 +676,118 @@ __global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
     }
 }
 
-// Pair-distance histogram over the cluster-pair list (analysis for the
-// radial distribution functions of Sec. II.C, Eq. 18): every unordered pair
-// within r_max <= r_cut once, by species pair (a <= b) and bin
-// k = floor(r / dr).  The traversal is the force kernel's (chunks, staged
-// atoms, column queues), so the distances are the force evaluation's.  Counts
-// go to a block histogram in shared memory (when it fits, else straight to
-// global memory) and are added to the global one as 64-bit integers.
+// Walks of the cluster-pair list for the analyses: every unordered pair of
+// atoms within r_cut once, with the force kernel's traversal (chunks, staged
+// atoms, column queues), so the distances are the force evaluation's.  The
+// per-pair work is an operation type:
+//   RdfOp   pair-distance histogram for the radial distribution functions of
+//           Sec. II.C, Eq. 18: every pair within r_max <= r_cut by species
+//           pair (a <= b) and bin k = floor(r / dr), counted in a block
+//           histogram in shared memory (when it fits, else straight to global
+//           memory) and added to the global one as 64-bit integers;
+//   FragOp  fragments for the ion yields of Sec. III: every pair closer than
+//           r_frag <= r_cut joins the atoms' sets in a lock-free union-find
+//           whose parent indices only decrease, so each root is its set's
+//           smallest atom index.
 template <bool FP64>
-struct RdfWarp {
+struct WalkWarp {
     typename Prec<FP64>::S4 ix[kFiRow];                  // x, y, z, species of the SC atoms (-1: none)
     typename Prec<FP64>::S4 jx[kChunk * kClusterSize];   // the chunk's j-atoms, shifted
+    int ia[kFiRow];                                      // their atom indices (-1: none)
+    int ja[kChunk * kClusterSize];
 };
 
 template <bool FP64>
-__global__ void __launch_bounds__(256) k_rdf(Params p, int n_bins, double r_max, int smem_hist,
-                                             unsigned long long* hist)
+struct RdfOp {
+    using T = typename Prec<FP64>::T;
+    using S4 = typename Prec<FP64>::S4;
+    int n_bins, nsp, smem_hist;
+    T rmax2, inv_dr;
+    unsigned long long* hist;
+    unsigned* s_h;
+    __device__ size_t smem_bytes() const
+    {
+        return smem_hist ? ((size_t)nsp * nsp * n_bins * sizeof(unsigned) + 15) / 16 * 16 : 0;
+    }
+    __device__ void init(unsigned char* smem)
+    {
+        s_h = reinterpret_cast<unsigned*>(smem);
+        if (smem_hist)
+            for (int k = threadIdx.x; k < nsp * nsp * n_bins; k += blockDim.x) s_h[k] = 0u;
+    }
+    __device__ void pair(const S4& a, int, const S4& b, int, bool ok)
+    {
+        const T dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+        const T r2 = Prec<FP64>::fma(dz, dz, Prec<FP64>::fma(dy, dy, dx * dx));
+        if (ok && r2 < rmax2 && a.w >= T(0) && b.w >= T(0)) {
+            const int k = min((int)(sqrt(r2) * inv_dr), n_bins - 1);
+            const int sa = (int)a.w, sb = (int)b.w;
+            const int idx = (min(sa, sb) * nsp + max(sa, sb)) * n_bins + k;
+            if (smem_hist) atomicAdd(&s_h[idx], 1u);
+            else atomicAdd(&hist[idx], 1ull);
+        }
+    }
+    __device__ void finish()
+    {
+        if (smem_hist) {
+            __syncthreads();
+            for (int k = threadIdx.x; k < nsp * nsp * n_bins; k += blockDim.x)
+                if (s_h[k]) atomicAdd(&hist[k], (unsigned long long)s_h[k]);
+        }
+    }
+};
+
+// Root of x's set.  Parents only ever point to smaller indices, so the walk
+// ends within x steps; each step halves the path (the grandparent written is
+// an ancestor whichever thread wrote last).
+__device__ __forceinline__ int uf_find(int* parent, int x)
+{
+    while (true) {
+        const int px = __ldcg(parent + x);
+        if (px == x) return x;
+        const int gp = __ldcg(parent + px);
+        if (gp != px) parent[x] = gp;
+        x = px;
+    }
+}
+
+// Joins the sets of a and b: the larger root is hooked under the smaller one
+// by a compare-and-swap that succeeds only on a root.  A failed swap means
+// another thread hooked that root meanwhile; each retry follows a merge, so
+// there are fewer retries than atoms (bounded anyway, with an error flag).
+__device__ __forceinline__ void uf_unite(int* parent, int a, int b, int n, unsigned* err)
+{
+    for (int it = 0; it <= n; ++it) {
+        a = uf_find(parent, a);
+        b = uf_find(parent, b);
+        if (a == b) return;
+        if (a > b) { const int t = a; a = b; b = t; }
+        if (atomicCAS(parent + b, b, a) == b) return;
+    }
+    atomicOr(err, ERR_OVERFLOW);
+}
+
+template <bool FP64>
+struct FragOp {
+    using T = typename Prec<FP64>::T;
+    using S4 = typename Prec<FP64>::S4;
+    T rf2;
+    int* parent;
+    int n;
+    unsigned* err;
+    __device__ size_t smem_bytes() const { return 0; }
+    __device__ void init(unsigned char*) {}
+    __device__ void pair(const S4& a, int ia, const S4& b, int ib, bool ok)
+    {
+        const T dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+        const T r2 = Prec<FP64>::fma(dz, dz, Prec<FP64>::fma(dy, dy, dx * dx));
+        if (ok && r2 < rf2 && ia >= 0 && ib >= 0) uf_unite(parent, ia, ib, n, err);
+    }
+    __device__ void finish() {}
+};
+
+template <bool FP64, class Op>
+__global__ void __launch_bounds__(256) k_walk(Params p, Op op)
 {
     using P = Prec<FP64>;
     using T = typename P::T;
@@ -699,15 +795,11 @@ __global__ void __launch_bounds__(256) k_rdf(Params p, int n_bins, double r_max,
     using S4 = typename P::S4;
     constexpr unsigned kFull = 0xffffffffu;
     extern __shared__ __align__(16) unsigned char smem[];
-    const int nsp = p.n_species;
-    const int nh = nsp * nsp * n_bins;
-    unsigned* s_h = reinterpret_cast<unsigned*>(smem);
-    const size_t hb = smem_hist ? ((size_t)nh * sizeof(unsigned) + 15) / 16 * 16 : 0;
+    const size_t hb = op.smem_bytes();
+    op.init(smem);
     unsigned* s_kq = reinterpret_cast<unsigned*>(smem + hb);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    RdfWarp<FP64>& w = reinterpret_cast<RdfWarp<FP64>*>(smem + hb + 256 * sizeof(unsigned))[warp];
-    if (smem_hist)
-        for (int k = threadIdx.x; k < nh; k += blockDim.x) s_h[k] = 0u;
+    WalkWarp<FP64>& w = reinterpret_cast<WalkWarp<FP64>*>(smem + hb + 256 * sizeof(unsigned))[warp];
     for (int c = threadIdx.x; c < 256; c += blockDim.x) {
         unsigned q = 0x88888888u;
         int n = 0;
@@ -718,22 +810,13 @@ __global__ void __launch_bounds__(256) k_rdf(Params p, int n_bins, double r_max,
             }
         s_kq[c] = q;
     }
-    if (lane < kClusterSize) w.ix[kSCAtoms + lane] = P::mk(T(-1.0e6), T(-1.0e6), T(-1.0e6), T(-1));
+    if (lane < kClusterSize) {
+        w.ix[kSCAtoms + lane] = P::mk(T(-1.0e6), T(-1.0e6), T(-1.0e6), T(-1));
+        w.ia[kSCAtoms + lane] = -1;
+    }
     __syncthreads();
     const int tx = lane & 7, ty = lane >> 3;
     const int n_chunks = min(p.counters[7], p.chunk_cap);
-    const T rmax2 = T(r_max * r_max), inv_dr = T((double)n_bins / r_max);
-    auto count = [&](const S4& a, const S4& b, bool ok) {
-        const T dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
-        const T r2 = P::fma(dz, dz, P::fma(dy, dy, dx * dx));
-        if (ok && r2 < rmax2 && a.w >= T(0) && b.w >= T(0)) {
-            const int k = min((int)(sqrt(r2) * inv_dr), n_bins - 1);
-            const int sa = (int)a.w, sb = (int)b.w;
-            const int idx = (min(sa, sb) * nsp + max(sa, sb)) * n_bins + k;
-            if (smem_hist) atomicAdd(&s_h[idx], 1u);
-            else atomicAdd(&hist[idx], 1ull);
-        }
-    };
     while (true) {
         int item = 0;
         if (lane == 0) item = atomicAdd(&p.counters[2], 1);
@@ -751,6 +834,7 @@ __global__ void __launch_bounds__(256) k_rdf(Params p, int n_bins, double r_max,
                 const T4 v = P::pos(p, slot);
                 const int at = p.atom_of[slot];
                 w.ix[a] = P::mk(v.x, v.y, v.z, at >= 0 ? T(p.species[at]) : T(-1));
+                w.ia[a] = at;
             }
         }
         for (int a0 = 0; a0 < kChunk * kClusterSize; a0 += 32) {
@@ -767,6 +851,7 @@ __global__ void __launch_bounds__(256) k_rdf(Params p, int n_bins, double r_max,
                 if (FP64) w.jx[a] = P::mk(v.x + T(dx * g.edge[0]), v.y + T(dy * g.edge[1]), v.z + T(dz * g.edge[2]), sp);
                 else w.jx[a] = P::mk(v.x + T((float)dx * g.edge_f[0]), v.y + T((float)dy * g.edge_f[1]),
                                      v.z + T((float)dz * g.edge_f[2]), sp);
+                w.ja[a] = at;
             }
         }
         __syncwarp();
@@ -776,42 +861,65 @@ __global__ void __launch_bounds__(256) k_rdf(Params p, int n_bins, double r_max,
             const unsigned mlo = __shfl_sync(kFull, ent.z, v), mhi = __shfl_sync(kFull, ent.w, v);
             if ((mlo | mhi) == 0u) continue;
             const int kdiag = (code & 0xffu) == 0u ? jcl - fc : -1;
-            const S4 a0 = w.jx[v * kClusterSize + ty], a1 = w.jx[v * kClusterSize + ty + 4];
+            const int j0 = v * kClusterSize + ty;
+            const S4 a0 = w.jx[j0], a1 = w.jx[j0 + 4];
+            const int b0 = w.ja[j0], b1 = w.ja[j0 + 4];
             const unsigned col0 = ((tx < 4 ? mlo : mhi) >> ((tx & 3) * 8)) & 0xffu;
             const int n_t = (int)__reduce_max_sync(kFull, (unsigned)__popc(col0));
             unsigned kq = s_kq[col0];
             for (int t = 0; t < n_t; ++t) {
                 const int k = (int)(kq & 0xfu);
                 kq >>= 4;
-                const S4 xi = w.ix[k * kClusterSize + tx];
+                const int si = k * kClusterSize + tx;
+                const S4 xi = w.ix[si];
+                const int ii = w.ia[si];
                 const bool dg = k == kdiag;
-                count(xi, a0, !dg || tx < ty);
-                count(xi, a1, !dg || tx < ty + 4);
+                op.pair(xi, ii, a0, b0, !dg || tx < ty);
+                op.pair(xi, ii, a1, b1, !dg || tx < ty + 4);
             }
         }
     }
-    if (smem_hist) {
-        __syncthreads();
-        for (int k = threadIdx.x; k < nh; k += blockDim.x)
-            if (s_h[k]) atomicAdd(&hist[k], (unsigned long long)s_h[k]);
-    }
+    op.finish();
+}
+
+template <bool FP64, class Op>
+static void launch_walk(const Params& p, cudaStream_t s, int blocks, Op op, size_t op_smem)
+{
+    const size_t smem = op_smem + 256 * sizeof(unsigned) + 8 * sizeof(WalkWarp<FP64>);
+    cudaFuncSetAttribute(k_walk<FP64, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    k_walk<FP64, Op><<<blocks, 256, smem, s>>>(p, op);
+}
+
+template <bool FP64>
+static void rdf_typed(const Params& p, cudaStream_t s, int blocks, int n_bins, double r_max, unsigned long long* hist)
+{
+    RdfOp<FP64> op{};
+    op.n_bins = n_bins;
+    op.nsp = p.n_species;
+    op.rmax2 = (typename Prec<FP64>::T)(r_max * r_max);
+    op.inv_dr = (typename Prec<FP64>::T)((double)n_bins / r_max);
+    op.hist = hist;
+    const size_t nh = (size_t)p.n_species * p.n_species * n_bins;
+    const size_t base = 256 * sizeof(unsigned) + 8 * sizeof(WalkWarp<FP64>);
+    const size_t hb = (nh * sizeof(unsigned) + 15) / 16 * 16;
+    op.smem_hist = base + hb <= 160 * 1024 ? 1 : 0;
+    launch_walk<FP64>(p, s, blocks, op, op.smem_hist ? hb : 0);
 }
 
 void launch_rdf(const Params& p, cudaStream_t s, int blocks, int n_bins, double r_max, unsigned long long* hist)
 {
-    const size_t nh = (size_t)p.n_species * p.n_species * n_bins;
-    const bool fp64 = p.precision != 0;
-    const size_t warp_b = fp64 ? sizeof(RdfWarp<true>) : sizeof(RdfWarp<false>);
-    const size_t base = 256 * sizeof(unsigned) + 8 * warp_b;
-    const size_t hb = (nh * sizeof(unsigned) + 15) / 16 * 16;
-    const int smem_hist = base + hb <= 160 * 1024 ? 1 : 0;
-    const size_t smem = base + (smem_hist ? hb : 0);
-    if (fp64) {
-        cudaFuncSetAttribute(k_rdf<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        k_rdf<true><<<blocks, 256, smem, s>>>(p, n_bins, r_max, smem_hist, hist);
+    if (p.precision != 0) rdf_typed<true>(p, s, blocks, n_bins, r_max, hist);
+    else rdf_typed<false>(p, s, blocks, n_bins, r_max, hist);
+}
+
+void launch_frag_link(const Params& p, cudaStream_t s, int blocks, double r_frag, int* parent)
+{
+    if (p.precision != 0) {
+        FragOp<true> op{r_frag * r_frag, parent, p.n_atoms, p.err};
+        launch_walk<true>(p, s, blocks, op, 0);
     } else {
-        cudaFuncSetAttribute(k_rdf<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        k_rdf<false><<<blocks, 256, smem, s>>>(p, n_bins, r_max, smem_hist, hist);
+        FragOp<false> op{(float)(r_frag * r_frag), parent, p.n_atoms, p.err};
+        launch_walk<false>(p, s, blocks, op, 0);
     }
 }
 

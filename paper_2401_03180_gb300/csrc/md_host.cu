@@ -1385,6 +1385,59 @@ md_status md_rdf(md_handle* h, double r_max, int n_bins, int64_t* counts)
     return MD_OK;
 }
 
+md_status md_fragments(md_handle* h, double r_frag, int mass_max, int charge_max, int32_t* label, int64_t* counts)
+{
+    if (!h) return fail(nullptr, MD_ERR_INVALID_ARG, "null handle");
+    if (!(r_frag > 0.0) || r_frag > h->cfg.r_cut) return fail(h, MD_ERR_INVALID_ARG, "r_frag must be in (0, r_cut]");
+    if (mass_max < 0 || mass_max > 1000000 || charge_max < 0 || charge_max > 100000 || (!label && !counts))
+        return fail(h, MD_ERR_INVALID_ARG, "mass_max, charge_max out of range or no output");
+    const size_t nc = (size_t)h->R * (mass_max + 1) * (charge_max + 1);
+    if (nc > ((size_t)1 << 28)) return fail(h, MD_ERR_INVALID_ARG, "count array too large");
+    if (h->pending && !h->poisoned) {
+        md_status st_ = md_sync(h);
+        if (st_ != MD_OK) return st_;
+    }
+    if (h->poisoned) return fail(h, MD_ERR_BAD_STATE, "handle is in an error state: " + h->err);
+    const int N = h->N;
+    int *d_parent = nullptr, *d_label = nullptr, *d_mass = nullptr, *d_charge = nullptr;
+    unsigned long long* d_counts = nullptr;
+    md_status st = dalloc(h, &d_parent, N);
+    if (st == MD_OK) st = dalloc(h, &d_label, N);
+    if (st == MD_OK) st = dalloc(h, &d_mass, N);
+    if (st == MD_OK) st = dalloc(h, &d_charge, N);
+    if (st == MD_OK) st = dalloc(h, &d_counts, nc);
+    auto release = [&]() {
+        for (void* ptr : {(void*)d_parent, (void*)d_label, (void*)d_mass, (void*)d_charge, (void*)d_counts})
+            if (ptr) dfree(h, ptr);
+    };
+    if (st != MD_OK) {
+        release();
+        return st;
+    }
+    int an[kMaxSpecies] = {0};
+    for (int k = 0; k < h->NS; ++k) an[k] = (int)std::lround(h->cfg.mass[k]);   // mass numbers
+    // the list of the last build covers every pair within r_cut at the current
+    // positions, and the packed records hold the current positions
+    cudaStream_t s = h->stream;
+    cudaMemsetAsync(d_counts, 0, nc * sizeof(unsigned long long), s);
+    launch_frag_init(h->P, s, d_parent, d_mass, d_charge);
+    cudaMemsetAsync(h->P.counters + 2, 0, sizeof(int), s);
+    launch_frag_link(h->P, s, h->n_sm * 4, r_frag, d_parent);
+    cudaMemsetAsync(h->P.counters + 2, 0, sizeof(int), s);
+    launch_frag_count(h->P, s, d_parent, d_label, d_mass, d_charge, an, mass_max, charge_max, d_counts);
+    cudaError_t e = cudaGetLastError();
+    std::vector<unsigned long long> tmp(counts ? nc : 0);
+    if (e == cudaSuccess && label)
+        e = cudaMemcpyAsync(label, d_label, (size_t)N * sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && counts)
+        e = cudaMemcpyAsync(tmp.data(), d_counts, nc * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    release();
+    if (e != cudaSuccess) return fail(h, MD_ERR_CUDA, std::string("md_fragments: ") + cudaGetErrorString(e));
+    for (size_t k = 0; k < tmp.size(); ++k) counts[k] = (int64_t)tmp[k];
+    return check_device_flags(h);
+}
+
 md_status md_get_probe_series(md_handle* h, int replica, int first, int n, int64_t* q_sum, double* d2_sum)
 {
     if (!h) return fail(nullptr, MD_ERR_INVALID_ARG, "null handle");

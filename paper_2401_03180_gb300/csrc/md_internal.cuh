@@ -300,6 +300,10 @@ void launch_refresh(const Params& p, cudaStream_t s);
 void launch_rdf(const Params& p, cudaStream_t s, int blocks, int n_bins, double r_max, unsigned long long* hist);
 void launch_bonded(const Params& p, cudaStream_t s, bool energy);
 void launch_probe(const Params& p, cudaStream_t s, bool rewrite);
+void launch_frag_link(const Params& p, cudaStream_t s, int blocks, double r_frag, int* parent);
+void launch_frag_init(const Params& p, cudaStream_t s, int* parent, int* mass, int* charge);
+void launch_frag_count(const Params& p, cudaStream_t s, const int* parent, int* label, int* mass, int* charge,
+                       const int* mass_number, int mass_max, int charge_max, unsigned long long* counts);
 int pair_max_blocks_per_sm(bool fp64, bool energy, bool hyb, int warps, int n_ts);
 // message returned by md_last_error(NULL) (host side)
 void set_global_error(const std::string& msg);

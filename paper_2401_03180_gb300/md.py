@@ -121,6 +121,7 @@ def lib():
             L.md_set_charge_table.argtypes = [P, C.c_int, P, C.c_int]
             L.md_rdf.argtypes = [P, C.c_double, C.c_int, P]
             L.md_get_probe_series.argtypes = [P, C.c_int, C.c_int, C.c_int, P, P]
+            L.md_fragments.argtypes = [P, C.c_double, C.c_int, C.c_int, P, P]
             L.md_probe_displacement.argtypes = [P, C.c_int, C.c_int, C.c_int, C.POINTER(MDPulse), C.c_int, P]
             L.md_structure_factor.argtypes = [P, C.c_int, C.c_double, C.c_double, C.c_double, C.c_int, C.c_double,
                                               C.c_double, P, C.c_int, P]
@@ -203,6 +204,13 @@ def md_rdf(h, n_species: int, r_max: float, n_bins: int):
     out = np.zeros((n_species, n_species, n_bins), dtype=np.int64)
     _check(lib().md_rdf(h, float(r_max), int(n_bins), _p(out)), h)
     return out
+
+
+def md_fragments(h, n_atoms: int, n_replicas: int, r_frag: float, mass_max: int, charge_max: int):
+    label = np.zeros(n_atoms, dtype=np.int32)
+    counts = np.zeros((n_replicas, mass_max + 1, charge_max + 1), dtype=np.int64)
+    _check(lib().md_fragments(h, float(r_frag), int(mass_max), int(charge_max), _p(label), _p(counts)), h)
+    return label, counts
 
 
 def md_get_probe_series(h, n_species: int, replica: int, first: int, n: int):
@@ -432,6 +440,10 @@ class IonisingMD:
     def rdf(self, r_max, n_bins):
         """Pair counts [n_species][n_species][n_bins] by distance bin (md_rdf)."""
         return md_rdf(self.h, self.ns, r_max, n_bins)
+
+    def fragments(self, r_frag, mass_max=64, charge_max=32):
+        """Fragment label of every atom and fragment counts [R][mass][charge] (md_fragments)."""
+        return md_fragments(self.h, self.n, self.R, r_frag, mass_max, charge_max)
 
     def probe_series(self, replica=0, first=0, n=None):
         """Probe records (q_sum, d2_sum), [n][n_species], of the states after
