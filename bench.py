@@ -309,13 +309,14 @@ def run_gpu(args, rank, world, local):
             h_in[:] = dF_tab[:, step]
             t0 = time.perf_counter()
             M2.md_set_fluence_at(ge.h, step, h_in)                  # H2D: this step's fluence, per replica
-            ge.step(1)
-            ge.get_state(M2.MD_FIELD_Q | M2.MD_FIELD_PLASMA, out=outs)  # D2H: charges + plasma
+            ge.step(1, wait=False)                                   # the step's graph, enqueued
+            ge.get_state(M2.MD_FIELD_Q | M2.MD_FIELD_PLASMA, out=outs)  # D2H: charges + plasma + status
             tot += time.perf_counter() - t0
         ge.close()
         e2e = {"value": world * n_atoms * K / tot, "unit": UNIT,
                "h2d_bytes_per_step": int(8 * s.n_replicas),
-               "d2h_bytes_per_step": int(n_atoms + 32 * s.n_replicas)}
+               # charges, each replica's 104-byte state record, the 4-byte error flags
+               "d2h_bytes_per_step": int(n_atoms + 104 * s.n_replicas + 4)}
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W_,

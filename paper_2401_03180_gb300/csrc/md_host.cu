@@ -40,6 +40,7 @@ struct md_handle {
     long long pending = 0;               // enqueued steps whose status is not read yet
     bool poisoned = false;
     unsigned* h_err = nullptr;           // pinned
+    RepState* h_rs = nullptr;            // pinned [R] copy of the replicas' state (md_get_state)
     double pair_ms = 0.0;
     long long pair_launches = 0, steps = 0, last_pairs = 0;
     double* d_scratch = nullptr;         // [3N] doubles for state exchange
@@ -126,11 +127,9 @@ void pulse_table_host(const md_pulse* pulses, int n_pulses, double t_start_fs, d
     }
 }
 
-md_status check_device_flags(md_handle* h)
+// The status of device error flags already read (nonzero flags poison the handle).
+md_status flags_status(md_handle* h, unsigned e)
 {
-    CU(cudaMemcpyAsync(h->h_err, h->P.err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
-    CU(cudaStreamSynchronize(h->stream));
-    unsigned e = *h->h_err;
     if (!e) return MD_OK;
     h->poisoned = true;
     if (e & ERR_NONFINITE) return fail(h, MD_ERR_NONFINITE, "non-finite position or velocity");
@@ -138,6 +137,13 @@ md_status check_device_flags(md_handle* h)
     if (e & ERR_CELL) return fail(h, MD_ERR_CELL_OVERFLOW, "cell-list capacity exceeded");
     if (e & ERR_TABLE_END) return fail(h, MD_ERR_TABLE_END, "stepped past the pulse table");
     return fail(h, MD_ERR_CUDA, "unknown device error flag");
+}
+
+md_status check_device_flags(md_handle* h)
+{
+    CU(cudaMemcpyAsync(h->h_err, h->P.err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    return flags_status(h, *h->h_err);
 }
 
 // Whether the next force evaluation happens at the positions of the list build
@@ -597,6 +603,7 @@ static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* 
         for (cudaEvent_t& ev : h->prof_pool) CU(cudaEventCreate(&ev));
     }
     CU(cudaMallocHost(&h->h_err, sizeof(unsigned)));
+    CU(cudaMallocHost(&h->h_rs, (size_t)std::max(sys->n_replicas, 1) * sizeof(RepState)));
 
     // ---- type states and tables ----
     h->z.assign(c.z, c.z + c.n_species);
@@ -971,6 +978,7 @@ void md_finalize(md_handle* h)
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->body_stream) cudaStreamDestroy(h->body_stream);
     if (h->h_err) cudaFreeHost(h->h_err);
+    if (h->h_rs) cudaFreeHost(h->h_rs);
     delete h;
 }
 
@@ -1150,7 +1158,7 @@ md_status md_sync(md_handle* h)
         if (e != ERR_LIST) {
             h->steps += h->pending;
             h->pending = 0;
-            st = check_device_flags(h);
+            st = flags_status(h, e);
             if (st != MD_OK) return st;
             return drain_profile(h);
         }
@@ -1183,26 +1191,12 @@ md_status md_step(md_handle* h, int n_steps)
     return md_sync(h);
 }
 
-md_status md_get_state(md_handle* h, md_state* out, unsigned fields)
+// The copies of md_get_state that need no host-side reordering (velocities,
+// forces, charges, K holes, the replicas' plasma state into pinned memory),
+// enqueued on the handle's stream.
+static md_status get_state_async(md_handle* h, md_state* out, unsigned fields)
 {
-    if (!h) return fail(nullptr, MD_ERR_INVALID_ARG, "null handle");
-    if (!out) return fail(h, MD_ERR_INVALID_ARG, "null state");
-    if (h->pending && !h->poisoned) {
-        md_status st_ = md_sync(h);
-        if (st_ != MD_OK) return st_;
-    }
     const int N = h->N, R = h->R;
-    CU(cudaStreamSynchronize(h->stream));
-    std::vector<double> tmp;
-    if (fields & MD_FIELD_X) {
-        if (!out->x) return fail(h, MD_ERR_INVALID_ARG, "x buffer missing");
-        tmp.resize(N);
-        double* src[3] = {h->P.x, h->P.y, h->P.z};
-        for (int d = 0; d < 3; ++d) {
-            CU(cudaMemcpy(tmp.data(), src[d], N * sizeof(double), cudaMemcpyDeviceToHost));
-            for (int i = 0; i < N; ++i) out->x[3 * i + d] = tmp[i];
-        }
-    }
     if (fields & MD_FIELD_V) {
         if (!out->v) return fail(h, MD_ERR_INVALID_ARG, "v buffer missing");
         launch_velocity_out(h->P, h->d_scratch, h->stream);
@@ -1221,20 +1215,73 @@ md_status md_get_state(md_handle* h, md_state* out, unsigned fields)
         if (!out->h) return fail(h, MD_ERR_INVALID_ARG, "h buffer missing");
         CU(cudaMemcpyAsync(out->h, h->P.h, N, cudaMemcpyDeviceToHost, h->stream));
     }
-    if (fields & (MD_FIELD_PLASMA | MD_FIELD_COUNTS)) {
-        std::vector<RepState> rs(R);
-        CU(cudaMemcpyAsync(rs.data(), h->P.rs, R * sizeof(RepState), cudaMemcpyDeviceToHost, h->stream));
-        CU(cudaStreamSynchronize(h->stream));
-        for (int r = 0; r < R; ++r) {
-            if (fields & MD_FIELD_PLASMA) {
-                if (out->n_e) out->n_e[r] = rs[r].n_e;
-                if (out->e_gas_mev) out->e_gas_mev[r] = rs[r].e_gas;
-                if (out->te_ev) out->te_ev[r] = rs[r].te_ev;
-                if (out->kappa) out->kappa[r] = rs[r].kappa;
-            }
-            if ((fields & MD_FIELD_COUNTS) && out->event_counts)
-                for (int k = 0; k < 4; ++k) out->event_counts[4 * r + k] = rs[r].counts[k];
+    if (fields & (MD_FIELD_PLASMA | MD_FIELD_COUNTS))
+        CU(cudaMemcpyAsync(h->h_rs, h->P.rs, R * sizeof(RepState), cudaMemcpyDeviceToHost, h->stream));
+    return MD_OK;
+}
+
+// The plasma fields from the pinned copy of the replicas' state (after the
+// stream has been synchronised).
+static void unpack_rep_state(md_handle* h, md_state* out, unsigned fields)
+{
+    if (!(fields & (MD_FIELD_PLASMA | MD_FIELD_COUNTS))) return;
+    const RepState* rs = h->h_rs;
+    for (int r = 0; r < h->R; ++r) {
+        if (fields & MD_FIELD_PLASMA) {
+            if (out->n_e) out->n_e[r] = rs[r].n_e;
+            if (out->e_gas_mev) out->e_gas_mev[r] = rs[r].e_gas;
+            if (out->te_ev) out->te_ev[r] = rs[r].te_ev;
+            if (out->kappa) out->kappa[r] = rs[r].kappa;
         }
+        if ((fields & MD_FIELD_COUNTS) && out->event_counts)
+            for (int k = 0; k < 4; ++k) out->event_counts[4 * r + k] = rs[r].counts[k];
+    }
+}
+
+md_status md_get_state(md_handle* h, md_state* out, unsigned fields)
+{
+    if (!h) return fail(nullptr, MD_ERR_INVALID_ARG, "null handle");
+    if (!out) return fail(h, MD_ERR_INVALID_ARG, "null state");
+    // Fields copied without host-side reordering, after steps still in flight:
+    // the copies and the error flags are read in one round trip.  Any flag
+    // set (a list overflow, an error) falls back to md_sync and copies again.
+    const unsigned host_side = MD_FIELD_X | MD_FIELD_XLIST;
+    if (h->pending && !h->poisoned && !(fields & host_side)) {
+        md_status st = get_state_async(h, out, fields);
+        if (st != MD_OK) return st;
+        CU(cudaMemcpyAsync(h->h_err, h->P.err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+        CU(cudaStreamSynchronize(h->stream));
+        if (*h->h_err == 0) {
+            h->steps += h->pending;
+            h->pending = 0;
+            st = drain_profile(h);
+            if (st != MD_OK) return st;
+            unpack_rep_state(h, out, fields);
+            if (fields & MD_FIELD_STEP) out->step = h->host_step;
+            return MD_OK;
+        }
+    }
+    if (h->pending && !h->poisoned) {
+        md_status st_ = md_sync(h);
+        if (st_ != MD_OK) return st_;
+    }
+    const int N = h->N;
+    CU(cudaStreamSynchronize(h->stream));
+    std::vector<double> tmp;
+    if (fields & MD_FIELD_X) {
+        if (!out->x) return fail(h, MD_ERR_INVALID_ARG, "x buffer missing");
+        tmp.resize(N);
+        double* src[3] = {h->P.x, h->P.y, h->P.z};
+        for (int d = 0; d < 3; ++d) {
+            CU(cudaMemcpy(tmp.data(), src[d], N * sizeof(double), cudaMemcpyDeviceToHost));
+            for (int i = 0; i < N; ++i) out->x[3 * i + d] = tmp[i];
+        }
+    }
+    {
+        md_status st = get_state_async(h, out, fields);
+        if (st != MD_OK) return st;
+        CU(cudaStreamSynchronize(h->stream));
+        unpack_rep_state(h, out, fields);
     }
     if (fields & MD_FIELD_STEP) out->step = h->host_step;
     if (fields & MD_FIELD_XLIST) {
