@@ -52,6 +52,19 @@ def test_async_steps_equal_sync_steps():
     _same(states[0], states[1])
     _same(states[0], states[2])
     assert states[0]["step"] == 30
+    # fields read without host-side reordering: the copies and the status of
+    # the pending steps come back in one round trip
+    fused = M.MD_FIELD_V | M.MD_FIELD_F | M.MD_FIELD_Q | M.MD_FIELD_H | M.MD_FIELD_PLASMA | M.MD_FIELD_COUNTS | M.MD_FIELD_STEP
+    g = M.IonisingMD(s, atom, **kw)
+    g.set_pulse(p)
+    got = []
+    for _ in range(3):
+        g.step(10, wait=False)
+        got.append(g.get_state(fused))
+    g.close()
+    for k in ("v", "f", "q", "h", "n_e", "e_gas_mev", "te_ev", "kappa", "event_counts"):
+        assert np.array_equal(got[-1][k], states[0][k]), k
+    assert [st["step"] for st in got] == [10, 20, 30]
 
 
 def test_profile_timing_counts_every_step():
@@ -119,6 +132,16 @@ def test_list_growth_keeps_the_trajectory(prec):
     assert t1.list_grows > t0.list_grows
     assert t1.list_capacity >= max(need)
     _same(ref, got)
+    # the same with the steps in flight when the state is read: the one-round-trip
+    # read sees the overflow flag, lets md_sync grow the list, and copies again
+    g = M.IonisingMD(s, atom, list_reserve=reserve, **kw)
+    g.step(steps, wait=False)
+    got2 = g.get_state(M.MD_FIELD_V | M.MD_FIELD_F | M.MD_FIELD_Q | M.MD_FIELD_PLASMA | M.MD_FIELD_STEP)
+    assert g.timing().list_grows > 0
+    g.close()
+    for k in ("v", "f", "q", "n_e", "e_gas_mev"):
+        assert np.array_equal(got2[k], ref[k]), k
+    assert got2["step"] == steps
 
 
 def test_list_growth_on_set_state():
