@@ -159,8 +159,8 @@ __global__ void __launch_bounds__(64) k_bonded(Params p)
 }  // namespace
 
 // Blocks of 64 threads, at most max_blocks of them: in the step graph the
-// kernel runs beside the pair kernel, whose three 256-thread blocks of 80
-// registers per SM leave 4,096 registers, room for one such block.
+// kernel runs beside the pair kernel, whose three 256-thread blocks per SM
+// leave room for a few small blocks only.
 void launch_bonded(const Params& p, cudaStream_t s, bool energy, int max_blocks)
 {
     const long long nt = (long long)p.n_bonds + p.n_angles;

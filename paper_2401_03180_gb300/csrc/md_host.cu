@@ -209,10 +209,10 @@ void enqueue_step_forces(md_handle* h, cudaStream_t s)
     launch_pair_forces(h->P, s, false, h->pair_blocks, h->pair_warps);
     if (h->cfg.profile) cudaEventRecordWithFlags(h->ev_pair1, s, cudaEventRecordExternal);
     if (bonded) {
-        // one 64-thread block per SM: it fits in the registers three resident
-        // pair blocks leave, whichever kernel's blocks are placed first
+        // created after the pair kernel, so its few blocks take the room the
+        // pair kernel's resident blocks leave rather than delaying them
         cudaStreamWaitEvent(h->side_stream, h->ev_fork, 0);
-        launch_bonded(h->P, h->side_stream, false, h->n_sm);
+        launch_bonded(h->P, h->side_stream, false, 4 * h->n_sm);
         cudaEventRecord(h->ev_join, h->side_stream);
         cudaStreamWaitEvent(s, h->ev_join, 0);
     }
