@@ -166,16 +166,6 @@ void launch_bonded(const Params& p, cudaStream_t s, bool energy, int max_blocks)
     const long long nt = (long long)p.n_bonds + p.n_angles;
     if (nt <= 0) return;
     const int blocks = (int)std::max<long long>(1, std::min<long long>((nt + 63) / 64, max_blocks));
-    static bool carveout = false;
-    if (!carveout) {
-        // the pair kernel's shared-memory configuration, so that blocks of both
-        // can share an SM
-        cudaFuncSetAttribute(k_bonded<float, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        cudaFuncSetAttribute(k_bonded<float, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        cudaFuncSetAttribute(k_bonded<double, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        cudaFuncSetAttribute(k_bonded<double, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        carveout = true;
-    }
     if (p.precision == 0) {
         if (energy) k_bonded<float, true><<<blocks, 64, 0, s>>>(p);
         else k_bonded<float, false><<<blocks, 64, 0, s>>>(p);
