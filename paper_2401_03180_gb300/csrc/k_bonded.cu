@@ -158,14 +158,13 @@ __global__ void __launch_bounds__(64) k_bonded(Params p)
 
 }  // namespace
 
-// Blocks of 64 threads, at most max_blocks of them: in the step graph the
-// kernel runs beside the pair kernel, whose three 256-thread blocks per SM
-// leave room for a few small blocks only.
-void launch_bonded(const Params& p, cudaStream_t s, bool energy, int max_blocks)
+// Blocks of 64 threads: in the step graph the kernel runs beside the pair
+// kernel, whose three 256-thread blocks per SM leave room for small blocks only.
+void launch_bonded(const Params& p, cudaStream_t s, bool energy)
 {
     const long long nt = (long long)p.n_bonds + p.n_angles;
     if (nt <= 0) return;
-    const int blocks = (int)std::max<long long>(1, std::min<long long>((nt + 63) / 64, max_blocks));
+    const int blocks = (int)std::min<long long>((nt + 63) / 64, 152LL * 32);
     if (p.precision == 0) {
         if (energy) k_bonded<float, true><<<blocks, 64, 0, s>>>(p);
         else k_bonded<float, false><<<blocks, 64, 0, s>>>(p);

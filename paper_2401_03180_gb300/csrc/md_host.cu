@@ -164,7 +164,7 @@ void enqueue_rebuild(md_handle* h, cudaStream_t s, bool energy)
     launch_pair_list(h->P, s, h->list_blocks);
     set_build_step(h, s, true);   // forces at the build positions: the list may be pruned
     launch_pair_forces(h->P, s, energy, h->pair_blocks, h->pair_warps);
-    launch_bonded(h->P, s, energy, 4 * h->n_sm);
+    launch_bonded(h->P, s, energy);
     launch_probe(h->P, s, true);
 }
 
@@ -193,7 +193,7 @@ void enqueue_rebuild_from_ref(md_handle* h, cudaStream_t s)
     launch_refresh(P, s);
     set_build_step(h, s, false);  // forces away from the build positions: no pruning
     launch_pair_forces(P, s, false, h->pair_blocks, h->pair_warps);
-    launch_bonded(P, s, false, 4 * h->n_sm);
+    launch_bonded(P, s, false);
     launch_probe(P, s, true);
 }
 
@@ -203,19 +203,17 @@ void enqueue_rebuild_from_ref(md_handle* h, cudaStream_t s)
 void enqueue_step_forces(md_handle* h, cudaStream_t s)
 {
     const bool bonded = h->P.n_bonds + h->P.n_angles > 0;
-    if (bonded) cudaEventRecord(h->ev_fork, s);
+    if (bonded) {
+        cudaEventRecord(h->ev_fork, s);
+        cudaStreamWaitEvent(h->side_stream, h->ev_fork, 0);
+        launch_bonded(h->P, h->side_stream, false);
+        cudaEventRecord(h->ev_join, h->side_stream);
+    }
     // external event nodes: the events are recorded on every graph replay
     if (h->cfg.profile) cudaEventRecordWithFlags(h->ev_pair0, s, cudaEventRecordExternal);
     launch_pair_forces(h->P, s, false, h->pair_blocks, h->pair_warps);
     if (h->cfg.profile) cudaEventRecordWithFlags(h->ev_pair1, s, cudaEventRecordExternal);
-    if (bonded) {
-        // created after the pair kernel, so its few blocks take the room the
-        // pair kernel's resident blocks leave rather than delaying them
-        cudaStreamWaitEvent(h->side_stream, h->ev_fork, 0);
-        launch_bonded(h->P, h->side_stream, false, 4 * h->n_sm);
-        cudaEventRecord(h->ev_join, h->side_stream);
-        cudaStreamWaitEvent(s, h->ev_join, 0);
-    }
+    if (bonded) cudaStreamWaitEvent(s, h->ev_join, 0);
     launch_probe(h->P, s, false);
 }
 
@@ -1605,7 +1603,7 @@ md_status md_get_energies(md_handle* h, double* e_kin, double* e_pot, int64_t* n
     launch_refresh(h->P, h->stream);
     set_build_step(h, h->stream, false);
     launch_pair_forces(h->P, h->stream, true, h->pair_blocks, h->pair_warps);
-    launch_bonded(h->P, h->stream, true, 4 * h->n_sm);
+    launch_bonded(h->P, h->stream, true);
     launch_energy(h->P, h->d_ekin, h->d_epot, h->stream);
     CU(cudaGetLastError());
     std::vector<double> ek(R);
