@@ -141,7 +141,7 @@ __device__ void angle_term(const Params& p, const T* par, int t)
 }
 
 template <typename T, bool ENERGY>
-__global__ void __launch_bounds__(64) k_bonded(Params p)
+__global__ void __launch_bounds__(256) k_bonded(Params p)
 {
     // a failed cell build leaves slot_of undefined; a full list stops the step
     if (*p.err & (ERR_CELL | ERR_LIST)) return;
@@ -158,19 +158,17 @@ __global__ void __launch_bounds__(64) k_bonded(Params p)
 
 }  // namespace
 
-// Blocks of 64 threads: in the step graph the kernel runs beside the pair
-// kernel, whose three 256-thread blocks per SM leave room for small blocks only.
 void launch_bonded(const Params& p, cudaStream_t s, bool energy)
 {
     const long long nt = (long long)p.n_bonds + p.n_angles;
     if (nt <= 0) return;
-    const int blocks = (int)std::min<long long>((nt + 63) / 64, 152LL * 32);
+    const int blocks = (int)std::min<long long>((nt + 255) / 256, 152LL * 8);
     if (p.precision == 0) {
-        if (energy) k_bonded<float, true><<<blocks, 64, 0, s>>>(p);
-        else k_bonded<float, false><<<blocks, 64, 0, s>>>(p);
+        if (energy) k_bonded<float, true><<<blocks, 256, 0, s>>>(p);
+        else k_bonded<float, false><<<blocks, 256, 0, s>>>(p);
     } else {
-        if (energy) k_bonded<double, true><<<blocks, 64, 0, s>>>(p);
-        else k_bonded<double, false><<<blocks, 64, 0, s>>>(p);
+        if (energy) k_bonded<double, true><<<blocks, 256, 0, s>>>(p);
+        else k_bonded<double, false><<<blocks, 256, 0, s>>>(p);
     }
 }
 

@@ -27,8 +27,6 @@ struct md_handle {
     cudaStream_t stream = nullptr;       // caller's stream (NULL = legacy default)
     cudaStream_t cap_stream = nullptr;   // private stream used for graph capture
     cudaStream_t body_stream = nullptr;  // captures the bodies of the rebuild IF node
-    cudaStream_t side_stream = nullptr;  // the bonded kernel's branch of the step graph
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t ev_pair0 = nullptr, ev_pair1 = nullptr;   // captured into the graph
     cudaGraph_t graph = nullptr;                          // kept for event-node updates
@@ -197,33 +195,18 @@ void enqueue_rebuild_from_ref(md_handle* h, cudaStream_t s)
     launch_probe(P, s, true);
 }
 
-// The forces of a step inside a step graph: the bonded terms on a branch of
-// their own beside the pair kernel (both add integer atomics to the same
-// sums, so the order does not matter), joined before the graph ends.
-void enqueue_step_forces(md_handle* h, cudaStream_t s)
-{
-    const bool bonded = h->P.n_bonds + h->P.n_angles > 0;
-    if (bonded) {
-        cudaEventRecord(h->ev_fork, s);
-        cudaStreamWaitEvent(h->side_stream, h->ev_fork, 0);
-        launch_bonded(h->P, h->side_stream, false);
-        cudaEventRecord(h->ev_join, h->side_stream);
-    }
-    // external event nodes: the events are recorded on every graph replay
-    if (h->cfg.profile) cudaEventRecordWithFlags(h->ev_pair0, s, cudaEventRecordExternal);
-    launch_pair_forces(h->P, s, false, h->pair_blocks, h->pair_warps);
-    if (h->cfg.profile) cudaEventRecordWithFlags(h->ev_pair1, s, cudaEventRecordExternal);
-    if (bonded) cudaStreamWaitEvent(s, h->ev_join, 0);
-    launch_probe(h->P, s, false);
-}
-
 void enqueue_step(md_handle* h, cudaStream_t s)
 {
     int mode = STEP_KICK_DRIFT | STEP_ADVANCE | (h->cfg.cr_enabled ? STEP_CR : 0);
     launch_step_a(h->P, mode, s, h->grid_atoms);
     launch_cells(h->P, s, h->grid_atoms, h->grid_cells);
     launch_pair_list(h->P, s, h->list_blocks);
-    enqueue_step_forces(h, s);
+    // external event nodes: the events are recorded on every graph replay
+    if (h->cfg.profile) cudaEventRecordWithFlags(h->ev_pair0, s, cudaEventRecordExternal);
+    launch_pair_forces(h->P, s, false, h->pair_blocks, h->pair_warps);
+    if (h->cfg.profile) cudaEventRecordWithFlags(h->ev_pair1, s, cudaEventRecordExternal);
+    launch_bonded(h->P, s, false);
+    launch_probe(h->P, s, false);
 }
 
 // Device error flags without acting on them.
@@ -317,7 +300,11 @@ md_status capture_buffered_step(md_handle* h)
     launch_pair_list(h->P, h->body_stream, h->list_blocks);
     CU(cudaStreamEndCapture(h->body_stream, &rebuild));
     CU(cudaStreamUpdateCaptureDependencies(s, &cn, nullptr, 1, cudaStreamSetCaptureDependencies));
-    enqueue_step_forces(h, s);
+    if (h->cfg.profile) cudaEventRecordWithFlags(h->ev_pair0, s, cudaEventRecordExternal);
+    launch_pair_forces(h->P, s, false, h->pair_blocks, h->pair_warps);
+    if (h->cfg.profile) cudaEventRecordWithFlags(h->ev_pair1, s, cudaEventRecordExternal);
+    launch_bonded(h->P, s, false);
+    launch_probe(h->P, s, false);
     return MD_OK;
 }
 
@@ -609,9 +596,6 @@ static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* 
     CU(cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, dev));
     CU(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
     CU(cudaStreamCreateWithFlags(&h->body_stream, cudaStreamNonBlocking));
-    CU(cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking));
-    CU(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
-    CU(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
     CU(cudaEventCreate(&h->ev_pair0));
     CU(cudaEventCreate(&h->ev_pair1));
     if (c.profile) {
@@ -993,9 +977,6 @@ void md_finalize(md_handle* h)
     if (h->graph) cudaGraphDestroy(h->graph);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->body_stream) cudaStreamDestroy(h->body_stream);
-    if (h->side_stream) cudaStreamDestroy(h->side_stream);
-    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
-    if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->h_err) cudaFreeHost(h->h_err);
     if (h->h_rs) cudaFreeHost(h->h_rs);
     delete h;
