@@ -65,7 +65,7 @@ def test_all_rows_together_match_oracle(oracle_mod, prec, charges):
     qg, dg = gpu.probe_series()
     gpu.close()
     assert np.array_equal(st["q"], ora.q) and st["n_e"][0] == ora.n_e[0]
-    assert ora.q.sum() > s.q0.sum()
+    assert (ora.q != s.q0).sum() > 50               # the charges moved (the table resets the start's)
     L = s.box[0]
     d = st["x"] - ora.x
     d -= L * np.round(d / L)
