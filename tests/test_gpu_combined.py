@@ -82,6 +82,7 @@ def test_all_rows_together_match_oracle(oracle_mod, prec, charges):
 
 def test_checkpoint_of_all_rows_resumes_bit_exact():
     s, rc = _sample(300)
+    rc -= 0.06                                      # room for the skin: box >= 3 (r_cut + skin)
     atom = W.atomic_data(6.0, pi_scale=1500.0, ci_scale=20.0)
     p = [W.Pulse(6.0, 4.0, 3e12, 0.0)]
     kw = dict(r_cut=rc, max_steps=60, t_start_fs=-1.5, screening="hybrid", langevin_g=np.full(5, 0.3),
