@@ -1466,13 +1466,19 @@ md_status md_fragments(md_handle* h, double r_frag, int mass_max, int charge_max
     // the list of the last build covers every pair within r_cut at the current
     // positions, and the packed records hold the current positions
     cudaStream_t s = h->stream;
-    cudaMemsetAsync(d_counts, 0, nc * sizeof(unsigned long long), s);
-    launch_frag_init(h->P, s, d_parent, d_mass, d_charge);
-    cudaMemsetAsync(h->P.counters + 2, 0, sizeof(int), s);
-    launch_frag_link(h->P, s, h->n_sm * 4, r_frag, d_parent);
-    cudaMemsetAsync(h->P.counters + 2, 0, sizeof(int), s);
-    launch_frag_count(h->P, s, d_parent, d_label, d_mass, d_charge, an, mass_max, charge_max, d_counts);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = cudaMemsetAsync(d_counts, 0, nc * sizeof(unsigned long long), s);
+    if (e == cudaSuccess) {
+        launch_frag_init(h->P, s, d_parent, d_mass, d_charge);
+        e = cudaMemsetAsync(h->P.counters + 2, 0, sizeof(int), s);
+    }
+    if (e == cudaSuccess) {
+        launch_frag_link(h->P, s, h->n_sm * 4, r_frag, d_parent);
+        e = cudaMemsetAsync(h->P.counters + 2, 0, sizeof(int), s);
+    }
+    if (e == cudaSuccess) {
+        launch_frag_count(h->P, s, d_parent, d_label, d_mass, d_charge, an, mass_max, charge_max, d_counts);
+        e = cudaGetLastError();
+    }
     std::vector<unsigned long long> tmp(counts ? nc : 0);
     if (e == cudaSuccess && label)
         e = cudaMemcpyAsync(label, d_label, (size_t)N * sizeof(int), cudaMemcpyDeviceToHost, s);
