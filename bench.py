@@ -457,8 +457,10 @@ def ionised_force_errors(wl, atom, states, screening):
         ss = dataclasses.replace(s, x=st["x"], q0=st["q"].astype(np.uint8))
         t0 = time.perf_counter()
         F_ref = O.forces_of_atoms(ss, atom, idx, r_cut=1.2, kappa=st["kappa"])
-        out[prec] = dict(force_error_stats(st["f"][idx], F_ref), steps=int(steps),
-                         n_e=[int(v) for v in st["n_e"]], kappa=[float(v) for v in st["kappa"]],
+        ne, kap = np.asarray(st["n_e"]), np.asarray(st["kappa"])
+        plasma = ({"n_e": [int(v) for v in ne], "kappa": [float(v) for v in kap]} if len(ne) <= 8 else
+                  {"n_e_total": int(ne.sum()), "kappa_min": float(kap.min()), "kappa_max": float(kap.max())})
+        out[prec] = dict(force_error_stats(st["f"][idx], F_ref), steps=int(steps), **plasma,
                          atoms=int(m), oracle_s=round(time.perf_counter() - t0, 2))
     return out
 
