@@ -413,9 +413,13 @@ __global__ void __launch_bounds__(kHalfShell * 32) k_pair_list(Params p)
 }
 
 // Forces over the cluster-pair list.  A warp takes one chunk (up to kChunk
-// entries of one SC) at a time from an atomic counter.
+// entries of one SC) at a time from an atomic counter.  Blocks of 4, 8 or 12
+// warps (the FP32 bounds keep 85 registers per thread either way: three
+// 8-warp or two 12-warp blocks per SM); each block holds its own copy of the
+// LJ table, so with many type states the 12-warp shape keeps more warps
+// resident than the shared memory allows 8-warp blocks.
 template <bool FP64, bool ENERGY, bool HYB>
-__global__ void __launch_bounds__(256, FP64 ? 2 : 3) k_pair(Params p)
+__global__ void __launch_bounds__(FP64 ? 256 : 384, 2) k_pair(Params p)
 {
     using P = Prec<FP64>;
     using T = typename P::T;

@@ -380,8 +380,9 @@ md_status autotune(md_handle* h)
     CU(cudaEventCreate(&b));
     float best = 1e30f;
     int bw = h->pair_warps, bb = h->pair_blocks;
-    const int warps_c[] = {4, 8};
+    const int warps_c[] = {4, 8, 12};
     for (int w : warps_c) {
+        if (fp64 && w > 8) continue;   // the FP64 kernel takes up to 256 threads per block
         int maxb = pair_max_blocks_per_sm(fp64, false, h->P.screening != 0, w, h->NTS_LJ);
         for (int bps = 1; bps <= maxb; ++bps) {
             int blocks = bps * h->n_sm;
@@ -933,8 +934,18 @@ static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* 
     }
     h->grid_atoms = (N + 255) / 256;
     h->grid_cells = std::max(1, std::min(C, h->n_sm * 8));
-    h->pair_warps = 8;
-    h->pair_blocks = h->n_sm * pair_max_blocks_per_sm(c.precision == MD_PREC_FP64, false, c.screening != 0, 8, h->NTS_LJ);
+    {
+        // the shape with the most resident warps per SM (8-warp blocks on a tie):
+        // with many LJ type states the per-block table limits 8-warp blocks
+        const bool fp64 = c.precision == MD_PREC_FP64;
+        h->pair_warps = 8;
+        int best = 8 * pair_max_blocks_per_sm(fp64, false, c.screening != 0, 8, h->NTS_LJ);
+        if (!fp64) {
+            const int w12 = 12 * pair_max_blocks_per_sm(fp64, false, c.screening != 0, 12, h->NTS_LJ);
+            if (w12 > best) { best = w12; h->pair_warps = 12; }
+        }
+        h->pair_blocks = h->n_sm * (best / h->pair_warps);
+    }
     h->list_blocks = std::max(1, std::min(P.sc_cap, 4 * h->n_sm));
     CU(cudaDeviceSynchronize());
 
