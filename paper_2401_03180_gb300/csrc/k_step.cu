@@ -357,7 +357,7 @@ __device__ __forceinline__ CrRates cr_rates(const Params& p, const RepState& st,
 template <bool SETCOND>
 __global__ void __launch_bounds__(kStepThreads) k_step_a(Params p, int mode)
 {
-    extern __shared__ CrRates s_cr[];   // [kCrTab] when p.cr_tab (dynamic: no shared memory otherwise)
+    __shared__ CrRates s_cr[kCrTab];
     __shared__ long long s_acc[kRepWindow][6];
     __shared__ unsigned long long s_bmin[kRepWindow][3], s_bmax[kRepWindow][3];
     __shared__ int s_last;
@@ -727,12 +727,11 @@ void launch_step_a(const Params& p, int mode, cudaStream_t s, int grid_atoms)
     (void)grid_atoms;
     const int blocks = (p.n_atoms + kStepAtoms - 1) / kStepAtoms;
     const int fin_blocks = (p.n_rep * 32 + 255) / 256;
-    const size_t smem = p.cr_tab ? kCrTab * sizeof(CrRates) : 0;
     if (mode & STEP_SETCOND) {
-        k_step_a<true><<<blocks, kStepThreads, smem, s>>>(p, mode);
+        k_step_a<true><<<blocks, kStepThreads, 0, s>>>(p, mode);
         if (p.n_rep > kInlineReps) k_step_fin<true><<<fin_blocks, 256, 0, s>>>(p, mode);
     } else {
-        k_step_a<false><<<blocks, kStepThreads, smem, s>>>(p, mode);
+        k_step_a<false><<<blocks, kStepThreads, 0, s>>>(p, mode);
         if (p.n_rep > kInlineReps) k_step_fin<false><<<fin_blocks, 256, 0, s>>>(p, mode);
     }
 }
