@@ -331,7 +331,6 @@ struct CrRates {
 };
 constexpr int kCrTab = 256;   // table entries of one block
 
-template <bool WITH_L>
 __device__ __forceinline__ CrRates cr_rates(const Params& p, const RepState& st, double dF, int s, int q, int h)
 {
     const int Z = p.zs[s];
@@ -345,8 +344,7 @@ __device__ __forceinline__ CrRates cr_rates(const Params& p, const RepState& st,
     e.c1 = __dadd_rn(e.a_pi, a_a);
     e.c2 = __dadd_rn(e.c1, a_ci);
     e.lam = __dadd_rn(e.c2, a_rec);
-    e.L = 0ull;
-    if (WITH_L && e.lam > 0.0) e.L = __double2ull_ru(__dmul_rn(e.lam, 9007199254740992.0));   // 2^53
+    e.L = e.lam > 0.0 ? __double2ull_ru(__dmul_rn(e.lam, 9007199254740992.0)) : 0ull;   // 2^53
     e.pos = (a_a > 0.0 ? 1 : 0) | (a_ci > 0.0 ? 2 : 0) | (a_rec > 0.0 ? 4 : 0);
     return e;
 }
@@ -405,7 +403,7 @@ __global__ void __launch_bounds__(kStepThreads) k_step_a(Params p, int mode)
             const int rr = r0 + w;
             const int sp = p.cts_sp[c];
             const double dFr = step < p.max_steps ? p.dF[(long long)rr * p.max_steps + step] : 0.0;
-            s_cr[e] = cr_rates<true>(p, p.rs[rr], dFr, sp, c - p.lj_ts_off[sp], hh);
+            s_cr[e] = cr_rates(p, p.rs[rr], dFr, sp, c - p.lj_ts_off[sp], hh);
         }
         asm volatile("bar.sync 1, %0;" ::"r"(kStepThreads - kStepAtoms));
     }
@@ -588,24 +586,22 @@ __global__ void __launch_bounds__(kStepThreads) k_step_a(Params p, int mode)
         const int ts = p.ts_off[s] + qi;
         if (step >= p.max_steps) atomicOr(p.err, ERR_TABLE_END);
         const int w = r - r0;
-        const bool tab = cr_tab && w < n_win;
         CrRates cr;
-        if (tab) {
+        if (cr_tab && w < n_win) {
             cr = s_cr[(w * n_tsp + p.lj_ts_off[s] + qi) * 2 + hi];
         } else {
             const double dF = step < p.max_steps ? p.dF[(long long)r * p.max_steps + step] : 0.0;
-            cr = cr_rates<false>(p, p.rs[r], dF, s, qi, hi);
+            cr = cr_rates(p, p.rs[r], dF, s, qi, hi);
         }
         int ch = -1;
-        if (tab ? cr.L != 0ull : cr.lam > 0.0) {
+        if (cr.L != 0ull) {
             const unsigned long long sd = p.seed[r];
             const uint4 w4 = philox4x32_10(make_uint4((unsigned)p.local_id[i], (unsigned)step, 0u, 0u),
                                            make_uint2((unsigned)sd, (unsigned)(sd >> 32)));
-            // 1 - e^{-lam} <= lam, so u0 >= lam decides "no event" exactly; with a
-            // table entry as an integer comparison (u0 = m 2^-53, m >= L)
+            // u0 = m 2^-53; 1 - e^{-lam} <= lam, so u0 >= lam (m >= L) decides
+            // "no event" exactly, without FP64 arithmetic
             const unsigned long long m0 = ((unsigned long long)(w4.x >> 5) << 26) | (unsigned long long)(w4.y >> 6);
-            const bool below = tab ? m0 < cr.L : u53(w4.x, w4.y) < cr.lam;
-            if (below && u53(w4.x, w4.y) < one_minus_exp_neg(cr.lam, p.etab, p.inv12)) {
+            if (m0 < cr.L && u53(w4.x, w4.y) < one_minus_exp_neg(cr.lam, p.etab, p.inv12)) {
                 const double t = __dmul_rn(u53(w4.z, w4.w), cr.lam);
                 if (t < cr.a_pi) ch = 0;
                 else if (t < cr.c1) ch = 1;
