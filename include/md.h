@@ -184,13 +184,6 @@ typedef struct md_config {
                                 the probe-weighted displacement of Eq. 17
                                 (md_get_probe_series, md_probe_displacement).
                                 Costs one kernel per step. 0 (default): off.  */
-    int rate_tables;         /* tuning of the charge update (MD_CHARGE_RATES):
-                                the step kernel may tabulate the rates of
-                                every (type state, K hole) once per block
-                                instead of once per atom.  Results are
-                                identical either way.  0 (default): for
-                                systems of 2^19 atoms or more, where the FP64
-                                pipe bounds the step; 1: always; 2: never.    */
 } md_config;
 
 /*

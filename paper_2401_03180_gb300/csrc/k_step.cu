@@ -386,13 +386,11 @@ __global__ void __launch_bounds__(kStepThreads) k_step_a(Params p, int mode)
     int r = live ? p.rep[i] : -1;
     // ---- the rates of this block's replicas for every (type state of the
     // species present, K hole), once per block instead of once per atom; the
-    // charge-update warps fill it and wait for each other only.  It pays where
-    // the FP64 pipe bounds the kernel (large systems); in a small, latency-bound
-    // one its fill lengthens the critical path, and the host leaves it off
+    // charge-update warps fill it and wait for each other only
     const int n_tsp = p.n_ts_lj;
     int n_win = 0;
     bool cr_tab = false;
-    if (p.cr_tab && (mode & STEP_CR) && p.charge_mode != kChargeTable) {
+    if ((mode & STEP_CR) && p.charge_mode != kChargeTable) {
         const int r_last = p.rep[min(first + kStepAtoms, p.n_atoms) - 1];
         n_win = min(r_last - r0 + 1, kRepWindow);
         cr_tab = n_win * n_tsp * 2 <= kCrTab;

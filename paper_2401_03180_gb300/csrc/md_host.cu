@@ -479,7 +479,6 @@ md_status validate(const md_config* c, const md_system* s)
     for (int k = 0; k < MD_MAX_SPECIES; ++k)
         if (!(c->langevin_g[k] >= 0.0) || !(c->langevin_g[k] < 1e30))
             return fail(h, MD_ERR_INVALID_ARG, "langevin_g must be finite and >= 0");
-    if (c->rate_tables < 0 || c->rate_tables > 2) return fail(h, MD_ERR_INVALID_ARG, "rate_tables must be 0, 1 or 2");
     if (c->charge_mode != MD_CHARGE_RATES && c->charge_mode != MD_CHARGE_TABLE)
         return fail(h, MD_ERR_INVALID_ARG, "charge_mode must be MD_CHARGE_RATES or MD_CHARGE_TABLE");
     if (c->max_steps < 1) return fail(h, MD_ERR_INVALID_ARG, "max_steps must be >= 1");
@@ -774,9 +773,6 @@ static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* 
         DALLOC(P.hrep, R);
     }
     P.charge_mode = c.charge_mode;
-    // per-block CR rate tables: measured 1.1 % faster steps on 1.4-2 M atoms
-    // (FP64-bound step kernel), 1.4 % slower on 30,000 atoms (latency-bound)
-    P.cr_tab = c.rate_tables == 1 ? 1 : (c.rate_tables == 2 ? 0 : (h->N >= (1 << 19) ? 1 : 0));
     if (c.charge_mode == MD_CHARGE_TABLE) {
         // every atom neutral until a table is set: running sums of 1 everywhere
         const size_t n = (size_t)R * (c.max_steps + 1) * nts;

@@ -108,7 +108,6 @@ struct Params {
     int screening;           // MD_SCREEN_*
     int langevin;            // 1: electron-ion coupling (some langevin_g > 0)
     int charge_mode;         // MD_CHARGE_*
-    int cr_tab;              // 1: the step kernel tabulates the CR rates per block (large systems)
     int z_max;               // largest nuclear charge of the species present
     double dt, r_cut, rc2, kappa_fixed, te_floor, four_pi_f, coulomb_f, inv_dte;
     float rc2_f, rc_f;

@@ -48,7 +48,7 @@ class MDConfig(C.Structure):
                 ("dev_free", FREE_FN), ("alloc_ctx", C.c_void_p), ("autotune", C.c_int),
                 ("profile", C.c_int), ("list_reserve", C.c_int), ("list_skin_nm", C.c_double),
                 ("screening", C.c_int), ("langevin_g", C.c_double * MD_MAX_SPECIES),
-                ("charge_mode", C.c_int), ("probe_record", C.c_int), ("rate_tables", C.c_int)]
+                ("charge_mode", C.c_int), ("probe_record", C.c_int)]
 
 
 class MDSystem(C.Structure):
@@ -406,7 +406,7 @@ class IonisingMD:
                  plasma_mode=MD_PLASMA_BOOKKEEPING, max_steps=1000, kappa_fixed=-1.0, t_start_fs=0.0,
                  te_floor_ev=1.0, coulomb_f=COULOMB_F, autotune=False, profile=False, list_reserve=0,
                  list_skin_nm=0.0, screening="debye", langevin_g=None, charge_mode="rates",
-                 probe_record=False, rate_tables=0, torch_allocator=True, sigma0=None, eps0=None, mass=None):
+                 probe_record=False, torch_allocator=True, sigma0=None, eps0=None, mass=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("IonisingMD needs a CUDA GPU (no CPU fallback)")
@@ -420,7 +420,6 @@ class IonisingMD:
                                   list_skin_nm=list_skin_nm, screening=screening, langevin_g=langevin_g,
                                   charge_mode=charge_mode, sigma0=sigma0, eps0=eps0, mass=mass)
         cfg.probe_record = int(bool(probe_record))
-        cfg.rate_tables = int(rate_tables)
         self._keep = keep_c
         self._alloc = TorchAllocator() if torch_allocator else None
         if self._alloc is not None:

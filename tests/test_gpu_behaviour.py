@@ -49,18 +49,16 @@ def test_runs_are_bit_identical_and_tile_invariant(prec):
     _same(a, c)
 
 
-@pytest.mark.parametrize("rate_tables", [0, 1])
-def test_batched_replicas_equal_solo_runs(rate_tables):
+def test_batched_replicas_equal_solo_runs():
     # six replicas: more than the step kernel reduces itself, so the batch takes
-    # the warp-per-replica reduction and each solo run the in-kernel one; with
-    # the rate tables forced on, a block's table spans several replicas
+    # the warp-per-replica reduction and each solo run the in-kernel one
     reps = [methane(n, seed=k + 1) for k, n in enumerate((40, 75, 23, 31, 52, 18))]
     for k, r in enumerate(reps):
         r.seed[:] = 500 + k
     atom = W.atomic_data(8.0, pi_scale=1500.0, ci_scale=10.0)
     pulses = [[W.Pulse(8.0, 10.0, f, 0.0)] for f in (1e12, 3e11, 2e12, 5e11, 1.5e12, 8e11)]
     batch = W.concat(reps)
-    g = M.IonisingMD(batch, atom, max_steps=80, t_start_fs=-5.0, rate_tables=rate_tables)
+    g = M.IonisingMD(batch, atom, max_steps=80, t_start_fs=-5.0)
     for k, p in enumerate(pulses):
         g.set_pulse(p, replica=k)
     g.step(60)

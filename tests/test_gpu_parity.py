@@ -68,12 +68,11 @@ def test_forces_match_oracle(oracle_mod, prec, case):
 
 
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
-@pytest.mark.parametrize("rate_tables", [1, 2])      # per-block rate tables forced on / off
-def test_charge_sequences_bit_exact(oracle_mod, prec, rate_tables):
+def test_charge_sequences_bit_exact(oracle_mod, prec):
     s = methane(60, charge_frac=0.0)
     atom = W.atomic_data(8.0, pi_scale=2000.0, ci_scale=20.0, rec_scale=500.0)
     pulses = [W.Pulse(8.0, 10.0, 1e12, 0.0)]
-    kw = dict(r_cut=1.2, cr_enabled=True, max_steps=300, t_start_fs=-7.0, rate_tables=rate_tables)
+    kw = dict(r_cut=1.2, cr_enabled=True, max_steps=300, t_start_fs=-7.0)
     gpu = M.IonisingMD(s, atom, precision=prec, **kw)
     gpu.set_pulse(pulses)
     ora = oracle_mod.OracleMD(s, atom, r_cut=1.2, cr_enabled=True, t_start_fs=-7.0, pulses=[pulses],
