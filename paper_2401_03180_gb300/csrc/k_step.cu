@@ -146,7 +146,7 @@ __device__ __forceinline__ void half_kick(const Params& p, int s, int slot, doub
 {
     const double c = p.hdtm[s];
     if (p.precision == 0) {
-        const float cf = p.hdtm_f[s];   // (float)(c 2^-32), formed on the host
+        const float cf = (float)(c * kFixInv);
         ax = (double)(cf * (float)p.fx[slot]);
         ay = (double)(cf * (float)p.fy[slot]);
         az = (double)(cf * (float)p.fz[slot]);
@@ -320,42 +320,12 @@ __device__ void finalize_step(const Params& p, int mode, long long next, unsigne
     }
 }
 
-// The rates of one (replica, type state, K hole) at this step and their
-// running sums (reading of Sec. II.A), in the order the oracle adds them.
-// L = ceil(lambda 2^53): with u0 = m 2^-53 exactly (u53), u0 < lambda holds
-// exactly when m < L, an integer comparison (0: no event possible).
-struct CrRates {
-    double a_pi, c1, c2, lam;
-    unsigned long long L;
-    int pos;   // bit 0: a_a > 0, bit 1: a_ci > 0, bit 2: a_rec > 0
-};
-constexpr int kCrTab = 256;   // table entries of one block
-
-__device__ __forceinline__ CrRates cr_rates(const Params& p, const RepState& st, double dF, int s, int q, int h)
-{
-    const int Z = p.zs[s];
-    const int ts = p.ts_off[s] + q;
-    CrRates e;
-    e.a_pi = __dmul_rn(p.sigma_pi[2 * ts + h], dF);
-    const double a_a = h ? p.auger_dt[s] : 0.0;
-    double a_ci = 0.0, a_rec = 0.0;
-    if (q < Z) a_ci = __dmul_rn(st.ne_dt, interp(p.k_ci + (long long)ts * p.n_te, st.it0, st.wt));
-    if (q > 0 && h == 0) a_rec = __dmul_rn(st.ne_dt, interp(p.k_rec + (long long)ts * p.n_te, st.it0, st.wt));
-    e.c1 = __dadd_rn(e.a_pi, a_a);
-    e.c2 = __dadd_rn(e.c1, a_ci);
-    e.lam = __dadd_rn(e.c2, a_rec);
-    e.L = e.lam > 0.0 ? __double2ull_ru(__dmul_rn(e.lam, 9007199254740992.0)) : 0ull;   // 2^53
-    e.pos = (a_a > 0.0 ? 1 : 0) | (a_ci > 0.0 ? 2 : 0) | (a_rec > 0.0 ? 4 : 0);
-    return e;
-}
-
 // SETCOND: the Verlet-buffered variant that decides the rebuild and sets the
 // graph condition (ncu does not profile kernels that can set one, so the
 // every-step variant is a separate instantiation).
 template <bool SETCOND>
 __global__ void __launch_bounds__(kStepThreads) k_step_a(Params p, int mode)
 {
-    __shared__ CrRates s_cr[kCrTab];
     __shared__ long long s_acc[kRepWindow][6];
     __shared__ unsigned long long s_bmin[kRepWindow][3], s_bmax[kRepWindow][3];
     __shared__ int s_last;
@@ -384,27 +354,6 @@ __global__ void __launch_bounds__(kStepThreads) k_step_a(Params p, int mode)
     const bool live = i < p.n_atoms;
     const int lane = tid & 31;
     int r = live ? p.rep[i] : -1;
-    // ---- the rates of this block's replicas for every (type state of the
-    // species present, K hole), once per block instead of once per atom; the
-    // charge-update warps fill it and wait for each other only
-    const int n_tsp = p.n_ts_lj;
-    int n_win = 0;
-    bool cr_tab = false;
-    if ((mode & STEP_CR) && p.charge_mode != kChargeTable) {
-        const int r_last = p.rep[min(first + kStepAtoms, p.n_atoms) - 1];
-        n_win = min(r_last - r0 + 1, kRepWindow);
-        cr_tab = n_win * n_tsp * 2 <= kCrTab;
-    }
-    if (cr_tab && cr_role) {
-        for (int e = tid - kStepAtoms; e < n_win * n_tsp * 2; e += kStepThreads - kStepAtoms) {
-            const int w = e / (2 * n_tsp), c = (e >> 1) - w * n_tsp, hh = e & 1;
-            const int rr = r0 + w;
-            const int sp = p.cts_sp[c];
-            const double dFr = step < p.max_steps ? p.dF[(long long)rr * p.max_steps + step] : 0.0;
-            s_cr[e] = cr_rates(p, p.rs[rr], dFr, sp, c - p.lj_ts_off[sp], hh);
-        }
-        asm volatile("bar.sync 1, %0;" ::"r"(kStepThreads - kStepAtoms));
-    }
     double pos[3] = {0.0, 0.0, 0.0};
     bool vac = false;
     // inputs of this atom's re-pack (Verlet-buffered list), loaded before the
@@ -449,10 +398,9 @@ __global__ void __launch_bounds__(kStepThreads) k_step_a(Params p, int mode)
                 vy = cs.x * vy + cs.y * gy;
                 vz = cs.x * vz + cs.y * gz;
             }
-            // x + dt v with one rounding (GB300 issues FP64 at 2 lanes per SM per clock)
-            x = __fma_rn(p.dt, vx, x);
-            y = __fma_rn(p.dt, vy, y);
-            z = __fma_rn(p.dt, vz, z);
+            x += p.dt * vx;
+            y += p.dt * vy;
+            z += p.dt * vz;
             const Grid& g = p.grid[r];
             if (g.periodic) {
                 // wrap only atoms that left the box (FP64 division is slow); the
@@ -582,30 +530,33 @@ __global__ void __launch_bounds__(kStepThreads) k_step_a(Params p, int mode)
         const int qi = p.q[i], hi = p.h[i];
         s_q[i - first] = (uint8_t)qi;   // replaced below if an event changes it
         const int ts = p.ts_off[s] + qi;
-        if (step >= p.max_steps) atomicOr(p.err, ERR_TABLE_END);
-        const int w = r - r0;
-        CrRates cr;
-        if (cr_tab && w < n_win) {
-            cr = s_cr[(w * n_tsp + p.lj_ts_off[s] + qi) * 2 + hi];
-        } else {
-            const double dF = step < p.max_steps ? p.dF[(long long)r * p.max_steps + step] : 0.0;
-            cr = cr_rates(p, p.rs[r], dF, s, qi, hi);
-        }
+        const RepState st = p.rs[r];
+        double dF = 0.0;
+        if (step < p.max_steps) dF = p.dF[(long long)r * p.max_steps + step];
+        else atomicOr(p.err, ERR_TABLE_END);
+        const double a_pi = __dmul_rn(p.sigma_pi[2 * ts + hi], dF);
+        const double a_a = hi ? p.auger_dt[s] : 0.0;
+        double a_ci = 0.0, a_rec = 0.0;
+        if (qi < Z) a_ci = __dmul_rn(st.ne_dt, interp(p.k_ci + (long long)ts * p.n_te, st.it0, st.wt));
+        if (qi > 0 && hi == 0)
+            a_rec = __dmul_rn(st.ne_dt, interp(p.k_rec + (long long)ts * p.n_te, st.it0, st.wt));
+        const double c1 = __dadd_rn(a_pi, a_a);
+        const double c2 = __dadd_rn(c1, a_ci);
+        const double lam = __dadd_rn(c2, a_rec);
         int ch = -1;
-        if (cr.L != 0ull) {
+        if (lam > 0.0) {
             const unsigned long long sd = p.seed[r];
             const uint4 w4 = philox4x32_10(make_uint4((unsigned)p.local_id[i], (unsigned)step, 0u, 0u),
                                            make_uint2((unsigned)sd, (unsigned)(sd >> 32)));
-            // u0 = m 2^-53; 1 - e^{-lam} <= lam, so u0 >= lam (m >= L) decides
-            // "no event" exactly, without FP64 arithmetic
-            const unsigned long long m0 = ((unsigned long long)(w4.x >> 5) << 26) | (unsigned long long)(w4.y >> 6);
-            if (m0 < cr.L && u53(w4.x, w4.y) < one_minus_exp_neg(cr.lam, p.etab, p.inv12)) {
-                const double t = __dmul_rn(u53(w4.z, w4.w), cr.lam);
-                if (t < cr.a_pi) ch = 0;
-                else if (t < cr.c1) ch = 1;
-                else if (t < cr.c2) ch = 2;
-                else if (t < cr.lam) ch = 3;
-                else ch = (cr.pos & 4) ? 3 : ((cr.pos & 2) ? 2 : ((cr.pos & 1) ? 1 : 0));
+            const double u0 = u53(w4.x, w4.y);
+            // 1 - e^{-lam} <= lam, so u0 >= lam decides "no event" exactly
+            if (u0 < lam && u0 < one_minus_exp_neg(lam, p.etab, p.inv12)) {
+                const double t = __dmul_rn(u53(w4.z, w4.w), lam);
+                if (t < a_pi) ch = 0;
+                else if (t < c1) ch = 1;
+                else if (t < c2) ch = 2;
+                else if (t < lam) ch = 3;
+                else ch = a_rec > 0.0 ? 3 : (a_ci > 0.0 ? 2 : (a_a > 0.0 ? 1 : 0));
             }
         }
         if (ch >= 0) {
@@ -631,6 +582,7 @@ __global__ void __launch_bounds__(kStepThreads) k_step_a(Params p, int mode)
             p.q[i] = (uint8_t)qn;
             p.h[i] = (uint8_t)hn;
             s_q[i - first] = (uint8_t)qn;
+            const int w = r - r0;
             if (w < kRepWindow) {
                 atomicAdd((unsigned long long*)&s_acc[w][0], (unsigned long long)(ch == 3 ? -1ll : 1ll));
                 atomicAdd((unsigned long long*)&s_acc[w][1], (unsigned long long)de);
