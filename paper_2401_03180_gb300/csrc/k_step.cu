@@ -146,7 +146,7 @@ __device__ __forceinline__ void half_kick(const Params& p, int s, int slot, doub
 {
     const double c = p.hdtm[s];
     if (p.precision == 0) {
-        const float cf = (float)(c * kFixInv);
+        const float cf = p.hdtm_f[s];   // (float)(c 2^-32), formed on the host
         ax = (double)(cf * (float)p.fx[slot]);
         ay = (double)(cf * (float)p.fy[slot]);
         az = (double)(cf * (float)p.fz[slot]);
@@ -398,9 +398,10 @@ __global__ void __launch_bounds__(kStepThreads) k_step_a(Params p, int mode)
                 vy = cs.x * vy + cs.y * gy;
                 vz = cs.x * vz + cs.y * gz;
             }
-            x += p.dt * vx;
-            y += p.dt * vy;
-            z += p.dt * vz;
+            // x + dt v with one rounding (GB300 issues FP64 at 2 lanes per SM per clock)
+            x = __fma_rn(p.dt, vx, x);
+            y = __fma_rn(p.dt, vy, y);
+            z = __fma_rn(p.dt, vz, z);
             const Grid& g = p.grid[r];
             if (g.periodic) {
                 // wrap only atoms that left the box (FP64 division is slow); the

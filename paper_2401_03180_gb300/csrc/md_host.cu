@@ -746,6 +746,14 @@ static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* 
     DALLOC(d_etab, kNEtab); DALLOC(d_inv, 13);
     DALLOC(d_ljf, (size_t)nts_lj * nts_lj); DALLOC(d_ljd, (size_t)nts_lj * nts_lj);
     P.hdtm = d_hdtm; P.mass = d_mass; P.zs = d_z; P.ts_off = d_tsoff; P.lj_ts_off = d_ljtsoff; P.auger_dt = d_auger;
+    {
+        float* d_hf;
+        DALLOC(d_hf, NS);
+        std::vector<float> hf(NS);
+        for (int sp = 0; sp < NS; ++sp) hf[sp] = (float)(hdtm[sp] * kFixInv);
+        CU(cudaMemcpy(d_hf, hf.data(), NS * sizeof(float), cudaMemcpyHostToDevice));
+        P.hdtm_f = d_hf;
+    }
     P.sigma_pi = d_sigma; P.k_ci = d_kci; P.k_rec = d_krec; P.ip_mev = d_ip; P.e_pi_mev = d_epi;
     P.e_auger_mev = d_eaug; P.etab = d_etab; P.inv12 = d_inv; P.lj_f = d_ljf; P.lj_d = d_ljd;
     unsigned long long* d_seed;

@@ -122,6 +122,7 @@ struct Params {
 
     // species / type-state tables
     const double* hdtm;      // [n_species] 0.5 dt / m
+    const float* hdtm_f;     // [n_species] (float)(0.5 dt / m 2^-32): the mixed path's half kick per fixed-point unit
     const double* mass;      // [n_species]
     const int* zs;           // [n_species]
     const int* ts_off;       // [n_species + 1]
