@@ -177,9 +177,13 @@ __global__ void __launch_bounds__(256) k_cell_scatter(Params p)
 
 // One CTA per cell: rank sort of the cell's keys (Hilbert index, atom), with
 // up to 8 threads sharing the count of one element; then the packed arrays
-// and the cluster bounding boxes.
+// and the cluster bounding boxes.  Launched with 1,024 threads when there are
+// few cells per SM (large cells, all sorted at once) and 256 when there are
+// many: a cell's phases are latency-bound, and seven 256-thread CTAs per SM
+// keep more cells in flight than two 1,024-thread ones.
 __global__ void __launch_bounds__(kSortThreads) k_cell_sort_pack(Params p)
 {
+    const int nt = blockDim.x;
     __shared__ unsigned long long s_key[kSortMax];
     if (*p.err & ERR_CELL) return;
     const int tid = threadIdx.x;
@@ -210,11 +214,11 @@ __global__ void __launch_bounds__(kSortThreads) k_cell_sort_pack(Params p)
         const bool in_smem = n <= kSortMax;
         const unsigned long long* keys = in_smem ? s_key : p.tmp_key + b;
         if (in_smem)
-            for (int e = tid; e < n; e += kSortThreads) s_key[e] = p.tmp_key[b + e];
+            for (int e = tid; e < n; e += nt) s_key[e] = p.tmp_key[b + e];
         __syncthreads();
         int tpe = 1;
-        while (tpe < 8 && 2 * tpe * n <= kSortThreads) tpe *= 2;
-        const int per_pass = kSortThreads / tpe;
+        while (tpe < 8 && 2 * tpe * n <= nt) tpe *= 2;
+        const int per_pass = nt / tpe;
         const int sub = tid & (tpe - 1);
         for (int base = 0; base < n; base += per_pass) {
             const int e = base + tid / tpe;
@@ -233,7 +237,7 @@ __global__ void __launch_bounds__(kSortThreads) k_cell_sort_pack(Params p)
                 pack_slot(p, slot, i, cen, g);
             }
         }
-        for (int e = n + tid; e < npad; e += kSortThreads) {     // padding: far away, no charge
+        for (int e = n + tid; e < npad; e += nt) {     // padding: far away, no charge
             const int slot = ps + e;
             const double far = 1.0e6 + 1024.0 * (double)slot;
             p.atom_of[slot] = -1;
@@ -245,7 +249,7 @@ __global__ void __launch_bounds__(kSortThreads) k_cell_sort_pack(Params p)
         __syncthreads();
         // cluster bounding boxes (real atoms only) and fragment ranges
         const int ncl = npad / kClusterSize;
-        for (int k = tid; k < ncl; k += kSortThreads) {
+        for (int k = tid; k < ncl; k += nt) {
             float lx = 3.0e38f, ly = 3.0e38f, lz = 3.0e38f, hx = -3.0e38f, hy = -3.0e38f, hz = -3.0e38f;
             int fmin = 0x7fffffff, fmax = (int)0x80000000;
             for (int a = 0; a < kClusterSize; ++a) {
@@ -298,12 +302,12 @@ void launch_refresh(const Params& p, cudaStream_t s)
     k_refresh<<<(p.slot_cap + 255) / 256, 256, 0, s>>>(p);
 }
 
-void launch_cells(const Params& p, cudaStream_t s, int grid_atoms, int grid_cells)
+void launch_cells(const Params& p, cudaStream_t s, int grid_atoms, int grid_cells, int sort_threads)
 {
     k_cell_assign<<<(p.slot_cap + 255) / 256, 256, 0, s>>>(p);
     k_cell_scan<<<1, kScanThreads, 0, s>>>(p);
     k_cell_scatter<<<grid_atoms, 256, 0, s>>>(p);
-    k_cell_sort_pack<<<grid_cells, kSortThreads, 0, s>>>(p);
+    k_cell_sort_pack<<<grid_cells, sort_threads, 0, s>>>(p);
 }
 
 }  // namespace mdg

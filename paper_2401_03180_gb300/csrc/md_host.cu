@@ -34,7 +34,7 @@ struct md_handle {
     std::vector<cudaEvent_t> prof_pool;                   // [2 * kProfPool] pair-kernel events
     int prof_next = 0;                                    // pairs in flight
     long long list_grows = 0;
-    int grid_atoms = 1, grid_cells = 1;
+    int grid_atoms = 1, grid_cells = 1, sort_threads = 1024;
     int pair_blocks = 1, pair_warps = 8, list_blocks = 1;
     long long host_step = 0;             // steps enqueued
     long long pending = 0;               // enqueued steps whose status is not read yet
@@ -158,7 +158,7 @@ void set_build_step(md_handle* h, cudaStream_t s, bool at_build)
 void enqueue_rebuild(md_handle* h, cudaStream_t s, bool energy)
 {
     launch_step_a(h->P, 0, s, h->grid_atoms);
-    launch_cells(h->P, s, h->grid_atoms, h->grid_cells);
+    launch_cells(h->P, s, h->grid_atoms, h->grid_cells, h->sort_threads);
     launch_pair_list(h->P, s, h->list_blocks);
     set_build_step(h, s, true);   // forces at the build positions: the list may be pruned
     launch_pair_forces(h->P, s, energy, h->pair_blocks, h->pair_warps);
@@ -179,7 +179,7 @@ void enqueue_rebuild_from_ref(md_handle* h, cudaStream_t s)
         cudaMemcpyAsync(cur[d], ref[d], nb, cudaMemcpyDeviceToDevice, s);
     }
     launch_step_a(P, 0, s, h->grid_atoms);
-    launch_cells(P, s, h->grid_atoms, h->grid_cells);
+    launch_cells(P, s, h->grid_atoms, h->grid_cells, h->sort_threads);
     launch_pair_list(P, s, h->list_blocks);
     // a force pass at the build positions trims the entries' masks as the step
     // of the original build did (its forces are discarded; the trimmed atoms
@@ -199,7 +199,7 @@ void enqueue_step(md_handle* h, cudaStream_t s)
 {
     int mode = STEP_KICK_DRIFT | STEP_ADVANCE | (h->cfg.cr_enabled ? STEP_CR : 0);
     launch_step_a(h->P, mode, s, h->grid_atoms);
-    launch_cells(h->P, s, h->grid_atoms, h->grid_cells);
+    launch_cells(h->P, s, h->grid_atoms, h->grid_cells, h->sort_threads);
     launch_pair_list(h->P, s, h->list_blocks);
     // external event nodes: the events are recorded on every graph replay
     if (h->cfg.profile) cudaEventRecordWithFlags(h->ev_pair0, s, cudaEventRecordExternal);
@@ -296,7 +296,7 @@ md_status capture_buffered_step(md_handle* h)
     CU(cudaGraphAddNode(&cn, g, deps, nullptr, nd, &cp));
     cudaGraph_t rebuild = cp.conditional.phGraph_out[0];
     CU(cudaStreamBeginCaptureToGraph(h->body_stream, rebuild, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    launch_cells(h->P, h->body_stream, h->grid_atoms, h->grid_cells);
+    launch_cells(h->P, h->body_stream, h->grid_atoms, h->grid_cells, h->sort_threads);
     launch_pair_list(h->P, h->body_stream, h->list_blocks);
     CU(cudaStreamEndCapture(h->body_stream, &rebuild));
     CU(cudaStreamUpdateCaptureDependencies(s, &cn, nullptr, 1, cudaStreamSetCaptureDependencies));
@@ -942,6 +942,8 @@ static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* 
     }
     h->grid_atoms = (N + 255) / 256;
     h->grid_cells = std::max(1, std::min(C, h->n_sm * 8));
+    // many cells per SM: small CTAs keep more (latency-bound) cells in flight
+    h->sort_threads = C >= 4 * h->n_sm ? 256 : 1024;
     {
         // the shape with the most resident warps per SM (8-warp blocks on a tie):
         // with many LJ type states the per-block table limits 8-warp blocks

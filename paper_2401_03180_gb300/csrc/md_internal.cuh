@@ -289,7 +289,7 @@ __device__ __forceinline__ void pack_slot(const Params& p, int slot, int i, cons
 
 // Launch helpers implemented in the .cu files.
 void launch_step_a(const Params& p, int mode, cudaStream_t s, int grid_atoms);
-void launch_cells(const Params& p, cudaStream_t s, int grid_atoms, int grid_cells);
+void launch_cells(const Params& p, cudaStream_t s, int grid_atoms, int grid_cells, int sort_threads);
 void launch_pair_list(const Params& p, cudaStream_t s, int blocks);
 void launch_pair_forces(const Params& p, cudaStream_t s, bool energy, int blocks, int warps);
 void launch_velocity_out(const Params& p, double* d_v_out, cudaStream_t s);

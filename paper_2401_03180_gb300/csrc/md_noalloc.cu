@@ -284,7 +284,7 @@ extern "C" md_status md_forces_noalloc(const md_forces_input* in, double* d_f, v
     const int warps = 8;
     const int blocks = n_sm * pair_max_blocks_per_sm(in->precision == MD_PREC_FP64, false, false, warps, nts);
     launch_step_a(P, 0, s, (n + 255) / 256);                           // grid and screening
-    launch_cells(P, s, (n + 255) / 256, std::max(1, std::min(g.cell_cap, n_sm * 8)));
+    launch_cells(P, s, (n + 255) / 256, std::max(1, std::min(g.cell_cap, n_sm * 8)), 1024);
     launch_pair_list(P, s, std::max(1, std::min(P.sc_cap, 4 * n_sm)));
     launch_pair_forces(P, s, false, blocks, warps);
     launch_force_out(P, d_f, s);
