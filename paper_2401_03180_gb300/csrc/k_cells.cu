@@ -86,55 +86,85 @@ __global__ void __launch_bounds__(256) k_cell_assign(Params p)
 }
 
 // Single-CTA scan over all cells: unpadded starts, padded starts, and the
-// super-cluster table (cell, first cluster, cluster count).
+// super-cluster table (cell, first cluster, cluster count).  Each warp owns a
+// contiguous run of cells and reads it 32 cells at a time (coalesced): a
+// first pass sums the run, a scan over the 32 warps gives each run its base,
+// and a second pass scans every 32-cell group with shuffles and writes.
+__device__ __forceinline__ void cell_sizes(int n, int& pad, int& nsc)
+{
+    pad = (n + kClusterSize - 1) / kClusterSize * kClusterSize;
+    nsc = (pad / kClusterSize + kSuperClusters - 1) / kSuperClusters;
+}
+
 __global__ void __launch_bounds__(kScanThreads) k_cell_scan(Params p)
 {
-    __shared__ int s_n[kScanThreads], s_p[kScanThreads], s_s[kScanThreads];
+    constexpr unsigned kFull = 0xffffffffu;
+    constexpr int kWarps = kScanThreads / 32;
+    __shared__ int s_tot[kWarps][3], s_base[kWarps][3];
     // the grid of this build stays with the list until the next build
     if (p.grid_b != p.grid)
         for (int r = threadIdx.x; r < p.n_rep; r += blockDim.x) p.grid_b[r] = p.grid[r];
     const int C = p.cell_cap_total;
-    const int t = threadIdx.x;
-    const int chunk = (C + kScanThreads - 1) / kScanThreads;
-    const int c0 = min(t * chunk, C), c1 = min(c0 + chunk, C);
-    int sn = 0, sp = 0, ss = 0;
-    for (int c = c0; c < c1; ++c) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int run = ((C + kWarps - 1) / kWarps + 31) & ~31;
+    const int c_lo = min(warp * run, C), c_hi = min(c_lo + run, C);
+    int tn = 0, tp = 0, ts = 0;
+    for (int c = c_lo + lane; c < c_hi; c += 32) {
         const int n = p.cell_count[c];
-        const int pad = (n + kClusterSize - 1) / kClusterSize * kClusterSize;
-        const int ncl = pad / kClusterSize;
-        sn += n;
-        sp += pad;
-        ss += (ncl + kSuperClusters - 1) / kSuperClusters;
+        int pad, nsc;
+        cell_sizes(n, pad, nsc);
+        tn += n; tp += pad; ts += nsc;
     }
-    s_n[t] = sn; s_p[t] = sp; s_s[t] = ss;
+    for (int o = 16; o; o >>= 1) {
+        tn += __shfl_xor_sync(kFull, tn, o);
+        tp += __shfl_xor_sync(kFull, tp, o);
+        ts += __shfl_xor_sync(kFull, ts, o);
+    }
+    if (lane == 0) { s_tot[warp][0] = tn; s_tot[warp][1] = tp; s_tot[warp][2] = ts; }
     __syncthreads();
-    // Hillis-Steele inclusive scan over the per-thread sums
-    for (int o = 1; o < kScanThreads; o <<= 1) {
-        int an = 0, ap = 0, as = 0;
-        if (t >= o) { an = s_n[t - o]; ap = s_p[t - o]; as = s_s[t - o]; }
-        __syncthreads();
-        s_n[t] += an; s_p[t] += ap; s_s[t] += as;
-        __syncthreads();
-    }
-    int on = s_n[t] - sn, op = s_p[t] - sp, os = s_s[t] - ss;
-    for (int c = c0; c < c1; ++c) {
-        const int n = p.cell_count[c];
-        const int pad = (n + kClusterSize - 1) / kClusterSize * kClusterSize;
-        const int ncl = pad / kClusterSize;
-        p.cell_start[c] = on;
-        p.cell_pstart[c] = op;
-        const int nsc = (ncl + kSuperClusters - 1) / kSuperClusters;
-        for (int k = 0; k < nsc; ++k) {
-            if (os + k < p.sc_cap) {
-                p.sc_cell[os + k] = c;
-                p.sc_first[os + k] = op / kClusterSize + k * kSuperClusters;
-                p.sc_ncl[os + k] = min(kSuperClusters, ncl - k * kSuperClusters);
+    if (warp == 0) {   // exclusive scan of the runs' totals
+        int v[3], inc[3];
+        for (int k = 0; k < 3; ++k) v[k] = inc[k] = s_tot[lane][k];
+        for (int o = 1; o < 32; o <<= 1)
+            for (int k = 0; k < 3; ++k) {
+                const int u = __shfl_up_sync(kFull, inc[k], o);
+                if (lane >= o) inc[k] += u;
             }
-        }
-        on += n; op += pad; os += nsc;
-        p.cell_count[c] = 0;     // ready for the next build
+        for (int k = 0; k < 3; ++k) s_base[lane][k] = inc[k] - v[k];
     }
-    if (t == kScanThreads - 1) {
+    __syncthreads();
+    int bn = s_base[warp][0], bp = s_base[warp][1], bs = s_base[warp][2];
+    for (int g0 = c_lo; g0 < c_hi; g0 += 32) {
+        const int c = g0 + lane;
+        const int n = c < c_hi ? p.cell_count[c] : 0;
+        int pad, nsc;
+        cell_sizes(n, pad, nsc);
+        int in_ = n, ip = pad, is = nsc;   // inclusive scans over the group
+        for (int o = 1; o < 32; o <<= 1) {
+            const int un = __shfl_up_sync(kFull, in_, o), up = __shfl_up_sync(kFull, ip, o), us = __shfl_up_sync(kFull, is, o);
+            if (lane >= o) { in_ += un; ip += up; is += us; }
+        }
+        if (c < c_hi) {
+            const int on = bn + in_ - n, op = bp + ip - pad, os = bs + is - nsc;
+            p.cell_start[c] = on;
+            p.cell_pstart[c] = op;
+            const int ncl = pad / kClusterSize;
+            for (int k = 0; k < nsc; ++k)
+                if (os + k < p.sc_cap) {
+                    p.sc_cell[os + k] = c;
+                    p.sc_first[os + k] = op / kClusterSize + k * kSuperClusters;
+                    p.sc_ncl[os + k] = min(kSuperClusters, ncl - k * kSuperClusters);
+                }
+            p.cell_count[c] = 0;     // ready for the next build
+        }
+        bn += __shfl_sync(kFull, in_, 31);
+        bp += __shfl_sync(kFull, ip, 31);
+        bs += __shfl_sync(kFull, is, 31);
+    }
+    if (threadIdx.x == 0) {
+        const int on = s_base[kWarps - 1][0] + s_tot[kWarps - 1][0];
+        const int op = s_base[kWarps - 1][1] + s_tot[kWarps - 1][1];
+        const int os = s_base[kWarps - 1][2] + s_tot[kWarps - 1][2];
         p.cell_start[C] = on;
         p.cell_pstart[C] = op;
         const bool over = op > p.slot_cap || os > p.sc_cap;
