@@ -1,6 +1,7 @@
 """GPU path vs the FP64 CPU oracle, through the C ABI (-m gpu).
 
-Tolerances (stated by the method's targets, and derived in the design doc):
+Tolerances (the method's stated targets; the FP64 ones from the fixed-point
+rounding of 2^-32 per contribution against forces of ~1e2-1e4 kJ/mol/nm):
   * charges, K-holes, electron counts, gas energy, event counts: bit-exact;
   * kappa (double, Eq. 3): bit-exact;
   * forces, mixed path: RMS relative error <= 1e-5; FP64 path: <= 1e-12;
