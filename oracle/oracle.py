@@ -20,8 +20,8 @@ What it computes, in the paper's order (arXiv 2401.03180):
   (Eq. 11) and LJ excluded inside a native fragment.
 * Sec. II.B, Eq. 12: Newton's equation, integrated with velocity Verlet.
 * Sec. II.A (optional, ``charge_table``): charges assigned from per-step
-  charge-state fractions of a CR calculation, "stochastically, so that they
-  match on average" -- read as quantile coupling: each atom keeps one uniform
+  charge-state fractions of a CR calculation, drawn at random so that they
+  reproduce the fractions on average -- read as quantile coupling: each atom keeps one uniform
   quantile u (Philox stream 2, counter (atom, 0, 2, 0), res53) and takes the
   smallest charge whose cumulative fraction of its species exceeds u.
 * Sec. II.B, Eqs. 9-10 (optional, a sample with a ``topology``): Morse bonds
