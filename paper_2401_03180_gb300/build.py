@@ -64,8 +64,26 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     deps.append(os.path.abspath(__file__))
     stamp = os.path.join(BUILD, "stamp")
     dg = _digest(deps)
-    if not force and os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == dg:
+
+    def current():
+        return os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == dg
+
+    if not force and current():
         return LIB
+    # one builder at a time (several ranks of one job may call this at once);
+    # the others find the library current once they hold the lock
+    import fcntl
+    with open(os.path.join(BUILD, "lock"), "w") as lk:
+        fcntl.flock(lk, fcntl.LOCK_EX)
+        try:
+            if not force and current():
+                return LIB
+            return _compile(dg, stamp, verbose, ptxas_info)
+        finally:
+            fcntl.flock(lk, fcntl.LOCK_UN)
+
+
+def _compile(dg: str, stamp: str, verbose: bool, ptxas_info: bool) -> str:
     nvcc = _nvcc()
 
     def one(src):
