@@ -7,6 +7,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <exception>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -538,6 +540,22 @@ md_status validate(const md_config* c, const md_system* s)
 
 void mdg::set_global_error(const std::string& msg) { g_init_error = msg; }
 
+// Runs one entry point's body; host memory exhaustion (or any other C++
+// exception) becomes a status instead of crossing the C ABI.
+template <class F>
+static md_status guarded(md_handle* h, F&& f)
+{
+    try {
+        return f();
+    } catch (const std::bad_alloc&) {
+        return fail(h, MD_ERR_OOM, "host memory exhausted");
+    } catch (const std::exception& e) {
+        return fail(h, MD_ERR_CUDA, std::string("internal error: ") + e.what());
+    } catch (...) {
+        return fail(h, MD_ERR_CUDA, "internal error");
+    }
+}
+
 // ============================================================================
 // C ABI
 // ============================================================================
@@ -551,7 +569,7 @@ const char* md_last_error(const md_handle* h)
     return h->err.c_str();
 }
 
-md_status md_pulse_table(const md_pulse* p, int n_pulses, double t_start_fs, double dt_fs, int n_steps,
+static md_status md_pulse_table_body(const md_pulse* p, int n_pulses, double t_start_fs, double dt_fs, int n_steps,
                          double* out)
 {
     md_handle* h = nullptr;
@@ -565,9 +583,15 @@ md_status md_pulse_table(const md_pulse* p, int n_pulses, double t_start_fs, dou
     return MD_OK;
 }
 
+md_status md_pulse_table(const md_pulse* p, int n_pulses, double t_start_fs, double dt_fs, int n_steps,
+                         double* out)
+{
+    return guarded(nullptr, [&]() { return md_pulse_table_body(p, n_pulses, t_start_fs, dt_fs, n_steps, out); });
+}
+
 static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* sys);
 
-md_status md_init(const md_config* cfg, const md_system* sys, md_handle** out)
+static md_status md_init_body(const md_config* cfg, const md_system* sys, md_handle** out)
 {
     if (out) *out = nullptr;
     if (!out) return fail(nullptr, MD_ERR_INVALID_ARG, "out is null");
@@ -582,6 +606,11 @@ md_status md_init(const md_config* cfg, const md_system* sys, md_handle** out)
     }
     *out = h;
     return MD_OK;
+}
+
+md_status md_init(const md_config* cfg, const md_system* sys, md_handle** out)
+{
+    return guarded(nullptr, [&]() { return md_init_body(cfg, sys, out); });
 }
 
 static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* sys)
@@ -1018,7 +1047,7 @@ static md_status check_replica(md_handle* h, int replica)
     return MD_OK;
 }
 
-md_status md_set_pulse(md_handle* h, int replica, const md_pulse* p, int n_pulses)
+static md_status md_set_pulse_body(md_handle* h, int replica, const md_pulse* p, int n_pulses)
 {
     md_status st = check_replica(h, replica);
     if (st != MD_OK) return st;
@@ -1035,7 +1064,12 @@ md_status md_set_pulse(md_handle* h, int replica, const md_pulse* p, int n_pulse
     return md_set_pulse_table(h, replica, tab.data(), h->cfg.max_steps);
 }
 
-md_status md_set_pulse_table(md_handle* h, int replica, const double* dF, int n_steps)
+md_status md_set_pulse(md_handle* h, int replica, const md_pulse* p, int n_pulses)
+{
+    return guarded(h, [&]() { return md_set_pulse_body(h, replica, p, n_pulses); });
+}
+
+static md_status md_set_pulse_table_body(md_handle* h, int replica, const double* dF, int n_steps)
 {
     md_status st = check_replica(h, replica);
     if (st != MD_OK) return st;
@@ -1054,7 +1088,12 @@ md_status md_set_pulse_table(md_handle* h, int replica, const double* dF, int n_
     return MD_OK;
 }
 
-md_status md_set_pulse_table_at(md_handle* h, int replica, int first_step, const double* dF, int n)
+md_status md_set_pulse_table(md_handle* h, int replica, const double* dF, int n_steps)
+{
+    return guarded(h, [&]() { return md_set_pulse_table_body(h, replica, dF, n_steps); });
+}
+
+static md_status md_set_pulse_table_at_body(md_handle* h, int replica, int first_step, const double* dF, int n)
 {
     md_status st = check_replica(h, replica);
     if (st != MD_OK) return st;
@@ -1070,6 +1109,11 @@ md_status md_set_pulse_table_at(md_handle* h, int replica, int first_step, const
     return MD_OK;
 }
 
+md_status md_set_pulse_table_at(md_handle* h, int replica, int first_step, const double* dF, int n)
+{
+    return guarded(h, [&]() { return md_set_pulse_table_at_body(h, replica, first_step, dF, n); });
+}
+
 md_status md_set_fluence_at(md_handle* h, int step, const double* dF)
 {
     if (!h) return fail(nullptr, MD_ERR_INVALID_ARG, "null handle");
@@ -1083,7 +1127,7 @@ md_status md_set_fluence_at(md_handle* h, int step, const double* dF)
     return MD_OK;
 }
 
-md_status md_set_charge_table(md_handle* h, int replica, const double* frac, int n_rows)
+static md_status md_set_charge_table_body(md_handle* h, int replica, const double* frac, int n_rows)
 {
     md_status st = check_replica(h, replica);
     if (st != MD_OK) return st;
@@ -1113,7 +1157,12 @@ md_status md_set_charge_table(md_handle* h, int replica, const double* frac, int
     return MD_OK;
 }
 
-md_status md_set_plasma_table(md_handle* h, int replica, const double* ne, const double* te, int n_steps)
+md_status md_set_charge_table(md_handle* h, int replica, const double* frac, int n_rows)
+{
+    return guarded(h, [&]() { return md_set_charge_table_body(h, replica, frac, n_rows); });
+}
+
+static md_status md_set_plasma_table_body(md_handle* h, int replica, const double* ne, const double* te, int n_steps)
 {
     md_status st = check_replica(h, replica);
     if (st != MD_OK) return st;
@@ -1132,6 +1181,11 @@ md_status md_set_plasma_table(md_handle* h, int replica, const double* ne, const
     CU(cudaGetLastError());
     CU(cudaStreamSynchronize(h->stream));
     return MD_OK;
+}
+
+md_status md_set_plasma_table(md_handle* h, int replica, const double* ne, const double* te, int n_steps)
+{
+    return guarded(h, [&]() { return md_set_plasma_table_body(h, replica, ne, te, n_steps); });
 }
 
 namespace {
@@ -1157,7 +1211,7 @@ md_status launch_steps(md_handle* h, int n)
 
 }  // namespace
 
-md_status md_step_async(md_handle* h, int n_steps)
+static md_status md_step_async_body(md_handle* h, int n_steps)
 {
     if (!h) return fail(nullptr, MD_ERR_INVALID_ARG, "null handle");
     if (h->poisoned) return fail(h, MD_ERR_BAD_STATE, "handle is in an error state: " + h->err);
@@ -1168,7 +1222,12 @@ md_status md_step_async(md_handle* h, int n_steps)
     return launch_steps(h, n_steps);
 }
 
-md_status md_sync(md_handle* h)
+md_status md_step_async(md_handle* h, int n_steps)
+{
+    return guarded(h, [&]() { return md_step_async_body(h, n_steps); });
+}
+
+static md_status md_sync_body(md_handle* h)
 {
     if (!h) return fail(nullptr, MD_ERR_INVALID_ARG, "null handle");
     if (h->poisoned) return fail(h, MD_ERR_BAD_STATE, "handle is in an error state: " + h->err);
@@ -1205,11 +1264,21 @@ md_status md_sync(md_handle* h)
     }
 }
 
-md_status md_step(md_handle* h, int n_steps)
+md_status md_sync(md_handle* h)
+{
+    return guarded(h, [&]() { return md_sync_body(h); });
+}
+
+static md_status md_step_body(md_handle* h, int n_steps)
 {
     md_status st = md_step_async(h, n_steps);
     if (st != MD_OK) return st;
     return md_sync(h);
+}
+
+md_status md_step(md_handle* h, int n_steps)
+{
+    return guarded(h, [&]() { return md_step_body(h, n_steps); });
 }
 
 // The copies of md_get_state that need no host-side reordering (velocities,
@@ -1259,7 +1328,7 @@ static void unpack_rep_state(md_handle* h, md_state* out, unsigned fields)
     }
 }
 
-md_status md_get_state(md_handle* h, md_state* out, unsigned fields)
+static md_status md_get_state_body(md_handle* h, md_state* out, unsigned fields)
 {
     if (!h) return fail(nullptr, MD_ERR_INVALID_ARG, "null handle");
     if (!out) return fail(h, MD_ERR_INVALID_ARG, "null state");
@@ -1319,7 +1388,12 @@ md_status md_get_state(md_handle* h, md_state* out, unsigned fields)
     return MD_OK;
 }
 
-md_status md_set_state(md_handle* h, const md_state* in, unsigned fields)
+md_status md_get_state(md_handle* h, md_state* out, unsigned fields)
+{
+    return guarded(h, [&]() { return md_get_state_body(h, out, fields); });
+}
+
+static md_status md_set_state_body(md_handle* h, const md_state* in, unsigned fields)
 {
     if (!h) return fail(nullptr, MD_ERR_INVALID_ARG, "null handle");
     if (!in) return fail(h, MD_ERR_INVALID_ARG, "null state");
@@ -1417,7 +1491,12 @@ md_status md_set_state(md_handle* h, const md_state* in, unsigned fields)
     return grown ? capture_graph(h) : MD_OK;
 }
 
-md_status md_rdf(md_handle* h, double r_max, int n_bins, int64_t* counts)
+md_status md_set_state(md_handle* h, const md_state* in, unsigned fields)
+{
+    return guarded(h, [&]() { return md_set_state_body(h, in, fields); });
+}
+
+static md_status md_rdf_body(md_handle* h, double r_max, int n_bins, int64_t* counts)
 {
     if (!h) return fail(nullptr, MD_ERR_INVALID_ARG, "null handle");
     if (!counts) return fail(h, MD_ERR_INVALID_ARG, "null counts");
@@ -1453,7 +1532,12 @@ md_status md_rdf(md_handle* h, double r_max, int n_bins, int64_t* counts)
     return MD_OK;
 }
 
-md_status md_fragments(md_handle* h, double r_frag, int mass_max, int charge_max, int32_t* label, int64_t* counts)
+md_status md_rdf(md_handle* h, double r_max, int n_bins, int64_t* counts)
+{
+    return guarded(h, [&]() { return md_rdf_body(h, r_max, n_bins, counts); });
+}
+
+static md_status md_fragments_body(md_handle* h, double r_frag, int mass_max, int charge_max, int32_t* label, int64_t* counts)
 {
     if (!h) return fail(nullptr, MD_ERR_INVALID_ARG, "null handle");
     if (!(r_frag > 0.0) || r_frag > h->cfg.r_cut) return fail(h, MD_ERR_INVALID_ARG, "r_frag must be in (0, r_cut]");
@@ -1512,7 +1596,12 @@ md_status md_fragments(md_handle* h, double r_frag, int mass_max, int charge_max
     return check_device_flags(h);
 }
 
-md_status md_get_probe_series(md_handle* h, int replica, int first, int n, int64_t* q_sum, double* d2_sum)
+md_status md_fragments(md_handle* h, double r_frag, int mass_max, int charge_max, int32_t* label, int64_t* counts)
+{
+    return guarded(h, [&]() { return md_fragments_body(h, r_frag, mass_max, charge_max, label, counts); });
+}
+
+static md_status md_get_probe_series_body(md_handle* h, int replica, int first, int n, int64_t* q_sum, double* d2_sum)
 {
     if (!h) return fail(nullptr, MD_ERR_INVALID_ARG, "null handle");
     if (!h->P.probe) return fail(h, MD_ERR_BAD_STATE, "probe records are off (md_config.probe_record = 0)");
@@ -1538,7 +1627,12 @@ md_status md_get_probe_series(md_handle* h, int replica, int first, int n, int64
     return MD_OK;
 }
 
-md_status md_probe_displacement(md_handle* h, int replica, int first, int n, const md_pulse* probe, int n_pulses,
+md_status md_get_probe_series(md_handle* h, int replica, int first, int n, int64_t* q_sum, double* d2_sum)
+{
+    return guarded(h, [&]() { return md_get_probe_series_body(h, replica, first, n, q_sum, d2_sum); });
+}
+
+static md_status md_probe_displacement_body(md_handle* h, int replica, int first, int n, const md_pulse* probe, int n_pulses,
                                 double* out)
 {
     if (!h) return fail(nullptr, MD_ERR_INVALID_ARG, "null handle");
@@ -1572,7 +1666,13 @@ md_status md_probe_displacement(md_handle* h, int replica, int first, int n, con
     return MD_OK;
 }
 
-md_status md_structure_factor(const int64_t* counts, int n_bins, double r_max, double n_a, double n_b, int same,
+md_status md_probe_displacement(md_handle* h, int replica, int first, int n, const md_pulse* probe, int n_pulses,
+                                double* out)
+{
+    return guarded(h, [&]() { return md_probe_displacement_body(h, replica, first, n, probe, n_pulses, out); });
+}
+
+static md_status md_structure_factor_body(const int64_t* counts, int n_bins, double r_max, double n_a, double n_b, int same,
                               double volume, double rho0, const double* q, int n_q, double* s)
 {
     if (!counts || !q || !s || n_bins < 1 || n_q < 1 || !(r_max > 0.0) || !(volume > 0.0) || !(rho0 >= 0.0))
@@ -1596,7 +1696,13 @@ md_status md_structure_factor(const int64_t* counts, int n_bins, double r_max, d
     return MD_OK;
 }
 
-md_status md_get_energies(md_handle* h, double* e_kin, double* e_pot, int64_t* n_pairs)
+md_status md_structure_factor(const int64_t* counts, int n_bins, double r_max, double n_a, double n_b, int same,
+                              double volume, double rho0, const double* q, int n_q, double* s)
+{
+    return guarded(nullptr, [&]() { return md_structure_factor_body(counts, n_bins, r_max, n_a, n_b, same, volume, rho0, q, n_q, s); });
+}
+
+static md_status md_get_energies_body(md_handle* h, double* e_kin, double* e_pot, int64_t* n_pairs)
 {
     if (!h) return fail(nullptr, MD_ERR_INVALID_ARG, "null handle");
     if (h->pending && !h->poisoned) {
@@ -1629,6 +1735,11 @@ md_status md_get_energies(md_handle* h, double* e_kin, double* e_pot, int64_t* n
     if (n_pairs) *n_pairs = np;
     h->last_pairs = np;
     return MD_OK;
+}
+
+md_status md_get_energies(md_handle* h, double* e_kin, double* e_pot, int64_t* n_pairs)
+{
+    return guarded(h, [&]() { return md_get_energies_body(h, e_kin, e_pot, n_pairs); });
 }
 
 md_status md_get_timing(md_handle* h, md_timing* out)
