@@ -346,9 +346,9 @@ def run_gpu(args, rank, world, local):
                      "flops_per_pair": FLOPS_PER_PAIR, "pair_kernel_ms": pair_ms,
                      "pair_kernel_share": pair_ms / (ms / K)},
         "e2e": e2e,
-        # per step: step kernel + force kernel (+ the bonded and probe kernels), and 5 more
-        # (4 cell kernels + list) in the steps whose list is rebuilt
-        "gpu_launches": (2 + (s.topology is not None) + bool(args.probe)) * K + 5 * int(tim.list_builds),
+        # per step: step kernel + force kernel (the bonded terms run inside it) (+ the
+        # probe kernel), and 5 more (4 cell kernels + list) in the steps whose list is rebuilt
+        "gpu_launches": (2 + bool(args.probe)) * K + 5 * int(tim.list_builds),
         "pair_list": {"skin_nm": args.skin, "builds": int(tim.list_builds), "steps": K,
                       "entries_last_build": int(tim.list_entries), "capacity": int(tim.list_capacity)},
         "clocks": clk.summary(),

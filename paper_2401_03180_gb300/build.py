@@ -26,7 +26,6 @@ SOURCES = {
     "k_cells.cu": [],
     "k_pair.cu": [],
     "md_noalloc.cu": [],
-    "k_bonded.cu": ["-fmad=false"],
     "k_probe.cu": ["-fmad=false"],
     "k_frag.cu": [],
 }

@@ -5,20 +5,19 @@
 //   angle i-j-k     V = c (k_theta / 2) (theta - theta_0)^2      (vertex j)
 //   c = max(0, 1 - zbar / N), zbar the summed charge of the term's N atoms (Eq. 9)
 //
-// One thread per term, grid-stride over the bonds and then the angles.  The
-// displacements are formed in FP64 from the FP64 positions (minimum image of
-// the replica's box), then evaluated in FP32 on the mixed path and FP64 on the
-// FP64 path.  Each atom's share is converted to 64-bit fixed point
-// (2^-32 kJ/mol/nm) and added with one integer atomic per component to the
-// same per-slot sums as the pair forces, so the totals are exact integer sums
-// whatever the order of the atomics, and the kernel may run before, after or
-// beside the pair kernel.
-#include <algorithm>
+// One thread per term.  The displacements are formed in FP64 from the FP64
+// positions (minimum image of the replica's box), then evaluated in FP32 on
+// the mixed path and FP64 on the FP64 path.  Each atom's share is converted
+// to 64-bit fixed point (2^-32 kJ/mol/nm) and added with one integer atomic
+// per component to the same per-slot sums as the pair forces, so the totals
+// are exact integer sums whatever the order of the atomics.  The force
+// kernel evaluates them in a prologue (k_pair.cu).
+#pragma once
 
 #include "md_internal.cuh"
 
 namespace mdg {
-namespace {
+namespace bonded {
 
 __device__ __forceinline__ float m_sqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double m_sqrt(double x) { return sqrt(x); }
@@ -140,36 +139,6 @@ __device__ void angle_term(const Params& p, const T* par, int t)
     }
 }
 
-template <typename T, bool ENERGY>
-__global__ void __launch_bounds__(256) k_bonded(Params p)
-{
-    // a failed cell build leaves slot_of undefined; a full list stops the step
-    if (*p.err & (ERR_CELL | ERR_LIST)) return;
-    const T* bp = nullptr;
-    const T* ap = nullptr;
-    if constexpr (sizeof(T) == 8) { bp = p.bond_pd; ap = p.angle_pd; }
-    else { bp = p.bond_pf; ap = p.angle_pf; }
-    const int nb = p.n_bonds, nt = p.n_bonds + p.n_angles;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
-        if (t < nb) bond_term<T, ENERGY>(p, bp, t);
-        else angle_term<T, ENERGY>(p, ap, t - nb);
-    }
-}
 
-}  // namespace
-
-void launch_bonded(const Params& p, cudaStream_t s, bool energy)
-{
-    const long long nt = (long long)p.n_bonds + p.n_angles;
-    if (nt <= 0) return;
-    const int blocks = (int)std::min<long long>((nt + 255) / 256, 152LL * 8);
-    if (p.precision == 0) {
-        if (energy) k_bonded<float, true><<<blocks, 256, 0, s>>>(p);
-        else k_bonded<float, false><<<blocks, 256, 0, s>>>(p);
-    } else {
-        if (energy) k_bonded<double, true><<<blocks, 256, 0, s>>>(p);
-        else k_bonded<double, false><<<blocks, 256, 0, s>>>(p);
-    }
-}
-
+}  // namespace bonded
 }  // namespace mdg

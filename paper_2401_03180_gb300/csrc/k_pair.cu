@@ -29,6 +29,7 @@
 //     exact integer sums, identical for every launch shape and schedule.
 #include <type_traits>
 
+#include "bonded_terms.cuh"
 #include "md_internal.cuh"
 
 namespace mdg {
@@ -457,6 +458,21 @@ __global__ void __launch_bounds__(FP64 ? 256 : 384, 2) k_pair(Params p)
     }
     __syncthreads();
     if (*p.err & (ERR_CELL | ERR_LIST)) return;
+
+    // bonded terms (Sec. II.B, Eqs. 9-10), one per thread over the grid before
+    // the chunks: their dependent loads overlap the other warps' pair work, and
+    // they add to the same fixed-point sums
+    if (p.n_bonds + p.n_angles > 0) {
+        const T* bp;
+        const T* ap;
+        if constexpr (FP64) { bp = p.bond_pd; ap = p.angle_pd; }
+        else { bp = p.bond_pf; ap = p.angle_pf; }
+        const int nb = p.n_bonds, nt = p.n_bonds + p.n_angles;
+        for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+            if (t < nb) bonded::bond_term<T, ENERGY>(p, bp, t);
+            else bonded::angle_term<T, ENERGY>(p, ap, t - nb);
+        }
+    }
 
     const int tx = lane & 7, ty = lane >> 3;
     const int n_chunks = min(p.counters[7], p.chunk_cap);

@@ -164,7 +164,6 @@ void enqueue_rebuild(md_handle* h, cudaStream_t s, bool energy)
     launch_pair_list(h->P, s, h->list_blocks);
     set_build_step(h, s, true);   // forces at the build positions: the list may be pruned
     launch_pair_forces(h->P, s, energy, h->pair_blocks, h->pair_warps);
-    launch_bonded(h->P, s, energy);
     launch_probe(h->P, s, true);
 }
 
@@ -193,7 +192,6 @@ void enqueue_rebuild_from_ref(md_handle* h, cudaStream_t s)
     launch_refresh(P, s);
     set_build_step(h, s, false);  // forces away from the build positions: no pruning
     launch_pair_forces(P, s, false, h->pair_blocks, h->pair_warps);
-    launch_bonded(P, s, false);
     launch_probe(P, s, true);
 }
 
@@ -207,7 +205,6 @@ void enqueue_step(md_handle* h, cudaStream_t s)
     if (h->cfg.profile) cudaEventRecordWithFlags(h->ev_pair0, s, cudaEventRecordExternal);
     launch_pair_forces(h->P, s, false, h->pair_blocks, h->pair_warps);
     if (h->cfg.profile) cudaEventRecordWithFlags(h->ev_pair1, s, cudaEventRecordExternal);
-    launch_bonded(h->P, s, false);
     launch_probe(h->P, s, false);
 }
 
@@ -305,7 +302,6 @@ md_status capture_buffered_step(md_handle* h)
     if (h->cfg.profile) cudaEventRecordWithFlags(h->ev_pair0, s, cudaEventRecordExternal);
     launch_pair_forces(h->P, s, false, h->pair_blocks, h->pair_warps);
     if (h->cfg.profile) cudaEventRecordWithFlags(h->ev_pair1, s, cudaEventRecordExternal);
-    launch_bonded(h->P, s, false);
     launch_probe(h->P, s, false);
     return MD_OK;
 }
@@ -1717,7 +1713,6 @@ static md_status md_get_energies_body(md_handle* h, double* e_kin, double* e_pot
     launch_refresh(h->P, h->stream);
     set_build_step(h, h->stream, false);
     launch_pair_forces(h->P, h->stream, true, h->pair_blocks, h->pair_warps);
-    launch_bonded(h->P, h->stream, true);
     launch_energy(h->P, h->d_ekin, h->d_epot, h->stream);
     CU(cudaGetLastError());
     std::vector<double> ek(R);

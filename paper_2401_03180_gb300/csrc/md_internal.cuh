@@ -299,7 +299,6 @@ void launch_philox(unsigned long long seed, const uint32_t* ctr, long long n, ui
 void launch_force_out(const Params& p, double* d_f_out, cudaStream_t s);
 void launch_refresh(const Params& p, cudaStream_t s);
 void launch_rdf(const Params& p, cudaStream_t s, int blocks, int n_bins, double r_max, unsigned long long* hist);
-void launch_bonded(const Params& p, cudaStream_t s, bool energy);
 void launch_probe(const Params& p, cudaStream_t s, bool rewrite);
 void launch_frag_link(const Params& p, cudaStream_t s, int blocks, double r_frag, int* parent);
 void launch_frag_init(const Params& p, cudaStream_t s, int* parent, int* mass, int* charge);
