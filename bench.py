@@ -538,7 +538,8 @@ def run_profile_case(args):
         wl.sample = W.with_topology(wl.sample)
     s = wl.sample
     g = M.IonisingMD(s, atom, precision=args.precision, r_cut=1.2, max_steps=max(wl.n_steps, args.warmup + args.steps + 1),
-                     t_start_fs=wl.t_start_fs, autotune=False, list_skin_nm=args.skin, screening=args.screening)
+                     t_start_fs=wl.t_start_fs, autotune=False, list_skin_nm=args.skin, screening=args.screening,
+                     langevin_g=args.langevin if args.langevin > 0 else None)
     g.set_pulse(wl.pulses[0])
     g.step(args.warmup)
     g.step(args.steps)
