@@ -177,12 +177,8 @@ __device__ __forceinline__ void pair(const typename Prec<FP64>::S4& xi, int row_
                      : xi.w * P::fma(qj, rinv, qjk);
     const T S = P::fma(lj6, E1, Cc);
     T fs = S * (rinv2 * e);                     // F(r)/r
-    // inside some ion's transition radius: each ion's -phi' from its own form.
-    // The warp vote makes the block a real branch, skipped by whole warps,
-    // rather than predicated code issued for every pair (every lane of the
-    // warp calls this function together)
-    const bool inner = HYB && in && r2 < ha.rpm2;
-    if (HYB && __any_sync(0xffffffffu, inner) && inner) {
+    if (HYB && in && r2 < ha.rpm2) {
+        // inside some ion's transition radius: each ion's -phi' from its own form
         const HybQ& Ri = ha.rows[(int)ha.qi];
         const HybQ& Rj = ha.rows[(int)qj];
         const T rpi = FP64 ? T(Ri.rp) : T(Ri.rpf), rpj = FP64 ? T(Rj.rp) : T(Rj.rpf);
