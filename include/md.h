@@ -367,7 +367,13 @@ md_status md_step_async(md_handle* h, int n_steps);
 md_status md_sync(md_handle* h);
 
 /* Copy the requested fields (MD_FIELD_* mask) to caller buffers, in the
- * original atom order.  Synchronises the handle's stream. */
+ * original atom order.  Synchronises the handle's stream.  After steps
+ * enqueued by md_step_async, and without MD_FIELD_X or MD_FIELD_XLIST (which
+ * are reordered on the host), the copies and the steps' status are read back
+ * together in one host round trip (use pinned buffers for asynchronous
+ * copies); if those steps raised a flag (a list that needs more room, an
+ * error), md_sync's handling runs first and the fields are copied again.
+ * Errors: those of md_sync, INVALID_ARG (a requested buffer is NULL), CUDA. */
 md_status md_get_state(md_handle* h, md_state* out, unsigned fields);
 
 /* Overwrite x, v, q, h, plasma counters and/or the step counter (mask);
