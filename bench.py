@@ -184,6 +184,10 @@ def profiled_traffic():
     return float(m.group(1)), h.group(1)
 
 
+def sms_count(torch):
+    return torch.cuda.get_device_properties(0).multi_processor_count
+
+
 def fp32_peak_tflops(torch):
     props = torch.cuda.get_device_properties(0)
     sms = props.multi_processor_count
@@ -287,6 +291,17 @@ def run_gpu(args, rank, world, local):
     state64 = g64.get_state(M.MD_FIELD_PLASMA | M.MD_FIELD_Q | M.MD_FIELD_X | M.MD_FIELD_F)
     g64.close()
     value64 = world * n_atoms * k64 / (ms64 / 1e3)
+    # the FP64 force kernel's own time: a short run with event nodes around it
+    g64p = make("fp64", profile=True)
+    for _ in range(min(W_, 3)):
+        g64p.step(1)
+    g64p.reset_timing()
+    timed_steps(g64p, min(k64, 30))
+    t64 = g64p.timing()
+    g64p.close()
+    pair_ms64 = t64.pair_ms / max(t64.pair_launches, 1)
+    peak64 = sms_count(torch) * 2 * 2 * fp32_peak_tflops(torch)[2] * 1e6 / 1e12   # 2 FP64 lanes per SM, FMA = 2
+    achieved64 = FLOPS_PER_PAIR * pairs / (pair_ms64 / 1e3) / 1e12
 
     # ---- end to end through the C ABI, host buffers ----
     e2e = None
@@ -339,7 +354,12 @@ def run_gpu(args, rank, world, local):
         "pair_interactions_per_s": world * pairs * K / (ms / 1e3),
         "pairs_per_step": pairs,
         "fp64_gpu": {"value": value64, "unit": UNIT, "steps": k64, "ms_per_step": ms64 / k64,
-                     "speedup_mixed_vs_fp64": value / value64},
+                     "speedup_mixed_vs_fp64": value / value64,
+                     "roofline": {"bound": "fp64", "kernel": "k_pair (FP64 path)", "achieved": achieved64,
+                                  "peak": peak64, "unit": "TFLOP/s", "frac": achieved64 / peak64,
+                                  "peak_basis": "SMs x 2 FP64 lanes x 2 x max SM clock (GB300 issues FP64 "
+                                                "at 2 lanes per SM per clock)",
+                                  "pair_kernel_ms": pair_ms64}},
         "roofline": {"bound": "alu", "kernel": "k_pair (FP32 FMA pipe)", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz (max SM clock)",
