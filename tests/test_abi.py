@@ -135,3 +135,37 @@ def test_bonded_topology_is_validated_on_the_host(libpath):
     for topo, msg in cases:
         st, err = _init_status(dataclasses.replace(base, topology=topo))
         assert st == M.MD_ERR_INVALID_ARG and msg in err, (st, err)
+
+
+def test_system_is_validated_on_the_host(libpath):
+    """Degenerate and malformed samples are refused with MD_ERR_INVALID_ARG
+    before any device work: no atoms, a replica without atoms, offsets that do
+    not span the atoms, a species or charge outside the tables, non-finite
+    coordinates and a periodic box shorter than three interaction ranges."""
+    import dataclasses
+    base = W.concat([W.methane_cluster(3, 1), W.methane_cluster(2, 2)])
+    n = base.n_atoms
+    cases = []
+    cases.append((dataclasses.replace(base, x=base.x[:0], v=base.v[:0], species=base.species[:0],
+                                      fragment=base.fragment[:0], q0=base.q0[:0],
+                                      replica_offset=np.array([0, 0], np.int32), seed=base.seed[:1],
+                                      box=base.box[:1], volume=base.volume[:1]), "n_atoms must be >= 1"))
+    off = base.replica_offset.copy(); off[1] = 0
+    cases.append((dataclasses.replace(base, replica_offset=off), "at least one atom"))
+    off = base.replica_offset.copy(); off[-1] = n - 1
+    cases.append((dataclasses.replace(base, replica_offset=off), "from 0 to n_atoms"))
+    sp = base.species.copy(); sp[4] = 200
+    cases.append((dataclasses.replace(base, species=sp), "species index out of range"))
+    q = base.q0.copy(); q[1] = W.Z[base.species[1]] + 1
+    cases.append((dataclasses.replace(base, q0=q), "q0 above Z"))
+    x = base.x.copy(); x[2, 1] = np.nan
+    cases.append((dataclasses.replace(base, x=x), "non-finite"))
+    v = base.v.copy(); v[3, 0] = np.inf
+    cases.append((dataclasses.replace(base, v=v), "non-finite"))
+    vol = base.volume.copy(); vol[1] = 0.0
+    cases.append((dataclasses.replace(base, volume=vol), "volume must be > 0"))
+    box = base.box.copy(); box[0] = [3.0, 3.0, 3.0]           # r_cut 1.2 + skin: 3.6 nm needed
+    cases.append((dataclasses.replace(base, box=box), "periodic box edges"))
+    for s, msg in cases:
+        st, err = _init_status(s)
+        assert st == M.MD_ERR_INVALID_ARG and msg in err, (msg, st, err)
