@@ -326,9 +326,13 @@ __device__ void finalize_step(const Params& p, int mode, long long next, unsigne
 
 // SETCOND: the Verlet-buffered variant that decides the rebuild and sets the
 // graph condition (ncu does not profile kernels that can set one, so the
-// every-step variant is a separate instantiation).
-template <bool SETCOND>
-__global__ void __launch_bounds__(kStepThreads) k_step_a(Params p, int mode)
+// every-step variant is a separate instantiation).  MINB: resident blocks per
+// SM the registers are sized for; 16 (64 registers) for grids of many blocks
+// per SM, where the FP64 pipe binds and more resident warps pay (2 M-atom
+// droplet: 3.80 -> 3.71 ms per step); 10 (96 registers) for small grids, which
+// are latency-bound (water box: 108.4 against 110.9 us per step with 16)
+template <bool SETCOND, int MINB>
+__global__ void __launch_bounds__(kStepThreads, MINB) k_step_a(Params p, int mode)
 {
     __shared__ long long s_acc[kRepWindow][6];
     __shared__ unsigned long long s_bmin[kRepWindow][3], s_bmax[kRepWindow][3];
@@ -674,16 +678,29 @@ __global__ void __launch_bounds__(256) k_step_fin(Params p, int mode)
     if (tid == 0) finalize_step<SETCOND>(p, mode, next, SETCOND ? __ldcg(p.maxd2) : 0u);
 }
 
+static int sm_count()
+{
+    int d = 0, n = 0;
+    if (cudaGetDevice(&d) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d) != cudaSuccess)
+        return 1;
+    return n > 0 ? n : 1;
+}
+
 void launch_step_a(const Params& p, int mode, cudaStream_t s, int grid_atoms)
 {
     (void)grid_atoms;
+    static const int n_sm = sm_count();
+    constexpr int kWide = 16;   // MINB of the variant for grids of many blocks per SM
     const int blocks = (p.n_atoms + kStepAtoms - 1) / kStepAtoms;
     const int fin_blocks = (p.n_rep * 32 + 255) / 256;
+    const bool wide = blocks >= kWide * n_sm;
     if (mode & STEP_SETCOND) {
-        k_step_a<true><<<blocks, kStepThreads, 0, s>>>(p, mode);
+        if (wide) k_step_a<true, kWide><<<blocks, kStepThreads, 0, s>>>(p, mode);
+        else k_step_a<true, 10><<<blocks, kStepThreads, 0, s>>>(p, mode);
         if (p.n_rep > kInlineReps) k_step_fin<true><<<fin_blocks, 256, 0, s>>>(p, mode);
     } else {
-        k_step_a<false><<<blocks, kStepThreads, 0, s>>>(p, mode);
+        if (wide) k_step_a<false, kWide><<<blocks, kStepThreads, 0, s>>>(p, mode);
+        else k_step_a<false, 10><<<blocks, kStepThreads, 0, s>>>(p, mode);
         if (p.n_rep > kInlineReps) k_step_fin<false><<<fin_blocks, 256, 0, s>>>(p, mode);
     }
 }
