@@ -367,8 +367,10 @@ def run_gpu(args, rank, world, local):
                      "pair_kernel_share": pair_ms / (ms / K)},
         "e2e": e2e,
         # per step: step kernel + force kernel (the bonded terms run inside it) (+ the
-        # probe kernel), and 5 more (4 cell kernels + list) in the steps whose list is rebuilt
-        "gpu_launches": (2 + bool(args.probe)) * K + 5 * int(tim.list_builds),
+        # probe kernel; + the warp-per-replica reduction above 4 replicas, the step
+        # kernel's inline limit), and 5 more (4 cell kernels + list) in the steps whose
+        # list is rebuilt
+        "gpu_launches": (2 + bool(args.probe) + (s.n_replicas > 4)) * K + 5 * int(tim.list_builds),
         "pair_list": {"skin_nm": args.skin, "builds": int(tim.list_builds), "steps": K,
                       "entries_last_build": int(tim.list_entries), "capacity": int(tim.list_capacity)},
         "clocks": clk.summary(),
