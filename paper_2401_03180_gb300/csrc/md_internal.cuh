@@ -38,6 +38,7 @@ enum : unsigned {
     ERR_CELL = 4u,
     ERR_TABLE_END = 8u,
     ERR_LIST = 16u,             // cluster-pair list capacity exceeded
+    ERR_INPUT = 32u,            // a species index or charge out of range in device-side input
 };
 
 // Cluster-pair list entry: x = j-cluster, y = half-shell index of the

@@ -95,7 +95,12 @@ md_status fail(md_status s, const std::string& m)
 }
 
 // Reset of the per-call state and the copy of the caller's atoms into the
-// scratch layout (structure-of-arrays, one replica).
+// scratch layout (structure-of-arrays, one replica).  The species and charge
+// arrays live on the device, so they are checked here: an atom whose species
+// index is not below n_species or whose charge exceeds its species' Z raises
+// ERR_INPUT (the call then returns MD_ERR_INVALID_ARG) and is stored as a
+// neutral atom of species 0, so that every later table lookup stays in bounds.
+// The error word is cleared on the stream before this kernel runs.
 __global__ void k_noalloc_prepare(Params p, const double* __restrict__ x, const uint8_t* __restrict__ sp,
                                   const uint8_t* __restrict__ q, const int32_t* __restrict__ fr, int slot_cap,
                                   int cell_cap)
@@ -107,8 +112,14 @@ __global__ void k_noalloc_prepare(Params p, const double* __restrict__ x, const 
         p.y[t] = x[3 * t + 1];
         p.z[t] = x[3 * t + 2];
         p.vx[t] = 0.0; p.vy[t] = 0.0; p.vz[t] = 0.0;
-        p.species[t] = sp[t];
-        p.q[t] = q[t];
+        int st = sp[t], qt = q[t];
+        if (st >= p.n_species || qt > p.zs[st]) {
+            atomicOr(p.err, ERR_INPUT);
+            st = 0;
+            qt = 0;
+        }
+        p.species[t] = (uint8_t)st;
+        p.q[t] = (uint8_t)qt;
         p.h[t] = 0;
         p.frag[t] = fr[t];
         p.rep[t] = 0;
@@ -129,7 +140,6 @@ __global__ void k_noalloc_prepare(Params p, const double* __restrict__ x, const 
     if (t == 0) {
         for (int k = 0; k < 8; ++k) p.counters[k] = 0;
         p.counters[1] = n;
-        *p.err = 0u;
         *p.step = 0;
         *p.kick_full = 0;
         *p.pair_count = 0;
@@ -276,6 +286,7 @@ extern "C" md_status md_forces_noalloc(const md_forces_input* in, double* d_f, v
     NA_CU(cudaMemcpyAsync(B + kL.rep_off, rep_off, sizeof(rep_off), cudaMemcpyHostToDevice, s));
     NA_CU(cudaMemcpyAsync(B + kL.grid, &g, sizeof(Grid), cudaMemcpyHostToDevice, s));
 
+    NA_CU(cudaMemsetAsync(P.err, 0, sizeof(unsigned), s));
     const int span = std::max(P.slot_cap, std::max(n, g.cell_cap));
     k_noalloc_prepare<<<(span + 255) / 256, 256, 0, s>>>(P, in->d_x, in->d_species, in->d_q, in->d_fragment,
                                                           P.slot_cap, g.cell_cap);
@@ -293,6 +304,8 @@ extern "C" md_status md_forces_noalloc(const md_forces_input* in, double* d_f, v
     NA_CU(cudaMemcpyAsync(&h_err, P.err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     NA_CU(cudaStreamSynchronize(s));
 #undef NA_CU
+    if (h_err & ERR_INPUT)
+        return fail(MD_ERR_INVALID_ARG, "md_forces_noalloc: a species index >= n_species or a charge > Z in the device input");
     if (h_err & ERR_OVERFLOW) return fail(MD_ERR_FIXED_OVERFLOW, "force beyond the 64-bit fixed-point range");
     if (h_err & ERR_NONFINITE) return fail(MD_ERR_NONFINITE, "non-finite input position");
     if (h_err & ERR_CELL) return fail(MD_ERR_CELL_OVERFLOW, "cell-list capacity exceeded");

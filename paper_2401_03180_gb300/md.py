@@ -27,6 +27,7 @@ MD_FIELD_X, MD_FIELD_V, MD_FIELD_F, MD_FIELD_Q, MD_FIELD_H = 1, 2, 4, 8, 16
 MD_FIELD_PLASMA, MD_FIELD_COUNTS, MD_FIELD_STEP, MD_FIELD_XLIST, MD_FIELD_ALL = 32, 64, 128, 256, 511
 MD_MAX_SPECIES = 8
 MD_NOALLOC_MAX_ATOMS = 16384
+MD_NOALLOC_MAX_CELLS = 4096
 COULOMB_F = 138.935458
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -140,6 +141,7 @@ def lib():
             L.md_finalize.restype = None
             L.md_pulse_table.argtypes = [C.POINTER(MDPulse), C.c_int, C.c_double, C.c_double, C.c_int, P]
             L.md_philox.argtypes = [C.c_uint64, P, C.c_int64, P, P]
+            L.md_fma_peak.argtypes = [C.c_int, C.c_int64, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), P]
             L.md_forces_noalloc.argtypes = [C.POINTER(MDForcesInput), P, P]
             L.md_version.restype = C.c_char_p
             _lib = L
@@ -295,6 +297,14 @@ def md_pulse_table(pulses, t_start_fs: float, dt_fs: float, n_steps: int) -> np.
     arr = _pulses(pulses)
     _check(lib().md_pulse_table(arr, len(pulses), float(t_start_fs), float(dt_fs), int(n_steps), _p(out)))
     return out
+
+
+def md_fma_peak(precision: int, iters: int, blocks_per_sm: int = 4, stream_ptr: int = 0):
+    """Measured FMA-pipe throughput of the current device: (flop/s, kernel seconds)."""
+    f, s = C.c_double(0.0), C.c_double(0.0)
+    _check(lib().md_fma_peak(int(precision), C.c_int64(iters), int(blocks_per_sm), C.byref(f), C.byref(s),
+                             C.c_void_p(stream_ptr)))
+    return f.value, s.value
 
 
 def md_philox(seed: int, d_ctr4_ptr: int, n: int, d_out_ptr: int, stream_ptr: int = 0):

@@ -40,6 +40,7 @@ def test_exports_every_declared_symbol(libpath):
     assert M.md_version().startswith("gb300")
     hdr = open(HEADER).read()
     assert int(re.search(r"#define MD_NOALLOC_MAX_ATOMS (\d+)", hdr).group(1)) == M.MD_NOALLOC_MAX_ATOMS
+    assert int(re.search(r"#define MD_NOALLOC_MAX_CELLS (\d+)", hdr).group(1)) == M.MD_NOALLOC_MAX_CELLS
 
 
 def test_struct_layout_matches_c(tmp_path):
