@@ -631,7 +631,7 @@ class OracleMD:
                  kappa_fixed=-1.0, te_floor_ev=1.0, t_start_fs=0.0, pulses=None,
                  dF_table=None, prescribed=None, n_steps_max=0, coulomb_f=COULOMB_F,
                  sigma0=None, eps0=None, mass=None, threads=None, screening="debye", langevin_g=None,
-                 charge_table=None):
+                 charge_table=None, with_forces=True):
         from paper_2401_03180_gb300 import workloads as W
         self.s = sample
         self.a = atomic
@@ -691,7 +691,16 @@ class OracleMD:
         self.e_gas = np.zeros(self.R, dtype=np.int64)
         self.counts = np.zeros((self.R, 4), dtype=np.int64)
         self.scal = [self._scalars(r, 0) for r in range(self.R)]
-        self.F, self.U, self.n_pairs = self.forces()
+        # with_forces=False: the charge dynamics alone.  Charges, K holes and the
+        # electron gas never read positions, velocities or forces (Sec. II.A: the
+        # gas is homogeneous, its volume fixed), so step() then advances exactly
+        # the charge sequence of the full step without the all-pairs forces; for
+        # systems far too large for all pairs.  Positions stay at their input.
+        self.with_forces = bool(with_forces)
+        if self.with_forces:
+            self.F, self.U, self.n_pairs = self.forces()
+        else:
+            self.F, self.U, self.n_pairs = np.zeros((self.n, 3)), np.zeros(self.n), 0
         # probe records (Eq. 17): per replica, the summed charge and squared
         # displacement from the initial positions of each species, after each step
         self.x0 = self.x.copy()
@@ -831,20 +840,29 @@ class OracleMD:
             self.h[sl] = 0
         return dNe, np.zeros(R, dtype=np.int64), cnt
 
-    def step(self):
-        n = self.step_index
-        hd = self.hdtm[self.sp][:, None]
-        self.v += hd * self.F
-        if self.langevin_g is not None:
-            self.langevin(n)
-        self.x += self.dt * self.v
-        self._wrap()
+    def charge_update(self, n):
+        """Steps 3-4 of step n: the charge update with the plasma scalars of
+        step n - 1, then the reduction to the scalars of step n + 1."""
         if self.cr_enabled:
             dNe, dE, cnt = self.table_step(n) if self.charge_table is not None else self.cr_step(n)
             self.n_e += dNe
             self.e_gas = np.maximum(self.e_gas + dE, 0)
             self.counts += cnt
         self.scal = [self._scalars(r, n + 1) for r in range(self.R)]
+
+    def step(self):
+        n = self.step_index
+        if not self.with_forces:
+            self.charge_update(n)
+            self.step_index = n + 1
+            return
+        hd = self.hdtm[self.sp][:, None]
+        self.v += hd * self.F
+        if self.langevin_g is not None:
+            self.langevin(n)
+        self.x += self.dt * self.v
+        self._wrap()
+        self.charge_update(n)
         self.F, self.U, self.n_pairs = self.forces()
         self.v += hd * self.F
         self.step_index = n + 1

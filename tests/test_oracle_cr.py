@@ -276,3 +276,34 @@ def test_cr_is_counter_based(oracle_mod):
     for k in range(20):
         c.step(k)
     assert not np.array_equal(a.md.q, c.md.q)
+
+
+@pytest.mark.parametrize("mode", ["rates", "table"])
+def test_charges_only_equals_the_full_step(oracle_mod, mode):
+    """OracleMD(with_forces=False) skips the all-pairs forces: charges, K holes
+    and the electron gas never read positions (Sec. II.A, homogeneous gas of
+    fixed volume), so its charge sequence must be the full step's, bit for bit,
+    on a batch of replicas with their own pulses and seeds, while the full run
+    moves (and Coulomb-explodes) the atoms."""
+    reps = [W.methane_cluster(n, seed=70 + k) for k, n in enumerate((30, 55, 12, 41, 23, 66))]
+    for k, r in enumerate(reps):
+        r.seed[:] = 3000 + 17 * k
+    s = W.concat(reps)
+    atom = W.atomic_data(8.0, pi_scale=2000.0, ci_scale=20.0, rec_scale=500.0)
+    pulses = [[W.Pulse(8.0, 10.0, f, 0.0)] for f in (1e12, 3e11, 2e12, 5e11, 1.5e12, 8e11)]
+    kw = dict(r_cut=1.2, t_start_fs=-4.0, pulses=pulses, n_steps_max=120)
+    if mode == "table":
+        kw["charge_table"] = np.stack([W.charge_fraction_table(p, -4.0, 0.05, 121, mean_final=1.0 + 0.4 * k)
+                                       for k, p in enumerate(pulses)])
+    full = oracle_mod.OracleMD(s, atom, **kw)
+    fast = oracle_mod.OracleMD(s, atom, with_forces=False, **kw)
+    x0 = full.x.copy()
+    for n in range(100):
+        full.step()
+        fast.step()
+        assert np.array_equal(fast.q, full.q) and np.array_equal(fast.h, full.h), n
+        assert np.array_equal(fast.n_e, full.n_e) and np.array_equal(fast.e_gas, full.e_gas), n
+        assert np.array_equal(fast.counts, full.counts), n
+        assert [sc["kappa"] for sc in fast.scal] == [sc["kappa"] for sc in full.scal], n
+    assert fast.q.any() and np.abs(full.x - x0).max() > 1e-3
+    assert np.array_equal(fast.x, x0)
