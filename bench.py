@@ -2,11 +2,15 @@
 """Benchmark of the GB300 ionising-MD hot path.
 
 One step = one full timestep of the method on the whole sample: kick/drift,
-stochastic charge update and free-electron reduction, cell-list rebuild,
-screened pair forces.  The default workload is the 30,000-atom periodic
-water box irradiated by a 6 keV, 25 fs, 5e12 ph/um^2 pulse, 1,000 steps of
-50 as (10 warm-up + 990 timed), mixed precision (FP32 pairs with 64-bit
-fixed-point sums, FP64 integrator and charge update).
+stochastic charge update and free-electron reduction, cell-list rebuild
+(when the Verlet-buffered list is used up), screened pair forces.  The
+default workload is the largest single-GPU one: the 2,000,000-atom water
+droplet (vacuum) irradiated by an 8 keV, 20 fs, 1e13 ph/um^2 pulse, 800
+steps of 50 as from -1 FWHM.  The timed window of K steps sits at the middle
+of that run, on the pulse peak: the state is advanced there by untimed steps
+and checkpointed, and every timed arm (mixed, FP64, end-to-end) restores the
+checkpoint, runs W warm-up steps and times K.  Mixed precision: FP32 pairs
+with 64-bit fixed-point sums, FP64 integrator and charge update.
 
 Prints ONE JSON line (rank 0).  Multi-GPU (torchrun): every rank runs an
 independent replica of the workload (weak scaling, no collective on the data
@@ -38,18 +42,21 @@ UNIT = "atom-steps/s"
 FLOPS_PER_PAIR = 41          # FP32 operations per in-cutoff pair in the pair kernel (FMA = 2)
 L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
 SKIN_NM = 0.08               # Verlet buffer of the pair list (measured choice for the water box)
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_pair_c2_water_30k.md")
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=990)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="c2_water_30k")
+    ap.add_argument("--workload", default="c5_droplet_2m")
     ap.add_argument("--scale", type=float, default=1.0)
-    ap.add_argument("--fp64-steps", type=int, default=100)
+    ap.add_argument("--fp64-steps", type=int, default=30)
+    ap.add_argument("--window", default="centre", choices=["centre", "start"],
+                    help="where the timed steps sit in the configured run: its middle (the pulse peak; "
+                         "reached by untimed steps) or its first steps")
+    ap.add_argument("--no-peaks", action="store_true", help="skip the FMA-pipe peak measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
@@ -171,12 +178,13 @@ def kernel_source_digest():
     return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per pair-kernel launch from the committed ncu summary, if
-    the kernel source is unchanged since the capture."""
-    if not os.path.exists(PROFILE_SUMMARY):
+def profiled_traffic(workload):
+    """DRAM bytes per pair-kernel launch of this workload from the committed
+    ncu summary, if the kernel source is unchanged since the capture."""
+    path = os.path.join(ROOT, "profiles", f"k_pair_{workload}.md") if workload else None
+    if not path or not os.path.exists(path):
         return None, None
-    txt = open(PROFILE_SUMMARY).read()
+    txt = open(path).read()
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
     h = re.search(r"k_pair_source_sha256_16:\s*([0-9a-f]+)", txt)
     if not m or not h or h.group(1) != kernel_source_digest():
@@ -189,6 +197,7 @@ def sms_count(torch):
 
 
 def fp32_peak_tflops(torch):
+    """FP32 peak from unit counts: SMs x 128 FP32 lanes x 2 x the maximum SM clock."""
     props = torch.cuda.get_device_properties(0)
     sms = props.multi_processor_count
     max_mhz = 2070.0
@@ -198,6 +207,34 @@ def fp32_peak_tflops(torch):
     except Exception:
         pass
     return sms * 128 * 2 * max_mhz * 1e6 / 1e12, sms, max_mhz
+
+
+def measured_fma_peaks(M, local):
+    """FP32 and FP64 FMA-pipe throughput of this device (md_fma_peak, an FMA
+    counted as two operations), in TFLOP/s: burst = best of three ~50 ms
+    launches; sustained = one ~1 s launch, with the SM clocks sampled during it."""
+    out = {}
+    for name, prec in (("fp32", M.MD_PREC_MIXED), ("fp64", M.MD_PREC_FP64)):
+        M.md_fma_peak(prec, 64)                              # load the kernel
+        f, sec = M.md_fma_peak(prec, 256)
+        it50 = max(int(256 * 0.05 / max(sec, 1e-6)), 1)      # ~50 ms per launch
+        burst = max(M.md_fma_peak(prec, it50)[0] for _ in range(3))
+        with ClockSampler(local) as clk:
+            sus, sec_s = M.md_fma_peak(prec, it50 * 20)
+        out[name] = {"burst_tflops": burst / 1e12, "sustained_tflops": sus / 1e12,
+                     "sustained_s": sec_s, "clocks_sustained": clk.summary()}
+    return out
+
+
+CKPT_KEYS = ("x", "v", "q", "h", "n_e", "e_gas_mev", "event_counts", "x_list")
+
+
+def window_start(n_steps, steps, warmup, where):
+    """Untimed steps before the warm-up: the timed window then sits at the
+    middle of the configured run (the pulse peak of every workload)."""
+    if where == "start":
+        return 0
+    return max(0, (n_steps - steps) // 2 - warmup)
 
 
 def run_gpu(args, rank, world, local):
@@ -218,14 +255,16 @@ def run_gpu(args, rank, world, local):
     s = wl.sample
     n_atoms = s.n_atoms
     W_, K = args.warmup, args.steps
-    max_steps = max(wl.n_steps, W_ + K + 1)
+    s0 = window_start(wl.n_steps, K, W_, args.window)
+    max_steps = max(wl.n_steps, s0 + W_ + K + 1)
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    peaks = None if args.no_peaks else measured_fma_peaks(M, local)
 
-    def make(prec, profile):
+    def make(prec, profile, autotune=None):
         g = M.IonisingMD(s, atom, precision=prec, r_cut=1.2, dt_ps=5e-5, max_steps=max_steps,
-                         t_start_fs=wl.t_start_fs, autotune=(prec == "mixed"), profile=profile,
-                         list_skin_nm=args.skin, screening=args.screening,
+                         t_start_fs=wl.t_start_fs, autotune=(prec == "mixed") if autotune is None else autotune,
+                         profile=profile, list_skin_nm=args.skin, screening=args.screening,
                          langevin_g=args.langevin if args.langevin > 0 else None,
                          charge_mode="table" if args.charge_table else "rates", probe_record=args.probe)
         for r in range(s.n_replicas):
@@ -233,6 +272,20 @@ def run_gpu(args, rank, world, local):
             if args.charge_table:
                 g.set_charge_table(W.charge_fraction_table(wl.pulses[r], wl.t_start_fs, 5e-5 * 1000.0, max_steps + 1),
                                    replica=r)
+        return g
+
+    # ---- untimed advance to the window, one checkpoint for every arm ----
+    ckpt = None
+    if s0 > 0:
+        g0 = make("mixed", profile=False, autotune=False)
+        g0.step(s0)
+        ckpt = g0.get_state(M.MD_FIELD_ALL)
+        g0.close()
+
+    def start(prec, profile):
+        g = make(prec, profile)
+        if ckpt is not None:
+            g.set_state(M.MD_FIELD_ALL, **{k: ckpt[k] for k in CKPT_KEYS}, step=ckpt["step"])
         return g
 
     def timed_steps(g, k_steps):
@@ -250,7 +303,7 @@ def run_gpu(args, rank, world, local):
         return sum(a.elapsed_time(b) for a, b in ev)
 
     # ---- mixed path, device-timed: the step graph without event nodes ----
-    g = make("mixed", profile=False)
+    g = start("mixed", profile=False)
     for _ in range(W_):
         g.step(1)
     _, _, pairs0 = g.energies()
@@ -268,7 +321,7 @@ def run_gpu(args, rank, world, local):
     g.close()
     # the force kernel's own time: the same steps again, with event nodes around
     # it in the step graph (they add inter-kernel gaps, so they stay out of `value`)
-    gp = make("mixed", profile=True)
+    gp = start("mixed", profile=True)
     for _ in range(W_):
         gp.step(1)
     gp.reset_timing()
@@ -278,36 +331,49 @@ def run_gpu(args, rank, world, local):
     pair_ms = ptim.pair_ms / max(ptim.pair_launches, 1)
     pairs = 0.5 * (pairs0 + pairs1)
     value = job_throughput(world, n_atoms, K, ms)
-    peak, sms, max_mhz = fp32_peak_tflops(torch)
+    peak_units, sms, max_mhz = fp32_peak_tflops(torch)
+    if peaks is not None:
+        peak = peaks["fp32"]["burst_tflops"]
+        peak_basis = (f"measured: FP32 FMA-pipe throughput of this GB300 (md_fma_peak, best of three ~50 ms "
+                      f"launches); {peaks['fp32']['sustained_tflops']:.1f} TFLOP/s sustained over "
+                      f"{peaks['fp32']['sustained_s']:.1f} s; {peak_units:.1f} from unit counts at {max_mhz:.0f} MHz")
+    else:
+        peak = peak_units
+        peak_basis = f"{sms} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz (max SM clock)"
     achieved = FLOPS_PER_PAIR * pairs / (pair_ms / 1e3) / 1e12
-    traffic, _ = profiled_traffic()
+    traffic, _ = profiled_traffic(args.workload if args.scale == 1.0 else None)
 
-    # ---- FP64 path on the same inputs ----
+    # ---- FP64 path on the same inputs and window ----
     k64 = min(args.fp64_steps, K)
-    g64 = make("fp64", profile=False)
-    for _ in range(min(W_, 3)):
+    g64 = start("fp64", profile=False)
+    for _ in range(W_):
         g64.step(1)
     ms64 = timed_steps(g64, k64)
     state64 = g64.get_state(M.MD_FIELD_PLASMA | M.MD_FIELD_Q | M.MD_FIELD_X | M.MD_FIELD_F)
     g64.close()
     value64 = world * n_atoms * k64 / (ms64 / 1e3)
     # the FP64 force kernel's own time: a short run with event nodes around it
-    g64p = make("fp64", profile=True)
-    for _ in range(min(W_, 3)):
+    g64p = start("fp64", profile=True)
+    for _ in range(W_):
         g64p.step(1)
     g64p.reset_timing()
-    timed_steps(g64p, min(k64, 30))
+    timed_steps(g64p, min(k64, 10))
     t64 = g64p.timing()
     g64p.close()
     pair_ms64 = t64.pair_ms / max(t64.pair_launches, 1)
-    peak64 = sms_count(torch) * 2 * 2 * fp32_peak_tflops(torch)[2] * 1e6 / 1e12   # 2 FP64 lanes per SM, FMA = 2
+    if peaks is not None:
+        peak64 = peaks["fp64"]["burst_tflops"]
+        peak64_basis = "measured: FP64 FMA-pipe throughput of this GB300 (md_fma_peak, best of three ~50 ms launches)"
+    else:
+        peak64 = sms * 2 * 2 * max_mhz * 1e6 / 1e12   # 2 FP64 lanes per SM, FMA = 2
+        peak64_basis = ("SMs x 2 FP64 lanes x 2 x max SM clock (GB300 issues FP64 at 2 lanes per SM per clock)")
     achieved64 = FLOPS_PER_PAIR * pairs / (pair_ms64 / 1e3) / 1e12
 
     # ---- end to end through the C ABI, host buffers ----
     e2e = None
     if not args.no_e2e:
         from paper_2401_03180_gb300 import md as M2
-        ge = make("mixed", profile=False)
+        ge = start("mixed", profile=False)
         # each replica's own pulse train, streamed one step at a time
         dF_tab = np.stack([M2.md_pulse_table([p for p in wl.pulses[r]], wl.t_start_fs, 5e-5 * 1000.0, max_steps)
                            for r in range(s.n_replicas)])
@@ -321,7 +387,7 @@ def run_gpu(args, rank, world, local):
         for k in range(K):
             flush.zero_()
             torch.cuda.synchronize()
-            step = W_ + k
+            step = s0 + W_ + k
             h_in[:] = dF_tab[:, step]
             t0 = time.perf_counter()
             M2.md_set_fluence_at(ge.h, step, h_in)                  # H2D: this step's fluence, per replica
@@ -334,6 +400,7 @@ def run_gpu(args, rank, world, local):
                # charges, each replica's 104-byte state record, the 4-byte error flags
                "d2h_bytes_per_step": int(n_atoms + 104 * s.n_replicas + 4)}
 
+    dt_fs = 5e-5 * 1000.0
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W_,
         "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -343,6 +410,10 @@ def run_gpu(args, rank, world, local):
                    "n_atoms": n_atoms, "replicas_per_gpu": s.n_replicas,
                    "box_nm": float(s.box[0, 0]) if s.box[0, 0] > 0 else None, "r_cut_nm": 1.2, "dt_as": 50,
                    "pulse": [vars(p) for p in wl.pulses[0]], "t_start_fs": wl.t_start_fs,
+                   "configured_steps": wl.n_steps,
+                   "timed_window": {"first_step": s0 + W_, "t_fs": [wl.t_start_fs + (s0 + W_) * dt_fs,
+                                                                     wl.t_start_fs + (s0 + W_ + K) * dt_fs],
+                                    "untimed_steps_before": s0, "placement": args.window},
                    "l2": "flushed between steps (256 MB write, untimed)",
                    "pair_tile": {"warps": tim.tile_warps, "blocks_per_sm": tim.tile_blocks_per_sm},
                    "list_skin_nm": args.skin, "screening": args.screening, "langevin_g": args.langevin,
@@ -357,14 +428,13 @@ def run_gpu(args, rank, world, local):
                      "speedup_mixed_vs_fp64": value / value64,
                      "roofline": {"bound": "fp64", "kernel": "k_pair (FP64 path)", "achieved": achieved64,
                                   "peak": peak64, "unit": "TFLOP/s", "frac": achieved64 / peak64,
-                                  "peak_basis": "SMs x 2 FP64 lanes x 2 x max SM clock (GB300 issues FP64 "
-                                                "at 2 lanes per SM per clock)",
-                                  "pair_kernel_ms": pair_ms64}},
+                                  "peak_basis": peak64_basis, "pair_kernel_ms": pair_ms64}},
         "roofline": {"bound": "alu", "kernel": "k_pair (FP32 FMA pipe)", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
-                     "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz (max SM clock)",
+                     "peak_basis": peak_basis, "frac_of_unit_count_peak": achieved / peak_units,
                      "flops_per_pair": FLOPS_PER_PAIR, "pair_kernel_ms": pair_ms,
                      "pair_kernel_share": pair_ms / (ms / K)},
+        "fma_peaks": peaks,
         "e2e": e2e,
         # per step: step kernel + force kernel (the bonded terms run inside it) (+ the
         # probe kernel; + the warp-per-replica reduction above 4 replicas, the step
@@ -372,15 +442,19 @@ def run_gpu(args, rank, world, local):
         # list is rebuilt
         "gpu_launches": (2 + bool(args.probe) + (s.n_replicas > 4)) * K + 5 * int(tim.list_builds),
         "pair_list": {"skin_nm": args.skin, "builds": int(tim.list_builds), "steps": K,
+                      "steps_per_build": (K / tim.list_builds) if tim.list_builds else None,
                       "entries_last_build": int(tim.list_entries), "capacity": int(tim.list_capacity)},
         "clocks": clk.summary(),
-        "charge_state": {"n_e": [int(v) for v in state["n_e"]], "te_ev": [float(v) for v in state["te_ev"]],
-                         "events_pi_auger_ci_rec": [int(v) for v in state["event_counts"][0]]},
+        "charge_state": ({"n_e": [int(v) for v in state["n_e"]], "te_ev": [float(v) for v in state["te_ev"]],
+                          "events_pi_auger_ci_rec": [int(v) for v in state["event_counts"][0]]}
+                         if s.n_replicas <= 8 else
+                         {"n_e_total": int(state["n_e"].sum()),
+                          "events_pi_auger_ci_rec": [int(v) for v in state["event_counts"].sum(0)]}),
     }
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"], out["force_error_vs_oracle"] = cpu_baseline(args, wl, atom)
         out["force_error_vs_oracle_ionised"] = ionised_force_errors(
-            wl, atom, {"mixed": (state, W_ + K), "fp64": (state64, min(W_, 3) + k64)}, args.screening)
+            wl, atom, {"mixed": (state, s0 + W_ + K), "fp64": (state64, s0 + W_ + k64)}, args.screening)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()

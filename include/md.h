@@ -299,17 +299,31 @@ typedef struct md_timing {
 typedef struct md_handle md_handle;
 
 /* Create a handle: validate, copy inputs, allocate, build the first cell
- * list and the initial forces F_0(x_0, q_0).  *out receives the handle or
- * NULL.  Errors: INVALID_ARG, OOM, CUDA. */
+ * list and the initial forces F_0(x_0, q_0).  The inputs are the sample of
+ * Sec. II.A/II.D (positions, velocities, species with their nuclear charge
+ * and the per-charge-state LJ sizes of Sec. II.B Eq. 11, initial charges,
+ * native fragments for the LJ exclusion of Sec. II.B, the electron-gas
+ * volume of Eq. 3) and the atomic data the CR model needs (cross sections,
+ * Auger lifetimes, ionisation potentials, rate coefficients; Sec. II.A).
+ * cfg and sys are read during the call only; *out receives the handle
+ * (owned by the caller, released with md_finalize) or NULL.  Errors:
+ * INVALID_ARG (inconsistent sizes, values out of range; the message names
+ * the field), OOM, CUDA. */
 md_status md_init(const md_config* cfg, const md_system* sys, md_handle** out);
 
 /* Issue all later device work on this cudaStream_t (NULL = legacy default). */
 md_status md_set_stream(md_handle* h, void* cuda_stream);
 
-/* Fluence per step of replica `replica` (-1: all) from n_pulses pulses,
- * over steps 0 .. max_steps-1.  Gaussian pulses integrate the normal CDF
- * with sigma_t = FWHM / (2 sqrt(2 ln 2)) over each step; flat-top pulses
- * the overlap.  Uploads the table (the only host-to-device copy of a run). */
+/* The X-ray pulse(s) of Sec. II.A that drive photo-ionisation (photon
+ * energy, FWHM, fluence, centre; Sec. II.D and IV give the paper's pulse
+ * shapes: Gaussian, pump and probe pulses): the fluence per step of replica
+ * `replica` (-1: all) from n_pulses pulses (host array, copied), over steps
+ * 0 .. max_steps-1.  Gaussian pulses integrate the normal CDF with
+ * sigma_t = FWHM / (2 sqrt(2 ln 2)) over each step; flat-top pulses the
+ * overlap.  Uploads the table (the only host-to-device copy of a run).
+ * Errors: INVALID_ARG (bad replica, a photon energy other than the
+ * cross-section table's, FWHM <= 0, negative fluence, unknown shape),
+ * BAD_STATE (poisoned handle), CUDA. */
 md_status md_set_pulse(md_handle* h, int replica, const md_pulse* p, int n_pulses);
 
 /* Same table given directly: dF[n] photons/nm^2 in step n (n < n_steps <= max_steps). */
@@ -346,8 +360,14 @@ md_status md_set_charge_table(md_handle* h, int replica, const double* frac, int
 md_status md_set_plasma_table(md_handle* h, int replica, const double* ne,
                               const double* te_ev, int n_steps);
 
-/* Advance every replica by n_steps timesteps (asynchronous on the handle's
- * stream except for a final 4-byte status read).  When the atoms crowd
+/* Advance every replica by n_steps timesteps of the method: per step, the
+ * velocity-Verlet half kick and drift (Sec. II.B, Eq. 12), the stochastic
+ * charge update (Sec. II.A) with the plasma scalars of the previous step, the
+ * free-electron reduction to the Debye length (Sec. II.A, Eq. 3), the
+ * neighbour list when the buffered one is used up (cutoff from the screening,
+ * Sec. II.B), the pair forces (Sec. II.A Eq. 2, Sec. II.B Eqs. 8 and 11) and
+ * the second half kick.  Asynchronous on the handle's stream except for a
+ * final 4-byte status read.  When the atoms crowd
  * together beyond what the cluster-pair list was sized for, the steps stop
  * after the one that needs more room, the list grows (through dev_alloc when
  * given) and the remaining steps follow: the trajectory is the same as with a
@@ -366,8 +386,11 @@ md_status md_step_async(md_handle* h, int n_steps);
  * (same errors as md_step). */
 md_status md_sync(md_handle* h);
 
-/* Copy the requested fields (MD_FIELD_* mask) to caller buffers, in the
- * original atom order.  Synchronises the handle's stream.  After steps
+/* The outputs the paper reads from a run (Sec. II.A-II.C: time-resolved
+ * ion charges and K holes, free-electron count, temperature and Debye
+ * screening, positions for the structure and displacement analyses, plus
+ * velocities, forces and event counts): copy the requested fields (MD_FIELD_*
+ * mask) to caller-owned host buffers, in the original atom order.  Synchronises the handle's stream.  After steps
  * enqueued by md_step_async, and without MD_FIELD_X or MD_FIELD_XLIST (which
  * are reordered on the host), the copies and the steps' status are read back
  * together in one host round trip (use pinned buffers for asynchronous
@@ -376,9 +399,13 @@ md_status md_sync(md_handle* h);
  * Errors: those of md_sync, INVALID_ARG (a requested buffer is NULL), CUDA. */
 md_status md_get_state(md_handle* h, md_state* out, unsigned fields);
 
-/* Overwrite x, v, q, h, plasma counters and/or the step counter (mask);
- * recomputes the cell list, plasma scalars and forces.  Checkpoint/resume
- * with md_get_state(MD_FIELD_ALL) continues bit for bit. */
+/* Overwrite x, v, q, h, plasma counters and/or the step counter (mask;
+ * caller-owned host buffers, copied); recomputes the cell list, the plasma
+ * scalars of Sec. II.A Eq. 3 and the forces of Eqs. 2, 8 and 11.
+ * Checkpoint/resume with md_get_state(MD_FIELD_ALL) continues bit for bit
+ * (the paper has no checkpoint; the state is the one Sec. II.A-II.B evolve).
+ * Errors: INVALID_ARG (a null buffer for a requested field, charges above Z,
+ * non-finite values), BAD_STATE, OOM, CUDA. */
 md_status md_set_state(md_handle* h, const md_state* in, unsigned fields);
 
 /* Kinetic and cutoff-shifted potential energy per replica ([n_replicas]
@@ -451,7 +478,8 @@ md_status md_get_timing(md_handle* h, md_timing* out);
 md_status md_reset_timing(md_handle* h);
 
 /* Last error message of the handle (or, when h is NULL, of the last failed
- * md_init, md_pulse_table, md_philox or md_forces_noalloc on this thread). */
+ * md_init, md_pulse_table, md_philox, md_fma_peak or md_forces_noalloc on
+ * this thread). */
 const char* md_last_error(const md_handle* h);
 
 /* Release the handle and its device memory.  NULL is a no-op. */
@@ -467,6 +495,18 @@ md_status md_pulse_table(const md_pulse* p, int n_pulses, double t_start_fs, dou
  * device buffers d_ctr4/d_out (n blocks) and the given stream. */
 md_status md_philox(uint64_t seed, const uint32_t* d_ctr4, int64_t n, uint32_t* d_out,
                     void* cuda_stream);
+
+/* Measurement: the throughput of the FP32 (precision MD_PREC_MIXED) or FP64
+ * (MD_PREC_FP64) fused multiply-add pipe of the current device, the
+ * denominator of the force kernel's roofline (the paper has no counterpart).
+ * One launch of blocks_per_sm x (SM count) blocks of 256 threads, each thread
+ * running 8 independent FMA chains for iters x 16 steps, timed with CUDA
+ * events on cuda_stream (synchronous).  *flops_per_s = 2 x FMAs / time
+ * (an FMA counts as two operations); *seconds (may be NULL) = the kernel's
+ * time.  Errors: INVALID_ARG for iters < 1, blocks_per_sm outside 1..64 or a
+ * bad precision; CUDA for a failed launch (message in md_last_error(NULL)). */
+md_status md_fma_peak(int precision, int64_t iters, int blocks_per_sm, double* flops_per_s, double* seconds,
+                      void* cuda_stream);
 
 /*
  * Allocation-free force evaluation (the paper has no counterpart; this is a
@@ -487,14 +527,17 @@ md_status md_philox(uint64_t seed, const uint32_t* d_ctr4, int64_t n, uint32_t* 
  * Inputs: device pointers d_x [3n] AoS positions (nm), d_species [n],
  * d_q [n] charges, d_fragment [n] (LJ excluded within a fragment); the screening
  * kappa = 1/lambda_D (nm^-1, 0 = bare Coulomb) and the species tables on the host.
- * species[i] < n_species and q[i] <= z[species[i]] are preconditions (the
- * device arrays are not inspected on the host).
+ * Every atom needs species[i] < n_species and q[i] <= z[species[i]]; the
+ * device arrays are checked on the device, and an atom that breaks this makes
+ * the call return MD_ERR_INVALID_ARG (its forces are then not meaningful).
  * Output: d_f [3n] AoS forces (kJ/mol/nm), device memory owned by the caller.
  * The result equals md_init (same sample, kappa_fixed = kappa, charges
  * frozen) followed by md_get_state(MD_FIELD_F).
  * The first call on a device looks up the scratch area's device address
  * (once per device, with that device current); make that first call before
- * any stream capture.  All calls share the one scratch area, which keeps the
+ * any stream capture.  The address is kept for the life of the process; a
+ * cudaDeviceReset on that device invalidates it, so do not call this entry
+ * point after resetting a device.  All calls share the one scratch area, which keeps the
  * last call's contents: every call resets what must start at zero, and calls
  * that overlap on the GPU (different streams or threads) race -- serialise
  * them.  The call is synchronous with respect to `cuda_stream` (it reads a

@@ -28,6 +28,7 @@ SOURCES = {
     "md_noalloc.cu": [],
     "k_probe.cu": ["-fmad=false"],
     "k_frag.cu": [],
+    "k_peak.cu": [],
 }
 
 
