@@ -41,7 +41,7 @@ METRIC = "atom-steps/s (pair forces + ionisation) on 1 GB300, mixed vs FP64 at s
 UNIT = "atom-steps/s"
 FLOPS_PER_PAIR = 41          # FP32 operations per in-cutoff pair in the pair kernel (FMA = 2)
 L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
-SKIN_NM = 0.08               # Verlet buffer of the pair list (measured choice for the water box)
+SKIN_NM = 0.12               # Verlet buffer of the pair list (measured: best at the pulse peak of the droplet and the water box)
 
 
 def parse():
@@ -416,6 +416,7 @@ def run_gpu(args, rank, world, local):
                                     "untimed_steps_before": s0, "placement": args.window},
                    "l2": "flushed between steps (256 MB write, untimed)",
                    "pair_tile": {"warps": tim.tile_warps, "blocks_per_sm": tim.tile_blocks_per_sm},
+                   "build_shape": {"sort_threads": tim.sort_threads, "list_blocks_per_sm": tim.list_blocks_per_sm},
                    "list_skin_nm": args.skin, "screening": args.screening, "langevin_g": args.langevin,
                    "charges": "table" if args.charge_table else "rates",
                    "bonded": ({"bonds": int(len(s.topology.bonds)), "angles": int(len(s.topology.angles))}
@@ -438,9 +439,9 @@ def run_gpu(args, rank, world, local):
         "e2e": e2e,
         # per step: step kernel + force kernel (the bonded terms run inside it) (+ the
         # probe kernel; + the warp-per-replica reduction above 4 replicas, the step
-        # kernel's inline limit), and 5 more (4 cell kernels + list) in the steps whose
-        # list is rebuilt
-        "gpu_launches": (2 + bool(args.probe) + (s.n_replicas > 4)) * K + 5 * int(tim.list_builds),
+        # kernel's inline limit), and 7 more (4 cell kernels + 3 list kernels) in the
+        # steps whose list is rebuilt
+        "gpu_launches": (2 + bool(args.probe) + (s.n_replicas > 4)) * K + 7 * int(tim.list_builds),
         "pair_list": {"skin_nm": args.skin, "builds": int(tim.list_builds), "steps": K,
                       "steps_per_build": (K / tim.list_builds) if tim.list_builds else None,
                       "entries_last_build": int(tim.list_entries), "capacity": int(tim.list_capacity)},
@@ -620,10 +621,10 @@ def run_reference(args, rank, world):
 
 
 def run_profile_case(args):
-    """Kernels launched: init 7 (step kernel, 4 cell kernels, list, forces), then
-    per step the step kernel and the forces, plus 5 when the list is rebuilt;
-    --profile-resume adds the checkpoint round trip (step kernel, 4 cell kernels,
-    list, two force launches, refresh)."""
+    """Kernels launched: init 9 (step kernel, 4 cell kernels, 3 list kernels,
+    forces), then per step the step kernel and the forces, plus 7 when the list
+    is rebuilt; --profile-resume adds the checkpoint round trip (step kernel, 4
+    cell kernels, 3 list kernels, two force launches, refresh)."""
     import torch
     from paper_2401_03180_gb300 import build as B
     from paper_2401_03180_gb300 import md as M

@@ -184,6 +184,16 @@ typedef struct md_config {
                                 the probe-weighted displacement of Eq. 17
                                 (md_get_probe_series, md_probe_displacement).
                                 Costs one kernel per step. 0 (default): off.  */
+    /* Launch shapes (the paper has no counterpart; they change no result: the
+     * fixed-point sums and the list's layout do not depend on them).  0 keeps
+     * the default, or the autotuner's choice when autotune = 1; a nonzero
+     * value pins that axis (the autotuner then leaves it alone).            */
+    int pair_warps;          /* warps per force-kernel block: 4, 8 or 12
+                                (FP64: 4 or 8)                                 */
+    int pair_blocks_per_sm;  /* force-kernel blocks per SM, >= 1, within the
+                                occupancy the shape allows                     */
+    int sort_threads;        /* threads per cell-sort block: 256 or 1024       */
+    int list_blocks_per_sm;  /* list-build blocks (8 warps) per SM: 1 .. 16    */
 } md_config;
 
 /*
@@ -294,6 +304,8 @@ typedef struct md_timing {
     int64_t list_grows;      /* times the list was enlarged on demand       */
     int64_t list_builds;     /* cell + list builds in md_step since init or
                                 md_reset_timing (equals steps when the skin is 0) */
+    int sort_threads;        /* cell-sort block size in use                 */
+    int list_blocks_per_sm;  /* list-build blocks per SM in use             */
 } md_timing;
 
 typedef struct md_handle md_handle;
@@ -515,7 +527,7 @@ md_status md_fma_peak(int precision, int64_t iters, int blocks_per_sm, double* f
  * budget, a memory-capped process, an inner loop that must keep the device
  * footprint fixed -- it computes the screened Coulomb + screened LJ forces of
  * one configuration using only a fixed scratch area compiled into the
- * library (a file-scope __device__ array of about 10.5 MB, held by every GPU
+ * library (a file-scope __device__ array of about 11 MB, held by every GPU
  * that loads the library until the process exits).  It calls no cudaMalloc,
  * cudaFree or other allocating routine.
  *

@@ -14,7 +14,7 @@ namespace mdg {
 
 constexpr int kScanThreads = 1024;
 constexpr int kSortThreads = 1024;
-constexpr int kSortMax = 4096;       // keys per cell kept in shared memory
+constexpr int kSortMax = 2048;       // keys per cell kept in shared memory (larger cells sort from global memory)
 
 __device__ __forceinline__ int cell_coord(double x, double origin, double inv_edge, int n)
 {
@@ -211,10 +211,22 @@ __global__ void __launch_bounds__(256) k_cell_scatter(Params p)
 // few cells per SM (large cells, all sorted at once) and 256 when there are
 // many: a cell's phases are latency-bound, and seven 256-thread CTAs per SM
 // keep more cells in flight than two 1,024-thread ones.
+// Order-preserving integer image of a float (for min/max with integer atomics).
+__device__ __forceinline__ int ord_f(float f)
+{
+    const int i = __float_as_int(f);
+    return i < 0 ? i ^ 0x7fffffff : i;
+}
+__device__ __forceinline__ float unord_f(int i) { return __int_as_float(i < 0 ? i ^ 0x7fffffff : i); }
+
 __global__ void __launch_bounds__(kSortThreads) k_cell_sort_pack(Params p)
 {
     const int nt = blockDim.x;
     __shared__ unsigned long long s_key[kSortMax];
+    // cluster boxes of a cell held in shared memory (ordered-integer min x, y, z,
+    // max x, y, z, min and max fragment), built with integer atomics as the
+    // atoms are packed
+    __shared__ int s_bb[kSortMax / kClusterSize][8];
     if (*p.err & ERR_CELL) return;
     const int tid = threadIdx.x;
     for (int c = blockIdx.x; c < p.cell_cap_total; c += gridDim.x) {
@@ -243,8 +255,16 @@ __global__ void __launch_bounds__(kSortThreads) k_cell_sort_pack(Params p)
                                g.origin[2] + (cz + 0.5) * g.edge[2]};
         const bool in_smem = n <= kSortMax;
         const unsigned long long* keys = in_smem ? s_key : p.tmp_key + b;
-        if (in_smem)
+        const int ncl = npad / kClusterSize;
+        if (in_smem) {
             for (int e = tid; e < n; e += nt) s_key[e] = p.tmp_key[b + e];
+            for (int k = tid; k < ncl; k += nt) {
+                s_bb[k][0] = s_bb[k][1] = s_bb[k][2] = 0x7fffffff;
+                s_bb[k][3] = s_bb[k][4] = s_bb[k][5] = (int)0x80000000;
+                s_bb[k][6] = 0x7fffffff;
+                s_bb[k][7] = (int)0x80000000;
+            }
+        }
         __syncthreads();
         int tpe = 1;
         while (tpe < 8 && 2 * tpe * n <= nt) tpe *= 2;
@@ -264,7 +284,15 @@ __global__ void __launch_bounds__(kSortThreads) k_cell_sort_pack(Params p)
                 const int slot = ps + rank;
                 p.atom_of[slot] = i;
                 p.slot_of[i] = slot;
-                pack_slot(p, slot, i, cen, g);
+                const float4 v = pack_slot(p, slot, i, cen, g);
+                if (in_smem) {
+                    int* bb = s_bb[rank / kClusterSize];
+                    atomicMin(bb + 0, ord_f(v.x)); atomicMin(bb + 1, ord_f(v.y)); atomicMin(bb + 2, ord_f(v.z));
+                    atomicMax(bb + 3, ord_f(v.x)); atomicMax(bb + 4, ord_f(v.y)); atomicMax(bb + 5, ord_f(v.z));
+                    const int fr = p.frag[i];
+                    atomicMin(bb + 6, fr);
+                    atomicMax(bb + 7, fr);
+                }
             }
         }
         for (int e = n + tid; e < npad; e += nt) {     // padding: far away, no charge
@@ -278,7 +306,17 @@ __global__ void __launch_bounds__(kSortThreads) k_cell_sort_pack(Params p)
         }
         __syncthreads();
         // cluster bounding boxes (real atoms only) and fragment ranges
-        const int ncl = npad / kClusterSize;
+        if (in_smem) {
+            for (int k = tid; k < ncl; k += nt) {
+                const int cl = ps / kClusterSize + k;
+                p.cl_cen[cl] = make_double4_32a(cen[0], cen[1], cen[2], 0.0);
+                p.bb_lo[cl] = make_float4(unord_f(s_bb[k][0]), unord_f(s_bb[k][1]), unord_f(s_bb[k][2]), 0.0f);
+                p.bb_hi[cl] = make_float4(unord_f(s_bb[k][3]), unord_f(s_bb[k][4]), unord_f(s_bb[k][5]), 0.0f);
+                p.bb_frag[cl] = make_int2(s_bb[k][6], s_bb[k][7]);
+            }
+            __syncthreads();
+            continue;
+        }
         for (int k = tid; k < ncl; k += nt) {
             float lx = 3.0e38f, ly = 3.0e38f, lz = 3.0e38f, hx = -3.0e38f, hy = -3.0e38f, hz = -3.0e38f;
             int fmin = 0x7fffffff, fmax = (int)0x80000000;

@@ -217,61 +217,73 @@ __device__ __forceinline__ void pair(const typename Prec<FP64>::S4& xi, int row_
     }
 }
 
-// Cluster-pair list (one block per super-cluster, one warp per half-shell
-// cell): every j-cluster whose bounding box comes within r_cut + skin of at
-// least one of the SC's i-cluster boxes gets an entry (j-cluster, half-shell
-// index, mask of the i-atoms of those clusters that lie within r_cut + skin of
-// the j-cluster's box).  An SC's entries are contiguous and cut into chunks of
-// kChunk, the work items of the force kernel.  A first pass counts, the second
-// repeats the box tests and writes, so no cell size limit applies.
-__global__ void __launch_bounds__(kHalfShell * 32) k_pair_list(Params p)
+// Cluster-pair list.  Every j-cluster whose bounding box comes within
+// r_cut + skin of at least one of a super-cluster's (SC's) i-cluster boxes gets
+// an entry (j-cluster, half-shell index, mask of the i-atoms of those clusters
+// that lie within r_cut + skin of the j-cluster's box).  An SC's entries are
+// contiguous, in half-shell order and by j-cluster within a cell, and cut into
+// chunks of kChunk, the work items of the force kernel.  The j-clusters of an
+// SC's 14 half-shell cells form one index range, swept 32 at a time with every
+// lane busy (cell by cell would leave lanes idle and chain one load latency per
+// cell).  Three kernels, with no block-level barrier:
+//   k_list_count  a warp per (SC, part of its index range) item counts the
+//                 entries of its part;
+//   k_list_scan   one block sums each SC's parts and scans the totals into
+//                 entry and chunk offsets (and flags a list too small for them);
+//   k_list_write  a warp per item repeats the box tests in the same rounding
+//                 and writes its entries from its offset (the SC's plus the
+//                 counts of the SC's earlier parts); the SC's first item writes
+//                 the SC's chunk descriptors.
+// An SC's range is split into 1, 2, 7 or 14 parts (list_parts): as few as keep
+// every warp of the grid busy, so that a system of many SCs stages each SC once
+// and a small one still spreads over the GPU.
+struct ListWarp {
+    float4 lo[kSuperClusters], hi[kSuperClusters];   // the SC's i-cluster boxes (cell frame)
+    int2 fr[kSuperClusters];                          // fragment range of each i-cluster
+    float4 ip[kSCAtoms];                              // the SC's atoms, [cluster k][atom a] (write pass)
+};
+constexpr int kListWarps = 8;
+
+// An SC's cell, in the grid of its replica.
+struct ListSC {
+    int sc, fc, ncl, rr, cx, cy, cz;
+};
+__device__ __forceinline__ ListSC list_sc(const Params& p, int sc)
 {
-    __shared__ float4 s_lo[kSuperClusters], s_hi[kSuperClusters];
-    __shared__ float4 s_ip[kSCAtoms];       // the SC's atom positions (cell frame), [atom a][cluster k]
-    __shared__ int2 s_fr[kSuperClusters];   // fragment range of each i-cluster
-    __shared__ int s_cnt[kHalfShell];
-    __shared__ int s_base, s_tot, s_cbase;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (*p.err & ERR_CELL) return;
-    const int n_sc = p.counters[0];
-    const float rcb = p.rlist_f + kBBoxMargin;   // r_cut + Verlet skin
-    const float rcb2 = rcb * rcb;
-    for (int sc = blockIdx.x; sc < n_sc; sc += gridDim.x) {
-        const int c = p.sc_cell[sc], fc = p.sc_first[sc], ncl = p.sc_ncl[sc];
-        if (threadIdx.x < ncl) {
-            s_lo[threadIdx.x] = p.bb_lo[fc + threadIdx.x];
-            s_hi[threadIdx.x] = p.bb_hi[fc + threadIdx.x];
-            s_fr[threadIdx.x] = p.bb_frag[fc + threadIdx.x];
-        }
-        if (threadIdx.x < ncl * kClusterSize) {
-            // column-major, like the entries' masks: row a * 8 + k holds atom a of i-cluster k
-            const int slot = fc * kClusterSize + threadIdx.x;
-            const int row = (threadIdx.x & 7) * kClusterSize + (threadIdx.x >> 3);
-            if (p.precision == 0) {
-                s_ip[row] = p.xq[slot];
-            } else {
-                const double4_32a t = p.xq64[slot];
-                s_ip[row] = make_float4((float)t.x, (float)t.y, (float)t.z, 0.0f);
-            }
-        }
-        int rr;
-        {
-            int lo = 0, hi = p.n_rep - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (p.grid_b[mid].cell_off <= c) lo = mid; else hi = mid - 1;
-            }
-            rr = lo;
-        }
-        const Grid& g = p.grid_b[rr];
-        const int local = c - g.cell_off;
-        const int cx = local % g.dims[0];
-        const int cy = (local / g.dims[0]) % g.dims[1];
-        const int cz = local / (g.dims[0] * g.dims[1]);
-        const int nb = warp;
+    ListSC s;
+    s.sc = sc;
+    const int c = p.sc_cell[sc];
+    s.fc = p.sc_first[sc];
+    s.ncl = p.sc_ncl[sc];
+    int lo = 0, hi = p.n_rep - 1;   // replicas own contiguous cell ranges
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (p.grid_b[mid].cell_off <= c) lo = mid; else hi = mid - 1;
+    }
+    s.rr = lo;
+    const Grid& g = p.grid_b[lo];
+    const int local = c - g.cell_off;
+    s.cx = local % g.dims[0];
+    s.cy = (local / g.dims[0]) % g.dims[1];
+    s.cz = local / (g.dims[0] * g.dims[1]);
+    return s;
+}
+
+// Lane nb < 14: half-shell cell nb of the SC (its first j-cluster, its number
+// of j-clusters, the clusters of the cells before it, its shift into the SC
+// cell's frame); *total: the SC's j-clusters over the 14 cells.
+struct ListCell {
+    int jr0, n, pre;
+    float Dx, Dy, Dz;
+};
+__device__ __forceinline__ ListCell list_cells(const Params& p, const ListSC& s, int lane, int* total)
+{
+    ListCell c{};
+    if (lane < kHalfShell) {
+        const Grid& g = p.grid_b[s.rr];
         int dx, dy, dz;
-        half_shell(nb, dx, dy, dz);
-        int ncx = cx + dx, ncy = cy + dy, ncz = cz + dz;
+        half_shell(lane, dx, dy, dz);
+        int ncx = s.cx + dx, ncy = s.cy + dy, ncz = s.cz + dz;
         bool valid = true;
         if (g.periodic) {
             ncx = ncx < 0 ? ncx + g.dims[0] : (ncx >= g.dims[0] ? ncx - g.dims[0] : ncx);
@@ -280,136 +292,291 @@ __global__ void __launch_bounds__(kHalfShell * 32) k_pair_list(Params p)
         } else {
             valid = ncx >= 0 && ncy >= 0 && ncz >= 0 && ncx < g.dims[0] && ncy < g.dims[1] && ncz < g.dims[2];
         }
-        int jr0 = 0, jr1 = 0;
         if (valid) {
             const int c2 = g.cell_off + ncx + g.dims[0] * (ncy + g.dims[1] * ncz);
-            jr0 = nb == 0 ? fc : p.cell_pstart[c2] / kClusterSize;
-            jr1 = p.cell_pstart[c2 + 1] / kClusterSize;
+            c.jr0 = lane == 0 ? s.fc : p.cell_pstart[c2] / kClusterSize;
+            c.n = p.cell_pstart[c2 + 1] / kClusterSize - c.jr0;
         }
-        const float Dfx = (float)dx * g.edge_f[0], Dfy = (float)dy * g.edge_f[1], Dfz = (float)dz * g.edge_f[2];
-        __syncthreads();   // boxes staged
+        c.Dx = (float)dx * g.edge_f[0];
+        c.Dy = (float)dy * g.edge_f[1];
+        c.Dz = (float)dz * g.edge_f[2];
+    }
+    int inc = c.n;   // inclusive scan over the 14 cells
+    for (int o = 1; o < 16; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += u;
+    }
+    c.pre = inc - c.n;
+    *total = __shfl_sync(0xffffffffu, inc, kHalfShell - 1);
+    return c;
+}
 
-        // mask of the SC's i-clusters in range of j-cluster jc (0 when out of range);
-        // explicit roundings, so that both passes reach the same masks
-        auto test = [&](int jc) -> unsigned {
-            unsigned m = 0;
-            if (jc < jr1) {
-                const float4 lo = p.bb_lo[jc], hi = p.bb_hi[jc];
-                const float jlx = lo.x + Dfx, jly = lo.y + Dfy, jlz = lo.z + Dfz;
-                const float jhx = hi.x + Dfx, jhy = hi.y + Dfy, jhz = hi.z + Dfz;
-                const int kmax = nb == 0 ? min(ncl, jc - fc + 1) : ncl;
+// The cell (nb) and j-cluster of flat index idx of the SC's range (every lane
+// takes part; lanes with idx out of range get some cell, unused).
+__device__ __forceinline__ void list_locate(const ListCell& c, int idx, int& nb, int& jc, float& Dx, float& Dy,
+                                            float& Dz)
+{
+    int lo = 0;   // the last cell whose first index is <= idx (cells of no cluster are skipped)
+#pragma unroll
+    for (int step = 8; step; step >>= 1) {
+        const int cand = min(lo + step, kHalfShell - 1);
+        if (__shfl_sync(0xffffffffu, c.pre, cand) <= idx) lo = cand;
+    }
+    nb = lo;
+    jc = __shfl_sync(0xffffffffu, c.jr0, lo) + idx - __shfl_sync(0xffffffffu, c.pre, lo);
+    Dx = __shfl_sync(0xffffffffu, c.Dx, lo);
+    Dy = __shfl_sync(0xffffffffu, c.Dy, lo);
+    Dz = __shfl_sync(0xffffffffu, c.Dz, lo);
+}
+
+// Mask of the SC's i-clusters whose boxes come within r_cut + skin of the
+// j-cluster box [jl, jh] (already shifted into the SC's frame); in the SC's own
+// cell (nb = 0) only i-clusters up to the j-cluster.  Explicit roundings, so
+// that the count and the write pass reach the same masks.
+__device__ __forceinline__ unsigned list_test(const ListWarp& w, int nb, int fc, int ncl, int jc, float4 jl,
+                                              float4 jh, float rcb2)
+{
+    unsigned m = 0;
+    const int kmax = nb == 0 ? min(ncl, jc - fc + 1) : ncl;
 #pragma unroll 2
-                for (int k = 0; k < kmax; ++k) {
-                    const float4 il = s_lo[k], ih = s_hi[k];
-                    const float gx = fmaxf(0.0f, fmaxf(il.x - jhx, jlx - ih.x));
-                    const float gy = fmaxf(0.0f, fmaxf(il.y - jhy, jly - ih.y));
-                    const float gz = fmaxf(0.0f, fmaxf(il.z - jhz, jlz - ih.z));
-                    if (__fmaf_rn(gz, gz, __fmaf_rn(gy, gy, __fmul_rn(gx, gx))) < rcb2) m |= 1u << k;
-                }
-            }
-            return m;
-        };
+    for (int k = 0; k < kmax; ++k) {
+        const float4 il = w.lo[k], ih = w.hi[k];
+        const float gx = fmaxf(0.0f, fmaxf(il.x - jh.x, jl.x - ih.x));
+        const float gy = fmaxf(0.0f, fmaxf(il.y - jh.y, jl.y - ih.y));
+        const float gz = fmaxf(0.0f, fmaxf(il.z - jh.z, jl.z - ih.z));
+        if (__fmaf_rn(gz, gz, __fmaf_rn(gy, gy, __fmul_rn(gx, gx))) < rcb2) m |= 1u << k;
+    }
+    return m;
+}
+
+// Parts of an SC's index range: the fewest of 1, 2, 7, 14 with at least as
+// many (SC, part) items as the grid has warps.
+__device__ __forceinline__ int list_parts(int n_sc)
+{
+    const long long warps = (long long)gridDim.x * kListWarps;
+    if ((long long)n_sc >= warps) return 1;
+    if (2LL * n_sc >= warps) return 2;
+    if (7LL * n_sc >= warps) return 7;
+    return 14;
+}
+
+// The box of flat index idx (when idx < i1), shifted into the SC's frame.
+struct ListJ {
+    int nb, jc;
+    unsigned m;
+    float4 jl, jh;
+};
+__device__ __forceinline__ ListJ list_j(const Params& p, const ListWarp& w, const ListSC& s, const ListCell& c,
+                                        int idx, int i1, float rcb2)
+{
+    ListJ j;
+    float Dx, Dy, Dz;
+    list_locate(c, idx, j.nb, j.jc, Dx, Dy, Dz);
+    j.m = 0u;
+    j.jl = j.jh = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (idx < i1) {
+        const float4 lo = p.bb_lo[j.jc], hi = p.bb_hi[j.jc];
+        j.jl = make_float4(lo.x + Dx, lo.y + Dy, lo.z + Dz, 0.0f);
+        j.jh = make_float4(hi.x + Dx, hi.y + Dy, hi.z + Dz, 0.0f);
+        j.m = list_test(w, j.nb, s.fc, s.ncl, j.jc, j.jl, j.jh, rcb2);
+    }
+    return j;
+}
+
+__global__ void __launch_bounds__(kListWarps * 32, 4) k_list_count(Params p)
+{
+    constexpr unsigned kFull = 0xffffffffu;
+    __shared__ ListWarp s_w[kListWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    ListWarp& w = s_w[warp];
+    if (*p.err & ERR_CELL) return;
+    const int n_sc = p.counters[0];
+    const int G = list_parts(n_sc);
+    const float rcb = p.rlist_f + kBBoxMargin;   // r_cut + Verlet skin
+    const float rcb2 = rcb * rcb;
+    for (int item = blockIdx.x * kListWarps + warp; item < n_sc * G; item += gridDim.x * kListWarps) {
+        const int sc = item / G, gr = item - sc * G;
+        const ListSC s = list_sc(p, sc);
+        int total;
+        const ListCell c = list_cells(p, s, lane, &total);
+        const int i0 = (int)((long long)total * gr / G), i1 = (int)((long long)total * (gr + 1) / G);
+        __syncwarp();
+        if (lane < s.ncl) {
+            w.lo[lane] = p.bb_lo[s.fc + lane];
+            w.hi[lane] = p.bb_hi[s.fc + lane];
+        }
+        __syncwarp();
         int cnt = 0;
-        unsigned m_first = 0;   // masks of the first 32 j-clusters, kept for the write pass
-        for (int base = jr0; base < jr1; base += 32) {
-            const unsigned m = test(base + lane);
-            if (base == jr0) m_first = m;
-            cnt += __popc(__ballot_sync(0xffffffffu, m != 0));
+        for (int base = i0; base < i1; base += 64) {   // two batches in flight
+            const ListJ ja = list_j(p, w, s, c, base + lane, i1, rcb2);
+            const ListJ jb = list_j(p, w, s, c, base + 32 + lane, i1, rcb2);
+            cnt += __popc(__ballot_sync(kFull, ja.m != 0u)) + __popc(__ballot_sync(kFull, jb.m != 0u));
         }
-        if (lane == 0) s_cnt[warp] = cnt;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int tot = 0;
-            for (int w = 0; w < kHalfShell; ++w) {
-                const int t = s_cnt[w];
-                s_cnt[w] = tot;
-                tot += t;
-            }
-            const unsigned long long nch = (unsigned long long)((tot + kChunk - 1) / kChunk);
-            // one reservation for both: entries in the low word, chunks in the high word
-            const unsigned long long old =
-                atomicAdd(reinterpret_cast<unsigned long long*>(p.counters + 6), (nch << 32) | (unsigned)tot);
-            int base = (int)(unsigned)old;
-            const int cbase = (int)(old >> 32);
-            if ((long long)base + tot > p.pl_cap || (long long)cbase + (long long)nch > p.chunk_cap) {
-                atomicOr(p.err, ERR_LIST);
-                base = -1;
-            }
-            s_base = base;
-            s_tot = tot;
-            s_cbase = cbase;
+        if (lane == 0) p.list_cnt[sc * kHalfShell + gr] = cnt;
+        if (gr == 0 && lane >= G && lane < kHalfShell) p.list_cnt[sc * kHalfShell + lane] = 0;   // unused parts
+    }
+}
+
+// One block: each SC's total over its parts, then exclusive scans of the SCs'
+// entry counts and chunk counts (each warp owns a contiguous run of SCs and
+// reads it 32 at a time), the totals into counters[6] (entries) and
+// counters[7] (chunks), ERR_LIST when the list is too small for them.
+__global__ void __launch_bounds__(1024) k_list_scan(Params p)
+{
+    constexpr unsigned kFull = 0xffffffffu;
+    constexpr int kWarps = 32;
+    __shared__ int s_tot[kWarps][2], s_base[kWarps][2];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n = (*p.err & ERR_CELL) ? 0 : p.counters[0];
+    const int run = ((n + kWarps - 1) / kWarps + 31) & ~31;
+    const int lo = min(warp * run, n), hi = min(lo + run, n);
+    int te = 0, tc = 0;
+    for (int s = lo + lane; s < hi; s += 32) {
+        int t = 0;
+#pragma unroll
+        for (int k = 0; k < kHalfShell; ++k) t += p.list_cnt[s * kHalfShell + k];
+        p.sc_tot[s] = t;
+        te += t;
+        tc += (t + kChunk - 1) / kChunk;
+    }
+    for (int o = 16; o; o >>= 1) {
+        te += __shfl_xor_sync(kFull, te, o);
+        tc += __shfl_xor_sync(kFull, tc, o);
+    }
+    if (lane == 0) { s_tot[warp][0] = te; s_tot[warp][1] = tc; }
+    __syncthreads();
+    if (warp == 0) {
+        int ie = s_tot[lane][0], ic = s_tot[lane][1];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int ue = __shfl_up_sync(kFull, ie, o), uc = __shfl_up_sync(kFull, ic, o);
+            if (lane >= o) { ie += ue; ic += uc; }
         }
-        __syncthreads();
-        const int base_sc = s_base, tot = s_tot, cbase = s_cbase;
-        if (base_sc >= 0) {
-            int off = base_sc + s_cnt[warp];
-            const int end = base_sc + tot;
-            for (int base = jr0; base < jr1; base += 32) {
-                const unsigned m = base == jr0 ? m_first : test(base + lane);
-                const unsigned bal = __ballot_sync(0xffffffffu, m != 0);
-                const int at = off + __popc(bal & ((1u << lane) - 1u));
-                // i-atoms of the clusters in range that lie within r_cut + skin of the
-                // j-cluster's box (padding slots are far away), one entry at a time
-                // across the warp.  The mask is column-major (bit a*8 + k: atom a of
-                // i-cluster k): lane l tests atom l >> 3 (low word) and 4 + (l >> 3)
-                // (high word) of i-cluster l & 7.  Each lane loads its own j-cluster's
-                // box once; the entry loop shuffles it.
-                unsigned my_lo = 0u, my_hi = 0u;
-                bool my_share = false;
-                float4 blo = make_float4(0.f, 0.f, 0.f, 0.f), bhi = blo;
-                int2 bfr = make_int2(0, 0);
-                if (m) {
-                    blo = p.bb_lo[base + lane];
-                    bhi = p.bb_hi[base + lane];
-                    bfr = p.bb_frag[base + lane];
+        s_base[lane][0] = ie - s_tot[lane][0];
+        s_base[lane][1] = ic - s_tot[lane][1];
+    }
+    __syncthreads();
+    int be = s_base[warp][0], bc = s_base[warp][1];
+    for (int g0 = lo; g0 < hi; g0 += 32) {
+        const int s = g0 + lane;
+        const int t = s < hi ? p.sc_tot[s] : 0;
+        const int ch = (t + kChunk - 1) / kChunk;
+        int ie = t, ic = ch;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int ue = __shfl_up_sync(kFull, ie, o), uc = __shfl_up_sync(kFull, ic, o);
+            if (lane >= o) { ie += ue; ic += uc; }
+        }
+        if (s < hi) {
+            p.sc_eoff[s] = be + ie - t;
+            p.sc_coff[s] = bc + ic - ch;
+        }
+        be += __shfl_sync(kFull, ie, 31);
+        bc += __shfl_sync(kFull, ic, 31);
+    }
+    if (threadIdx.x == 0) {
+        const long long E = (long long)s_base[kWarps - 1][0] + s_tot[kWarps - 1][0];
+        const long long Cn = (long long)s_base[kWarps - 1][1] + s_tot[kWarps - 1][1];
+        p.counters[6] = (int)min(E, (long long)0x7fffffff);
+        p.counters[7] = (int)min(Cn, (long long)0x7fffffff);
+        p.counters[2] = 0;   // work counter of the force kernel
+        if (E > p.pl_cap || Cn > p.chunk_cap) atomicOr(p.err, ERR_LIST);
+    }
+}
+
+// Entry of one j-cluster: the i-atoms of the clusters in range that lie within
+// r_cut + skin of the j-cluster's box (padding slots are far away), as a
+// column-major mask (bit a*8 + k: atom a of i-cluster k), and whether an
+// i-cluster in range may share a fragment with it.  The i-atoms are broadcast
+// reads of the staged SC.
+__device__ __forceinline__ uint4 list_entry(const Params& p, const ListWarp& w, const ListJ& j, unsigned any_m,
+                                            float rcb2)
+{
+    const int2 jfr = j.m ? p.bb_frag[j.jc] : make_int2(0, 0);
+    unsigned mlo = 0u, mhi = 0u;
+    bool share = false;
+#pragma unroll
+    for (int k = 0; k < kSuperClusters; ++k) {
+        if (!((any_m >> k) & 1u)) continue;   // no lane has i-cluster k in range
+        const bool kin = (j.m >> k) & 1u;
+#pragma unroll
+        for (int a = 0; a < kClusterSize; ++a) {
+            const float4 xi = w.ip[k * kClusterSize + a];
+            const float gx = fmaxf(0.0f, fmaxf(xi.x - j.jh.x, j.jl.x - xi.x));
+            const float gy = fmaxf(0.0f, fmaxf(xi.y - j.jh.y, j.jl.y - xi.y));
+            const float gz = fmaxf(0.0f, fmaxf(xi.z - j.jh.z, j.jl.z - xi.z));
+            const bool in = kin && __fmaf_rn(gz, gz, __fmaf_rn(gy, gy, __fmul_rn(gx, gx))) < rcb2;
+            if (a < 4) mlo |= (in ? 1u : 0u) << (a * 8 + k);
+            else mhi |= (in ? 1u : 0u) << ((a - 4) * 8 + k);
+        }
+        const int2 ifr = w.fr[k];
+        share |= kin && !(ifr.y < jfr.x || jfr.y < ifr.x);
+    }
+    return make_uint4((unsigned)j.jc, (unsigned)j.nb | (share ? kEntryExcl : 0u), mlo, mhi);
+}
+
+__global__ void __launch_bounds__(kListWarps * 32, 4) k_list_write(Params p)
+{
+    constexpr unsigned kFull = 0xffffffffu;
+    __shared__ ListWarp s_w[kListWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    ListWarp& w = s_w[warp];
+    if (*p.err & (ERR_CELL | ERR_LIST)) return;
+    const int n_sc = p.counters[0];
+    const int G = list_parts(n_sc);
+    const float rcb = p.rlist_f + kBBoxMargin;
+    const float rcb2 = rcb * rcb;
+    for (int item = blockIdx.x * kListWarps + warp; item < n_sc * G; item += gridDim.x * kListWarps) {
+        const int sc = item / G, gr = item - sc * G;
+        const int tot = p.sc_tot[sc];
+        if (tot == 0) continue;
+        const ListSC s = list_sc(p, sc);
+        const int e0 = p.sc_eoff[sc], c0 = p.sc_coff[sc];
+        if (gr == 0)
+            for (int t = lane; t * kChunk < tot; t += 32)
+                p.pl_chunk[c0 + t] = make_int4(sc, e0 + t * kChunk, min(kChunk, tot - t * kChunk), s.rr);
+        // this item's first entry: the SC's offset plus the counts of its earlier parts
+        const int cnt_l = lane < G ? p.list_cnt[sc * kHalfShell + lane] : 0;
+        int pre = lane < gr ? cnt_l : 0;
+        for (int o = 16; o; o >>= 1) pre += __shfl_xor_sync(kFull, pre, o);
+        const int mine = __shfl_sync(kFull, cnt_l, gr);
+        if (mine == 0) continue;
+        int total;
+        const ListCell c = list_cells(p, s, lane, &total);
+        const int i0 = (int)((long long)total * gr / G), i1 = (int)((long long)total * (gr + 1) / G);
+        __syncwarp();
+        if (lane < s.ncl) {
+            w.lo[lane] = p.bb_lo[s.fc + lane];
+            w.hi[lane] = p.bb_hi[s.fc + lane];
+            w.fr[lane] = p.bb_frag[s.fc + lane];
+        }
+        for (int a = lane; a < kSCAtoms; a += 32) {
+            // slot order (cluster k, atom a); absent clusters far away
+            float4 v = make_float4(1.0e6f, 1.0e6f, 1.0e6f, 0.0f);
+            if ((a >> 3) < s.ncl) {
+                const int slot = s.fc * kClusterSize + a;
+                if (p.precision == 0) {
+                    v = p.xq[slot];
+                } else {
+                    const double4_32a t = p.xq64[slot];
+                    v = make_float4((float)t.x, (float)t.y, (float)t.z, 0.0f);
                 }
-                for (unsigned pend = bal; pend; pend &= pend - 1u) {
-                    const int L = __ffs(pend) - 1;
-                    const unsigned mL = __shfl_sync(0xffffffffu, m, L);
-                    const float jlx = __shfl_sync(0xffffffffu, blo.x, L) + Dfx;
-                    const float jly = __shfl_sync(0xffffffffu, blo.y, L) + Dfy;
-                    const float jlz = __shfl_sync(0xffffffffu, blo.z, L) + Dfz;
-                    const float jhx = __shfl_sync(0xffffffffu, bhi.x, L) + Dfx;
-                    const float jhy = __shfl_sync(0xffffffffu, bhi.y, L) + Dfy;
-                    const float jhz = __shfl_sync(0xffffffffu, bhi.z, L) + Dfz;
-                    auto near = [&](float4 xi) {
-                        const float gx = fmaxf(0.0f, fmaxf(xi.x - jhx, jlx - xi.x));
-                        const float gy = fmaxf(0.0f, fmaxf(xi.y - jhy, jly - xi.y));
-                        const float gz = fmaxf(0.0f, fmaxf(xi.z - jhz, jlz - xi.z));
-                        return __fmaf_rn(gz, gz, __fmaf_rn(gy, gy, __fmul_rn(gx, gx))) < rcb2;
-                    };
-                    const bool kin = (mL >> (lane & 7)) & 1u;
-                    const bool in0 = kin && near(s_ip[lane]);
-                    const bool in1 = kin && near(s_ip[lane + 32]);
-                    const unsigned alo = __ballot_sync(0xffffffffu, in0);
-                    const unsigned ahi = __ballot_sync(0xffffffffu, in1);
-                    // fragment ranges of the i-clusters in range against the j-cluster's
-                    const int2 jfr = make_int2(__shfl_sync(0xffffffffu, bfr.x, L), __shfl_sync(0xffffffffu, bfr.y, L));
-                    const bool ov = lane < kSuperClusters && ((mL >> lane) & 1u) &&
-                                    !(s_fr[lane].y < jfr.x || jfr.y < s_fr[lane].x);
-                    const bool share = __any_sync(0xffffffffu, ov);
-                    if (lane == L) {
-                        my_lo = alo;
-                        my_hi = ahi;
-                        my_share = share;
-                    }
-                }
-                if (m && at < end)
-                    p.pl[at] = make_uint4((unsigned)(base + lane), (unsigned)nb | (my_share ? kEntryExcl : 0u), my_lo,
-                                          my_hi);
-                off += __popc(bal);
             }
-            // both passes see the same boxes and round identically, so `off` ends at
-            // this warp's share; should it fall short, pad with empty entries (a
-            // real cluster, no i-atom in range) rather than leave slots unwritten
-            for (int at = off + lane; at < min(base_sc + s_cnt[warp] + cnt, end); at += 32)
-                p.pl[at] = make_uint4((unsigned)fc, (unsigned)nb, 0u, 0u);
-            for (int t = threadIdx.x; t * kChunk < tot; t += blockDim.x)
-                p.pl_chunk[cbase + t] = make_int4(sc, base_sc + t * kChunk, min(kChunk, tot - t * kChunk), rr);
+            w.ip[a] = v;
         }
-        // the write pass re-reads the boxes (batches after the first): no warp may
-        // stage the next super-cluster's boxes before every warp is done with these
-        __syncthreads();
+        __syncwarp();
+        int off = e0 + pre;
+        const int end = off + mine;
+        for (int base = i0; base < i1; base += 32) {
+            const ListJ j = list_j(p, w, s, c, base + lane, i1, rcb2);
+            const unsigned bal = __ballot_sync(kFull, j.m != 0u);
+            const int at = off + __popc(bal & ((1u << lane) - 1u));
+            const uint4 e = list_entry(p, w, j, __reduce_or_sync(kFull, j.m), rcb2);
+            if (j.m && at < end) p.pl[at] = e;
+            off += __popc(bal);
+        }
+        // both passes see the same boxes and round identically, so `off` ends at
+        // `end`; should it fall short, pad with empty entries (a real cluster, no
+        // i-atom in range) rather than leave slots unwritten
+        for (int at = off + lane; at < end; at += 32) p.pl[at] = make_uint4((unsigned)s.fc, 0u, 0u, 0u);
     }
 }
 
@@ -589,7 +756,7 @@ __global__ void __launch_bounds__(FP64 ? 256 : 384, 2) k_pair(Params p)
             const int n_t = (int)__reduce_max_sync(kFull, (unsigned)__popc(col0));
 
             T fj0x = 0, fj0y = 0, fj0z = 0, fj1x = 0, fj1y = 0, fj1z = 0;
-            unsigned keep = 0u;   // PRUNE: this column's i-clusters with a j-atom in range
+            unsigned keep = 0u;   // PRUNE: i-clusters whose atom tx has a j-atom of this lane in range
             bool share = false;   // PRUNE: a pair in range within one fragment
             // DIAG: the self-cluster diagonal (i < j inside the cluster); EXCL:
             // pairs within one fragment are possible; PRUNE: build step
@@ -625,11 +792,10 @@ __global__ void __launch_bounds__(FP64 ? 256 : 384, 2) k_pair(Params p)
                                                   rc2, acc.x, acc.y, acc.z, fj1x, fj1y, fj1z, acc.w, npair, erc, irc,
                                                   r21, h1);
                     w.fi[ty * kFiRow + ia] = acc;
-                    if (PRUNE) {
+                    if (PRUNE) {   // this lane's pairs in range: combined over the warp after the entry
                         const bool n0 = ok0 && r20 < rl2, n1 = ok1 && r21 < rl2;
-                        const unsigned b = __ballot_sync(kFull, n0 || n1);
-                        if (k < 8 && (((b | (b >> 8) | (b >> 16) | (b >> 24)) >> tx) & 1u)) keep |= 1u << k;
-                        if (EXCL) share |= __any_sync(kFull, (n0 && ti.y == t0.y) || (n1 && ti.y == t1.y));
+                        if ((n0 || n1) && k < 8) keep |= 1u << k;
+                        if (EXCL) share |= (n0 && ti.y == t0.y) || (n1 && ti.y == t1.y);
                     }
                 }
             };
@@ -637,9 +803,11 @@ __global__ void __launch_bounds__(FP64 ? 256 : 384, 2) k_pair(Params p)
                 if ((unsigned)kdiag < (unsigned)ncl) tiles(std::true_type{}, std::true_type{}, std::true_type{});
                 else if (excl) tiles(std::false_type{}, std::true_type{}, std::true_type{});
                 else tiles(std::false_type{}, std::false_type{}, std::true_type{});
-                // columns back to the column-major mask (byte tx)
+                // columns back to the column-major mask (byte tx: the OR over the
+                // column's four lane rows), and any pair in range within a fragment
                 const unsigned klo = __reduce_or_sync(kFull, tx < 4 ? keep << ((tx & 3) * 8) : 0u);
                 const unsigned khi = __reduce_or_sync(kFull, tx >= 4 ? keep << ((tx & 3) * 8) : 0u);
+                share = __any_sync(kFull, share);
                 if (lane == 0) {
                     if (klo != mlo || khi != mhi)
                         *reinterpret_cast<uint2*>(&p.pl[ch.y + v].z) = make_uint2(klo, khi);
@@ -981,7 +1149,9 @@ static int max_blocks(int warps, int n_ts)
 
 void launch_pair_list(const Params& p, cudaStream_t s, int blocks)
 {
-    k_pair_list<<<blocks, kHalfShell * 32, 0, s>>>(p);
+    k_list_count<<<blocks, kListWarps * 32, 0, s>>>(p);
+    k_list_scan<<<1, 1024, 0, s>>>(p);
+    k_list_write<<<blocks, kListWarps * 32, 0, s>>>(p);
 }
 
 void launch_pair_forces(const Params& p, cudaStream_t s, bool energy, int blocks, int warps)

@@ -30,6 +30,7 @@ struct md_handle {
     cudaStream_t cap_stream = nullptr;   // private stream used for graph capture
     cudaStream_t body_stream = nullptr;  // captures the bodies of the rebuild IF node
     cudaGraphExec_t exec = nullptr;
+    cudaGraphExec_t exec_multi = nullptr;   // kMultiSteps consecutive steps in one graph (not in profile mode)
     cudaEvent_t ev_pair0 = nullptr, ev_pair1 = nullptr;   // captured into the graph
     cudaGraph_t graph = nullptr;                          // kept for event-node updates
     cudaGraphNode_t node_ev0 = nullptr, node_ev1 = nullptr;
@@ -37,7 +38,7 @@ struct md_handle {
     int prof_next = 0;                                    // pairs in flight
     long long list_grows = 0;
     int grid_atoms = 1, grid_cells = 1, sort_threads = 1024;
-    int pair_blocks = 1, pair_warps = 8, list_blocks = 1;
+    int pair_blocks = 1, pair_warps = 8, list_blocks = 1, list_bps = 8;
     long long host_step = 0;             // steps enqueued
     long long pending = 0;               // enqueued steps whose status is not read yet
     bool poisoned = false;
@@ -54,6 +55,7 @@ struct md_handle {
 namespace {
 
 constexpr int kProfPool = 256;   // pair-kernel event pairs in flight (profile mode)
+constexpr int kMultiSteps = 8;   // steps per launch of the multi-step graph
 
 thread_local std::string g_init_error;
 
@@ -195,16 +197,16 @@ void enqueue_rebuild_from_ref(md_handle* h, cudaStream_t s)
     launch_probe(P, s, true);
 }
 
-void enqueue_step(md_handle* h, cudaStream_t s)
+void enqueue_step(md_handle* h, cudaStream_t s, bool events)
 {
     int mode = STEP_KICK_DRIFT | STEP_ADVANCE | (h->cfg.cr_enabled ? STEP_CR : 0);
     launch_step_a(h->P, mode, s, h->grid_atoms);
     launch_cells(h->P, s, h->grid_atoms, h->grid_cells, h->sort_threads);
     launch_pair_list(h->P, s, h->list_blocks);
     // external event nodes: the events are recorded on every graph replay
-    if (h->cfg.profile) cudaEventRecordWithFlags(h->ev_pair0, s, cudaEventRecordExternal);
+    if (events) cudaEventRecordWithFlags(h->ev_pair0, s, cudaEventRecordExternal);
     launch_pair_forces(h->P, s, false, h->pair_blocks, h->pair_warps);
-    if (h->cfg.profile) cudaEventRecordWithFlags(h->ev_pair1, s, cudaEventRecordExternal);
+    if (events) cudaEventRecordWithFlags(h->ev_pair1, s, cudaEventRecordExternal);
     launch_probe(h->P, s, false);
 }
 
@@ -272,7 +274,7 @@ md_status rebuild_checked(md_handle* h, bool* grown, bool from_ref = false)
 // record in its slot, decides whether the list is used up and sets the
 // condition of an IF node whose body is the cell + list build; the forces
 // follow.
-md_status capture_buffered_step(md_handle* h)
+md_status capture_buffered_step(md_handle* h, bool events)
 {
     cudaStream_t s = h->cap_stream;
     cudaStreamCaptureStatus cs;
@@ -299,10 +301,40 @@ md_status capture_buffered_step(md_handle* h)
     launch_pair_list(h->P, h->body_stream, h->list_blocks);
     CU(cudaStreamEndCapture(h->body_stream, &rebuild));
     CU(cudaStreamUpdateCaptureDependencies(s, &cn, nullptr, 1, cudaStreamSetCaptureDependencies));
-    if (h->cfg.profile) cudaEventRecordWithFlags(h->ev_pair0, s, cudaEventRecordExternal);
+    if (events) cudaEventRecordWithFlags(h->ev_pair0, s, cudaEventRecordExternal);
     launch_pair_forces(h->P, s, false, h->pair_blocks, h->pair_warps);
-    if (h->cfg.profile) cudaEventRecordWithFlags(h->ev_pair1, s, cudaEventRecordExternal);
+    if (events) cudaEventRecordWithFlags(h->ev_pair1, s, cudaEventRecordExternal);
     launch_probe(h->P, s, false);
+    return MD_OK;
+}
+
+// kMultiSteps consecutive steps in one graph (each step with its own rebuild
+// IF node and conditional handle), so that md_step(n) issues n / kMultiSteps
+// graph launches; the steps are those of the single-step graph, in order.
+md_status capture_multi(md_handle* h)
+{
+    if (h->exec_multi) {
+        cudaGraphExecDestroy(h->exec_multi);
+        h->exec_multi = nullptr;
+    }
+    if (h->cfg.profile) return MD_OK;   // profile mode re-points per-step event nodes: one step per launch
+    CU(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < kMultiSteps; ++k) {
+        md_status st = MD_OK;
+        if (h->cfg.list_skin_nm > 0) st = capture_buffered_step(h, false);
+        else enqueue_step(h, h->cap_stream, false);
+        if (st != MD_OK) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(h->cap_stream, &g);
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+    }
+    cudaGraph_t g = nullptr;
+    CU(cudaStreamEndCapture(h->cap_stream, &g));
+    cudaError_t e = cudaGraphInstantiate(&h->exec_multi, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(h, MD_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
     return MD_OK;
 }
 
@@ -318,7 +350,7 @@ md_status capture_graph(md_handle* h)
     }
     CU(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
     if (h->cfg.list_skin_nm > 0) {
-        md_status st = capture_buffered_step(h);
+        md_status st = capture_buffered_step(h, h->cfg.profile != 0);
         if (st != MD_OK) {
             cudaGraph_t g = nullptr;
             cudaStreamEndCapture(h->cap_stream, &g);
@@ -326,7 +358,7 @@ md_status capture_graph(md_handle* h)
             return st;
         }
     } else {
-        enqueue_step(h, h->cap_stream);
+        enqueue_step(h, h->cap_stream, h->cfg.profile != 0);
     }
     CU(cudaStreamEndCapture(h->cap_stream, &h->graph));
     if (h->cfg.profile) {
@@ -350,7 +382,7 @@ md_status capture_graph(md_handle* h)
     }
     cudaError_t e = cudaGraphInstantiate(&h->exec, h->graph, 0);
     if (e != cudaSuccess) return fail(h, MD_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
-    return MD_OK;
+    return capture_multi(h);
 }
 
 // Pair-kernel times of the launched steps (profile mode).
@@ -368,36 +400,75 @@ md_status drain_profile(md_handle* h)
     return MD_OK;
 }
 
-// Choose the pair-kernel launch shape by timing (results are identical for
-// every shape: the fixed-point sums do not depend on it).
+// Choose the launch shapes by timing (results are identical for every shape:
+// the fixed-point sums and the list's layout do not depend on them): first the
+// cell sort's block size and the list build's blocks per SM (a full cell +
+// list build at the current positions, which leaves the same list), then the
+// force kernel's warps per block and blocks per SM.  Axes pinned in md_config
+// are left alone.
 md_status autotune(md_handle* h)
 {
     const bool fp64 = h->cfg.precision == MD_PREC_FP64;
     cudaEvent_t a, b;
     CU(cudaEventCreate(&a));
     CU(cudaEventCreate(&b));
+    auto timed = [&](auto&& launch, float* out) -> md_status {
+        float tot = 0.0f;
+        for (int rep = 0; rep < 4; ++rep) {
+            CU(cudaEventRecord(a, h->stream));
+            launch();
+            CU(cudaEventRecord(b, h->stream));
+            CU(cudaEventSynchronize(b));
+            float ms = 0.0f;
+            CU(cudaEventElapsedTime(&ms, a, b));
+            if (rep) tot += ms;
+        }
+        *out = tot;
+        return MD_OK;
+    };
+    {
+        const int st_c[] = {256, 1024};
+        const int lb_c[] = {2, 4, 8, 16};
+        float best = 1e30f;
+        int bs = h->sort_threads, bl = h->list_bps;
+        for (int st : st_c) {
+            if (h->cfg.sort_threads && st != h->cfg.sort_threads) continue;
+            for (int lb : lb_c) {
+                if (h->cfg.list_blocks_per_sm && lb != h->cfg.list_blocks_per_sm) continue;
+                const int lblocks =
+                    (int)std::max(1LL, std::min(((long long)h->P.sc_cap + 7) / 8, (long long)lb * h->n_sm));
+                float ms = 0.0f;
+                md_status s = timed([&]() {
+                    launch_cells(h->P, h->stream, h->grid_atoms, h->grid_cells, st);
+                    launch_pair_list(h->P, h->stream, lblocks);
+                }, &ms);
+                if (s != MD_OK) return s;
+                if (ms < best) { best = ms; bs = st; bl = lb; }
+            }
+        }
+        h->sort_threads = bs;
+        h->list_bps = bl;
+        h->list_blocks = (int)std::max(1LL, std::min(((long long)h->P.sc_cap + 7) / 8, (long long)bl * h->n_sm));
+    }
     float best = 1e30f;
     int bw = h->pair_warps, bb = h->pair_blocks;
     const int warps_c[] = {4, 8, 12};
     for (int w : warps_c) {
         if (fp64 && w > 8) continue;   // the FP64 kernel takes up to 256 threads per block
+        if (h->cfg.pair_warps && w != h->cfg.pair_warps) continue;
         int maxb = pair_max_blocks_per_sm(fp64, false, h->P.screening != 0, w, h->NTS_LJ);
         for (int bps = 1; bps <= maxb; ++bps) {
-            int blocks = bps * h->n_sm;
-            float tot = 0.0f;
-            for (int rep = 0; rep < 4; ++rep) {
+            if (h->cfg.pair_blocks_per_sm && bps != h->cfg.pair_blocks_per_sm) continue;
+            const int blocks = bps * h->n_sm;
+            float ms = 0.0f;
+            md_status s = timed([&]() {
                 // reset the work counter only (the list stays; forces are rebuilt afterwards)
-                CU(cudaMemsetAsync(h->P.counters + 2, 0, sizeof(int), h->stream));
-                CU(cudaEventRecord(a, h->stream));
+                cudaMemsetAsync(h->P.counters + 2, 0, sizeof(int), h->stream);
                 launch_pair_forces(h->P, h->stream, false, blocks, w);
-                CU(cudaEventRecord(b, h->stream));
-                CU(cudaEventSynchronize(b));
-                float ms = 0.0f;
-                CU(cudaEventElapsedTime(&ms, a, b));
-                if (rep) tot += ms;
-            }
-            if (tot < best) {
-                best = tot;
+            }, &ms);
+            if (s != MD_OK) return s;
+            if (ms < best) {
+                best = ms;
                 bw = w; bb = blocks;
             }
         }
@@ -500,6 +571,15 @@ md_status validate(const md_config* c, const md_system* s)
         return fail(h, MD_ERR_INVALID_ARG, "dev_alloc and dev_free must be given together");
     if (c->list_reserve < 0 || c->list_reserve > 4096)
         return fail(h, MD_ERR_INVALID_ARG, "list_reserve must be in [0, 4096]");
+    if (c->pair_warps != 0 && c->pair_warps != 4 && c->pair_warps != 8 &&
+        !(c->pair_warps == 12 && c->precision == MD_PREC_MIXED))
+        return fail(h, MD_ERR_INVALID_ARG, "pair_warps must be 0, 4, 8 or 12 (12: mixed precision only)");
+    if (c->pair_blocks_per_sm < 0 || c->pair_blocks_per_sm > 64)
+        return fail(h, MD_ERR_INVALID_ARG, "pair_blocks_per_sm must be in [0, 64]");
+    if (c->sort_threads != 0 && c->sort_threads != 256 && c->sort_threads != 1024)
+        return fail(h, MD_ERR_INVALID_ARG, "sort_threads must be 0, 256 or 1024");
+    if (c->list_blocks_per_sm < 0 || c->list_blocks_per_sm > 16)
+        return fail(h, MD_ERR_INVALID_ARG, "list_blocks_per_sm must be in [0, 16]");
     if (s->n_atoms < 1) return fail(h, MD_ERR_INVALID_ARG, "n_atoms must be >= 1");
     if (!s->x || !s->v || !s->species || !s->fragment || !s->replica_offset || !s->seed || !s->box ||
         !s->volume)
@@ -842,6 +922,8 @@ static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* 
     DALLOC(P.tmp_key, N);
     DALLOC(P.sc_cell, P.sc_cap); DALLOC(P.sc_first, P.sc_cap); DALLOC(P.sc_ncl, P.sc_cap);
     DALLOC(P.counters, 8);
+    DALLOC(P.list_cnt, (size_t)P.sc_cap * kHalfShell);
+    DALLOC(P.sc_tot, P.sc_cap); DALLOC(P.sc_eoff, P.sc_cap); DALLOC(P.sc_coff, P.sc_cap);
     P.pl = nullptr;
     P.pl_chunk = nullptr;
     {
@@ -968,20 +1050,31 @@ static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* 
     h->grid_atoms = (N + 255) / 256;
     h->grid_cells = std::max(1, std::min(C, h->n_sm * 8));
     // many cells per SM: small CTAs keep more (latency-bound) cells in flight
-    h->sort_threads = C >= 4 * h->n_sm ? 256 : 1024;
+    h->sort_threads = c.sort_threads ? c.sort_threads : (C >= 4 * h->n_sm ? 256 : 1024);
     {
         // the shape with the most resident warps per SM (8-warp blocks on a tie):
         // with many LJ type states the per-block table limits 8-warp blocks
         const bool fp64 = c.precision == MD_PREC_FP64;
-        h->pair_warps = 8;
-        int best = 8 * pair_max_blocks_per_sm(fp64, false, c.screening != 0, 8, h->NTS_LJ);
-        if (!fp64) {
-            const int w12 = 12 * pair_max_blocks_per_sm(fp64, false, c.screening != 0, 12, h->NTS_LJ);
-            if (w12 > best) { best = w12; h->pair_warps = 12; }
+        if (c.pair_warps) {
+            h->pair_warps = c.pair_warps;
+        } else {
+            h->pair_warps = 8;
+            int best = 8 * pair_max_blocks_per_sm(fp64, false, c.screening != 0, 8, h->NTS_LJ);
+            if (!fp64) {
+                const int w12 = 12 * pair_max_blocks_per_sm(fp64, false, c.screening != 0, 12, h->NTS_LJ);
+                if (w12 > best) h->pair_warps = 12;
+            }
         }
-        h->pair_blocks = h->n_sm * (best / h->pair_warps);
+        const int maxb = pair_max_blocks_per_sm(fp64, false, c.screening != 0, h->pair_warps, h->NTS_LJ);
+        if (c.pair_blocks_per_sm > maxb)
+            return fail(h, MD_ERR_INVALID_ARG, "pair_blocks_per_sm exceeds the " + std::to_string(maxb) +
+                                                   " blocks of " + std::to_string(h->pair_warps) +
+                                                   " warps an SM holds for this system");
+        h->pair_blocks = h->n_sm * (c.pair_blocks_per_sm ? c.pair_blocks_per_sm : maxb);
     }
-    h->list_blocks = std::max(1, std::min(P.sc_cap, 4 * h->n_sm));
+    // list kernels: one warp per super-cluster (or per group of its cells), 8 warps per block
+    h->list_bps = c.list_blocks_per_sm ? c.list_blocks_per_sm : 8;
+    h->list_blocks = (int)std::max(1LL, std::min(((long long)P.sc_cap + 7) / 8, (long long)h->list_bps * h->n_sm));
     CU(cudaDeviceSynchronize());
 
     // ---- initial cell list, cluster-pair list and forces F_0 ----
@@ -1012,6 +1105,7 @@ void md_finalize(md_handle* h)
     if (!h) return;
     cudaDeviceSynchronize();
     if (h->exec) cudaGraphExecDestroy(h->exec);
+    if (h->exec_multi) cudaGraphExecDestroy(h->exec_multi);
     for (void* p : h->allocs) {
         if (h->cfg.dev_free) h->cfg.dev_free(p, h->cfg.alloc_ctx);
         else cudaFree(p);
@@ -1188,7 +1282,10 @@ namespace {
 
 md_status launch_steps(md_handle* h, int n)
 {
-    for (int k = 0; k < n; ++k) {
+    int k = 0;
+    if (h->exec_multi)
+        for (; k + kMultiSteps <= n; k += kMultiSteps) CU(cudaGraphLaunch(h->exec_multi, h->stream));
+    for (; k < n; ++k) {
         if (h->cfg.profile) {
             if (h->prof_next == kProfPool) {
                 md_status st = drain_profile(h);
@@ -1755,6 +1852,8 @@ md_status md_get_timing(md_handle* h, md_timing* out)
     CU(cudaMemcpy(&used, h->P.counters + 6, sizeof(int), cudaMemcpyDeviceToHost));
     out->list_entries = used;
     out->list_grows = h->list_grows;
+    out->sort_threads = h->sort_threads;
+    out->list_blocks_per_sm = h->list_bps;
     if (h->cfg.list_skin_nm > 0) {
         int b = 0;
         CU(cudaMemcpy(&b, h->P.builds, sizeof(int), cudaMemcpyDeviceToHost));

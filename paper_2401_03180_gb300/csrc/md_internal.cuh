@@ -166,6 +166,10 @@ struct Params {
     int* sc_first;           // [sc_cap] first cluster
     int* sc_ncl;             // [sc_cap] clusters in the super-cluster
     int* counters;           // [0] n_sc, [1] n_slots, [2] work, [3] ticket, [6] list entries, [7] chunks
+    int* list_cnt;           // [sc_cap * kHalfShell] entries of each super-cluster in each half-shell cell
+    int* sc_tot;             // [sc_cap] entries per super-cluster
+    int* sc_eoff;            // [sc_cap] first entry of each super-cluster
+    int* sc_coff;            // [sc_cap] first chunk of each super-cluster
     PairEntry* pl;           // [pl_cap] cluster-pair list (j-cluster, half-shell index, i-atom mask)
     int4* pl_chunk;          // [chunk_cap] (SC, first entry, entries, replica)
     int pl_cap, chunk_cap;
@@ -266,9 +270,10 @@ __host__ __device__ __forceinline__ void half_shell(int nb, int& dx, int& dy, in
 // relative to the centre (minimum image when periodic: between list builds an
 // atom may have been wrapped across the box), charge, LJ type state, fragment;
 // the slot's force sums are cleared.  Used by the build and by the refresh
-// between builds, so both round identically.
-__device__ __forceinline__ void pack_record(const Params& p, int slot, const double xi[3], const double cen[3],
-                                            int periodic, const double box[3], int sp, int qi, int fr)
+// between builds, so both round identically.  Returns the relative position
+// rounded to FP32 (the precision of the cluster bounding boxes).
+__device__ __forceinline__ float4 pack_record(const Params& p, int slot, const double xi[3], const double cen[3],
+                                              int periodic, const double box[3], int sp, int qi, int fr)
 {
     double d[3] = {xi[0] - cen[0], xi[1] - cen[1], xi[2] - cen[2]};
     if (periodic)
@@ -281,11 +286,12 @@ __device__ __forceinline__ void pack_record(const Params& p, int slot, const dou
     else p.xq64[slot] = make_double4_32a(d[0], d[1], d[2], (double)qi);
     p.tf[slot] = make_int2(p.lj_ts_off[sp] + qi, fr);
     p.fx[slot] = 0; p.fy[slot] = 0; p.fz[slot] = 0; p.epot[slot] = 0;
+    return make_float4((float)d[0], (float)d[1], (float)d[2], 0.0f);
 }
-__device__ __forceinline__ void pack_slot(const Params& p, int slot, int i, const double cen[3], const Grid& g)
+__device__ __forceinline__ float4 pack_slot(const Params& p, int slot, int i, const double cen[3], const Grid& g)
 {
     const double xi[3] = {p.x[i], p.y[i], p.z[i]};
-    pack_record(p, slot, xi, cen, g.periodic, g.box, p.species[i], p.q[i], p.frag[i]);
+    return pack_record(p, slot, xi, cen, g.periodic, g.box, p.species[i], p.q[i], p.frag[i]);
 }
 
 // Launch helpers implemented in the .cu files.

@@ -8,7 +8,7 @@
 // entry point serves them: all the scratch it needs (cell list, packed
 // coordinates, fixed-point force sums, grid and screening bookkeeping) lives
 // in one file-scope __device__ array of a fixed, modest size
-// (MD_NOALLOC_MAX_ATOMS atoms, MD_NOALLOC_MAX_CELLS cells; about 10.5 MB) that
+// (MD_NOALLOC_MAX_ATOMS atoms, MD_NOALLOC_MAX_CELLS cells; about 11 MB) that
 // every GPU loading the library holds until the process exits.  The caller
 // passes inputs and the output buffer; nothing is allocated.
 //
@@ -42,7 +42,7 @@ struct Layout {
     size_t x, y, z, vx, vy, vz, species, q, h, frag, rep, local_id, slot_of, atom_cell, atom_rank;
     size_t zs, ts_off, hdtm, mass, auger, volume, rep_off, lj;
     size_t grid, rs, acc, cell_count, cell_start, cell_pstart, tmp_key, sc_cell, sc_first, sc_ncl;
-    size_t counters, xq, tf, atom_of, bb_lo, bb_hi, bb_frag, fx, fy, fz, epot, pair_count, err, step, kick;
+    size_t counters, list_cnt, sc_tot, sc_eoff, sc_coff, xq, tf, atom_of, bb_lo, bb_hi, bb_frag, fx, fy, fz, epot, pair_count, err, step, kick;
     size_t pl, pl_chunk, cl_cen;
     size_t total;
 };
@@ -66,6 +66,9 @@ constexpr Layout make_layout()
     L.tmp_key = take(8 * kNaMax);
     L.sc_cell = take(4 * kClusterCap); L.sc_first = take(4 * kClusterCap); L.sc_ncl = take(4 * kClusterCap);
     L.counters = take(4 * 8);
+    L.list_cnt = take(4 * (size_t)kClusterCap * kHalfShell);
+    L.sc_tot = take(4 * kClusterCap);
+    L.sc_eoff = take(4 * kClusterCap); L.sc_coff = take(4 * kClusterCap);
     L.xq = take(32 * (size_t)kSlotCap);                      // float4 or double4_32a
     L.tf = take(8 * (size_t)kSlotCap); L.atom_of = take(4 * (size_t)kSlotCap);
     L.bb_lo = take(16 * (size_t)kClusterCap); L.bb_hi = take(16 * (size_t)kClusterCap);
@@ -236,6 +239,8 @@ extern "C" md_status md_forces_noalloc(const md_forces_input* in, double* d_f, v
     P.cell_pstart = (int*)(B + kL.cell_pstart); P.tmp_key = (unsigned long long*)(B + kL.tmp_key);
     P.sc_cell = (int*)(B + kL.sc_cell); P.sc_first = (int*)(B + kL.sc_first); P.sc_ncl = (int*)(B + kL.sc_ncl);
     P.counters = (int*)(B + kL.counters);
+    P.list_cnt = (int*)(B + kL.list_cnt); P.sc_tot = (int*)(B + kL.sc_tot);
+    P.sc_eoff = (int*)(B + kL.sc_eoff); P.sc_coff = (int*)(B + kL.sc_coff);
     P.xq = (float4*)(B + kL.xq); P.xq64 = (double4_32a*)(B + kL.xq);
     P.tf = (int2*)(B + kL.tf); P.atom_of = (int*)(B + kL.atom_of);
     P.bb_lo = (float4*)(B + kL.bb_lo); P.bb_hi = (float4*)(B + kL.bb_hi); P.bb_frag = (int2*)(B + kL.bb_frag);
@@ -296,7 +301,7 @@ extern "C" md_status md_forces_noalloc(const md_forces_input* in, double* d_f, v
     const int blocks = n_sm * pair_max_blocks_per_sm(in->precision == MD_PREC_FP64, false, false, warps, nts);
     launch_step_a(P, 0, s, (n + 255) / 256);                           // grid and screening
     launch_cells(P, s, (n + 255) / 256, std::max(1, std::min(g.cell_cap, n_sm * 8)), 1024);
-    launch_pair_list(P, s, std::max(1, std::min(P.sc_cap, 4 * n_sm)));
+    launch_pair_list(P, s, std::max(1, std::min((P.sc_cap + 7) / 8, 8 * n_sm)));
     launch_pair_forces(P, s, false, blocks, warps);
     launch_force_out(P, d_f, s);
     NA_CU(cudaGetLastError());

@@ -49,7 +49,8 @@ class MDConfig(C.Structure):
                 ("dev_free", FREE_FN), ("alloc_ctx", C.c_void_p), ("autotune", C.c_int),
                 ("profile", C.c_int), ("list_reserve", C.c_int), ("list_skin_nm", C.c_double),
                 ("screening", C.c_int), ("langevin_g", C.c_double * MD_MAX_SPECIES),
-                ("charge_mode", C.c_int), ("probe_record", C.c_int)]
+                ("charge_mode", C.c_int), ("probe_record", C.c_int), ("pair_warps", C.c_int),
+                ("pair_blocks_per_sm", C.c_int), ("sort_threads", C.c_int), ("list_blocks_per_sm", C.c_int)]
 
 
 class MDSystem(C.Structure):
@@ -77,7 +78,7 @@ class MDTiming(C.Structure):
     _fields_ = [("pair_ms", C.c_double), ("pair_launches", C.c_int64), ("steps", C.c_int64),
                 ("pair_count_last", C.c_int64), ("tile_warps", C.c_int), ("tile_blocks_per_sm", C.c_int),
                 ("list_capacity", C.c_int64), ("list_entries", C.c_int64), ("list_grows", C.c_int64),
-                ("list_builds", C.c_int64)]
+                ("list_builds", C.c_int64), ("sort_threads", C.c_int), ("list_blocks_per_sm", C.c_int)]
 
 
 class MDForcesInput(C.Structure):
@@ -416,7 +417,10 @@ class IonisingMD:
                  plasma_mode=MD_PLASMA_BOOKKEEPING, max_steps=1000, kappa_fixed=-1.0, t_start_fs=0.0,
                  te_floor_ev=1.0, coulomb_f=COULOMB_F, autotune=False, profile=False, list_reserve=0,
                  list_skin_nm=0.0, screening="debye", langevin_g=None, charge_mode="rates",
-                 probe_record=False, torch_allocator=True, sigma0=None, eps0=None, mass=None):
+                 probe_record=False, torch_allocator=True, sigma0=None, eps0=None, mass=None,
+                 launch_shape=None):
+        """launch_shape: optional dict pinning md_config's launch-shape fields
+        (pair_warps, pair_blocks_per_sm, sort_threads, list_blocks_per_sm)."""
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("IonisingMD needs a CUDA GPU (no CPU fallback)")
@@ -430,6 +434,10 @@ class IonisingMD:
                                   list_skin_nm=list_skin_nm, screening=screening, langevin_g=langevin_g,
                                   charge_mode=charge_mode, sigma0=sigma0, eps0=eps0, mass=mass)
         cfg.probe_record = int(bool(probe_record))
+        for k, v in (launch_shape or {}).items():
+            if k not in ("pair_warps", "pair_blocks_per_sm", "sort_threads", "list_blocks_per_sm"):
+                raise ValueError(f"unknown launch-shape field {k}")
+            setattr(cfg, k, int(v))
         self._keep = keep_c
         self._alloc = TorchAllocator() if torch_allocator else None
         if self._alloc is not None:

@@ -49,6 +49,39 @@ def test_runs_are_bit_identical_and_tile_invariant(prec):
     _same(a, c)
 
 
+SHAPES = [dict(pair_warps=4, pair_blocks_per_sm=2, sort_threads=1024, list_blocks_per_sm=1),
+          dict(pair_warps=12, pair_blocks_per_sm=1, sort_threads=256, list_blocks_per_sm=16),
+          dict(pair_warps=8, pair_blocks_per_sm=3, sort_threads=256, list_blocks_per_sm=2)]
+
+
+@pytest.mark.parametrize("shape", range(len(SHAPES)))
+def test_launch_shapes_give_identical_runs(shape):
+    """Every launch shape the autotuner may pick (force-kernel warps and blocks
+    per SM, cell-sort block size, list-build blocks per SM, which also sets how
+    many warps share a super-cluster's cells) gives the same trajectory, bit
+    for bit, with the Verlet-buffered list rebuilt during the run: on a
+    periodic water box and on a vacuum batch of methane clusters."""
+    s, rc = water(800)
+    atom = W.atomic_data(6.0, pi_scale=500.0)
+    p = [W.Pulse(6.0, 5.0, 2e12, 0.0)]
+    kw = dict(r_cut=rc - 0.04, max_steps=40, t_start_fs=-1.0, list_skin_nm=0.03)   # box >= 3 (r_cut + skin)
+    _same(_run(s, atom, 30, p, **kw), _run(s, atom, 30, p, launch_shape=SHAPES[shape], **kw))
+    reps = [methane(n, seed=k + 31) for k, n in enumerate((40, 75, 23, 31, 52, 18))]
+    b = W.concat(reps)
+    atom8 = W.atomic_data(8.0, pi_scale=1500.0, ci_scale=10.0)
+    kw8 = dict(max_steps=40, t_start_fs=-5.0, list_skin_nm=0.03)
+    p8 = [W.Pulse(8.0, 10.0, 1e12, 0.0)]
+    _same(_run(b, atom8, 30, p8, **kw8), _run(b, atom8, 30, p8, launch_shape=SHAPES[shape], **kw8))
+
+
+def test_launch_shape_outside_occupancy_is_rejected():
+    s, rc = water(200)
+    with pytest.raises(M.MDError) as e:
+        M.IonisingMD(s, W.atomic_data(6.0), r_cut=rc, max_steps=4,
+                     launch_shape=dict(pair_warps=12, pair_blocks_per_sm=40))
+    assert e.value.status == M.MD_ERR_INVALID_ARG
+
+
 def test_batched_replicas_equal_solo_runs():
     # six replicas: more than the step kernel reduces itself, so the batch takes
     # the warp-per-replica reduction and each solo run the in-kernel one

@@ -282,3 +282,33 @@ def test_list_blocks_loop_over_super_clusters(oracle_mod, prec):
     ref = oracle_mod.forces_of_atoms(s, atom, idx, r_cut=1.2, kappa=1.5)
     rms, mx = force_errors(f[idx], ref)
     assert rms <= {"mixed": 1e-5, "fp64": 1e-12}[prec], (rms, mx)
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_cells_beyond_the_sort_shared_memory(oracle_mod, prec):
+    """Cells of more atoms than the cell sort keeps in shared memory (2,048):
+    a 12,000-atom water droplet (6 nm across) with r_cut = 3.1 nm is one cell of
+    12,000 atoms, which the sort ranks from global memory and whose cluster
+    boxes it builds without the shared-memory path.  Forces
+    against the oracle's all pairs, and a short ionising run with rebuilds."""
+    from gpu_common import force_errors
+    s = W.water_droplet(4000, seed=31)
+    rng = np.random.default_rng(22)
+    s.q0[rng.random(s.n_atoms) < 0.2] = 1
+    atom = W.atomic_data(8.0)
+    rc = 3.1
+    assert s.n_atoms > 2 * 2048 and (s.x.max(0) - s.x.min(0)).max() < 2 * (rc + 0.04)
+    g = M.IonisingMD(s, atom, precision=prec, r_cut=rc, cr_enabled=False, kappa_fixed=1.0, max_steps=8,
+                     list_skin_nm=0.04)
+    f = g.get_state(M.MD_FIELD_F)["f"]
+    ref = oracle_mod.OracleMD(s, atom, r_cut=rc, cr_enabled=False, kappa_fixed=1.0).F
+    rms, mx = force_errors(f, ref)
+    assert rms <= {"mixed": 1e-5, "fp64": 1e-12}[prec], (rms, mx)
+    g.step(5)
+    st = g.get_state(M.MD_FIELD_X | M.MD_FIELD_Q | M.MD_FIELD_F)
+    g.close()
+    s2 = W.Sample(x=st["x"], v=s.v, species=s.species, fragment=s.fragment, q0=st["q"],
+                  replica_offset=s.replica_offset, seed=s.seed, box=s.box, volume=s.volume)
+    ref2 = oracle_mod.OracleMD(s2, atom, r_cut=rc, cr_enabled=False, kappa_fixed=1.0).F
+    rms2, mx2 = force_errors(st["f"], ref2)
+    assert rms2 <= {"mixed": 1e-5, "fp64": 1e-12}[prec], (rms2, mx2)
