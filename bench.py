@@ -416,7 +416,8 @@ def run_gpu(args, rank, world, local):
                                     "untimed_steps_before": s0, "placement": args.window},
                    "l2": "flushed between steps (256 MB write, untimed)",
                    "pair_tile": {"warps": tim.tile_warps, "blocks_per_sm": tim.tile_blocks_per_sm},
-                   "build_shape": {"sort_threads": tim.sort_threads, "list_blocks_per_sm": tim.list_blocks_per_sm},
+                   "build_shape": {"sort_threads": tim.sort_threads, "list_blocks_per_sm": tim.list_blocks_per_sm,
+                                   "kernels_per_build": tim.build_kernels},
                    "list_skin_nm": args.skin, "screening": args.screening, "langevin_g": args.langevin,
                    "charges": "table" if args.charge_table else "rates",
                    "bonded": ({"bonds": int(len(s.topology.bonds)), "angles": int(len(s.topology.angles))}
@@ -439,9 +440,9 @@ def run_gpu(args, rank, world, local):
         "e2e": e2e,
         # per step: step kernel + force kernel (the bonded terms run inside it) (+ the
         # probe kernel; + the warp-per-replica reduction above 4 replicas, the step
-        # kernel's inline limit), and 7 more (4 cell kernels + 3 list kernels) in the
-        # steps whose list is rebuilt
-        "gpu_launches": (2 + bool(args.probe) + (s.n_replicas > 4)) * K + 7 * int(tim.list_builds),
+        # kernel's inline limit), and the build's kernels (cells + list, 5 to 12 by
+        # grid size) in the steps whose list is rebuilt
+        "gpu_launches": (2 + bool(args.probe) + (s.n_replicas > 4)) * K + tim.build_kernels * int(tim.list_builds),
         "pair_list": {"skin_nm": args.skin, "builds": int(tim.list_builds), "steps": K,
                       "steps_per_build": (K / tim.list_builds) if tim.list_builds else None,
                       "entries_last_build": int(tim.list_entries), "capacity": int(tim.list_capacity)},
@@ -621,9 +622,9 @@ def run_reference(args, rank, world):
 
 
 def run_profile_case(args):
-    """Kernels launched: init 9 (step kernel, 4 cell kernels, 3 list kernels,
-    forces), then per step the step kernel and the forces, plus 7 when the list
-    is rebuilt; --profile-resume adds the checkpoint round trip (step kernel, 4
+    """Kernels launched: init 10 (step kernel, 5 cell kernels, 3 list kernels,
+    forces), then per step the step kernel and the forces, plus 8 when the list
+    is rebuilt; --profile-resume adds the checkpoint round trip (step kernel, 5
     cell kernels, 3 list kernels, two force launches, refresh)."""
     import torch
     from paper_2401_03180_gb300 import build as B

@@ -306,6 +306,9 @@ typedef struct md_timing {
                                 md_reset_timing (equals steps when the skin is 0) */
     int sort_threads;        /* cell-sort block size in use                 */
     int list_blocks_per_sm;  /* list-build blocks per SM in use             */
+    int build_kernels;       /* kernels of one cell + list build in the step
+                                graph (5 to 12: the scans and the sort take
+                                one or several kernels by grid size)       */
 } md_timing;
 
 typedef struct md_handle md_handle;

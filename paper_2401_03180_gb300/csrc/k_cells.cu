@@ -8,6 +8,8 @@
 // packed arrays hold FP32 (or FP64) coordinates relative to the cell centre,
 // the charge, the type state and the fragment, plus one bounding box per
 // cluster for the pair kernel's prefilter.
+#include <algorithm>
+
 #include "md_internal.cuh"
 
 namespace mdg {
@@ -15,6 +17,9 @@ namespace mdg {
 constexpr int kScanThreads = 1024;
 constexpr int kSortThreads = 1024;
 constexpr int kSortMax = 2048;       // keys per cell kept in shared memory (larger cells sort from global memory)
+constexpr int kSmallCell = 256;      // cells up to this many atoms are sorted by one warp
+constexpr int kScanCellsMulti = 16384;   // grids of at least this many cells are scanned by many CTAs
+constexpr int kSmallWarps = 8;       // warps per block of the one-warp-per-cell sort
 
 __device__ __forceinline__ int cell_coord(double x, double origin, double inv_edge, int n)
 {
@@ -96,18 +101,20 @@ __device__ __forceinline__ void cell_sizes(int n, int& pad, int& nsc)
     nsc = (pad / kClusterSize + kSuperClusters - 1) / kSuperClusters;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_cell_scan(Params p)
+// One block's part of the scan: cells [lo, hi), from the running totals
+// base[0..2] (atoms, padded slots, super-clusters) of the cells before lo.
+// Writes the unpadded and padded starts and the super-cluster table of those
+// cells and clears their counts; leaves the block's totals in s_tot / s_base
+// (warp kWarps-1's base plus total).  WRITE = false: only the totals.
+template <bool WRITE>
+__device__ __forceinline__ void scan_cells(const Params& p, int lo, int hi, const int base[3],
+                                           int (*s_tot)[3], int (*s_base)[3])
 {
     constexpr unsigned kFull = 0xffffffffu;
     constexpr int kWarps = kScanThreads / 32;
-    __shared__ int s_tot[kWarps][3], s_base[kWarps][3];
-    // the grid of this build stays with the list until the next build
-    if (p.grid_b != p.grid)
-        for (int r = threadIdx.x; r < p.n_rep; r += blockDim.x) p.grid_b[r] = p.grid[r];
-    const int C = p.cell_cap_total;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int run = ((C + kWarps - 1) / kWarps + 31) & ~31;
-    const int c_lo = min(warp * run, C), c_hi = min(c_lo + run, C);
+    const int run = ((hi - lo + kWarps - 1) / kWarps + 31) & ~31;
+    const int c_lo = min(lo + warp * run, hi), c_hi = min(c_lo + run, hi);
     int tn = 0, tp = 0, ts = 0;
     for (int c = c_lo + lane; c < c_hi; c += 32) {
         const int n = p.cell_count[c];
@@ -130,9 +137,10 @@ __global__ void __launch_bounds__(kScanThreads) k_cell_scan(Params p)
                 const int u = __shfl_up_sync(kFull, inc[k], o);
                 if (lane >= o) inc[k] += u;
             }
-        for (int k = 0; k < 3; ++k) s_base[lane][k] = inc[k] - v[k];
+        for (int k = 0; k < 3; ++k) s_base[lane][k] = base[k] + inc[k] - v[k];
     }
     __syncthreads();
+    if (!WRITE) return;
     int bn = s_base[warp][0], bp = s_base[warp][1], bs = s_base[warp][2];
     for (int g0 = c_lo; g0 < c_hi; g0 += 32) {
         const int c = g0 + lane;
@@ -161,20 +169,111 @@ __global__ void __launch_bounds__(kScanThreads) k_cell_scan(Params p)
         bp += __shfl_sync(kFull, ip, 31);
         bs += __shfl_sync(kFull, is, 31);
     }
-    if (threadIdx.x == 0) {
-        const int on = s_base[kWarps - 1][0] + s_tot[kWarps - 1][0];
-        const int op = s_base[kWarps - 1][1] + s_tot[kWarps - 1][1];
-        const int os = s_base[kWarps - 1][2] + s_tot[kWarps - 1][2];
-        p.cell_start[C] = on;
-        p.cell_pstart[C] = op;
-        const bool over = op > p.slot_cap || os > p.sc_cap;
-        if (over) atomicOr(p.err, ERR_CELL);
-        p.counters[0] = over ? 0 : os;
-        p.counters[1] = over ? 0 : op;
-        p.counters[2] = 0;
-        p.counters[6] = 0;
-        p.counters[7] = 0;
+}
+
+// The scan's totals: the end of the last cell, the capacity check, the counters.
+__device__ __forceinline__ void scan_cells_finish(const Params& p, int on, int op, int os)
+{
+    const int C = p.cell_cap_total;
+    p.cell_start[C] = on;
+    p.cell_pstart[C] = op;
+    const bool over = op > p.slot_cap || os > p.sc_cap;
+    if (over) atomicOr(p.err, ERR_CELL);
+    p.counters[0] = over ? 0 : os;
+    p.counters[1] = over ? 0 : op;
+    p.counters[2] = 0;
+    p.counters[4] = 0;   // cells too large for the one-warp sort
+    p.counters[6] = 0;
+    p.counters[7] = 0;
+}
+
+// The grid of this build stays with the list until the next build.
+__device__ __forceinline__ void keep_build_grid(const Params& p)
+{
+    if (p.grid_b != p.grid)
+        for (int r = threadIdx.x; r < p.n_rep; r += blockDim.x) p.grid_b[r] = p.grid[r];
+}
+
+// Single-CTA scan over all cells (grids of few cells): unpadded starts, padded
+// starts, and the super-cluster table (cell, first cluster, cluster count).
+// Each warp owns a contiguous run of cells and reads it 32 cells at a time
+// (coalesced): a first pass sums the run, a scan over the 32 warps gives each
+// run its base, and a second pass scans every 32-cell group with shuffles and
+// writes.
+__global__ void __launch_bounds__(kScanThreads) k_cell_scan(Params p)
+{
+    constexpr int kWarps = kScanThreads / 32;
+    __shared__ int s_tot[kWarps][3], s_base[kWarps][3];
+    keep_build_grid(p);
+    const int zero[3] = {0, 0, 0};
+    scan_cells<true>(p, 0, p.cell_cap_total, zero, s_tot, s_base);
+    if (threadIdx.x == 0)
+        scan_cells_finish(p, s_base[kWarps - 1][0] + s_tot[kWarps - 1][0], s_base[kWarps - 1][1] + s_tot[kWarps - 1][1],
+                          s_base[kWarps - 1][2] + s_tot[kWarps - 1][2]);
+}
+
+// The same scan over many CTAs (grids of many cells), in three kernels: each
+// CTA sums its range of cells; one CTA scans those sums (and finishes); each
+// CTA scans its range from its base.  p.scan_tmp holds [CTA][3] sums, then
+// bases.
+__device__ __forceinline__ void cta_range(int n, int& lo, int& hi)
+{
+    const int per = ((n + (int)gridDim.x - 1) / (int)gridDim.x + 31) & ~31;
+    lo = min((int)blockIdx.x * per, n);
+    hi = min(lo + per, n);
+}
+__global__ void __launch_bounds__(kScanThreads) k_cell_scan_sums(Params p)
+{
+    constexpr int kWarps = kScanThreads / 32;
+    __shared__ int s_tot[kWarps][3], s_base[kWarps][3];
+    int lo, hi;
+    cta_range(p.cell_cap_total, lo, hi);
+    const int zero[3] = {0, 0, 0};
+    scan_cells<false>(p, lo, hi, zero, s_tot, s_base);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 3; ++k) p.scan_tmp[3 * blockIdx.x + k] = s_base[kWarps - 1][k] + s_tot[kWarps - 1][k];
+}
+__global__ void __launch_bounds__(1024) k_cell_scan_top(Params p, int n_ctas)
+{
+    constexpr unsigned kFull = 0xffffffffu;
+    __shared__ int s_w[32][3];
+    keep_build_grid(p);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int v[3] = {0, 0, 0}, inc[3];
+    if ((int)threadIdx.x < n_ctas)
+        for (int k = 0; k < 3; ++k) v[k] = p.scan_tmp[3 * threadIdx.x + k];
+    for (int k = 0; k < 3; ++k) inc[k] = v[k];
+    for (int o = 1; o < 32; o <<= 1)
+        for (int k = 0; k < 3; ++k) {
+            const int u = __shfl_up_sync(kFull, inc[k], o);
+            if (lane >= o) inc[k] += u;
+        }
+    if (lane == 31)
+        for (int k = 0; k < 3; ++k) s_w[warp][k] = inc[k];
+    __syncthreads();
+    if (warp == 0) {
+        int w[3], wi[3];
+        for (int k = 0; k < 3; ++k) w[k] = wi[k] = s_w[lane][k];
+        for (int o = 1; o < 32; o <<= 1)
+            for (int k = 0; k < 3; ++k) {
+                const int u = __shfl_up_sync(kFull, wi[k], o);
+                if (lane >= o) wi[k] += u;
+            }
+        for (int k = 0; k < 3; ++k) s_w[lane][k] = wi[k] - w[k];
+        if (lane == 31) scan_cells_finish(p, wi[0], wi[1], wi[2]);
     }
+    __syncthreads();
+    if ((int)threadIdx.x < n_ctas)
+        for (int k = 0; k < 3; ++k) p.scan_tmp[3 * threadIdx.x + k] = s_w[warp][k] + inc[k] - v[k];
+}
+__global__ void __launch_bounds__(kScanThreads) k_cell_scan_apply(Params p)
+{
+    constexpr int kWarps = kScanThreads / 32;
+    __shared__ int s_tot[kWarps][3], s_base[kWarps][3];
+    int lo, hi;
+    cta_range(p.cell_cap_total, lo, hi);
+    const int base[3] = {p.scan_tmp[3 * blockIdx.x], p.scan_tmp[3 * blockIdx.x + 1], p.scan_tmp[3 * blockIdx.x + 2]};
+    scan_cells<true>(p, lo, hi, base, s_tot, s_base);
 }
 
 __global__ void __launch_bounds__(256) k_cell_scatter(Params p)
@@ -219,7 +318,9 @@ __device__ __forceinline__ int ord_f(float f)
 }
 __device__ __forceinline__ float unord_f(int i) { return __int_as_float(i < 0 ? i ^ 0x7fffffff : i); }
 
-__global__ void __launch_bounds__(kSortThreads) k_cell_sort_pack(Params p)
+// small_max < 0: every cell; else only the cells k_cell_sort_small listed as
+// larger than it could take (p.big_cells[0 .. counters[4])).
+__global__ void __launch_bounds__(kSortThreads) k_cell_sort_pack(Params p, int small_max)
 {
     const int nt = blockDim.x;
     __shared__ unsigned long long s_key[kSortMax];
@@ -229,7 +330,9 @@ __global__ void __launch_bounds__(kSortThreads) k_cell_sort_pack(Params p)
     __shared__ int s_bb[kSortMax / kClusterSize][8];
     if (*p.err & ERR_CELL) return;
     const int tid = threadIdx.x;
-    for (int c = blockIdx.x; c < p.cell_cap_total; c += gridDim.x) {
+    const int n_cells = small_max < 0 ? p.cell_cap_total : p.counters[4];
+    for (int ci = blockIdx.x; ci < n_cells; ci += gridDim.x) {
+        const int c = small_max < 0 ? ci : p.big_cells[ci];
         const int b = p.cell_start[c];
         const int n = p.cell_start[c + 1] - b;
         const int ps = p.cell_pstart[c];
@@ -348,6 +451,90 @@ __global__ void __launch_bounds__(kSortThreads) k_cell_sort_pack(Params p)
     }
 }
 
+// Cells of up to kSmallCell atoms: one warp per cell, with the same rank sort,
+// packed records and cluster boxes as k_cell_sort_pack but no block barrier,
+// so that many more (latency-bound) cells are in flight.  Keys and boxes live
+// in the warp's share of shared memory; every lane reads the cell's keys as
+// broadcasts.
+__global__ void __launch_bounds__(kSmallWarps * 32) k_cell_sort_small(Params p)
+{
+    __shared__ unsigned long long s_key[kSmallWarps][kSmallCell];
+    __shared__ int s_bb[kSmallWarps][kSmallCell / kClusterSize][8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (*p.err & ERR_CELL) return;
+    unsigned long long* key = s_key[warp];
+    for (int c = blockIdx.x * kSmallWarps + warp; c < p.cell_cap_total; c += gridDim.x * kSmallWarps) {
+        const int b = p.cell_start[c];
+        const int n = p.cell_start[c + 1] - b;
+        const int ps = p.cell_pstart[c];
+        const int npad = p.cell_pstart[c + 1] - ps;
+        if (npad == 0) continue;                     // uniform across the warp
+        if (n > kSmallCell) {                        // left to k_cell_sort_pack
+            if (lane == 0) p.big_cells[atomicAdd(&p.counters[4], 1)] = c;
+            continue;
+        }
+        int lo = 0, hi = p.n_rep - 1;   // replicas own contiguous cell ranges
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (p.grid[mid].cell_off <= c) lo = mid; else hi = mid - 1;
+        }
+        const Grid& g = p.grid[lo];
+        const int local = c - g.cell_off;
+        const int cx = local % g.dims[0];
+        const int cy = (local / g.dims[0]) % g.dims[1];
+        const int cz = local / (g.dims[0] * g.dims[1]);
+        const double cen[3] = {g.origin[0] + (cx + 0.5) * g.edge[0],
+                               g.origin[1] + (cy + 0.5) * g.edge[1],
+                               g.origin[2] + (cz + 0.5) * g.edge[2]};
+        const int ncl = npad / kClusterSize;
+        __syncwarp();
+        for (int e = lane; e < n; e += 32) key[e] = p.tmp_key[b + e];
+        for (int k = lane; k < ncl; k += 32) {
+            int* bb = s_bb[warp][k];
+            bb[0] = bb[1] = bb[2] = 0x7fffffff;
+            bb[3] = bb[4] = bb[5] = (int)0x80000000;
+            bb[6] = 0x7fffffff;
+            bb[7] = (int)0x80000000;
+        }
+        __syncwarp();
+        for (int e = lane; e < n; e += 32) {
+            const unsigned long long ke = key[e];
+            int rank = 0;
+#pragma unroll 4
+            for (int f = 0; f < n; ++f) rank += key[f] < ke;
+            const int i = (int)(ke & 0xffffffffu);
+            const int slot = ps + rank;
+            p.atom_of[slot] = i;
+            p.slot_of[i] = slot;
+            const float4 v = pack_slot(p, slot, i, cen, g);
+            int* bb = s_bb[warp][rank / kClusterSize];
+            atomicMin(bb + 0, ord_f(v.x)); atomicMin(bb + 1, ord_f(v.y)); atomicMin(bb + 2, ord_f(v.z));
+            atomicMax(bb + 3, ord_f(v.x)); atomicMax(bb + 4, ord_f(v.y)); atomicMax(bb + 5, ord_f(v.z));
+            const int fr = p.frag[i];
+            atomicMin(bb + 6, fr);
+            atomicMax(bb + 7, fr);
+        }
+        for (int e = n + lane; e < npad; e += 32) {     // padding: far away, no charge
+            const int slot = ps + e;
+            const double far = 1.0e6 + 1024.0 * (double)slot;
+            p.atom_of[slot] = -1;
+            if (p.precision == 0) p.xq[slot] = make_float4((float)far, 1.0e6f, 1.0e6f, 0.0f);
+            else p.xq64[slot] = make_double4_32a(far, 1.0e6, 1.0e6, 0.0);
+            p.tf[slot] = make_int2(0, -1 - slot);
+            p.fx[slot] = 0; p.fy[slot] = 0; p.fz[slot] = 0; p.epot[slot] = 0;
+        }
+        __syncwarp();
+        for (int k = lane; k < ncl; k += 32) {
+            const int* bb = s_bb[warp][k];
+            const int cl = ps / kClusterSize + k;
+            p.cl_cen[cl] = make_double4_32a(cen[0], cen[1], cen[2], 0.0);
+            p.bb_lo[cl] = make_float4(unord_f(bb[0]), unord_f(bb[1]), unord_f(bb[2]), 0.0f);
+            p.bb_hi[cl] = make_float4(unord_f(bb[3]), unord_f(bb[4]), unord_f(bb[5]), 0.0f);
+            p.bb_frag[cl] = make_int2(bb[6], bb[7]);
+        }
+    }
+}
+
 // Between list builds: the packed records of the current positions and
 // charges in the slots of the last build (cell centres and grid of that build).
 __global__ void __launch_bounds__(256) k_refresh(Params p)
@@ -370,12 +557,32 @@ void launch_refresh(const Params& p, cudaStream_t s)
     k_refresh<<<(p.slot_cap + 255) / 256, 256, 0, s>>>(p);
 }
 
-void launch_cells(const Params& p, cudaStream_t s, int grid_atoms, int grid_cells, int sort_threads)
+int launch_cells(const Params& p, cudaStream_t s, int grid_atoms, int grid_cells, int sort_threads)
 {
+    int n = 0;
     k_cell_assign<<<(p.slot_cap + 255) / 256, 256, 0, s>>>(p);
-    k_cell_scan<<<1, kScanThreads, 0, s>>>(p);
+    if (p.cell_cap_total >= kScanCellsMulti) {
+        const int ctas = std::min(kScanCtasMax, (p.cell_cap_total + 1023) / 1024);
+        k_cell_scan_sums<<<ctas, kScanThreads, 0, s>>>(p);
+        k_cell_scan_top<<<1, 1024, 0, s>>>(p, ctas);
+        k_cell_scan_apply<<<ctas, kScanThreads, 0, s>>>(p);
+        n += 4;
+    } else {
+        k_cell_scan<<<1, kScanThreads, 0, s>>>(p);
+        n += 2;
+    }
     k_cell_scatter<<<grid_atoms, 256, 0, s>>>(p);
-    k_cell_sort_pack<<<grid_cells, sort_threads, 0, s>>>(p);
+    n += 1;
+    // Grids of many cells (sorted by 256-thread CTAs): cells of up to kSmallCell
+    // atoms one warp each, the rest one CTA each.  Grids of few, large cells:
+    // every cell one 1,024-thread CTA.
+    const int small_max = sort_threads <= 256 ? kSmallCell : -1;
+    if (small_max > 0) {
+        k_cell_sort_small<<<grid_cells, kSmallWarps * 32, 0, s>>>(p);
+        n += 1;
+    }
+    k_cell_sort_pack<<<grid_cells, sort_threads, 0, s>>>(p, small_max);
+    return n + 1;
 }
 
 }  // namespace mdg

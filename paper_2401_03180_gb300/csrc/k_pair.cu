@@ -27,6 +27,7 @@
 //     and one (SC, j-cluster) entry for the j side, then converted
 //     once to 64-bit fixed point (2^-32 kJ/mol/nm): the per-atom totals are
 //     exact integer sums, identical for every launch shape and schedule.
+#include <algorithm>
 #include <type_traits>
 
 #include "bonded_terms.cuh"
@@ -243,6 +244,7 @@ struct ListWarp {
     float4 ip[kSCAtoms];                              // the SC's atoms, [cluster k][atom a] (write pass)
 };
 constexpr int kListWarps = 8;
+constexpr int kScanScsMulti = 32768;   // super-cluster capacities from this size are scanned by many CTAs
 
 // An SC's cell, in the grid of its replica.
 struct ListSC {
@@ -417,25 +419,31 @@ __global__ void __launch_bounds__(kListWarps * 32, 4) k_list_count(Params p)
     }
 }
 
-// One block: each SC's total over its parts, then exclusive scans of the SCs'
-// entry counts and chunk counts (each warp owns a contiguous run of SCs and
-// reads it 32 at a time), the totals into counters[6] (entries) and
-// counters[7] (chunks), ERR_LIST when the list is too small for them.
-__global__ void __launch_bounds__(1024) k_list_scan(Params p)
+// Exclusive scans of the SCs' entry counts and chunk counts, each SC's total
+// summed over its parts first (stored in sc_tot).  One block's part: SCs
+// [lo, hi) from the running totals base[0..1] of the SCs before lo; each warp
+// owns a contiguous run of SCs and reads it 32 at a time.  Leaves the block's
+// totals in s_tot / s_base (warp 31's base plus total).  WRITE = false: the
+// totals (and sc_tot) only.
+template <bool WRITE>
+__device__ __forceinline__ void scan_scs(const Params& p, int lo, int hi, const int base[2], int (*s_tot)[2],
+                                         int (*s_base)[2])
 {
     constexpr unsigned kFull = 0xffffffffu;
     constexpr int kWarps = 32;
-    __shared__ int s_tot[kWarps][2], s_base[kWarps][2];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n = (*p.err & ERR_CELL) ? 0 : p.counters[0];
-    const int run = ((n + kWarps - 1) / kWarps + 31) & ~31;
-    const int lo = min(warp * run, n), hi = min(lo + run, n);
+    const int run = ((hi - lo + kWarps - 1) / kWarps + 31) & ~31;
+    const int s_lo = min(lo + warp * run, hi), s_hi = min(s_lo + run, hi);
     int te = 0, tc = 0;
-    for (int s = lo + lane; s < hi; s += 32) {
+    for (int s = s_lo + lane; s < s_hi; s += 32) {
         int t = 0;
+        if (!WRITE) {
 #pragma unroll
-        for (int k = 0; k < kHalfShell; ++k) t += p.list_cnt[s * kHalfShell + k];
-        p.sc_tot[s] = t;
+            for (int k = 0; k < kHalfShell; ++k) t += p.list_cnt[s * kHalfShell + k];
+            p.sc_tot[s] = t;
+        } else {
+            t = p.sc_tot[s];
+        }
         te += t;
         tc += (t + kChunk - 1) / kChunk;
     }
@@ -451,35 +459,111 @@ __global__ void __launch_bounds__(1024) k_list_scan(Params p)
             const int ue = __shfl_up_sync(kFull, ie, o), uc = __shfl_up_sync(kFull, ic, o);
             if (lane >= o) { ie += ue; ic += uc; }
         }
-        s_base[lane][0] = ie - s_tot[lane][0];
-        s_base[lane][1] = ic - s_tot[lane][1];
+        s_base[lane][0] = base[0] + ie - s_tot[lane][0];
+        s_base[lane][1] = base[1] + ic - s_tot[lane][1];
     }
     __syncthreads();
+    if (!WRITE) return;
     int be = s_base[warp][0], bc = s_base[warp][1];
-    for (int g0 = lo; g0 < hi; g0 += 32) {
+    for (int g0 = s_lo; g0 < s_hi; g0 += 32) {
         const int s = g0 + lane;
-        const int t = s < hi ? p.sc_tot[s] : 0;
+        const int t = s < s_hi ? p.sc_tot[s] : 0;
         const int ch = (t + kChunk - 1) / kChunk;
         int ie = t, ic = ch;
         for (int o = 1; o < 32; o <<= 1) {
             const int ue = __shfl_up_sync(kFull, ie, o), uc = __shfl_up_sync(kFull, ic, o);
             if (lane >= o) { ie += ue; ic += uc; }
         }
-        if (s < hi) {
+        if (s < s_hi) {
             p.sc_eoff[s] = be + ie - t;
             p.sc_coff[s] = bc + ic - ch;
         }
         be += __shfl_sync(kFull, ie, 31);
         bc += __shfl_sync(kFull, ic, 31);
     }
-    if (threadIdx.x == 0) {
-        const long long E = (long long)s_base[kWarps - 1][0] + s_tot[kWarps - 1][0];
-        const long long Cn = (long long)s_base[kWarps - 1][1] + s_tot[kWarps - 1][1];
-        p.counters[6] = (int)min(E, (long long)0x7fffffff);
-        p.counters[7] = (int)min(Cn, (long long)0x7fffffff);
-        p.counters[2] = 0;   // work counter of the force kernel
-        if (E > p.pl_cap || Cn > p.chunk_cap) atomicOr(p.err, ERR_LIST);
+}
+
+// The list's totals into counters[6] (entries) and counters[7] (chunks),
+// ERR_LIST when the list is too small for them.
+__device__ __forceinline__ void scan_scs_finish(const Params& p, long long E, long long Cn)
+{
+    p.counters[6] = (int)min(E, (long long)0x7fffffff);
+    p.counters[7] = (int)min(Cn, (long long)0x7fffffff);
+    p.counters[2] = 0;   // work counter of the force kernel
+    if (E > p.pl_cap || Cn > p.chunk_cap) atomicOr(p.err, ERR_LIST);
+}
+
+// Few SCs: one block does both passes.
+__global__ void __launch_bounds__(1024) k_list_scan(Params p)
+{
+    __shared__ int s_tot[32][2], s_base[32][2];
+    const int n = (*p.err & ERR_CELL) ? 0 : p.counters[0];
+    const int zero[2] = {0, 0};
+    scan_scs<false>(p, 0, n, zero, s_tot, s_base);
+    scan_scs<true>(p, 0, n, zero, s_tot, s_base);
+    if (threadIdx.x == 0)
+        scan_scs_finish(p, (long long)s_base[31][0] + s_tot[31][0], (long long)s_base[31][1] + s_tot[31][1]);
+}
+
+// Many SCs: each CTA sums its range; one CTA scans the sums (and finishes);
+// each CTA scans its range from its base (p.scan_tmp: [CTA][2]).
+__device__ __forceinline__ void sc_cta_range(int n, int& lo, int& hi)
+{
+    const int per = ((n + (int)gridDim.x - 1) / (int)gridDim.x + 31) & ~31;
+    lo = min((int)blockIdx.x * per, n);
+    hi = min(lo + per, n);
+}
+__global__ void __launch_bounds__(1024) k_list_scan_sums(Params p)
+{
+    __shared__ int s_tot[32][2], s_base[32][2];
+    const int n = (*p.err & ERR_CELL) ? 0 : p.counters[0];
+    int lo, hi;
+    sc_cta_range(n, lo, hi);
+    const int zero[2] = {0, 0};
+    scan_scs<false>(p, lo, hi, zero, s_tot, s_base);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 2; ++k) p.scan_tmp[2 * blockIdx.x + k] = s_base[31][k] + s_tot[31][k];
+}
+__global__ void __launch_bounds__(1024) k_list_scan_top(Params p, int n_ctas)
+{
+    constexpr unsigned kFull = 0xffffffffu;
+    __shared__ long long s_w[32][2];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    long long v[2] = {0, 0}, inc[2];
+    if ((int)threadIdx.x < n_ctas)
+        for (int k = 0; k < 2; ++k) v[k] = p.scan_tmp[2 * threadIdx.x + k];
+    for (int k = 0; k < 2; ++k) inc[k] = v[k];
+    for (int o = 1; o < 32; o <<= 1)
+        for (int k = 0; k < 2; ++k) {
+            const long long u = __shfl_up_sync(kFull, inc[k], o);
+            if (lane >= o) inc[k] += u;
+        }
+    if (lane == 31)
+        for (int k = 0; k < 2; ++k) s_w[warp][k] = inc[k];
+    __syncthreads();
+    if (warp == 0) {
+        long long w[2], wi[2];
+        for (int k = 0; k < 2; ++k) w[k] = wi[k] = s_w[lane][k];
+        for (int o = 1; o < 32; o <<= 1)
+            for (int k = 0; k < 2; ++k) {
+                const long long u = __shfl_up_sync(kFull, wi[k], o);
+                if (lane >= o) wi[k] += u;
+            }
+        for (int k = 0; k < 2; ++k) s_w[lane][k] = wi[k] - w[k];
+        if (lane == 31) scan_scs_finish(p, wi[0], wi[1]);
     }
+    __syncthreads();
+    if ((int)threadIdx.x < n_ctas)
+        for (int k = 0; k < 2; ++k) p.scan_tmp[2 * threadIdx.x + k] = (int)min(s_w[warp][k] + inc[k] - v[k], (long long)0x7fffffff);
+}
+__global__ void __launch_bounds__(1024) k_list_scan_apply(Params p)
+{
+    __shared__ int s_tot[32][2], s_base[32][2];
+    const int n = (*p.err & ERR_CELL) ? 0 : p.counters[0];
+    int lo, hi;
+    sc_cta_range(n, lo, hi);
+    const int base[2] = {p.scan_tmp[2 * blockIdx.x], p.scan_tmp[2 * blockIdx.x + 1]};
+    scan_scs<true>(p, lo, hi, base, s_tot, s_base);
 }
 
 // Entry of one j-cluster: the i-atoms of the clusters in range that lie within
@@ -1147,11 +1231,22 @@ static int max_blocks(int warps, int n_ts)
     return n;
 }
 
-void launch_pair_list(const Params& p, cudaStream_t s, int blocks)
+int launch_pair_list(const Params& p, cudaStream_t s, int blocks)
 {
+    int n = 2;
     k_list_count<<<blocks, kListWarps * 32, 0, s>>>(p);
-    k_list_scan<<<1, 1024, 0, s>>>(p);
+    if (p.sc_cap >= kScanScsMulti) {
+        const int ctas = std::min(kScanCtasMax, (p.sc_cap + 2047) / 2048);
+        k_list_scan_sums<<<ctas, 1024, 0, s>>>(p);
+        k_list_scan_top<<<1, 1024, 0, s>>>(p, ctas);
+        k_list_scan_apply<<<ctas, 1024, 0, s>>>(p);
+        n += 3;
+    } else {
+        k_list_scan<<<1, 1024, 0, s>>>(p);
+        n += 1;
+    }
     k_list_write<<<blocks, kListWarps * 32, 0, s>>>(p);
+    return n;
 }
 
 void launch_pair_forces(const Params& p, cudaStream_t s, bool energy, int blocks, int warps)

@@ -39,6 +39,7 @@ struct md_handle {
     long long list_grows = 0;
     int grid_atoms = 1, grid_cells = 1, sort_threads = 1024;
     int pair_blocks = 1, pair_warps = 8, list_blocks = 1, list_bps = 8;
+    int build_kernels = 0;               // kernels of one cell + list build in the step graph
     long long host_step = 0;             // steps enqueued
     long long pending = 0;               // enqueued steps whose status is not read yet
     bool poisoned = false;
@@ -201,8 +202,8 @@ void enqueue_step(md_handle* h, cudaStream_t s, bool events)
 {
     int mode = STEP_KICK_DRIFT | STEP_ADVANCE | (h->cfg.cr_enabled ? STEP_CR : 0);
     launch_step_a(h->P, mode, s, h->grid_atoms);
-    launch_cells(h->P, s, h->grid_atoms, h->grid_cells, h->sort_threads);
-    launch_pair_list(h->P, s, h->list_blocks);
+    h->build_kernels = launch_cells(h->P, s, h->grid_atoms, h->grid_cells, h->sort_threads) +
+                       launch_pair_list(h->P, s, h->list_blocks);
     // external event nodes: the events are recorded on every graph replay
     if (events) cudaEventRecordWithFlags(h->ev_pair0, s, cudaEventRecordExternal);
     launch_pair_forces(h->P, s, false, h->pair_blocks, h->pair_warps);
@@ -297,8 +298,8 @@ md_status capture_buffered_step(md_handle* h, bool events)
     CU(cudaGraphAddNode(&cn, g, deps, nullptr, nd, &cp));
     cudaGraph_t rebuild = cp.conditional.phGraph_out[0];
     CU(cudaStreamBeginCaptureToGraph(h->body_stream, rebuild, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    launch_cells(h->P, h->body_stream, h->grid_atoms, h->grid_cells, h->sort_threads);
-    launch_pair_list(h->P, h->body_stream, h->list_blocks);
+    h->build_kernels = launch_cells(h->P, h->body_stream, h->grid_atoms, h->grid_cells, h->sort_threads) +
+                       launch_pair_list(h->P, h->body_stream, h->list_blocks);
     CU(cudaStreamEndCapture(h->body_stream, &rebuild));
     CU(cudaStreamUpdateCaptureDependencies(s, &cn, nullptr, 1, cudaStreamSetCaptureDependencies));
     if (events) cudaEventRecordWithFlags(h->ev_pair0, s, cudaEventRecordExternal);
@@ -924,6 +925,8 @@ static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* 
     DALLOC(P.counters, 8);
     DALLOC(P.list_cnt, (size_t)P.sc_cap * kHalfShell);
     DALLOC(P.sc_tot, P.sc_cap); DALLOC(P.sc_eoff, P.sc_cap); DALLOC(P.sc_coff, P.sc_cap);
+    DALLOC(P.scan_tmp, 3 * kScanCtasMax);
+    DALLOC(P.big_cells, C);
     P.pl = nullptr;
     P.pl_chunk = nullptr;
     {
@@ -1854,6 +1857,7 @@ md_status md_get_timing(md_handle* h, md_timing* out)
     out->list_grows = h->list_grows;
     out->sort_threads = h->sort_threads;
     out->list_blocks_per_sm = h->list_bps;
+    out->build_kernels = h->build_kernels;
     if (h->cfg.list_skin_nm > 0) {
         int b = 0;
         CU(cudaMemcpy(&b, h->P.builds, sizeof(int), cudaMemcpyDeviceToHost));

@@ -30,6 +30,7 @@ constexpr double kLn2 = 0.69314718055994530942;   // ln 2 (scales the LJ table's
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kChargeTable = 1;                  // MD_CHARGE_TABLE
 constexpr float kBBoxMargin = 1e-4f;               // nm, slack of the cluster prefilter
+constexpr int kScanCtasMax = 1024;                 // CTAs of the multi-CTA scans (cells, super-clusters)
 
 // device error bits (mirrored to md_status by the host)
 enum : unsigned {
@@ -165,11 +166,13 @@ struct Params {
     int* sc_cell;            // [sc_cap]
     int* sc_first;           // [sc_cap] first cluster
     int* sc_ncl;             // [sc_cap] clusters in the super-cluster
-    int* counters;           // [0] n_sc, [1] n_slots, [2] work, [3] ticket, [6] list entries, [7] chunks
+    int* counters;           // [0] n_sc, [1] n_slots, [2] work, [3] ticket, [4] big cells, [6] list entries, [7] chunks
+    int* big_cells;          // [cell_cap_total] cells too large for the one-warp sort (counters[4] of them)
     int* list_cnt;           // [sc_cap * kHalfShell] entries of each super-cluster in each half-shell cell
     int* sc_tot;             // [sc_cap] entries per super-cluster
     int* sc_eoff;            // [sc_cap] first entry of each super-cluster
     int* sc_coff;            // [sc_cap] first chunk of each super-cluster
+    int* scan_tmp;           // [kScanCtasMax * 3] per-CTA sums and bases of the multi-CTA scans
     PairEntry* pl;           // [pl_cap] cluster-pair list (j-cluster, half-shell index, i-atom mask)
     int4* pl_chunk;          // [chunk_cap] (SC, first entry, entries, replica)
     int pl_cap, chunk_cap;
@@ -296,8 +299,9 @@ __device__ __forceinline__ float4 pack_slot(const Params& p, int slot, int i, co
 
 // Launch helpers implemented in the .cu files.
 void launch_step_a(const Params& p, int mode, cudaStream_t s, int grid_atoms);
-void launch_cells(const Params& p, cudaStream_t s, int grid_atoms, int grid_cells, int sort_threads);
-void launch_pair_list(const Params& p, cudaStream_t s, int blocks);
+// launch_cells and launch_pair_list return the number of kernels they launched
+int launch_cells(const Params& p, cudaStream_t s, int grid_atoms, int grid_cells, int sort_threads);
+int launch_pair_list(const Params& p, cudaStream_t s, int blocks);
 void launch_pair_forces(const Params& p, cudaStream_t s, bool energy, int blocks, int warps);
 void launch_velocity_out(const Params& p, double* d_v_out, cudaStream_t s);
 void launch_energy(const Params& p, double* d_ekin, long long* d_epot, cudaStream_t s);

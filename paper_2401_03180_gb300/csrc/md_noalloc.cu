@@ -42,7 +42,7 @@ struct Layout {
     size_t x, y, z, vx, vy, vz, species, q, h, frag, rep, local_id, slot_of, atom_cell, atom_rank;
     size_t zs, ts_off, hdtm, mass, auger, volume, rep_off, lj;
     size_t grid, rs, acc, cell_count, cell_start, cell_pstart, tmp_key, sc_cell, sc_first, sc_ncl;
-    size_t counters, list_cnt, sc_tot, sc_eoff, sc_coff, xq, tf, atom_of, bb_lo, bb_hi, bb_frag, fx, fy, fz, epot, pair_count, err, step, kick;
+    size_t counters, list_cnt, sc_tot, sc_eoff, sc_coff, scan_tmp, big_cells, xq, tf, atom_of, bb_lo, bb_hi, bb_frag, fx, fy, fz, epot, pair_count, err, step, kick;
     size_t pl, pl_chunk, cl_cen;
     size_t total;
 };
@@ -69,6 +69,8 @@ constexpr Layout make_layout()
     L.list_cnt = take(4 * (size_t)kClusterCap * kHalfShell);
     L.sc_tot = take(4 * kClusterCap);
     L.sc_eoff = take(4 * kClusterCap); L.sc_coff = take(4 * kClusterCap);
+    L.scan_tmp = take(4 * 3 * kScanCtasMax);
+    L.big_cells = take(4 * kNcMax);
     L.xq = take(32 * (size_t)kSlotCap);                      // float4 or double4_32a
     L.tf = take(8 * (size_t)kSlotCap); L.atom_of = take(4 * (size_t)kSlotCap);
     L.bb_lo = take(16 * (size_t)kClusterCap); L.bb_hi = take(16 * (size_t)kClusterCap);
@@ -241,6 +243,8 @@ extern "C" md_status md_forces_noalloc(const md_forces_input* in, double* d_f, v
     P.counters = (int*)(B + kL.counters);
     P.list_cnt = (int*)(B + kL.list_cnt); P.sc_tot = (int*)(B + kL.sc_tot);
     P.sc_eoff = (int*)(B + kL.sc_eoff); P.sc_coff = (int*)(B + kL.sc_coff);
+    P.scan_tmp = (int*)(B + kL.scan_tmp);
+    P.big_cells = (int*)(B + kL.big_cells);
     P.xq = (float4*)(B + kL.xq); P.xq64 = (double4_32a*)(B + kL.xq);
     P.tf = (int2*)(B + kL.tf); P.atom_of = (int*)(B + kL.atom_of);
     P.bb_lo = (float4*)(B + kL.bb_lo); P.bb_hi = (float4*)(B + kL.bb_hi); P.bb_frag = (int2*)(B + kL.bb_frag);

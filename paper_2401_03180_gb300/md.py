@@ -78,7 +78,8 @@ class MDTiming(C.Structure):
     _fields_ = [("pair_ms", C.c_double), ("pair_launches", C.c_int64), ("steps", C.c_int64),
                 ("pair_count_last", C.c_int64), ("tile_warps", C.c_int), ("tile_blocks_per_sm", C.c_int),
                 ("list_capacity", C.c_int64), ("list_entries", C.c_int64), ("list_grows", C.c_int64),
-                ("list_builds", C.c_int64), ("sort_threads", C.c_int), ("list_blocks_per_sm", C.c_int)]
+                ("list_builds", C.c_int64), ("sort_threads", C.c_int), ("list_blocks_per_sm", C.c_int),
+                ("build_kernels", C.c_int)]
 
 
 class MDForcesInput(C.Structure):
