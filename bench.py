@@ -42,6 +42,7 @@ UNIT = "atom-steps/s"
 FLOPS_PER_PAIR = 41          # FP32 operations per in-cutoff pair in the pair kernel (FMA = 2)
 L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
 SKIN_NM = 0.12               # Verlet buffer of the pair list (measured: best at the pulse peak of the droplet and the water box)
+SKIN_MODE = "fixed"          # "adaptive": the device drops the buffer while lists live under 4 steps
 
 
 def parse():
@@ -78,6 +79,8 @@ def parse():
                     help="record the per-species charge and displacement series of Eq. 17 every step")
     ap.add_argument("--skin", type=float, default=SKIN_NM,
                     help="Verlet buffer of the cluster-pair list (nm); 0 rebuilds every step")
+    ap.add_argument("--skin-mode", default=SKIN_MODE, choices=["fixed", "adaptive"],
+                    help="adaptive: unbuffered lists while buffered ones live fewer than 4 steps")
     return ap.parse_args()
 
 
@@ -265,6 +268,7 @@ def run_gpu(args, rank, world, local):
         g = M.IonisingMD(s, atom, precision=prec, r_cut=1.2, dt_ps=5e-5, max_steps=max_steps,
                          t_start_fs=wl.t_start_fs, autotune=(prec == "mixed") if autotune is None else autotune,
                          profile=profile, list_skin_nm=args.skin, screening=args.screening,
+                         list_skin_adaptive=args.skin_mode == "adaptive",
                          langevin_g=args.langevin if args.langevin > 0 else None,
                          charge_mode="table" if args.charge_table else "rates", probe_record=args.probe)
         for r in range(s.n_replicas):
@@ -418,7 +422,8 @@ def run_gpu(args, rank, world, local):
                    "pair_tile": {"warps": tim.tile_warps, "blocks_per_sm": tim.tile_blocks_per_sm},
                    "build_shape": {"sort_threads": tim.sort_threads, "list_blocks_per_sm": tim.list_blocks_per_sm,
                                    "kernels_per_build": tim.build_kernels},
-                   "list_skin_nm": args.skin, "screening": args.screening, "langevin_g": args.langevin,
+                   "list_skin_nm": args.skin, "list_skin_mode": args.skin_mode, "screening": args.screening,
+                   "langevin_g": args.langevin,
                    "charges": "table" if args.charge_table else "rates",
                    "bonded": ({"bonds": int(len(s.topology.bonds)), "angles": int(len(s.topology.angles))}
                               if s.topology is not None else None),
@@ -443,7 +448,8 @@ def run_gpu(args, rank, world, local):
         # kernel's inline limit), and the build's kernels (cells + list, 5 to 12 by
         # grid size) in the steps whose list is rebuilt
         "gpu_launches": (2 + bool(args.probe) + (s.n_replicas > 4)) * K + tim.build_kernels * int(tim.list_builds),
-        "pair_list": {"skin_nm": args.skin, "builds": int(tim.list_builds), "steps": K,
+        "pair_list": {"skin_nm": args.skin, "skin_mode": args.skin_mode, "builds": int(tim.list_builds),
+                      "unbuffered_builds": int(tim.list_unbuffered_builds), "steps": K,
                       "steps_per_build": (K / tim.list_builds) if tim.list_builds else None,
                       "entries_last_build": int(tim.list_entries), "capacity": int(tim.list_capacity)},
         "clocks": clk.summary(),
@@ -637,6 +643,7 @@ def run_profile_case(args):
     s = wl.sample
     g = M.IonisingMD(s, atom, precision=args.precision, r_cut=1.2, max_steps=max(wl.n_steps, args.warmup + args.steps + 1),
                      t_start_fs=wl.t_start_fs, autotune=False, list_skin_nm=args.skin, screening=args.screening,
+                     list_skin_adaptive=args.skin_mode == "adaptive",
                      langevin_g=args.langevin if args.langevin > 0 else None)
     g.set_pulse(wl.pulses[0])
     g.step(args.warmup)
@@ -653,7 +660,8 @@ def run_profile_case(args):
     g.close()
     return {"profile_case": args.workload, "n_atoms": s.n_atoms, "precision": args.precision,
             "warmup": args.warmup, "steps": args.steps, "tile_warps": t.tile_warps,
-            "tile_blocks_per_sm": t.tile_blocks_per_sm, "skin_nm": args.skin, "list_builds": t.list_builds}
+            "tile_blocks_per_sm": t.tile_blocks_per_sm, "skin_nm": args.skin, "skin_mode": args.skin_mode,
+            "list_builds": t.list_builds, "unbuffered_builds": t.list_unbuffered_builds}
 
 
 def main():

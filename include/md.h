@@ -194,6 +194,21 @@ typedef struct md_config {
                                 occupancy the shape allows                     */
     int sort_threads;        /* threads per cell-sort block: 256 or 1024       */
     int list_blocks_per_sm;  /* list-build blocks (8 warps) per SM: 1 .. 16    */
+    int list_skin_adaptive;  /* 1 (with list_skin_nm > 0): the device drops the
+                                Verlet buffer while it does not pay and takes
+                                it back when it would.  A buffered list that
+                                lived fewer than 3 steps makes the next lists
+                                unbuffered (cutoff r_cut, rebuilt every step,
+                                no trimming pass); while unbuffered, once the
+                                largest one-step displacement d of any atom is
+                                at most list_skin_nm / 12 (a buffered list would
+                                last 6 steps or more), the next list carries
+                                the skin again.  md_set_state starts again from
+                                a buffered list.  Same pair set within r_cut
+                                either way; the grouping of the FP32 partial
+                                sums follows the lists, so a checkpoint resumes
+                                bit for bit only with a fixed skin.  0
+                                (default): the skin is fixed.                */
 } md_config;
 
 /*
@@ -309,6 +324,8 @@ typedef struct md_timing {
     int build_kernels;       /* kernels of one cell + list build in the step
                                 graph (5 to 12: the scans and the sort take
                                 one or several kernels by grid size)       */
+    int64_t list_unbuffered_builds; /* of list_builds, those without the skin
+                                (list_skin_adaptive)                         */
 } md_timing;
 
 typedef struct md_handle md_handle;

@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(kListWarps * 32, 4) k_list_count(Params p)
     if (*p.err & ERR_CELL) return;
     const int n_sc = p.counters[0];
     const int G = list_parts(n_sc);
-    const float rcb = p.rlist_f + kBBoxMargin;   // r_cut + Verlet skin
+    const float rcb = list_rlist_f(p) + kBBoxMargin;   // r_cut + Verlet skin
     const float rcb2 = rcb * rcb;
     for (int item = blockIdx.x * kListWarps + warp; item < n_sc * G; item += gridDim.x * kListWarps) {
         const int sc = item / G, gr = item - sc * G;
@@ -606,7 +606,7 @@ __global__ void __launch_bounds__(kListWarps * 32, 4) k_list_write(Params p)
     if (*p.err & (ERR_CELL | ERR_LIST)) return;
     const int n_sc = p.counters[0];
     const int G = list_parts(n_sc);
-    const float rcb = p.rlist_f + kBBoxMargin;
+    const float rcb = list_rlist_f(p) + kBBoxMargin;
     const float rcb2 = rcb * rcb;
     for (int item = blockIdx.x * kListWarps + warp; item < n_sc * G; item += gridDim.x * kListWarps) {
         const int sc = item / G, gr = item - sc * G;
@@ -738,8 +738,9 @@ __global__ void __launch_bounds__(FP64 ? 256 : 384, 2) k_pair(Params p)
     // range inside one fragment.  Lane column tx always takes the atoms tx of
     // the entry's i-clusters in cluster order, so the dropped atoms only ever
     // added exact zeros: every sum comes out bit-identical with either mask.
-    const bool prune = p.builds != nullptr && p.half_skin2 > 0.0f && p.builds[1] != 0;
-    const T rl2 = T(p.rlist_f + kBBoxMargin) * T(p.rlist_f + kBBoxMargin);
+    const bool prune = p.builds != nullptr && list_half_skin2(p) > 0.0f && p.builds[1] != 0;
+    const float rlb = list_rlist_f(p) + kBBoxMargin;
+    const T rl2 = T(rlb) * T(rlb);
     const T rc2 = FP64 ? T(p.rc2) : T(p.rc2_f);
     const T irc = T(1.0 / p.r_cut);
     const T coulf = T(p.coulomb_f);

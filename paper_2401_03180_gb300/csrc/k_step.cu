@@ -107,8 +107,32 @@ __device__ void plasma_scalars(const Params& p, int r, long long step, RepState&
     st.kappa_f = (float)kf;
 }
 
+// Adaptive skin: whether this step rebuilds (x) and whether the list it builds
+// carries the skin (y), from the step's largest displacement and the current
+// list.  A pure function, so that the warps sizing the grids and the thread
+// that records the decision agree.
+__device__ __forceinline__ int2 adapt_decision(const Params& p, unsigned maxd2)
+{
+    const ListCtl& c = *p.lc;
+    if (c.buffered) {
+        const int rebuild = maxd2 > __float_as_uint(c.half_skin2) ? 1 : 0;
+        return make_int2(rebuild, rebuild && c.since_build + 1 < kAdaptOffLife ? 0 : 1);
+    }
+    // one step since the last build: maxd2 is the largest one-step
+    // displacement d, and a buffered list would last (skin/2) / d steps
+    return make_int2(1, __uint_as_float(maxd2) * (float)(kAdaptOnLife * kAdaptOnLife) <= p.half_skin2 ? 1 : 0);
+}
+
+// Radius of the list this step builds: the cells' smallest edge.
+template <bool SETCOND>
+__device__ __forceinline__ double next_rlist(const Params& p, unsigned maxd2)
+{
+    if (SETCOND && p.lc) return adapt_decision(p, maxd2).y ? p.r_list : p.r_cut;
+    return list_rlist(p);
+}
+
 __device__ void make_grid(const Params& p, int r, const unsigned long long* mn,
-                          const unsigned long long* mx)
+                          const unsigned long long* mx, double rl)
 {
     Grid& g = p.grid[r];
     if (g.periodic) return;   // periodic grids are fixed at init
@@ -118,12 +142,12 @@ __device__ void make_grid(const Params& p, int r, const unsigned long long* mn,
         hi[d] = mx[d] == 0ull ? 0.0 : from_ordered(mx[d]);
         if (!(hi[d] >= lo[d])) { lo[d] = 0.0; hi[d] = 0.0; }
     }
-    double f = 1.0;
+    double f = 1.0;   // cell edges >= rl, the radius of the list built on the grid
     int n[3];
     for (int it = 0; it < 400; ++it) {
         long long prod = 1;
         for (int d = 0; d < 3; ++d) {
-            double m = floor((hi[d] - lo[d]) / (p.r_list * f));
+            double m = floor((hi[d] - lo[d]) / (rl * f));
             n[d] = m < 1.0 ? 1 : (m > 1.0e6 ? 1000000 : (int)m);
             prod *= n[d];
         }
@@ -132,7 +156,7 @@ __device__ void make_grid(const Params& p, int r, const unsigned long long* mn,
     }
     for (int d = 0; d < 3; ++d) {
         double ext = hi[d] - lo[d];
-        double e = n[d] == 1 ? (ext > p.r_list ? ext : p.r_list) : ext / n[d];
+        double e = n[d] == 1 ? (ext > rl ? ext : rl) : ext / n[d];
         g.origin[d] = lo[d];
         g.edge[d] = e;
         g.inv_edge[d] = 1.0 / e;
@@ -244,7 +268,7 @@ __device__ void hyb_table(const Params& p, int rr, int lane, double kap, double 
 // Replica rr's per-step reduction by one warp: lane c reads accumulator copy
 // c and clears it, the warp reduces, lane 0 updates the plasma scalars (Eq. 3)
 // and the next grid.
-__device__ void finalize_replica(const Params& p, int rr, int lane, long long next)
+__device__ void finalize_replica(const Params& p, int rr, int lane, long long next, double rl)
 {
     RepAccum* a = p.acc + (size_t)rr * kAccCopies;
     RepState st;
@@ -283,7 +307,7 @@ __device__ void finalize_replica(const Params& p, int rr, int lane, long long ne
         for (int k = 0; k < 4; ++k) st.counts[k] += v[2 + k];
         plasma_scalars(p, rr, next, st);
         p.rs[rr] = st;
-        make_grid(p, rr, mn, mx);
+        make_grid(p, rr, mn, mx, rl);
     }
     if (p.screening) {
         const double kap = __shfl_sync(0xffffffffu, st.kappa_force, 0);
@@ -317,7 +341,23 @@ __device__ void finalize_step(const Params& p, int mode, long long next, unsigne
         // rebuild once some atom may have closed half of the skin: pairs
         // within r_cut now were within r_cut + skin at the build
         *p.maxd2 = 0u;
-        const int rebuild = maxd2 > __float_as_uint(p.half_skin2) ? 1 : 0;
+        int rebuild;
+        if (p.lc) {
+            // adaptive skin: the buffer stays only while lists live long enough to pay
+            ListCtl& c = *p.lc;
+            const int2 d = adapt_decision(p, maxd2);
+            rebuild = d.x;
+            if (d.y != c.buffered) {
+                c.buffered = d.y;
+                c.rlist_f = d.y ? p.rlist_f : p.rc_f;
+                c.r_list = d.y ? p.r_list : p.r_cut;
+                c.half_skin2 = d.y ? p.half_skin2 : 0.0f;
+            }
+            if (rebuild && !d.y) c.unbuffered_builds += 1;
+            c.since_build = rebuild ? 0 : c.since_build + 1;
+        } else {
+            rebuild = maxd2 > __float_as_uint(p.half_skin2) ? 1 : 0;
+        }
         p.builds[0] += rebuild;
         p.builds[1] = rebuild;
         cudaGraphSetConditional(p.cond, (unsigned)rebuild);
@@ -338,6 +378,7 @@ __global__ void __launch_bounds__(kStepThreads, MINB) k_step_a(Params p, int mod
     __shared__ unsigned long long s_bmin[kRepWindow][3], s_bmax[kRepWindow][3];
     __shared__ int s_last;
     __shared__ unsigned s_maxd2;
+    __shared__ double s_rl;
     __shared__ uint8_t s_q[kStepAtoms];   // charges after this step's update (charge-update warps)
     // a cluster-pair list overflow freezes the state at the step whose forces
     // are missing; the host grows the list, recomputes them and resumes
@@ -650,10 +691,16 @@ __global__ void __launch_bounds__(kStepThreads, MINB) k_step_a(Params p, int mod
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    const unsigned m2 = (SETCOND && tid == 0) ? __ldcg(p.maxd2) : 0u;   // issued early
+    unsigned m2 = 0u;
+    if (tid == 0) {   // the list radius of this step's build, before finalize_step records it
+        m2 = SETCOND ? __ldcg(p.maxd2) : 0u;
+        s_rl = next_rlist<SETCOND>(p, m2);
+    }
+    __syncthreads();
+    const double rl = s_rl;
     const long long next = (mode & STEP_ADVANCE) ? step + 1 : step;
     const int warp = tid >> 5, n_warps = blockDim.x >> 5;
-    for (int rr = warp; rr < p.n_rep; rr += n_warps) finalize_replica(p, rr, lane, next);
+    for (int rr = warp; rr < p.n_rep; rr += n_warps) finalize_replica(p, rr, lane, next, rl);
     if (tid == 0) finalize_step<SETCOND>(p, mode, next, m2);
 }
 
@@ -668,7 +715,9 @@ __global__ void __launch_bounds__(256) k_step_fin(Params p, int mode)
     const long long step = *p.step;
     const long long next = (mode & STEP_ADVANCE) ? step + 1 : step;
     const int rr = (blockIdx.x * blockDim.x + tid) >> 5;
-    if (rr < p.n_rep) finalize_replica(p, rr, lane, next);
+    // every block reads maxd2 and the list state before the last one records the decision
+    const double rl = next_rlist<SETCOND>(p, SETCOND ? __ldcg(p.maxd2) : 0u);
+    if (rr < p.n_rep) finalize_replica(p, rr, lane, next, rl);
     __threadfence();
     __syncthreads();
     if (tid == 0) s_last = (atomicAdd(&p.counters[3], 1) == (int)gridDim.x - 1);

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <exception>
@@ -156,6 +157,20 @@ md_status check_device_flags(md_handle* h)
 void set_build_step(md_handle* h, cudaStream_t s, bool at_build)
 {
     cudaMemsetAsync(h->P.builds + 1, at_build ? 0x01 : 0x00, sizeof(int), s);   // nonzero / zero
+}
+
+// Adaptive skin: the next list carries the skin again (init and restores);
+// the count of unbuffered builds is kept.
+cudaError_t reset_list_ctl(md_handle* h)
+{
+    const Params& P = h->P;
+    ListCtl c{};
+    c.rlist_f = P.rlist_f;
+    c.half_skin2 = P.half_skin2;
+    c.r_list = P.r_list;
+    c.buffered = 1;
+    c.since_build = 0;
+    return cudaMemcpy(P.lc, &c, offsetof(ListCtl, unbuffered_builds), cudaMemcpyHostToDevice);
 }
 
 // Cell list + cluster-pair list + forces at the current positions/charges
@@ -540,6 +555,8 @@ md_status validate(const md_config* c, const md_system* s)
         return fail(h, MD_ERR_INVALID_ARG, "dt_ps and r_cut must be positive");
     if (!(c->list_skin_nm >= 0) || !(c->list_skin_nm <= c->r_cut))
         return fail(h, MD_ERR_INVALID_ARG, "list_skin_nm must be in [0, r_cut]");
+    if (c->list_skin_adaptive != 0 && c->list_skin_adaptive != 1)
+        return fail(h, MD_ERR_INVALID_ARG, "list_skin_adaptive must be 0 or 1");
     if (c->precision != MD_PREC_MIXED && c->precision != MD_PREC_FP64)
         return fail(h, MD_ERR_INVALID_ARG, "precision must be MD_PREC_MIXED or MD_PREC_FP64");
     if (c->plasma_mode != MD_PLASMA_BOOKKEEPING && c->plasma_mode != MD_PLASMA_PRESCRIBED)
@@ -945,9 +962,11 @@ static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* 
     DALLOC(P.cl_cen, P.cluster_cap);
     DALLOC(P.maxd2, 1);
     DALLOC(P.builds, 2);
+    P.lc = nullptr;
     if (c.list_skin_nm > 0) {
         DALLOC(P.grid_b, R);
         DALLOC(P.xr, N); DALLOC(P.yr, N); DALLOC(P.zr, N);
+        if (c.list_skin_adaptive) DALLOC(P.lc, 1);
     } else {
         P.grid_b = P.grid;   // rebuilt every step: the build grid is the grid
         P.xr = P.yr = P.zr = nullptr;
@@ -1010,6 +1029,10 @@ static md_status init_impl(md_handle* h, const md_config* cfg, const md_system* 
             CU(cudaMemcpy(P.grid_b, h->grid0.data(), R * sizeof(Grid), cudaMemcpyHostToDevice));
         CU(cudaMemset(P.maxd2, 0, sizeof(unsigned)));
         CU(cudaMemset(P.builds, 0, 2 * sizeof(int)));
+        if (P.lc) {
+            CU(cudaMemset(P.lc, 0, sizeof(ListCtl)));
+            CU(reset_list_ctl(h));
+        }
         CU(cudaMemcpy(d_seed, sys->seed, R * sizeof(unsigned long long), cudaMemcpyHostToDevice));
         CU(cudaMemcpy(d_vol, sys->volume, R * sizeof(double), cudaMemcpyHostToDevice));
         CU(cudaMemcpy(d_repoff, h->rep_off.data(), (R + 1) * sizeof(int), cudaMemcpyHostToDevice));
@@ -1581,6 +1604,7 @@ static md_status md_set_state_body(md_handle* h, const md_state* in, unsigned fi
             from_ref = true;
         }
     }
+    if (h->P.lc) CU(reset_list_ctl(h));   // the restored list carries the skin
     bool grown = false;
     md_status st = rebuild_checked(h, &grown, from_ref);
     if (st != MD_OK) return st;
@@ -1865,6 +1889,13 @@ md_status md_get_timing(md_handle* h, md_timing* out)
     } else {
         out->list_builds = h->steps;
     }
+    out->list_unbuffered_builds = 0;
+    if (h->P.lc) {
+        long long u = 0;
+        CU(cudaMemcpy(&u, reinterpret_cast<char*>(h->P.lc) + offsetof(ListCtl, unbuffered_builds), sizeof(u),
+                      cudaMemcpyDeviceToHost));
+        out->list_unbuffered_builds = u;
+    }
     return MD_OK;
 }
 
@@ -1879,6 +1910,8 @@ md_status md_reset_timing(md_handle* h)
     h->pair_launches = 0;
     h->steps = 0;
     CU(cudaMemset(h->P.builds, 0, sizeof(int)));
+    if (h->P.lc)
+        CU(cudaMemset(reinterpret_cast<char*>(h->P.lc) + offsetof(ListCtl, unbuffered_builds), 0, sizeof(long long)));
     return MD_OK;
 }
 

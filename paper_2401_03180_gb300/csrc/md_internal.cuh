@@ -79,6 +79,26 @@ struct HybRep {              // per replica
     float c2f, rpm2f;
 };
 
+// The current cluster-pair list's radius (adaptive Verlet buffer): the step
+// kernel decides each rebuild and the radius of the next list; the cell grid,
+// the list kernels and the force kernel read it.
+// Break-even from the measured costs on the 2 M-atom droplet: a buffered step
+// costs the force kernel on the trimmed list plus (build + trimming pass) / L
+// for lists of L steps, an unbuffered one the force kernel on the r_cut list
+// plus a build; the two meet at L = 3.  Taking the skin back waits for twice
+// that, estimated from the one-step displacement (straight-line motion, which
+// overestimates the lifetime of accelerating atoms).
+constexpr int kAdaptOffLife = 3;   // a buffered list that lived fewer steps: drop the skin
+constexpr int kAdaptOnLife = 6;    // unbuffered, and a buffered list would last this long: take it back
+struct ListCtl {
+    float rlist_f;           // r_cut (+ skin) of the current list
+    float half_skin2;        // (skin/2)^2 of the current list; 0: rebuilt every step
+    double r_list;
+    int buffered;            // 1: the current list carries the skin
+    int since_build;         // steps since the last build
+    long long unbuffered_builds;
+};
+
 struct RepState {            // plasma and bookkeeping of one replica
     long long n_e;           // free electrons
     long long e_gas;         // gas energy, meV
@@ -113,9 +133,10 @@ struct Params {
     int z_max;               // largest nuclear charge of the species present
     double dt, r_cut, rc2, kappa_fixed, te_floor, four_pi_f, coulomb_f, inv_dte;
     float rc2_f, rc_f;
-    double r_list;           // r_cut + Verlet skin: cell edge and list cutoff
+    double r_list;           // r_cut + Verlet skin: cell edge and list cutoff (fixed skin)
     float rlist_f;
     float half_skin2;        // (skin/2)^2; 0: rebuild every step
+    ListCtl* lc;             // adaptive skin: the current list's radius (else null: the values above)
 
     // atoms, original order
     double *x, *y, *z, *vx, *vy, *vz;
@@ -296,6 +317,11 @@ __device__ __forceinline__ float4 pack_slot(const Params& p, int slot, int i, co
     const double xi[3] = {p.x[i], p.y[i], p.z[i]};
     return pack_record(p, slot, xi, cen, g.periodic, g.box, p.species[i], p.q[i], p.frag[i]);
 }
+
+// Radius and half skin of the current list (adaptive or fixed).
+__device__ __forceinline__ float list_rlist_f(const Params& p) { return p.lc ? p.lc->rlist_f : p.rlist_f; }
+__device__ __forceinline__ double list_rlist(const Params& p) { return p.lc ? p.lc->r_list : p.r_list; }
+__device__ __forceinline__ float list_half_skin2(const Params& p) { return p.lc ? p.lc->half_skin2 : p.half_skin2; }
 
 // Launch helpers implemented in the .cu files.
 void launch_step_a(const Params& p, int mode, cudaStream_t s, int grid_atoms);

@@ -50,7 +50,8 @@ class MDConfig(C.Structure):
                 ("profile", C.c_int), ("list_reserve", C.c_int), ("list_skin_nm", C.c_double),
                 ("screening", C.c_int), ("langevin_g", C.c_double * MD_MAX_SPECIES),
                 ("charge_mode", C.c_int), ("probe_record", C.c_int), ("pair_warps", C.c_int),
-                ("pair_blocks_per_sm", C.c_int), ("sort_threads", C.c_int), ("list_blocks_per_sm", C.c_int)]
+                ("pair_blocks_per_sm", C.c_int), ("sort_threads", C.c_int), ("list_blocks_per_sm", C.c_int),
+                ("list_skin_adaptive", C.c_int)]
 
 
 class MDSystem(C.Structure):
@@ -79,7 +80,7 @@ class MDTiming(C.Structure):
                 ("pair_count_last", C.c_int64), ("tile_warps", C.c_int), ("tile_blocks_per_sm", C.c_int),
                 ("list_capacity", C.c_int64), ("list_entries", C.c_int64), ("list_grows", C.c_int64),
                 ("list_builds", C.c_int64), ("sort_threads", C.c_int), ("list_blocks_per_sm", C.c_int),
-                ("build_kernels", C.c_int)]
+                ("build_kernels", C.c_int), ("list_unbuffered_builds", C.c_int64)]
 
 
 class MDForcesInput(C.Structure):
@@ -349,7 +350,7 @@ def make_config(atomic, *, dt_ps=5e-5, r_cut=1.2, precision="mixed", cr_enabled=
                 plasma_mode=MD_PLASMA_BOOKKEEPING, max_steps=1000, kappa_fixed=-1.0, t_start_fs=0.0,
                 te_floor_ev=1.0, coulomb_f=COULOMB_F, autotune=False, profile=False, list_reserve=0,
                 list_skin_nm=0.0, screening="debye", langevin_g=None, charge_mode="rates",
-                sigma0=None, eps0=None, mass=None):
+                sigma0=None, eps0=None, mass=None, list_skin_adaptive=False):
     """An md_config for the atomic data and options (argument marshalling);
     returns it with the arrays it points into, which must outlive md_init."""
     from . import workloads as W
@@ -375,6 +376,7 @@ def make_config(atomic, *, dt_ps=5e-5, r_cut=1.2, precision="mixed", cr_enabled=
     cfg.autotune, cfg.profile = int(bool(autotune)), int(bool(profile))
     cfg.list_reserve = int(list_reserve)
     cfg.list_skin_nm = float(list_skin_nm)
+    cfg.list_skin_adaptive = int(list_skin_adaptive)
     if screening not in ("debye", "hybrid"):
         raise ValueError("screening must be 'debye' or 'hybrid'")
     cfg.screening = MD_SCREEN_HYBRID if screening == "hybrid" else MD_SCREEN_DEBYE
@@ -419,7 +421,7 @@ class IonisingMD:
                  te_floor_ev=1.0, coulomb_f=COULOMB_F, autotune=False, profile=False, list_reserve=0,
                  list_skin_nm=0.0, screening="debye", langevin_g=None, charge_mode="rates",
                  probe_record=False, torch_allocator=True, sigma0=None, eps0=None, mass=None,
-                 launch_shape=None):
+                 launch_shape=None, list_skin_adaptive=False):
         """launch_shape: optional dict pinning md_config's launch-shape fields
         (pair_warps, pair_blocks_per_sm, sort_threads, list_blocks_per_sm)."""
         import torch
@@ -433,7 +435,8 @@ class IonisingMD:
                                   t_start_fs=t_start_fs, te_floor_ev=te_floor_ev, coulomb_f=coulomb_f,
                                   autotune=autotune, profile=profile, list_reserve=list_reserve,
                                   list_skin_nm=list_skin_nm, screening=screening, langevin_g=langevin_g,
-                                  charge_mode=charge_mode, sigma0=sigma0, eps0=eps0, mass=mass)
+                                  charge_mode=charge_mode, sigma0=sigma0, eps0=eps0, mass=mass,
+                                  list_skin_adaptive=list_skin_adaptive)
         cfg.probe_record = int(bool(probe_record))
         for k, v in (launch_shape or {}).items():
             if k not in ("pair_warps", "pair_blocks_per_sm", "sort_threads", "list_blocks_per_sm"):
