@@ -49,6 +49,9 @@ def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps-per-launch", type=int, default=1,
+                    help="steps per timed md_step_async call (the L2 is flushed between calls); "
+                         "md_step runs eight steps per graph launch")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="c5_droplet_2m")
@@ -294,13 +297,16 @@ def run_gpu(args, rank, world, local):
 
     def timed_steps(g, k_steps):
         # steps are enqueued without a host round trip (their status is read
-        # once at the end), so the events bracket the device work of each step
+        # once at the end), so the events bracket the device work of each call
+        # of steps_per_launch steps
+        spl = max(1, args.steps_per_launch)
+        calls = [min(spl, k_steps - k) for k in range(0, k_steps, spl)]
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(k_steps)]
-        for k in range(k_steps):
-            flush.zero_()                       # evict the 129 MB L2 between steps
+              for _ in calls]
+        for k, n in enumerate(calls):
+            flush.zero_()                       # evict the 129 MB L2 between calls
             ev[k][0].record(stream)
-            g.step(1, wait=False)
+            g.step(n, wait=False)
             ev[k][1].record(stream)
         g.sync()
         torch.cuda.synchronize()
@@ -418,7 +424,9 @@ def run_gpu(args, rank, world, local):
                    "timed_window": {"first_step": s0 + W_, "t_fs": [wl.t_start_fs + (s0 + W_) * dt_fs,
                                                                      wl.t_start_fs + (s0 + W_ + K) * dt_fs],
                                     "untimed_steps_before": s0, "placement": args.window},
-                   "l2": "flushed between steps (256 MB write, untimed)",
+                   "l2": ("flushed between steps (256 MB write, untimed)" if args.steps_per_launch <= 1 else
+                          f"flushed between calls of {args.steps_per_launch} steps (256 MB write, untimed)"),
+                   "steps_per_launch": max(1, args.steps_per_launch),
                    "pair_tile": {"warps": tim.tile_warps, "blocks_per_sm": tim.tile_blocks_per_sm},
                    "build_shape": {"sort_threads": tim.sort_threads, "list_blocks_per_sm": tim.list_blocks_per_sm,
                                    "kernels_per_build": tim.build_kernels},
