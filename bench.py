@@ -198,6 +198,13 @@ def profiled_traffic(workload):
     return float(m.group(1)), h.group(1)
 
 
+def step_calls(k_steps, per_call):
+    """Sizes of the timed md_step calls: k_steps in calls of per_call steps,
+    the last one shorter when per_call does not divide k_steps."""
+    n = max(1, int(per_call))
+    return [min(n, k_steps - k) for k in range(0, k_steps, n)]
+
+
 def sms_count(torch):
     return torch.cuda.get_device_properties(0).multi_processor_count
 
@@ -299,8 +306,7 @@ def run_gpu(args, rank, world, local):
         # steps are enqueued without a host round trip (their status is read
         # once at the end), so the events bracket the device work of each call
         # of steps_per_launch steps
-        spl = max(1, args.steps_per_launch)
-        calls = [min(spl, k_steps - k) for k in range(0, k_steps, spl)]
+        calls = step_calls(k_steps, args.steps_per_launch)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in calls]
         for k, n in enumerate(calls):

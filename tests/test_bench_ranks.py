@@ -27,6 +27,18 @@ def test_ranks_get_independent_replicas():
     assert not np.array_equal(wl0.sample.seed, wl1.sample.seed)  # own ionisation stream
 
 
+def test_timed_calls_cover_every_step_once():
+    import bench
+    assert bench.step_calls(100, 1) == [1] * 100
+    assert bench.step_calls(100, 8) == [8] * 12 + [4]
+    assert bench.step_calls(96, 8) == [8] * 12
+    assert bench.step_calls(5, 8) == [5]
+    assert bench.step_calls(0, 8) == []
+    for k in range(0, 40):
+        for n in (1, 3, 8):
+            assert sum(bench.step_calls(k, n)) == k
+
+
 def test_job_throughput_counts_every_rank():
     import bench
     assert bench.job_throughput(1, 1000, 10, 2.0) == pytest.approx(5.0e6)
