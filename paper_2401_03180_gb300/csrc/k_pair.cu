@@ -78,7 +78,7 @@ struct Prec<true> {
     using S4 = double4_16a;
     using C2 = double2;        // -6 c6, -ln2 c12
     static __device__ __forceinline__ T4 pos(const Params& p, int slot) { return p.xq64[slot]; }
-    static __device__ __forceinline__ T rsq(T x) { return 1.0 / sqrt(x); }
+    static __device__ __forceinline__ T rsq(T x) { return rsqrt(x); }   // within 1 ulp, without a division
     static __device__ __forceinline__ T expneg(T x) { return exp(-x); }
     static __device__ __forceinline__ T exp2_(T x) { return exp2(x); }
     static __device__ __forceinline__ long long fix(T v) { return __double2ll_rn(v * 4294967296.0); }
