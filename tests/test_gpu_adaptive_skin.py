@@ -152,3 +152,85 @@ def test_adaptive_flag_is_validated():
     with pytest.raises(M.MDError) as e:
         _gpu_run(s, "mixed", 2)
     assert e.value.status == M.MD_ERR_INVALID_ARG
+
+
+def _check_replicas(gpu, ora, rc, parts, where):
+    """Pair count and forces of a batch against the oracle: parts lists each
+    replica's (slice, periodic box or None)."""
+    st = gpu.get_state(XQF)
+    F, _, n_ref = ora.forces(x=st["x"], q=st["q"], kappa=np.zeros(len(parts)))
+    _, _, n = gpu.energies()
+    slack = sum(near_cutoff_pairs(st["x"][sl], box, rc, 1e-5) for sl, box in parts)
+    assert abs(n - n_ref) <= slack, (where, n, n_ref, slack)
+    for sl, _ in parts:
+        if not np.any(F[sl]):
+            assert np.all(st["f"][sl] == 0.0), (where, sl)
+            continue
+        rms, mx = force_errors(st["f"][sl], F[sl])
+        assert rms <= TOL_F["mixed"], (where, sl, rms, mx)
+    return st
+
+
+def test_adaptive_skin_in_a_batch_with_a_periodic_replica(oracle_mod):
+    """One decision serves every replica of a handle: next to the colliding
+    ions (vacuum) a neutral periodic water box gets unbuffered lists too, whose
+    cells stay sized for r_cut + skin while the list radius is r_cut.  Both
+    replicas keep every pair at every step."""
+    from gpu_common import water
+    w, _ = water(1000)                      # 3.11 nm box, 3,000 atoms
+    w.q0[:] = 0
+    b = W.concat([collision_sample(), w])
+    rc = 0.9                                # box >= 3 (r_cut + skin)
+    gpu = M.IonisingMD(b, W.atomic_data(8.0), dt_ps=DT, r_cut=rc, cr_enabled=False, kappa_fixed=0.0,
+                       max_steps=120, list_skin_nm=SKIN, list_skin_adaptive=True)
+    ora = oracle_mod.OracleMD(b, W.atomic_data(8.0), dt_ps=DT, r_cut=rc, cr_enabled=False, kappa_fixed=0.0)
+    off = b.replica_offset
+    parts = [(slice(0, off[1]), None), (slice(off[1], off[2]), b.box[1])]
+    pattern = []
+    b0 = u0 = 0
+    for k in range(100):
+        gpu.step(1)
+        ora.step()
+        t = gpu.timing()
+        built, unbuf = t.list_builds - b0, t.list_unbuffered_builds - u0
+        b0, u0 = t.list_builds, t.list_unbuffered_builds
+        pattern.append("U" if unbuf else ("B" if built else "."))
+        st = _check_replicas(gpu, ora, rc, parts, k)
+    pattern = "".join(pattern)
+    assert re.search(r"U+[B.]*\.[B.]*U", pattern), pattern
+    d = st["x"] - ora.x
+    L = b.box[1]
+    d[off[1]:] -= L * np.round(d[off[1]:] / L)
+    assert float(np.sqrt((d ** 2).sum(1).mean())) <= TOL_X["mixed"]
+    gpu.close()
+
+
+def test_adaptive_skin_on_a_hot_periodic_box(oracle_mod):
+    """A periodic water box in which 5 % of the atoms fly at 40 nm/ps: with a
+    0.01 nm skin the buffered lists live 3 steps, then one lives 2 and the
+    lists turn unbuffered for good; every pair is found at every step."""
+    from gpu_common import water
+    s, _ = water(1000)
+    rng = np.random.default_rng(3)
+    d = rng.normal(size=s.v.shape)
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    hot = rng.random(s.n_atoms) < 0.05
+    s.v[hot] = 40.0 * d[hot]
+    rc = 0.9
+    gpu = M.IonisingMD(s, W.atomic_data(6.0), r_cut=rc, cr_enabled=False, kappa_fixed=2.0, max_steps=60,
+                       list_skin_nm=0.01, list_skin_adaptive=True)
+    ora = oracle_mod.OracleMD(s, W.atomic_data(6.0), r_cut=rc, cr_enabled=False, kappa_fixed=2.0)
+    parts = [(slice(0, s.n_atoms), s.box[0])]
+    for k in range(40):
+        gpu.step(1)
+        ora.step()
+        st = gpu.get_state(XQF)
+        F, _, n_ref = ora.forces(x=st["x"], q=st["q"], kappa=np.full(1, 2.0))
+        _, _, n = gpu.energies()
+        slack = near_cutoff_pairs(st["x"], s.box[0], rc, 1e-5)
+        assert abs(n - n_ref) <= slack, (k, n, n_ref, slack)
+        rms, mx = force_errors(st["f"], F)
+        assert rms <= TOL_F["mixed"], (k, rms, mx)
+    t = gpu.timing()
+    gpu.close()
+    assert t.list_unbuffered_builds >= 20, (t.list_builds, t.list_unbuffered_builds)
