@@ -105,6 +105,7 @@ struct WarpSmem {
     typename Prec<FP64>::S4 fi[4 * kFiRow];    // [ty][atom] force (+energy)
     typename Prec<FP64>::S4 jx[kChunk * kClusterSize];   // the chunk's j-atoms, shifted: x, y, z, q
     int2 jt[kChunk * kClusterSize];                      // their LJ column byte offset, fragment
+    PairEntry ent[kChunk];                               // the chunk's list entries
     HybSmem<FP64, HYB> hy;
 };
 
@@ -702,6 +703,7 @@ __global__ void __launch_bounds__(FP64 ? 256 : 384, 2) k_pair(Params p)
             }
         s_kq[c] = q;
     }
+    for (int k = lane; k < 4 * kFiRow; k += 32) w.fi[k] = P::mk(T(0), T(0), T(0), T(0));
     if (lane < kClusterSize) {
         w.ix[kSCAtoms + lane] = P::mk(T(-1.0e6), T(-1.0e6), T(-1.0e6), T(0));
         w.it[kSCAtoms + lane] = make_int2(0, (int)0x80000000);
@@ -752,7 +754,8 @@ __global__ void __launch_bounds__(FP64 ? 256 : 384, 2) k_pair(Params p)
         if (item >= n_chunks) break;
         const int4 ch = p.pl_chunk[item];          // (sc, first entry, entries, replica)
         const int sc = ch.x, n_ent = ch.z, rr = ch.w;
-        const PairEntry ent = lane < n_ent ? p.pl[ch.y + lane] : make_uint4(0u, 0u, 0u, 0u);
+        __syncwarp();   // the previous chunk's reads of the staged entries are done
+        if (lane < n_ent) w.ent[lane] = p.pl[ch.y + lane];
         const int fc = p.sc_first[sc], ncl = p.sc_ncl[sc];
         const Grid& g = p.grid_b[rr];
         const T kap = FP64 ? T(p.rs[rr].kappa_force) : T(p.rs[rr].kappa_f);
@@ -771,8 +774,8 @@ __global__ void __launch_bounds__(FP64 ? 256 : 384, 2) k_pair(Params p)
         }
 
         // the super-cluster's atoms and the chunk's j-atoms (shifted into the
-        // SC's cell frame) into shared memory, partial forces cleared: one load
-        // latency per chunk instead of one per entry
+        // SC's cell frame) into shared memory: one load latency per chunk
+        // instead of one per entry
         __syncwarp();
         for (int a = lane; a < kSCAtoms; a += 32) {
             if ((a >> 3) < ncl) {
@@ -790,9 +793,8 @@ __global__ void __launch_bounds__(FP64 ? 256 : 384, 2) k_pair(Params p)
         }
         for (int a0 = 0; a0 < kChunk * kClusterSize; a0 += 32) {
             const int a = a0 + lane, e = a >> 3;                 // entry e, atom a & 7
-            const unsigned jc = __shfl_sync(kFull, ent.x, e);
-            const unsigned cd = __shfl_sync(kFull, ent.y, e);
             if (e < n_ent) {
+                const unsigned jc = w.ent[e].x, cd = w.ent[e].y;
                 int dx, dy, dz;
                 half_shell((int)(cd & 0xffu), dx, dy, dz);
                 const int slot = (int)jc * kClusterSize + (a & 7);
@@ -808,16 +810,16 @@ __global__ void __launch_bounds__(FP64 ? 256 : 384, 2) k_pair(Params p)
                 }
             }
         }
-        for (int k = lane; k < 4 * kFiRow; k += 32) w.fi[k] = P::mk(T(0), T(0), T(0), T(0));
         __syncwarp();
         int npair = 0;
 
         for (int v = 0; v < n_ent; ++v) {
-            const int jcl = (int)__shfl_sync(kFull, ent.x, v);
-            const unsigned code = __shfl_sync(kFull, ent.y, v);
+            const PairEntry e4 = w.ent[v];   // one broadcast read
+            const int jcl = (int)e4.x;
+            const unsigned code = e4.y;
             const int nb = (int)(code & 0xffu);
             const bool excl = (code & kEntryExcl) != 0u;
-            const unsigned mlo = __shfl_sync(kFull, ent.z, v), mhi = __shfl_sync(kFull, ent.w, v);
+            const unsigned mlo = e4.z, mhi = e4.w;
             if ((mlo | mhi) == 0u) continue;   // no i-atom in range (or emptied by pruning)
             const int s0 = jcl * kClusterSize + ty, s1 = s0 + 4;
             const S4 a0 = w.jx[v * kClusterSize + ty], a1 = w.jx[v * kClusterSize + ty + 4];
@@ -879,7 +881,7 @@ __global__ void __launch_bounds__(FP64 ? 256 : 384, 2) k_pair(Params p)
                     w.fi[ty * kFiRow + ia] = acc;
                     if (PRUNE) {   // this lane's pairs in range: combined over the warp after the entry
                         const bool n0 = ok0 && r20 < rl2, n1 = ok1 && r21 < rl2;
-                        if ((n0 || n1) && k < 8) keep |= 1u << k;
+                        if (n0 || n1) keep |= 1u << k;   // never for the far stand-in row
                         if (EXCL) share |= (n0 && ti.y == t0.y) || (n1 && ti.y == t1.y);
                     }
                 }
@@ -925,12 +927,16 @@ __global__ void __launch_bounds__(FP64 ? 256 : 384, 2) k_pair(Params p)
             }
         }
         __syncwarp();
-        // i forces of this chunk: sum the 4 ty partials of each atom
+        // i forces of this chunk: sum the 4 ty partials of each atom, clearing
+        // them for the next chunk (tiles touch only the rows of the SC's
+        // clusters, which this loop covers, and the stand-in rows, which stay 0)
         for (int a = lane; a < ncl * kClusterSize; a += 32) {
             S4 sum = w.fi[a];
+            w.fi[a] = P::mk(T(0), T(0), T(0), T(0));
 #pragma unroll
             for (int q = 1; q < 4; ++q) {
                 const S4 v = w.fi[q * kFiRow + a];
+                w.fi[q * kFiRow + a] = P::mk(T(0), T(0), T(0), T(0));
                 sum.x += v.x; sum.y += v.y; sum.z += v.z;
                 if (ENERGY) sum.w += v.w;
             }
