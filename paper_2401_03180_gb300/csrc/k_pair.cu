@@ -105,6 +105,7 @@ struct WarpSmem {
     typename Prec<FP64>::S4 fi[4 * kFiRow];    // [ty][atom] force (+energy)
     typename Prec<FP64>::S4 jx[kChunk * kClusterSize];   // the chunk's j-atoms, shifted: x, y, z, q
     int2 jt[kChunk * kClusterSize];                      // their LJ column byte offset, fragment
+    typename Prec<FP64>::T jqk[kChunk * kClusterSize];   // their q kappa
     PairEntry ent[kChunk];                               // the chunk's list entries
     HybSmem<FP64, HYB> hy;
 };
@@ -804,6 +805,7 @@ __global__ void __launch_bounds__(FP64 ? 256 : 384, 2) k_pair(Params p)
                 else w.jx[a] = P::mk(v.x + T((float)dx * g.edge_f[0]), v.y + T((float)dy * g.edge_f[1]),
                                      v.z + T((float)dz * g.edge_f[2]), v.w);
                 w.jt[a] = make_int2(t.x * (int)sizeof(C2), t.y);   // byte offset of the LJ column
+                w.jqk[a] = v.w * kap;
                 if constexpr (HYB) {
                     const HybQ& hq = hrows[(int)v.w];
                     w.hy.jG[a] = FP64 ? T(hq.G) : T(hq.Gf);
@@ -826,7 +828,7 @@ __global__ void __launch_bounds__(FP64 ? 256 : 384, 2) k_pair(Params p)
             const int2 t0 = w.jt[v * kClusterSize + ty], t1 = w.jt[v * kClusterSize + ty + 4];
             const T x0 = a0.x, y0 = a0.y, z0 = a0.z;
             const T x1 = a1.x, y1 = a1.y, z1 = a1.z;
-            const T q0k = a0.w * kap, q1k = a1.w * kap;
+            const T q0k = w.jqk[v * kClusterSize + ty], q1k = w.jqk[v * kClusterSize + ty + 4];
             const int j0off = t0.x, j1off = t1.x;
             HybArg<T> h0 = ha, h1 = ha;   // the j-atom halves of the hybrid arguments
             if constexpr (HYB) {
@@ -839,7 +841,7 @@ __global__ void __launch_bounds__(FP64 ? 256 : 384, 2) k_pair(Params p)
 
             // this lane column's i-clusters (byte tx of the column-major mask: bit k
             // when atom tx of i-cluster k is in); a tile takes the next one of every column
-            const unsigned col0 = ((tx < 4 ? mlo : mhi) >> ((tx & 3) * 8)) & 0xffu;
+            const unsigned col0 = __byte_perm(mlo, mhi, (unsigned)tx) & 0xffu;   // byte tx of (mhi:mlo)
             const int n_t = (int)__reduce_max_sync(kFull, (unsigned)__popc(col0));
 
             T fj0x = 0, fj0y = 0, fj0z = 0, fj1x = 0, fj1y = 0, fj1z = 0;
