@@ -333,6 +333,15 @@ __device__ __forceinline__ void list_locate(const ListCell& c, int idx, int& nb,
     Dz = __shfl_sync(0xffffffffu, c.Dz, lo);
 }
 
+// Largest of three floats in one instruction (max selects, so this equals
+// fmaxf(c, fmaxf(a, b)) for the finite operands of the box tests).
+__device__ __forceinline__ float max3f(float a, float b, float c)
+{
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 // Mask of the SC's i-clusters whose boxes come within r_cut + skin of the
 // j-cluster box [jl, jh] (already shifted into the SC's frame); in the SC's own
 // cell (nb = 0) only i-clusters up to the j-cluster.  Explicit roundings, so
@@ -345,9 +354,9 @@ __device__ __forceinline__ unsigned list_test(const ListWarp& w, int nb, int fc,
 #pragma unroll 2
     for (int k = 0; k < kmax; ++k) {
         const float4 il = w.lo[k], ih = w.hi[k];
-        const float gx = fmaxf(0.0f, fmaxf(il.x - jh.x, jl.x - ih.x));
-        const float gy = fmaxf(0.0f, fmaxf(il.y - jh.y, jl.y - ih.y));
-        const float gz = fmaxf(0.0f, fmaxf(il.z - jh.z, jl.z - ih.z));
+        const float gx = max3f(il.x - jh.x, jl.x - ih.x, 0.0f);
+        const float gy = max3f(il.y - jh.y, jl.y - ih.y, 0.0f);
+        const float gz = max3f(il.z - jh.z, jl.z - ih.z, 0.0f);
         if (__fmaf_rn(gz, gz, __fmaf_rn(gy, gy, __fmul_rn(gx, gx))) < rcb2) m |= 1u << k;
     }
     return m;
@@ -586,9 +595,9 @@ __device__ __forceinline__ uint4 list_entry(const Params& p, const ListWarp& w, 
 #pragma unroll
         for (int a = 0; a < kClusterSize; ++a) {
             const float4 xi = w.ip[k * kClusterSize + a];
-            const float gx = fmaxf(0.0f, fmaxf(xi.x - j.jh.x, j.jl.x - xi.x));
-            const float gy = fmaxf(0.0f, fmaxf(xi.y - j.jh.y, j.jl.y - xi.y));
-            const float gz = fmaxf(0.0f, fmaxf(xi.z - j.jh.z, j.jl.z - xi.z));
+            const float gx = max3f(xi.x - j.jh.x, j.jl.x - xi.x, 0.0f);
+            const float gy = max3f(xi.y - j.jh.y, j.jl.y - xi.y, 0.0f);
+            const float gz = max3f(xi.z - j.jh.z, j.jl.z - xi.z, 0.0f);
             const bool in = kin && __fmaf_rn(gz, gz, __fmaf_rn(gy, gy, __fmul_rn(gx, gx))) < rcb2;
             if (a < 4) mlo |= (in ? 1u : 0u) << (a * 8 + k);
             else mhi |= (in ? 1u : 0u) << ((a - 4) * 8 + k);
