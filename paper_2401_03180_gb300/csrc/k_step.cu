@@ -36,10 +36,18 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
     return c;
 }
 
+// The 53-bit uniform ((a >> 5) 2^26 + (b >> 6)) 2^-53.  Its value is the
+// integer m times a power of two, exactly, so the double is assembled from m
+// in the integer pipe (GB300 issues FP64 at 2 lanes per SM per clock): the
+// exponent from the leading one of m, the 52 bits below it as the mantissa.
 __device__ __forceinline__ double u53(unsigned a, unsigned b)
 {
-    double hi = (double)(a >> 5), lo = (double)(b >> 6);
-    return __dmul_rn(__dadd_rn(__dmul_rn(hi, 67108864.0), lo), 1.1102230246251565e-16);
+    const unsigned long long m = ((unsigned long long)(a >> 5) << 26) | (unsigned long long)(b >> 6);
+    if (m == 0ull) return 0.0;
+    const int lz = __clzll((long long)m);                           // 11 .. 63
+    const unsigned long long mant = ((m << lz) << 1) >> 12;         // the bits below the leading one
+    const unsigned long long ex = (unsigned long long)(1033 - lz);  // 1023 + (63 - lz) - 53
+    return __longlong_as_double((long long)((ex << 52) | mant));
 }
 
 // 1 - e^{-x}: x = k/16 + r, (1 - E_k) + E_k (1 - e^{-r}), degree-12 Taylor
@@ -595,13 +603,16 @@ __global__ void __launch_bounds__(kStepThreads, MINB) k_step_a(Params p, int mod
         const double c2 = __dadd_rn(c1, a_ci);
         const double lam = __dadd_rn(c2, a_rec);
         int ch = -1;
-        if (lam > 0.0) {
+        // lam and u0 are non-negative doubles, whose order is that of their
+        // bit patterns: the tests run in the integer pipe
+        if (__double_as_longlong(lam) > 0ll) {
             const unsigned long long sd = p.seed[r];
             const uint4 w4 = philox4x32_10(make_uint4((unsigned)p.local_id[i], (unsigned)step, 0u, 0u),
                                            make_uint2((unsigned)sd, (unsigned)(sd >> 32)));
             const double u0 = u53(w4.x, w4.y);
             // 1 - e^{-lam} <= lam, so u0 >= lam decides "no event" exactly
-            if (u0 < lam && u0 < one_minus_exp_neg(lam, p.etab, p.inv12)) {
+            if ((unsigned long long)__double_as_longlong(u0) < (unsigned long long)__double_as_longlong(lam) &&
+                u0 < one_minus_exp_neg(lam, p.etab, p.inv12)) {
                 const double t = __dmul_rn(u53(w4.z, w4.w), lam);
                 if (t < a_pi) ch = 0;
                 else if (t < c1) ch = 1;
