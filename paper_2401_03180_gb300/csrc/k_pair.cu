@@ -592,15 +592,20 @@ __device__ __forceinline__ uint4 list_entry(const Params& p, const ListWarp& w, 
     for (int k = 0; k < kSuperClusters; ++k) {
         if (!((any_m >> k) & 1u)) continue;   // no lane has i-cluster k in range
         const bool kin = (j.m >> k) & 1u;
+        unsigned klo = 0u, khi = 0u;   // column k's bits, kept only if cluster k is in range
 #pragma unroll
         for (int a = 0; a < kClusterSize; ++a) {
             const float4 xi = w.ip[k * kClusterSize + a];
             const float gx = max3f(xi.x - j.jh.x, j.jl.x - xi.x, 0.0f);
             const float gy = max3f(xi.y - j.jh.y, j.jl.y - xi.y, 0.0f);
             const float gz = max3f(xi.z - j.jh.z, j.jl.z - xi.z, 0.0f);
-            const bool in = kin && __fmaf_rn(gz, gz, __fmaf_rn(gy, gy, __fmul_rn(gx, gx))) < rcb2;
-            if (a < 4) mlo |= (in ? 1u : 0u) << (a * 8 + k);
-            else mhi |= (in ? 1u : 0u) << ((a - 4) * 8 + k);
+            const bool in = __fmaf_rn(gz, gz, __fmaf_rn(gy, gy, __fmul_rn(gx, gx))) < rcb2;
+            if (a < 4) klo |= (in ? 1u : 0u) << (a * 8 + k);
+            else khi |= (in ? 1u : 0u) << ((a - 4) * 8 + k);
+        }
+        if (kin) {
+            mlo |= klo;
+            mhi |= khi;
         }
         const int2 ifr = w.fr[k];
         share |= kin && !(ifr.y < jfr.x || jfr.y < ifr.x);
